@@ -1,0 +1,87 @@
+"""Candidate sets, rank-1 lattices and the reconstructing-lattice search (oracle side).
+
+- Candidate set of the coupled step t (Algorithm 1, step 2):
+    J_t = (I^(1..t-1) x I^(t)) intersected with P_(1..t)(Gamma),
+  kept as an ordered list: lexicographic in (position in I^(1..t-1), position in
+  I^(t)).  For the cube Gamma = [-N,N]^d the intersection keeps every element.
+- Rank-1 lattice Lambda(z, M) = { (i/M) z mod 1 : i = 0..M-1 } (Appendix A); its
+  node i has coordinates y_ij = (i z_j mod M)/M (Eq. (3.4)), kept here as the exact
+  integers n_ij = i z_j mod M.
+- A lattice reconstructs J when k -> k.z mod M is injective on J; then the length-M
+  DFT of the lattice samples returns the projected coefficient of every k in J at
+  index k.z mod M (Appendix A; single rank-1 lattice approach).
+
+The paper gives no construction of the generating vector for this step (it cites
+other work) and states that its lattice sizes are prime (proof of Lemma 3.1).  The
+reading used here (the same on both sides, so (z, M) are bit-exact):
+
+- admissible sizes are the 7-smooth integers (radix-2/3/5/7 FFTs); the first size
+  tried is the smallest admissible M >= |J|, every next one the smallest admissible
+  M' >= ceil(1.05 M) = floor((105 M + 99)/100) (integer arithmetic);
+- at every size, trials tr = 0..T-1 draw z_1 = 1 and z_j = uniform integer in
+  [1, M-1] (j = 2..t) from key(seed, PHASE_LATTICE, t, M, tr, j); the first z that
+  is injective on J is accepted.
+
+Pins (tests/test_oracle_lattice.py): on tiny sets, the injectivity test agrees with
+the definition through the lattice Fourier matrix (its columns for J are orthonormal
+exactly when the lattice reconstructs J), enumerated over every z.
+"""
+import numpy as np
+
+from . import rng
+
+
+def candidate_set(I_prev: np.ndarray, I_t: np.ndarray, N: int) -> np.ndarray:
+    """J_t as int64 [|I_prev| * |I_t|, t]; I_prev is [n, t-1], I_t is a 1-D list of k_t."""
+    rows = []
+    for kp in I_prev:
+        for kt in I_t:
+            k = np.concatenate([kp, [kt]])
+            if np.all(np.abs(k) <= N):           # P_(1..t)(Gamma) for Gamma = [-N,N]^d
+                rows.append(k)
+    t = I_prev.shape[1] + 1
+    if not rows:
+        return np.zeros((0, t), dtype=np.int64)
+    return np.array(rows, dtype=np.int64)
+
+
+def is_smooth7(m: int) -> bool:
+    if m < 1:
+        return False
+    for p in (2, 3, 5, 7):
+        while m % p == 0:
+            m //= p
+    return m == 1
+
+
+def next_admissible(x: int) -> int:
+    m = max(int(x), 1)
+    while not is_smooth7(m):
+        m += 1
+    return m
+
+
+def lattice_indices(J: np.ndarray, z: np.ndarray, M: int) -> np.ndarray:
+    """m_k = (k . z) mod M in [0, M) for every k in J (exact integer arithmetic)."""
+    return np.mod(J.astype(np.int64) @ z.astype(np.int64), M)
+
+
+def is_reconstructing(J: np.ndarray, z: np.ndarray, M: int) -> bool:
+    m = lattice_indices(J, z, M)
+    return len(np.unique(m)) == len(m)
+
+
+def search(J: np.ndarray, t: int, seed: int, trials: int = 64, max_sizes: int = 400):
+    """(z, M) of the first reconstructing lattice under the rule in the module header."""
+    if len(J) == 0:
+        return np.zeros(t, dtype=np.int64), 0
+    M = next_admissible(len(J))
+    for _ in range(max_sizes):
+        for tr in range(trials):
+            z = np.ones(t, dtype=np.int64)
+            for j in range(2, t + 1):
+                z[j - 1] = rng.uniform_int(1, M - 1, seed, rng.PHASE_LATTICE, t, M, tr, j) if M > 1 else 0
+            if is_reconstructing(J, z, M):
+                return z, M
+        M = next_admissible((105 * M + 99) // 100)
+    raise RuntimeError("no reconstructing lattice found")

@@ -1,0 +1,104 @@
+"""Pins of the oracle's increment driver: exact recovery of trigonometric polynomials
+(Theorem 1.1) and the structural invariants of Algorithm 1 (CPU only)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import rng
+from oracle.usfft import OracleRun
+
+
+def _support(prob):
+    out = []
+    for g in range(prob.G):
+        terms = {}
+        for f, c in zip(prob.tp_freqs[g], prob.tp_coefs[g]):
+            if c != 0:
+                terms[tuple(int(v) for v in f)] = c
+        out.append(terms)
+    return out
+
+
+def _projected(terms, coords, tail_coords, tails):
+    """sum over h with the same projection onto `coords` of c_h exp(2 pi i h_tail . y')."""
+    acc = {}
+    for h, c in terms.items():
+        k = tuple(h[j] for j in coords)
+        ph = sum(h[j] * tails[j] for j in tail_coords)
+        acc[k] = acc.get(k, 0) + c * np.exp(2j * np.pi * ph)
+    return acc
+
+
+def _margins_ok(prob, params, theta):
+    sup = _support(prob)
+    d = prob.d
+    for t in range(1, d + 1):
+        for i in range(1, params.r + 1):
+            tails = {j - 1: rng.uniform(params.seed, rng.PHASE_1D_TAIL, t, i, j) for j in range(1, d + 1) if j != t}
+            for terms in sup:
+                for v in _projected(terms, [t - 1], sorted(tails), tails).values():
+                    if 0 < abs(v) < 10 * theta:
+                        return False
+        if t >= 2:
+            for i in range(1, (params.r if t < d else 1) + 1):
+                tails = {j - 1: rng.uniform(params.seed, rng.PHASE_TAIL, t, i, j) for j in range(t + 1, d + 1)}
+                for terms in sup:
+                    for v in _projected(terms, list(range(t)), sorted(tails), tails).values():
+                        if 0 < abs(v) < 10 * theta:
+                            return False
+    return True
+
+
+@pytest.mark.parametrize("G,seed", [(1, 3), (5, 11), (12, 4)])
+def test_exact_recovery_of_trigonometric_polynomials(G, seed):
+    d, N = 4, 5
+    prob = W.trigpoly(G=G, d=d, N=N, seed=seed, base_terms=5, node_terms=2, kmax=3, mag_lo=1e-4)
+    params = W.Params(N=N, s=40, s_local=40, delta=1e-9, delta_is_relative=False, r=1, seed=seed)
+    assert _margins_ok(prob, params, params.delta)
+    run = OracleRun(prob, params, keep=True)
+    sup = _support(prob)
+    union = set().union(*[set(s) for s in sup])
+    prev = None
+    for t in range(1, d + 1):
+        I = run.increment()
+        want = {k[:t] for k in union}
+        got = {tuple(int(v) for v in row) for row in I}
+        assert got == want, t
+        # the detected set lies in J_t and projects into the previous detected set
+        if t >= 2:
+            Jset = {tuple(int(v) for v in row) for row in run.J}
+            assert got <= Jset
+            assert {k[:t - 1] for k in got} <= {tuple(int(v) for v in row) for row in prev}
+        prev = I
+    # at t = d there are no tails: the coefficients are the polynomial's own (Theorem 1.1)
+    last = run.records[-1]
+    assert last.coupled and last.t == d
+    for g in range(G):
+        for col, k in enumerate(run.J):
+            want_c = sup[g].get(tuple(int(v) for v in k), 0.0)
+            assert abs(last.C[g, col] - want_c) < 1e-13
+
+
+def test_relative_threshold_uses_first_mean_coefficient():
+    w = W.c1(2)
+    run = OracleRun(w.problem, w.params, keep=True)
+    run.increment()
+    rec = run.records[0]
+    A = np.max(np.abs(rec.C[:, w.params.N]))
+    assert run.theta == w.params.delta * A
+    # k = 0 is the mean over y_1 of u, so it is detected everywhere and A > 0
+    assert 0 in run.I1d[1] and A > 0
+
+
+def test_last_increment_uses_one_iteration_and_s():
+    # Algorithm 1, step 2: r~ = 1 and s~ = s at t = d
+    prob = W.trigpoly(G=3, d=3, N=4, seed=2, base_terms=4, node_terms=1, kmax=2, mag_lo=1e-3)
+    params = W.Params(N=4, s=2, s_local=30, delta=1e-9, delta_is_relative=False, r=3, seed=5)
+    run = OracleRun(prob, params, keep=True)
+    for _ in range(3):
+        run.increment()
+    last = [r for r in run.records if r.coupled and r.t == 3]
+    assert len(last) == 1
+    assert all(len(s) <= 2 for s in last[0].selected)
+    mid = [r for r in run.records if r.coupled and r.t == 2]
+    assert len(mid) == 3

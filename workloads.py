@@ -1,0 +1,182 @@
+"""Seeded synthetic workloads shared by the oracle, the tests and the benchmark.
+
+This module holds only input definitions: problem parameters and seeded random
+test polynomials.  It contains none of the usFFT arithmetic (no lattice, no
+transform, no solve, no selection), so both the CPU oracle and the CUDA path may
+import it without sharing method code.
+
+The PDE workloads stand in for the paper's numerical examples (Sec. 4.1-4.3,
+Table 4.1): the same stochastic dimensions, search domains, sparsities and
+coefficient families, on uniform meshes instead of the paper's unstructured
+mesh (which is not available).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import Optional
+
+import numpy as np
+
+# problem kinds
+PDE_1D = 1
+PDE_2D = 2
+TRIGPOLY = 3
+
+# coefficient models (periodic in y, so no periodization is needed; Sec. 3.2)
+COEF_AFFINE_SIN = 1     # a = 1 + sum_j c j^-mu psi_j(x) sin(2 pi y_j)
+COEF_LOGNORMAL_SIN = 2  # a = exp(sum_j c j^-mu psi_j(x) sin(2 pi y_j))
+
+PRECISION_FP64 = 0
+PRECISION_MIXED = 1
+
+
+@dataclass
+class Problem:
+    """The parametric elliptic problem -div(a(x,y) grad u) = f, u = 0 on the boundary (Eq. (1.1))."""
+    kind: int
+    n: int                      # interior nodes per side (PDE); G = n (1-D) or n*n (2-D)
+    d: int                      # stochastic dimension
+    coef_model: int = COEF_AFFINE_SIN
+    coef_scale: float = 0.9 * 6.0 / math.pi ** 2   # c = 0.9/zeta(2) (Sec. 4.2)
+    coef_decay: float = 2.0                        # mu
+    f_const: float = 1.0
+    # TRIGPOLY black box: per node g a list of (frequency, coefficient) terms
+    tp_freqs: Optional[np.ndarray] = None   # int8 [G][nterms][d]
+    tp_coefs: Optional[np.ndarray] = None   # complex128 [G][nterms] (0 pads unused slots)
+
+    @property
+    def G(self) -> int:
+        if self.kind == PDE_1D:
+            return self.n
+        if self.kind == PDE_2D:
+            return self.n * self.n
+        return int(self.tp_freqs.shape[0])
+
+
+@dataclass
+class Params:
+    """Detection parameters of Algorithm 1 (search domain [-N,N]^d, s, s_local, theta, r)."""
+    N: int
+    s: int
+    s_local: int
+    delta: float
+    delta_is_relative: bool
+    r: int
+    seed: int
+    precision: int = PRECISION_FP64
+    hbm_budget_bytes: int = 0          # 0 = no budget
+    max_cg_iters: int = 4000
+    max_lattice_trials: int = 64
+    cg_tol: float = 0.0                # 0 = library default
+
+
+@dataclass
+class Workload:
+    name: str
+    problem: Problem
+    params: Params
+    note: str = ""
+
+
+def c1(seed: int = 1) -> Workload:
+    """1-D, 31 interior nodes, d=4, Gamma=[-16,16]^4, s=50, delta=1e-12 relative, r=1."""
+    return Workload(
+        "c1_1d_n31_d4",
+        Problem(kind=PDE_1D, n=31, d=4),
+        Params(N=16, s=50, s_local=50, delta=1e-12, delta_is_relative=True, r=1, seed=seed),
+        "1-D P1 FE, f=1, a=1+sum_{j<=4} 0.5471 j^-2 sin(j pi x) sin(2 pi y_j)")
+
+
+def c2(seed: int = 1) -> Workload:
+    """2-D 63x63 interior (64x64 squares, 8192 triangles), d=10, Gamma=[-32,32]^10, s=500, delta=1e-10 rel, r=2."""
+    return Workload(
+        "c2_2d_n63_d10",
+        Problem(kind=PDE_2D, n=63, d=10),
+        Params(N=32, s=500, s_local=500, delta=1e-10, delta_is_relative=True, r=2, seed=seed),
+        "2-D P1 FE on the unit square, f=1, affine periodic coefficient, modes ordered by j1+j2")
+
+
+def c3(seed: int = 1) -> Workload:
+    """2-D 127x127 interior, lognormal-type coefficient, d=20, Gamma=[-32,32]^20, s=1000."""
+    return Workload(
+        "c3_2d_n127_d20_lognormal",
+        Problem(kind=PDE_2D, n=127, d=20, coef_model=COEF_LOGNORMAL_SIN, coef_scale=0.5, coef_decay=2.0),
+        Params(N=32, s=1000, s_local=1000, delta=1e-10, delta_is_relative=True, r=2, seed=seed,
+               precision=PRECISION_MIXED),
+        "a = exp(sum_{j<=20} 0.5 j^-2 phi_j(x) sin(2 pi y_j))")
+
+
+def small_2d(n: int = 15, d: int = 4, seed: int = 1, N: int = 8, s: int = 40, r: int = 1) -> Workload:
+    """A 2-D instance small enough for the banded-Cholesky oracle to finish in seconds."""
+    return Workload(
+        f"small_2d_n{n}_d{d}",
+        Problem(kind=PDE_2D, n=n, d=d),
+        Params(N=N, s=s, s_local=s, delta=1e-10, delta_is_relative=True, r=r, seed=seed))
+
+
+def trigpoly(G: int, d: int, N: int, seed: int, base_terms: int = 6, node_terms: int = 2,
+             max_active: int = 3, kmax: int = 4, mag_lo: float = 1e-6, mag_hi: float = 1.0) -> Problem:
+    """Seeded real trigonometric polynomials p^(g), g=1..G (the black box of Theorem 1.1).
+
+    Each p^(g) is real: its support is closed under k -> -k and its coefficients are
+    Hermitian (c_{-k} = conj(c_k)).  The supports overlap: a common base set plus a few
+    per-node frequencies.  Frequencies have at most `max_active` nonzero components,
+    each of size <= min(kmax, N); magnitudes are log-uniform in [mag_lo, mag_hi].
+    """
+    rng = np.random.default_rng(seed)
+    kmax = min(kmax, N)
+
+    def draw_freq():
+        k = np.zeros(d, dtype=np.int64)
+        na = int(rng.integers(1, max_active + 1))
+        dims = rng.choice(d, size=min(na, d), replace=False)
+        for j in dims:
+            v = 0
+            while v == 0:
+                v = int(rng.integers(-kmax, kmax + 1))
+            k[j] = v
+        return k
+
+    def draw_coef():
+        mag = math.exp(rng.uniform(math.log(mag_lo), math.log(mag_hi)))
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        return mag * complex(math.cos(ph), math.sin(ph))
+
+    base = []
+    seen = set()
+    while len(base) < base_terms:
+        k = draw_freq()
+        key = tuple(k)
+        if key in seen or tuple(-k) in seen:
+            continue
+        seen.add(key)
+        base.append(k)
+    per_node = []
+    width = 1 + 2 * (base_terms + node_terms)
+    freqs = np.zeros((G, width, d), dtype=np.int8)
+    coefs = np.zeros((G, width), dtype=np.complex128)
+    for g in range(G):
+        terms = {tuple([0] * d): complex(rng.uniform(0.5, 1.0), 0.0)}
+        for k in base:
+            c = draw_coef()
+            terms[tuple(k)] = c
+            terms[tuple(-k)] = c.conjugate()
+        extra = 0
+        while extra < node_terms:
+            k = draw_freq()
+            if tuple(k) in terms or tuple(-k) in terms:
+                continue
+            c = draw_coef()
+            terms[tuple(k)] = c
+            terms[tuple(-k)] = c.conjugate()
+            extra += 1
+        for slot, (k, c) in enumerate(sorted(terms.items())):
+            freqs[g, slot] = np.array(k, dtype=np.int8)
+            coefs[g, slot] = c
+        per_node.append(len(terms))
+    return Problem(kind=TRIGPOLY, n=0, d=d, tp_freqs=freqs, tp_coefs=coefs)
+
+
+def with_precision(w: Workload, precision: int) -> Workload:
+    return replace(w, params=replace(w.params, precision=precision))
