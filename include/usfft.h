@@ -1,0 +1,213 @@
+/*
+ * usfft.h -- C ABI of the GB300 (sm_103a) usFFT sampling-and-detection library.
+ *
+ * The library runs the dimension-incremental detection of the uniform sparse FFT
+ * (usFFT; Kaemmerer, Potts, Taubert, "The uniform sparse FFT with application to PDEs
+ * with random coefficients", Algorithm 1, steps 1, 2a and 2) for the parametric
+ * elliptic problem -div(a(x,y) grad u) = f, u = 0 on the boundary (Eq. (1.1)), with
+ * the PDE solved on the GPU at every sampling node (the "black box" of Sec. 2.1).
+ *
+ * One increment t (see usfft_increment) runs, on one GPU:
+ *   - the 1-D detections of dimension t (Algorithm 1, steps 1 & 2a);
+ *   - for t >= 2 the coupled step t (Algorithm 1, step 2): candidate set J_t, a
+ *     reconstructing rank-1 lattice (Appendix A), FE solves at its M nodes
+ *     (fused coefficient assembly + cyclic reduction in 1-D / preconditioned CG in
+ *     2-D), one length-M FFT per mesh node with the gather at k.z mod M, per-node
+ *     selection of the <= s~ largest coefficients >= theta and the union over nodes.
+ *
+ * Conventions for every entry point:
+ *   - Return value: usfft_status; USFFT_OK (0) on success.  No call aborts the process.
+ *     On failure the plan's message is available through usfft_last_error(plan)
+ *     (or usfft_last_error(NULL) for failures before a plan exists).
+ *   - Pointers are host pointers unless the argument says "device".
+ *   - A plan is not thread-safe: one host thread at a time per plan.
+ *   - Device memory: the plan owns every buffer it allocates.  If params->alloc is
+ *     non-NULL all device memory comes from that allocator (the Python binding passes
+ *     PyTorch's caching allocator); otherwise cudaMalloc/cudaFree are used.
+ *   - Stream: all device work of a plan is issued on the stream given to usfft_plan
+ *     (NULL = the legacy default stream).  Calls that return host data synchronise
+ *     that stream with a host-side deadline (USFFT_ETIMEOUT, never a device trap).
+ */
+#ifndef USFFT_H
+#define USFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    USFFT_OK = 0,
+    USFFT_EINVAL = 1,     /* invalid argument or problem (e.g. a_min <= 0, sizes out of range) */
+    USFFT_ENOMEM = 2,     /* allocation failed or the hbm_budget_bytes would be exceeded */
+    USFFT_ELATTICE = 3,   /* no reconstructing lattice within max_lattice_trials x 400 sizes */
+    USFFT_ENOCONV = 4,    /* a CG solve hit max_cg_iters before its tolerance */
+    USFFT_ETIMEOUT = 5,   /* the device did not finish before the host-side deadline */
+    USFFT_ECUDA = 6,      /* a CUDA runtime call failed (message holds the CUDA error string) */
+    USFFT_ESTATE = 7      /* call not valid in the plan's state (e.g. increment after t = d) */
+} usfft_status;
+
+/* problem kinds */
+#define USFFT_PDE_1D 1        /* (0,1), n interior nodes, P1 elements of width h = 1/(n+1)        */
+#define USFFT_PDE_2D 2        /* unit square, n*n interior nodes, "/"-split squares of side 1/(n+1) */
+#define USFFT_TRIGPOLY 3      /* test black box: G real trigonometric polynomials (Theorem 1.1)   */
+
+/* coefficient models, periodic in y (Eq. (1.2) with Theta_j(y) = sin(2 pi y_j), Sec. 4.1):
+ *   AFFINE_SIN:    a(x,y) = 1 + sum_{j<=d} c j^-mu psi_j(x) sin(2 pi y_j)
+ *   LOGNORMAL_SIN: a(x,y) = exp(sum_{j<=d} c j^-mu psi_j(x) sin(2 pi y_j))
+ * psi_j(x) = sin(j pi x) in 1-D; sin(j1 pi x1) sin(j2 pi x2) in 2-D with (j1, j2) the
+ * j-th pair of the diagonal enumeration of Sec. 4.2 / Table 4.2, shifted by one:
+ * (1,1), (1,2), (2,1), (1,3), (2,2), (3,1), ...  The coefficient of an element is taken
+ * at its centroid (midpoint in 1-D). */
+#define USFFT_COEF_AFFINE_SIN 1
+#define USFFT_COEF_LOGNORMAL_SIN 2
+
+/* precision of the sampler */
+#define USFFT_FP64 0          /* fp64 everywhere */
+#define USFFT_MIXED 1         /* 2-D: fp32 CG inner solves + fp64-residual iterative refinement;
+                                 1-D: fp64; FFT, gather and selection stay fp64 */
+
+typedef struct {
+    int kind;                 /* USFFT_PDE_1D | USFFT_PDE_2D | USFFT_TRIGPOLY */
+    int n;                    /* PDE: interior nodes per side, 1 <= n <= 1023 (1-D), n <= 127 (2-D) */
+    int d;                    /* stochastic dimension, 1 <= d <= 64 */
+    int coef_model;           /* USFFT_COEF_* (PDE kinds) */
+    double coef_scale;        /* c  */
+    double coef_decay;        /* mu */
+    double f_const;           /* constant right-hand side f */
+    /* TRIGPOLY only (copied at plan time; the caller keeps ownership):
+     * G = tp_nodes polynomials, each with tp_nterms slots; slot (g, s) holds the frequency
+     * tp_freqs[(g*tp_nterms + s)*d + j] (j = 0..d-1) and the complex coefficient
+     * (tp_coefs[2*(g*tp_nterms+s)], tp_coefs[2*(g*tp_nterms+s)+1]); a zero coefficient marks
+     * an unused slot.  The sample is the real part of the sum, so supports should be closed
+     * under k -> -k with conjugate coefficients. */
+    int tp_nodes;
+    int tp_nterms;
+    const int8_t* tp_freqs;
+    const double* tp_coefs;
+} usfft_problem;
+
+/* Device allocator hook: alloc(bytes, stream, ctx) returns device memory or NULL;
+ * free(ptr, stream, ctx) releases it. */
+typedef void* (*usfft_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*usfft_free_fn)(void* ptr, void* stream, void* ctx);
+
+typedef struct {
+    int N;                    /* search domain Gamma = [-N, N]^d, 1 <= N <= 127 */
+    int s;                    /* sparsity s (s~ of the last increment, t = d) */
+    int s_local;              /* s_local (s~ of increments t < d and of the 1-D detections) */
+    double delta;             /* threshold: theta = delta (absolute) or delta * A (relative) */
+    int delta_is_relative;    /* relative: A = max_g |c~_{g,0}| of the 1-D detection t=1, i=1 */
+    int r;                    /* detection iterations r (r~ = 1 at t = d) */
+    uint64_t seed;            /* key of the counter-based SplitMix64 draws (tails, lattices) */
+    int precision;            /* USFFT_FP64 | USFFT_MIXED */
+    size_t hbm_budget_bytes;  /* 0 = unlimited; otherwise ENOMEM beyond this many plan bytes */
+    int max_cg_iters;         /* per CG solve (inner solve in MIXED); 0 = 4000 */
+    int max_lattice_trials;   /* generating vectors tried per lattice size; 0 = 64 */
+    double cg_tol;            /* relative residual target of the FE solve; 0 = 1e-13 */
+    usfft_alloc_fn alloc;     /* NULL = cudaMalloc */
+    usfft_free_fn free;
+    void* alloc_ctx;
+} usfft_params;
+
+typedef struct {
+    int t;                    /* increment just completed (1-based) */
+    int64_t M;                /* lattice size of the coupled step (0 for t = 1) */
+    int64_t n_candidates;     /* |J_t| (K_t = 2N+1 for t = 1) */
+    int64_t n_detected;       /* |I^(1..t)| */
+    int64_t n_1d;             /* |I^(t)| */
+    int64_t samples;          /* lattice samples (FE solves) this increment: r*K + r~*M */
+    int64_t cg_iters_total;   /* summed over all solves (2-D); 0 for 1-D / TRIGPOLY */
+    int32_t cg_iters_max;
+    int32_t kernel_launches;  /* kernels this increment launched */
+    double theta;             /* absolute threshold in use */
+    double ms_device;         /* device time of the increment's kernels (CUDA events) */
+    double ms_host_plan;      /* host time of J_t construction + lattice search */
+} usfft_increment_info;
+
+typedef struct usfft_plan_s usfft_plan_t;
+
+/* Create a plan: validates the problem (uniform ellipticity, Eq. (2.1): a_min > 0 for the
+ * affine model), copies it, precomputes the mode table psi_j(centroid_e) on the device.
+ * stream: a cudaStream_t (NULL = default stream).  *out receives the plan or NULL. */
+usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params,
+                        void* stream, usfft_plan_t** out);
+
+/* Run the next increment t = (previous t) + 1 <= d (semantics in the file header).
+ * info may be NULL.  Synchronises the plan's stream before returning (the detected
+ * set is host data). */
+usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info);
+
+/* Re-run the device part of the last coupled step (sampling, FFT + gather, selection,
+ * union for all r~ iterations) on the resident lattice, candidate indices and tails,
+ * without any host planning or host<->device copies; the detected set is recomputed on
+ * the device.  For timing; the result equals the last increment's.  If sync == 0 the call
+ * returns after enqueueing (kernel count in *launches, may be NULL). */
+usfft_status usfft_replay(usfft_plan_t* plan, int sync, int32_t* launches);
+
+/* Go back to the state after increment t (0 <= t <= current); the plan keeps every
+ * detected set, so a later usfft_increment recomputes increment t+1 exactly. */
+usfft_status usfft_rewind(usfft_plan_t* plan, int t);
+
+/* Current detected set I^(1..t): *n receives |I|; if freqs is non-NULL it receives
+ * |I| rows of t int8 values (capacity *n_capacity rows; EINVAL if too small). */
+usfft_status usfft_get_set(const usfft_plan_t* plan, int8_t* freqs, int64_t n_capacity,
+                           int64_t* n, int32_t* t);
+
+/* Final coefficients (Algorithm 1, step 3) on the current set I with one reconstructing
+ * rank-1 lattice for I (no threshold): coefs receives [G][|I|][2] (re, im) fp64, host or
+ * device pointer (coefs_on_device != 0).  freqs (may be NULL) receives [|I|][t] int8.
+ * With coefs == NULL only *n is set. */
+usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, double* coefs,
+                               int coefs_on_device);
+
+/* Inspection of the last detection step (the coupled step of the last increment, or the
+ * 1-D detection when t = 1): lattice, candidates J_t with their DFT indices k.z mod M,
+ * and the samples U [M][G], coefficients C [G][|J|] and union bitmap of its LAST detection
+ * iteration (the resident buffers).  Sizes are queried with NULL outputs.  The copies
+ * synchronise the plan's stream. */
+usfft_status usfft_get_lattice(const usfft_plan_t* plan, int64_t* z /* [t] or NULL */,
+                               int64_t* M, int32_t* t);
+usfft_status usfft_get_candidates(const usfft_plan_t* plan, int8_t* J /* [|J|][t] or NULL */,
+                                  int64_t* n, int64_t* m /* [|J|] DFT indices or NULL */);
+usfft_status usfft_get_samples(const usfft_plan_t* plan, double* U /* host [M][G] or NULL */,
+                               int64_t* M, int64_t* G);
+usfft_status usfft_get_coefficients(const usfft_plan_t* plan, double* C /* host [G][|J|][2] or NULL */,
+                                    int64_t* G, int64_t* n);
+usfft_status usfft_get_selection(const usfft_plan_t* plan, uint32_t* bitmap /* host, ceil(|J|/32) */,
+                                 int64_t* n);
+
+/* Message of the last failure of this plan (plan == NULL: of the calling thread). */
+const char* usfft_last_error(const usfft_plan_t* plan);
+
+/* Free every device buffer and the plan.  NULL is ignored. */
+void usfft_destroy(usfft_plan_t* plan);
+
+/* Library build information, e.g. "usfft sm_103a cudart 13000". */
+const char* usfft_version(void);
+
+/* ---- Host-only planner utilities (no device work; usable without a GPU) ---- */
+
+/* The reconstructing rank-1 lattice search used by usfft_increment for the candidate set
+ * J ([n][t] int8, row-major): the smallest admissible (7-smooth) size M >= n, then
+ * M' = smallest admissible >= ceil(1.05 M); at each size `trials` generating vectors
+ * z = (1, z_2, ..., z_t), z_j uniform in [1, M-1] from the counter-based draws keyed by
+ * (seed, 3, t, M, trial, j); the first z with k -> k.z mod M injective on J is returned
+ * (Appendix A: a reconstructing lattice makes the single-lattice DFT exact on J).
+ * z receives t entries.  USFFT_ELATTICE if none is found within max_sizes sizes. */
+usfft_status usfft_search_lattice(const int8_t* J, int64_t n, int t, uint64_t seed, int trials,
+                                  int max_sizes, int64_t* z, int64_t* M);
+
+/* Counter-based SplitMix64 draws (Steele, Lea, Flood 2014) used for the random tails
+ * y' of Algorithm 1 (steps 1/2a and 2b) and the lattice search: the fields are folded one
+ * SplitMix64 step each, h <- mix64((h ^ field) + 0x9E3779B97F4A7C15), starting from h = seed.
+ * usfft_draw_key returns h; usfft_draw_uniform returns (h >> 11) * 2^-53 in [0, 1). */
+uint64_t usfft_draw_key(uint64_t seed, const uint64_t* fields, int nfields);
+double usfft_draw_uniform(uint64_t seed, const uint64_t* fields, int nfields);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* USFFT_H */

@@ -20,7 +20,9 @@ reading used here (the same on both sides, so (z, M) are bit-exact):
   M' >= ceil(1.05 M) = floor((105 M + 99)/100) (integer arithmetic);
 - at every size, trials tr = 0..T-1 draw z_1 = 1 and z_j = uniform integer in
   [1, M-1] (j = 2..t) from key(seed, PHASE_LATTICE, t, M, tr, j); the first z that
-  is injective on J is accepted.
+  is injective on J is accepted;
+- the search gives up on a repeated candidate, after 400 sizes, or beyond
+  M = 4096^2 (a limit of the library's FFT, adopted here so both sides agree).
 
 Pins (tests/test_oracle_lattice.py): on tiny sets, the injectivity test agrees with
 the definition through the lattice Fourier matrix (its columns for J are orthonormal
@@ -29,6 +31,8 @@ exactly when the lattice reconstructs J), enumerated over every z.
 import numpy as np
 
 from . import rng
+
+MAX_LATTICE_SIZE = 4096 * 4096
 
 
 def candidate_set(I_prev: np.ndarray, I_t: np.ndarray, N: int) -> np.ndarray:
@@ -75,8 +79,12 @@ def search(J: np.ndarray, t: int, seed: int, trials: int = 64, max_sizes: int = 
     """(z, M) of the first reconstructing lattice under the rule in the module header."""
     if len(J) == 0:
         return np.zeros(t, dtype=np.int64), 0
+    if len(np.unique(J, axis=0)) < len(J):
+        raise RuntimeError("repeated candidate: no lattice can separate it")
     M = next_admissible(len(J))
     for _ in range(max_sizes):
+        if M > MAX_LATTICE_SIZE:
+            break
         for tr in range(trials):
             z = np.ones(t, dtype=np.int64)
             for j in range(2, t + 1):

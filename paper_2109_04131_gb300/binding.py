@@ -1,0 +1,353 @@
+"""ctypes binding of the C ABI in include/usfft.h (argument marshalling only).
+
+Every numeric step runs in libusfft.so.  If the library is missing this module raises;
+there is no CPU fallback.  Device memory of a plan comes from PyTorch's caching
+allocator (through the allocator hook of usfft_params) and its work runs on the
+current PyTorch stream unless another stream is given.
+
+Module-level functions carry the C names (usfft_plan, usfft_increment, usfft_replay,
+usfft_rewind, usfft_get_set, usfft_reconstruct, usfft_get_lattice, usfft_get_candidates,
+usfft_get_samples, usfft_get_coefficients, usfft_get_selection, usfft_last_error,
+usfft_destroy); ``Plan`` wraps them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libusfft.so")
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ELATTICE", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ECUDA", 7: "ESTATE"}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class UsfftProblem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("d", ctypes.c_int), ("coef_model", ctypes.c_int),
+                ("coef_scale", ctypes.c_double), ("coef_decay", ctypes.c_double), ("f_const", ctypes.c_double),
+                ("tp_nodes", ctypes.c_int), ("tp_nterms", ctypes.c_int),
+                ("tp_freqs", ctypes.c_void_p), ("tp_coefs", ctypes.c_void_p)]
+
+
+class UsfftParams(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("s", ctypes.c_int), ("s_local", ctypes.c_int), ("delta", ctypes.c_double),
+                ("delta_is_relative", ctypes.c_int), ("r", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("max_cg_iters", ctypes.c_int), ("max_lattice_trials", ctypes.c_int), ("cg_tol", ctypes.c_double),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class UsfftIncrementInfo(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int), ("M", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
+                ("n_detected", ctypes.c_int64), ("n_1d", ctypes.c_int64), ("samples", ctypes.c_int64),
+                ("cg_iters_total", ctypes.c_int64), ("cg_iters_max", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("theta", ctypes.c_double), ("ms_device", ctypes.c_double),
+                ("ms_host_plan", ctypes.c_double)]
+
+
+# exported symbols and their signatures (restype, argtypes)
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "usfft_plan": (ctypes.c_int, [ctypes.POINTER(UsfftProblem), ctypes.POINTER(UsfftParams), _P, ctypes.POINTER(_P)]),
+    "usfft_increment": (ctypes.c_int, [_P, ctypes.POINTER(UsfftIncrementInfo)]),
+    "usfft_replay": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]),
+    "usfft_rewind": (ctypes.c_int, [_P, ctypes.c_int]),
+    "usfft_get_set": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int32)]),
+    "usfft_reconstruct": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), _P, _P, ctypes.c_int]),
+    "usfft_get_lattice": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+    "usfft_get_candidates": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), _P]),
+    "usfft_get_samples": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "usfft_get_coefficients": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "usfft_get_selection": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "usfft_last_error": (ctypes.c_char_p, [_P]),
+    "usfft_destroy": (None, [_P]),
+    "usfft_version": (ctypes.c_char_p, []),
+    "usfft_search_lattice": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                            ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "usfft_draw_key": (ctypes.c_uint64, [ctypes.c_uint64, _P, ctypes.c_int]),
+    "usfft_draw_uniform": (ctypes.c_double, [ctypes.c_uint64, _P, ctypes.c_int]),
+}
+
+_lib = None
+
+
+def load_library(force_reload: bool = False):
+    """Load libusfft.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and not force_reload:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first (no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class UsfftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st, handle=None):
+    if st != 0:
+        lib = load_library()
+        msg = lib.usfft_last_error(handle)
+        raise UsfftError(st, msg.decode() if msg else "")
+
+
+def _torch_allocator(device_index):
+    import torch
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=device_index, stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return ALLOC_FN(alloc), FREE_FN(free)
+
+
+def make_problem(prob) -> tuple:
+    """(UsfftProblem, keep-alive arrays) from a workloads.Problem."""
+    p = UsfftProblem()
+    p.kind = prob.kind
+    p.n = prob.n
+    p.d = prob.d
+    p.coef_model = prob.coef_model
+    p.coef_scale = prob.coef_scale
+    p.coef_decay = prob.coef_decay
+    p.f_const = prob.f_const
+    keep = []
+    if prob.tp_freqs is not None:
+        f = np.ascontiguousarray(prob.tp_freqs, dtype=np.int8)
+        c = np.ascontiguousarray(np.stack([prob.tp_coefs.real, prob.tp_coefs.imag], axis=-1), dtype=np.float64)
+        p.tp_nodes = f.shape[0]
+        p.tp_nterms = f.shape[1]
+        p.tp_freqs = f.ctypes.data
+        p.tp_coefs = c.ctypes.data
+        keep += [f, c]
+    return p, keep
+
+
+def make_params(par, alloc=None, free=None) -> UsfftParams:
+    q = UsfftParams()
+    q.N = par.N
+    q.s = par.s
+    q.s_local = par.s_local
+    q.delta = par.delta
+    q.delta_is_relative = int(par.delta_is_relative)
+    q.r = par.r
+    q.seed = par.seed
+    q.precision = par.precision
+    q.hbm_budget_bytes = par.hbm_budget_bytes
+    q.max_cg_iters = par.max_cg_iters
+    q.max_lattice_trials = par.max_lattice_trials
+    q.cg_tol = par.cg_tol
+    q.alloc = alloc if alloc is not None else ALLOC_FN()
+    q.free = free if free is not None else FREE_FN()
+    q.alloc_ctx = None
+    return q
+
+
+# ---- C-named functions -------------------------------------------------------------------
+def usfft_plan(problem, params, stream=None, torch_alloc=True):
+    return Plan(problem, params, stream=stream, torch_alloc=torch_alloc)
+
+
+def usfft_increment(plan):
+    return plan.increment()
+
+
+def usfft_replay(plan, sync=True):
+    return plan.replay(sync)
+
+
+def usfft_rewind(plan, t):
+    return plan.rewind(t)
+
+
+def usfft_get_set(plan):
+    return plan.get_set()
+
+
+def usfft_reconstruct(plan):
+    return plan.reconstruct()
+
+
+def usfft_get_lattice(plan):
+    return plan.get_lattice()
+
+
+def usfft_get_candidates(plan):
+    return plan.get_candidates()
+
+
+def usfft_get_samples(plan):
+    return plan.get_samples()
+
+
+def usfft_get_coefficients(plan):
+    return plan.get_coefficients()
+
+
+def usfft_get_selection(plan):
+    return plan.get_selection()
+
+
+def usfft_last_error(plan=None):
+    lib = load_library()
+    msg = lib.usfft_last_error(plan.handle if plan is not None else None)
+    return msg.decode() if msg else ""
+
+
+def usfft_destroy(plan):
+    plan.close()
+
+
+def usfft_search_lattice(J, t, seed, trials=64, max_sizes=400):
+    """Host-only lattice search of the library: (z, M) for the candidate rows J [n][t]."""
+    lib = load_library()
+    Jc = np.ascontiguousarray(J, dtype=np.int8).reshape(-1, t) if len(J) else np.zeros((0, t), np.int8)
+    z = np.zeros(t, dtype=np.int64)
+    M = ctypes.c_int64(0)
+    st = lib.usfft_search_lattice(Jc.ctypes.data if len(Jc) else None, len(Jc), t, seed, trials, max_sizes,
+                                  z.ctypes.data, ctypes.byref(M))
+    _check(st, None)
+    return z, M.value
+
+
+def usfft_draw_key(seed, *fields):
+    lib = load_library()
+    f = (ctypes.c_uint64 * max(1, len(fields)))(*fields)
+    return int(lib.usfft_draw_key(seed, f, len(fields)))
+
+
+def usfft_draw_uniform(seed, *fields):
+    lib = load_library()
+    f = (ctypes.c_uint64 * max(1, len(fields)))(*fields)
+    return float(lib.usfft_draw_uniform(seed, f, len(fields)))
+
+
+class Plan:
+    """One usFFT detection run (problem + parameters) on the current CUDA device."""
+
+    def __init__(self, problem, params, stream=None, torch_alloc=True):
+        lib = load_library()
+        self._lib = lib
+        self.problem = problem
+        self.params = params
+        self.handle = None
+        self._keep = []
+        alloc = free = None
+        if stream is None or torch_alloc:
+            import torch
+            dev = torch.cuda.current_device()
+            if stream is None:
+                stream = torch.cuda.current_stream(dev).cuda_stream
+            if torch_alloc:
+                alloc, free = _torch_allocator(dev)
+        self._alloc, self._free = alloc, free
+        self.stream = int(stream or 0)
+        prob, keep = make_problem(problem)
+        self._keep += keep
+        par = make_params(params, alloc, free)
+        h = ctypes.c_void_p()
+        st = lib.usfft_plan(ctypes.byref(prob), ctypes.byref(par), ctypes.c_void_p(self.stream), ctypes.byref(h))
+        _check(st, None)
+        self.handle = h
+
+    def _ck(self, st):
+        _check(st, self.handle)
+
+    def increment(self) -> dict:
+        info = UsfftIncrementInfo()
+        self._ck(self._lib.usfft_increment(self.handle, ctypes.byref(info)))
+        return {name: getattr(info, name) for name, _ in UsfftIncrementInfo._fields_}
+
+    def replay(self, sync=True) -> int:
+        n = ctypes.c_int32(0)
+        self._ck(self._lib.usfft_replay(self.handle, int(bool(sync)), ctypes.byref(n)))
+        return n.value
+
+    def rewind(self, t: int) -> None:
+        self._ck(self._lib.usfft_rewind(self.handle, int(t)))
+
+    def get_set(self) -> np.ndarray:
+        n = ctypes.c_int64(0)
+        t = ctypes.c_int32(0)
+        self._ck(self._lib.usfft_get_set(self.handle, None, 0, ctypes.byref(n), ctypes.byref(t)))
+        out = np.zeros((n.value, t.value), dtype=np.int8)
+        if n.value:
+            self._ck(self._lib.usfft_get_set(self.handle, out.ctypes.data, n.value, ctypes.byref(n), ctypes.byref(t)))
+        return out.astype(np.int64)
+
+    def reconstruct(self):
+        n = ctypes.c_int64(0)
+        self._ck(self._lib.usfft_reconstruct(self.handle, ctypes.byref(n), None, None, 0))
+        return n.value
+
+    def get_lattice(self):
+        M = ctypes.c_int64(0)
+        t = ctypes.c_int32(0)
+        self._ck(self._lib.usfft_get_lattice(self.handle, None, ctypes.byref(M), ctypes.byref(t)))
+        z = np.zeros(t.value, dtype=np.int64)
+        self._ck(self._lib.usfft_get_lattice(self.handle, z.ctypes.data, ctypes.byref(M), ctypes.byref(t)))
+        return z, M.value
+
+    def get_candidates(self):
+        n = ctypes.c_int64(0)
+        self._ck(self._lib.usfft_get_candidates(self.handle, None, ctypes.byref(n), None))
+        z, M = self.get_lattice()
+        t = len(z)
+        J = np.zeros((n.value, t), dtype=np.int8)
+        m = np.zeros(n.value, dtype=np.int64)
+        self._ck(self._lib.usfft_get_candidates(self.handle, J.ctypes.data, ctypes.byref(n), m.ctypes.data))
+        return J.astype(np.int64), m
+
+    def get_samples(self) -> np.ndarray:
+        M = ctypes.c_int64(0)
+        G = ctypes.c_int64(0)
+        self._ck(self._lib.usfft_get_samples(self.handle, None, ctypes.byref(M), ctypes.byref(G)))
+        U = np.zeros((M.value, G.value), dtype=np.float64)
+        self._ck(self._lib.usfft_get_samples(self.handle, U.ctypes.data, ctypes.byref(M), ctypes.byref(G)))
+        return U
+
+    def get_coefficients(self) -> np.ndarray:
+        G = ctypes.c_int64(0)
+        n = ctypes.c_int64(0)
+        self._ck(self._lib.usfft_get_coefficients(self.handle, None, ctypes.byref(G), ctypes.byref(n)))
+        C = np.zeros((G.value, n.value, 2), dtype=np.float64)
+        self._ck(self._lib.usfft_get_coefficients(self.handle, C.ctypes.data, ctypes.byref(G), ctypes.byref(n)))
+        return C[..., 0] + 1j * C[..., 1]
+
+    def get_selection(self) -> np.ndarray:
+        n = ctypes.c_int64(0)
+        self._ck(self._lib.usfft_get_selection(self.handle, None, ctypes.byref(n)))
+        words = np.zeros((n.value + 31) // 32, dtype=np.uint32)
+        self._ck(self._lib.usfft_get_selection(self.handle, words.ctypes.data, ctypes.byref(n)))
+        bits = np.unpackbits(words.view(np.uint8), bitorder="little")[: n.value]
+        return bits.astype(bool)
+
+    def close(self):
+        if self.handle:
+            self._lib.usfft_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,705 @@
+// C ABI of the library: plans, increments (Algorithm 1, steps 1, 2a and 2), replay, rewind
+// and inspection.  Host work here is planning and marshalling only (candidate sets, the
+// lattice search, the counter-based draws of the tails, gather buckets); every numeric
+// step of the path runs in the kernels of k_*.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "usfft.h"
+#include "usfft_internal.h"
+
+using namespace usfft;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Snapshot {
+    int t = 0;
+    std::vector<int8_t> Ipre;
+    int64_t nIpre = 0;
+    std::vector<std::vector<int>> I1d;
+    double theta = 0.0, A = 0.0;
+    bool theta_set = false;
+};
+
+thread_local std::string g_last_error;
+
+}  // namespace
+
+struct usfft_plan_s {
+    usfft_problem prob;
+    usfft_params par;
+    std::vector<int8_t> tp_freqs;
+    std::vector<double> tp_coefs;
+    cudaStream_t stream = nullptr;
+    int G = 0, E = 0, d = 0, N = 0, K = 0;
+    int t = 0;
+    double theta = 0.0, A = 0.0;
+    bool theta_set = false;
+    std::vector<std::vector<int>> I1d;
+    std::vector<int8_t> Ipre;
+    int64_t nIpre = 0;
+    std::vector<Snapshot> hist;
+    // last detection step (coupled, or the 1-D detection of t = 1)
+    bool last_coupled = false;
+    int last_t = 0;
+    std::vector<int8_t> J;
+    int64_t nJ = 0;
+    std::vector<int64_t> z;
+    int64_t M = 0;
+    std::vector<int64_t> m;
+    int s_tilde = 0;
+    std::vector<NodeSpec> specs;
+    FftPlan fp{};
+    // device buffers
+    Buf psi, U, C, bitmap, twid, goff, gk, gm2, fftscr, cgscr, iters, failc, scal, tpf, tpc, tpaux;
+    size_t bytes = 0;
+    int cg_blocks = 0;
+    int launches = 0;
+    int64_t cg_iters_total = 0;
+    int cg_iters_max = 0;
+    bool replay_valid = false;
+    double* pinned = nullptr;   // small pinned staging area
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs = nullptr;
+    std::string err;
+};
+
+namespace {
+
+usfft_status fail(usfft_plan_t* p, usfft_status st, const std::string& msg) {
+    if (p) p->err = msg;
+    g_last_error = msg;
+    return st;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t _e = (call);                                                                     \
+        if (_e != cudaSuccess)                                                                       \
+            return fail(plan, USFFT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e));     \
+    } while (0)
+
+void buf_free(usfft_plan_t* plan, Buf& b) {
+    if (!b.p) return;
+    if (plan->par.alloc && plan->par.free)
+        plan->par.free(b.p, plan->stream, plan->par.alloc_ctx);
+    else
+        cudaFree(b.p);
+    plan->bytes -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+usfft_status ensure(usfft_plan_t* plan, Buf& b, size_t bytes, const char* what) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return USFFT_OK;
+    size_t want = bytes + bytes / 8;
+    size_t after = plan->bytes - b.bytes + want;
+    if (plan->par.hbm_budget_bytes && after > plan->par.hbm_budget_bytes) {
+        want = bytes;
+        after = plan->bytes - b.bytes + want;
+        if (after > plan->par.hbm_budget_bytes) {
+            char msg[256];
+            snprintf(msg, sizeof msg, "%s: %zu bytes would exceed the budget of %zu bytes (plan holds %zu)", what,
+                     bytes, plan->par.hbm_budget_bytes, plan->bytes);
+            return fail(plan, USFFT_ENOMEM, msg);
+        }
+    }
+    buf_free(plan, b);
+    void* p = nullptr;
+    if (plan->par.alloc) {
+        p = plan->par.alloc(want, plan->stream, plan->par.alloc_ctx);
+    } else if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (!p) {
+        char msg[256];
+        snprintf(msg, sizeof msg, "%s: device allocation of %zu bytes failed", what, want);
+        return fail(plan, USFFT_ENOMEM, msg);
+    }
+    b.p = p;
+    b.bytes = want;
+    plan->bytes += want;
+    return USFFT_OK;
+}
+
+double timeout_seconds() {
+    const char* e = getenv("USFFT_TIMEOUT_S");
+    double v = e ? atof(e) : 0.0;
+    return v > 0 ? v : 3600.0;
+}
+
+// Wait for the plan's stream with a host-side deadline (never a device-side trap).
+usfft_status wait_stream(usfft_plan_t* plan) {
+    cudaError_t e = cudaEventRecord(plan->evs, plan->stream);
+    if (e != cudaSuccess) return fail(plan, USFFT_ECUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+    auto t0 = std::chrono::steady_clock::now();
+    const double limit = timeout_seconds();
+    int spins = 0;
+    for (;;) {
+        e = cudaEventQuery(plan->evs);
+        if (e == cudaSuccess) return USFFT_OK;
+        if (e != cudaErrorNotReady)
+            return fail(plan, USFFT_ECUDA, std::string("device error: ") + cudaGetErrorString(e));
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > limit) return fail(plan, USFFT_ETIMEOUT, "device work did not finish before the host deadline");
+        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+NodeSpec spec_1d(const usfft_plan_t* p, int t, int i) {
+    NodeSpec ns;
+    memset(&ns, 0, sizeof ns);
+    ns.M = p->K;
+    ns.d = p->d;
+    for (int j = 1; j <= p->d; ++j) {
+        if (j == t) {
+            ns.z[j - 1] = 1;
+        } else {
+            ns.z[j - 1] = -1;
+            uint64_t f[4] = {PHASE_1D_TAIL, (uint64_t)t, (uint64_t)i, (uint64_t)j};
+            ns.tail[j - 1] = rng_uniform(p->par.seed, f, 4);
+        }
+    }
+    return ns;
+}
+
+NodeSpec spec_coupled(const usfft_plan_t* p, int t, int i) {
+    NodeSpec ns;
+    memset(&ns, 0, sizeof ns);
+    ns.M = p->M;
+    ns.d = p->d;
+    for (int j = 1; j <= p->d; ++j) {
+        if (j <= t) {
+            ns.z[j - 1] = p->z[(size_t)(j - 1)];
+        } else {
+            ns.z[j - 1] = -1;
+            uint64_t f[4] = {PHASE_TAIL, (uint64_t)t, (uint64_t)i, (uint64_t)j};
+            ns.tail[j - 1] = rng_uniform(p->par.seed, f, 4);
+        }
+    }
+    return ns;
+}
+
+// sampler dispatch: U[0..M)[G] for the node set
+usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns) {
+    const int kind = plan->prob.kind;
+    if (kind == USFFT_PDE_1D) {
+        CK(launch_sample_1d(ns, plan->prob.n, plan->prob.coef_model, plan->prob.f_const, (const double*)plan->psi.p,
+                            0, ns.M, (double*)plan->U.p, plan->stream, &plan->launches));
+    } else if (kind == USFFT_PDE_2D) {
+        CgConfig cg;
+        cg.precision = plan->par.precision;
+        cg.max_iters = plan->par.max_cg_iters;
+        cg.tol = plan->par.cg_tol;
+        cg.blocks = plan->cg_blocks;
+        CK(launch_sample_2d(ns, plan->prob.n, plan->prob.coef_model, plan->prob.f_const, (const double*)plan->psi.p, cg,
+                            0, ns.M, (double*)plan->U.p, (int*)plan->iters.p, (unsigned int*)plan->failc.p,
+                            (double*)plan->cgscr.p, plan->cgscr.bytes, plan->stream, &plan->launches));
+    } else {
+        CK(launch_sample_trigpoly(ns, plan->G, plan->prob.tp_nterms, (const int8_t*)plan->tpf.p,
+                                  (const double*)plan->tpc.p, (double*)plan->tpaux.p, (double*)plan->U.p,
+                                  plan->stream, &plan->launches));
+    }
+    return USFFT_OK;
+}
+
+// buffers and gather plan for a detection step with nJ candidates at indices m, lattice size M
+usfft_status prepare_step(usfft_plan_t* plan, int64_t M, const std::vector<int64_t>& m) {
+    const int64_t nJ = (int64_t)m.size();
+    usfft_status st;
+    plan->fp = make_fft_plan(M);
+    if (plan->fp.L2 <= 0) return fail(plan, USFFT_EINVAL, "lattice size has no factorisation into FFT passes <= 4096");
+    const int G = plan->G;
+    if ((st = ensure(plan, plan->U, sizeof(double) * (size_t)M * G, "samples")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->C, sizeof(double2) * (size_t)nJ * G, "coefficients")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->twid, sizeof(double2) * (size_t)M, "twiddles")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->fftscr, fft_scratch_bytes(plan->fp, G), "fft scratch")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->bitmap, sizeof(uint32_t) * (size_t)((nJ + 31) / 32), "bitmap")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->iters, sizeof(int) * (size_t)M, "cg iterations")) != USFFT_OK) return st;
+    const int L1 = plan->fp.L1;
+    std::vector<int> off((size_t)L1 + 1, 0), bk((size_t)nJ), bm2((size_t)nJ);
+    for (int64_t k = 0; k < nJ; ++k) off[(size_t)(m[(size_t)k] % L1) + 1]++;
+    for (int b = 0; b < L1; ++b) off[(size_t)b + 1] += off[(size_t)b];
+    std::vector<int> fill(off.begin(), off.end() - 1);
+    for (int64_t k = 0; k < nJ; ++k) {
+        const int b = (int)(m[(size_t)k] % L1);
+        const int e = fill[(size_t)b]++;
+        bk[(size_t)e] = (int)k;
+        bm2[(size_t)e] = (int)(m[(size_t)k] / L1);
+    }
+    if ((st = ensure(plan, plan->goff, sizeof(int) * off.size(), "gather offsets")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->gk, sizeof(int) * (size_t)std::max<int64_t>(nJ, 1), "gather k")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->gm2, sizeof(int) * (size_t)std::max<int64_t>(nJ, 1), "gather m2")) != USFFT_OK) return st;
+    CK(cudaMemcpyAsync(plan->goff.p, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, plan->stream));
+    if (nJ) {
+        CK(cudaMemcpyAsync(plan->gk.p, bk.data(), sizeof(int) * (size_t)nJ, cudaMemcpyHostToDevice, plan->stream));
+        CK(cudaMemcpyAsync(plan->gm2.p, bm2.data(), sizeof(int) * (size_t)nJ, cudaMemcpyHostToDevice, plan->stream));
+    }
+    // host vectors must outlive the asynchronous copies
+    CK(cudaStreamSynchronize(plan->stream));
+    CK(launch_twiddles(M, (double2*)plan->twid.p, plan->stream, &plan->launches));
+    plan->M = M;
+    plan->m = m;
+    plan->nJ = nJ;
+    return USFFT_OK;
+}
+
+// device part of a detection step: r~ iterations of sample -> FFT+gather -> select/union
+usfft_status run_step_device(usfft_plan_t* plan, bool first_1d_sets_theta) {
+    const int64_t nJ = plan->nJ;
+    CK(cudaMemsetAsync(plan->bitmap.p, 0, sizeof(uint32_t) * (size_t)((nJ + 31) / 32), plan->stream));
+    if (nJ == 0) return USFFT_OK;
+    GatherPlan gp{(const int*)plan->goff.p, (const int*)plan->gk.p, (const int*)plan->gm2.p};
+    for (size_t it = 0; it < plan->specs.size(); ++it) {
+        usfft_status st = run_sampler(plan, plan->specs[it]);
+        if (st != USFFT_OK) return st;
+        CK(launch_fft_gather(plan->fp, plan->G, (const double*)plan->U.p, (const double2*)plan->twid.p, gp, nJ,
+                             (double2*)plan->fftscr.p, (double2*)plan->C.p, plan->stream, &plan->launches));
+        if (first_1d_sets_theta && it == 0 && !plan->theta_set) {
+            // relative threshold: theta = delta * max_g |c_{g,0}| of the first 1-D detection
+            CK(launch_absmax_column((const double2*)plan->C.p, plan->G, nJ, plan->N, (double*)plan->scal.p,
+                                    plan->stream, &plan->launches));
+            CK(cudaMemcpyAsync(plan->pinned, plan->scal.p, sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
+            usfft_status w = wait_stream(plan);
+            if (w != USFFT_OK) return w;
+            plan->A = plan->pinned[0];
+            plan->theta = plan->par.delta * plan->A;
+            plan->theta_set = true;
+        }
+        if (plan->s_tilde > 0)
+            CK(launch_select_union((const double2*)plan->C.p, plan->G, nJ, plan->theta, plan->s_tilde,
+                                   (uint32_t*)plan->bitmap.p, plan->stream, &plan->launches));
+    }
+    return USFFT_OK;
+}
+
+usfft_status read_bitmap(usfft_plan_t* plan, std::vector<uint32_t>& bits) {
+    const size_t words = (size_t)((plan->nJ + 31) / 32);
+    bits.assign(words, 0u);
+    if (words) CK(cudaMemcpyAsync(bits.data(), plan->bitmap.p, 4 * words, cudaMemcpyDeviceToHost, plan->stream));
+    return wait_stream(plan);
+}
+
+usfft_status read_cg_stats(usfft_plan_t* plan, int64_t count) {
+    if (plan->prob.kind != USFFT_PDE_2D || count <= 0) return USFFT_OK;
+    std::vector<int> it((size_t)count);
+    unsigned int fails = 0;
+    CK(cudaMemcpyAsync(it.data(), plan->iters.p, sizeof(int) * (size_t)count, cudaMemcpyDeviceToHost, plan->stream));
+    CK(cudaMemcpyAsync(&fails, plan->failc.p, sizeof(unsigned), cudaMemcpyDeviceToHost, plan->stream));
+    usfft_status st = wait_stream(plan);
+    if (st != USFFT_OK) return st;
+    for (int v : it) {
+        plan->cg_iters_total += v;
+        plan->cg_iters_max = std::max(plan->cg_iters_max, v);
+    }
+    if (fails) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "%u FE solves did not reach the CG tolerance within max_cg_iters", fails);
+        return fail(plan, USFFT_ENOCONV, msg);
+    }
+    return USFFT_OK;
+}
+
+void take_snapshot(usfft_plan_t* p) {
+    Snapshot s;
+    s.t = p->t;
+    s.Ipre = p->Ipre;
+    s.nIpre = p->nIpre;
+    s.I1d = p->I1d;
+    s.theta = p->theta;
+    s.A = p->A;
+    s.theta_set = p->theta_set;
+    if ((int)p->hist.size() > p->t) p->hist.resize((size_t)p->t);
+    p->hist.push_back(s);
+}
+
+}  // namespace
+
+extern "C" {
+
+#define USFFT_STR2(x) #x
+#define USFFT_STR(x) USFFT_STR2(x)
+const char* usfft_version(void) { return "usfft sm_103a cudart " USFFT_STR(CUDART_VERSION); }
+
+const char* usfft_last_error(const usfft_plan_t* plan) {
+    if (plan) return plan->err.c_str();
+    return g_last_error.c_str();
+}
+
+usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params, void* stream, usfft_plan_t** out) {
+    usfft_plan_t* plan = nullptr;
+    if (!out) return fail(nullptr, USFFT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!problem || !params) return fail(nullptr, USFFT_EINVAL, "problem or params is NULL");
+    const usfft_problem& pr = *problem;
+    const usfft_params& pa = *params;
+    if (pr.d < 1 || pr.d > USFFT_MAX_D) return fail(nullptr, USFFT_EINVAL, "d must lie in [1, 64]");
+    if (pa.N < 1 || pa.N > 127) return fail(nullptr, USFFT_EINVAL, "N must lie in [1, 127] (int8 frequencies)");
+    if (pa.r < 1 || pa.s < 0 || pa.s_local < 0) return fail(nullptr, USFFT_EINVAL, "r >= 1, s >= 0, s_local >= 0");
+    if (!(pa.delta >= 0.0)) return fail(nullptr, USFFT_EINVAL, "delta must be >= 0");
+    if (pa.precision != USFFT_FP64 && pa.precision != USFFT_MIXED) return fail(nullptr, USFFT_EINVAL, "precision");
+    int G = 0, E = 0;
+    if (pr.kind == USFFT_PDE_1D) {
+        if (pr.n < 1 || pr.n > 1023) return fail(nullptr, USFFT_EINVAL, "1-D: n must lie in [1, 1023]");
+        G = pr.n;
+        E = pr.n + 1;
+    } else if (pr.kind == USFFT_PDE_2D) {
+        if (pr.n < 1 || pr.n > 63) return fail(nullptr, USFFT_EINVAL, "2-D: n must lie in [1, 63] in this version");
+        if (pa.precision == USFFT_MIXED && pr.n < 4) return fail(nullptr, USFFT_EINVAL, "2-D mixed: n >= 4");
+        G = pr.n * pr.n;
+        E = 2 * (pr.n + 1) * (pr.n + 1);
+    } else if (pr.kind == USFFT_TRIGPOLY) {
+        if (pr.tp_nodes < 1 || pr.tp_nterms < 1 || !pr.tp_freqs || !pr.tp_coefs)
+            return fail(nullptr, USFFT_EINVAL, "TRIGPOLY: tp_nodes, tp_nterms, tp_freqs, tp_coefs required");
+        G = pr.tp_nodes;
+    } else {
+        return fail(nullptr, USFFT_EINVAL, "unknown problem kind");
+    }
+    if (pr.kind != USFFT_TRIGPOLY) {
+        if (pr.coef_model != USFFT_COEF_AFFINE_SIN && pr.coef_model != USFFT_COEF_LOGNORMAL_SIN)
+            return fail(nullptr, USFFT_EINVAL, "unknown coefficient model");
+        // uniform ellipticity (Eq. (2.1)) of the affine model: 1 - c sum_j j^-mu > 0
+        if (pr.coef_model == USFFT_COEF_AFFINE_SIN) {
+            double sum = 0.0;
+            for (int j = 1; j <= pr.d; ++j) sum += pow((double)j, -pr.coef_decay);
+            if (1.0 - fabs(pr.coef_scale) * sum <= 0.0)
+                return fail(nullptr, USFFT_EINVAL, "coefficient violates uniform ellipticity: a_min <= 0");
+        }
+    }
+    plan = new usfft_plan_s();
+    plan->prob = pr;
+    plan->par = pa;
+    if (plan->par.max_cg_iters <= 0) plan->par.max_cg_iters = 4000;
+    if (plan->par.max_lattice_trials <= 0) plan->par.max_lattice_trials = 64;
+    if (!(plan->par.cg_tol > 0.0)) plan->par.cg_tol = 1e-13;
+    plan->stream = (cudaStream_t)stream;
+    plan->G = G;
+    plan->E = E;
+    plan->d = pr.d;
+    plan->N = pa.N;
+    plan->K = 2 * pa.N + 1;
+    plan->I1d.assign((size_t)pr.d + 1, std::vector<int>());
+    if (!pa.delta_is_relative) {
+        plan->theta = pa.delta;
+        plan->theta_set = true;
+    }
+    usfft_status st;
+    auto bail = [&](usfft_status s) {
+        usfft_destroy(plan);
+        return s;
+    };
+    if (cudaEventCreate(&plan->ev0) != cudaSuccess || cudaEventCreate(&plan->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->evs, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        fail(plan, USFFT_ECUDA, "cudaEventCreate failed");
+        return bail(USFFT_ECUDA);
+    }
+    if (cudaMallocHost(&plan->pinned, 64) != cudaSuccess) {
+        cudaGetLastError();
+        fail(plan, USFFT_ECUDA, "cudaMallocHost failed");
+        return bail(USFFT_ECUDA);
+    }
+    if ((st = ensure(plan, plan->scal, 64, "scalars")) != USFFT_OK) return bail(st);
+    if ((st = ensure(plan, plan->failc, 64, "fail counter")) != USFFT_OK) return bail(st);
+    if (pr.kind == USFFT_TRIGPOLY) {
+        const size_t nt = (size_t)G * pr.tp_nterms;
+        plan->tp_freqs.assign(pr.tp_freqs, pr.tp_freqs + nt * pr.d);
+        plan->tp_coefs.assign(pr.tp_coefs, pr.tp_coefs + nt * 2);
+        if ((st = ensure(plan, plan->tpf, nt * pr.d, "trigpoly freqs")) != USFFT_OK) return bail(st);
+        if ((st = ensure(plan, plan->tpc, nt * 2 * sizeof(double), "trigpoly coefs")) != USFFT_OK) return bail(st);
+        if ((st = ensure(plan, plan->tpaux, nt * 3 * sizeof(double), "trigpoly aux")) != USFFT_OK) return bail(st);
+        if (cudaMemcpyAsync(plan->tpf.p, plan->tp_freqs.data(), nt * pr.d, cudaMemcpyHostToDevice, plan->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(plan->tpc.p, plan->tp_coefs.data(), nt * 2 * sizeof(double), cudaMemcpyHostToDevice,
+                            plan->stream) != cudaSuccess) {
+            cudaGetLastError();
+            fail(plan, USFFT_ECUDA, "copy of the trigonometric polynomials failed");
+            return bail(USFFT_ECUDA);
+        }
+        plan->prob.tp_freqs = nullptr;
+        plan->prob.tp_coefs = nullptr;
+    } else {
+        if ((st = ensure(plan, plan->psi, sizeof(double) * (size_t)E * pr.d, "mode table")) != USFFT_OK) return bail(st);
+        if (launch_psi_table(pr.kind, pr.n, pr.d, pr.coef_scale, pr.coef_decay, (double*)plan->psi.p, plan->stream) !=
+            cudaSuccess) {
+            fail(plan, USFFT_ECUDA, "mode table kernel failed");
+            return bail(USFFT_ECUDA);
+        }
+        if (pr.kind == USFFT_PDE_2D) {
+            plan->cg_blocks = sample_2d_default_blocks(pr.n, pa.precision);
+            size_t sb = sample_2d_scratch_bytes(pr.n, pa.precision, plan->cg_blocks);
+            if ((st = ensure(plan, plan->cgscr, sb, "cg scratch")) != USFFT_OK) return bail(st);
+        }
+    }
+    if ((st = wait_stream(plan)) != USFFT_OK) return bail(st);
+    take_snapshot(plan);
+    *out = plan;
+    return USFFT_OK;
+}
+
+usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (plan->t >= plan->d) return fail(plan, USFFT_ESTATE, "all d increments are done");
+    const int t = plan->t + 1;
+    const int N = plan->N, K = plan->K;
+    plan->launches = 0;
+    plan->cg_iters_total = 0;
+    plan->cg_iters_max = 0;
+    double ms_host = 0.0;
+    usfft_status st;
+    CK(cudaMemsetAsync(plan->failc.p, 0, sizeof(unsigned), plan->stream));
+    CK(cudaEventRecord(plan->ev0, plan->stream));
+    int64_t samples = 0;
+
+    // ---- 1-D detections of dimension t (Algorithm 1, steps 1 & 2a) ----
+    {
+        std::vector<int64_t> m((size_t)K);
+        for (int idx = 0; idx < K; ++idx) m[(size_t)idx] = ((idx - N) % K + K) % K;
+        if ((st = prepare_step(plan, K, m)) != USFFT_OK) return st;
+        plan->specs.clear();
+        for (int i = 1; i <= plan->par.r; ++i) plan->specs.push_back(spec_1d(plan, t, i));
+        plan->s_tilde = plan->par.s_local;
+        if ((st = run_step_device(plan, true)) != USFFT_OK) return st;
+        if ((st = read_cg_stats(plan, K)) != USFFT_OK) return st;
+        std::vector<uint32_t> bits;
+        if ((st = read_bitmap(plan, bits)) != USFFT_OK) return st;
+        plan->I1d[(size_t)t].clear();
+        for (int idx = 0; idx < K; ++idx)
+            if (bits[(size_t)idx >> 5] >> (idx & 31) & 1u) plan->I1d[(size_t)t].push_back(idx - N);
+        samples += (int64_t)K * plan->par.r;
+        plan->last_coupled = false;
+        plan->last_t = t;
+        plan->z.assign(1, 1);
+        plan->J.resize((size_t)K);
+        for (int idx = 0; idx < K; ++idx) plan->J[(size_t)idx] = (int8_t)(idx - N);
+    }
+    if (t == 1) {
+        plan->nIpre = (int64_t)plan->I1d[1].size();
+        plan->Ipre.assign(plan->I1d[1].begin(), plan->I1d[1].end());
+    } else {
+        // ---- coupled step t (Algorithm 1, step 2) ----
+        auto h0 = std::chrono::steady_clock::now();
+        std::vector<int8_t> J;
+        int64_t nJ = 0;
+        candidate_set(plan->Ipre.data(), plan->nIpre, t - 1, plan->I1d[(size_t)t], N, J, nJ);
+        std::vector<int64_t> z;
+        int64_t M = 0;
+        if (!lattice_search(J.data(), nJ, t, plan->par.seed, plan->par.max_lattice_trials, 400, z, M))
+            return fail(plan, USFFT_ELATTICE, "no reconstructing rank-1 lattice found");
+        std::vector<int64_t> m((size_t)nJ);
+        for (int64_t a = 0; a < nJ; ++a) {
+            int64_t acc = 0;
+            for (int j = 0; j < t; ++j) acc += (int64_t)J[(size_t)(a * t + j)] * z[(size_t)j];
+            int64_t mm = acc % M;
+            m[(size_t)a] = mm < 0 ? mm + M : mm;
+        }
+        ms_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
+        plan->J = J;
+        plan->z = z;
+        plan->last_coupled = true;
+        plan->last_t = t;
+        if (nJ > 0) {
+            if ((st = prepare_step(plan, M, m)) != USFFT_OK) return st;
+        } else {
+            plan->M = 0;
+            plan->m.clear();
+            plan->nJ = 0;
+        }
+        const int rt = t < plan->d ? plan->par.r : 1;
+        plan->s_tilde = t < plan->d ? plan->par.s_local : plan->par.s;
+        plan->specs.clear();
+        for (int i = 1; i <= rt && nJ > 0; ++i) plan->specs.push_back(spec_coupled(plan, t, i));
+        if ((st = run_step_device(plan, false)) != USFFT_OK) return st;
+        if ((st = read_cg_stats(plan, plan->M)) != USFFT_OK) return st;
+        std::vector<uint32_t> bits;
+        if ((st = read_bitmap(plan, bits)) != USFFT_OK) return st;
+        std::vector<int8_t> I;
+        int64_t nI = 0;
+        for (int64_t a = 0; a < nJ; ++a)
+            if (bits[(size_t)a >> 5] >> (a & 31) & 1u) {
+                I.insert(I.end(), J.begin() + a * t, J.begin() + (a + 1) * t);
+                ++nI;
+            }
+        plan->Ipre.swap(I);
+        plan->nIpre = nI;
+        samples += plan->M * (int64_t)plan->specs.size();
+    }
+    CK(cudaEventRecord(plan->ev1, plan->stream));
+    if ((st = wait_stream(plan)) != USFFT_OK) return st;
+    plan->t = t;
+    plan->replay_valid = true;
+    take_snapshot(plan);
+    if (info) {
+        memset(info, 0, sizeof *info);
+        info->t = t;
+        info->M = plan->last_coupled ? plan->M : 0;
+        info->n_candidates = plan->last_coupled ? plan->nJ : K;
+        info->n_detected = plan->nIpre;
+        info->n_1d = (int64_t)plan->I1d[(size_t)t].size();
+        info->samples = samples;
+        info->cg_iters_total = plan->cg_iters_total;
+        info->cg_iters_max = plan->cg_iters_max;
+        info->kernel_launches = plan->launches;
+        info->theta = plan->theta;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, plan->ev0, plan->ev1);
+        info->ms_device = ms;
+        info->ms_host_plan = ms_host;
+    }
+    return USFFT_OK;
+}
+
+usfft_status usfft_replay(usfft_plan_t* plan, int sync, int32_t* launches) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (plan->t < 1 || !plan->replay_valid) return fail(plan, USFFT_ESTATE, "no increment to replay");
+    plan->launches = 0;
+    usfft_status st = run_step_device(plan, false);
+    if (st != USFFT_OK) return st;
+    if (launches) *launches = plan->launches;
+    if (sync) return wait_stream(plan);
+    return USFFT_OK;
+}
+
+usfft_status usfft_rewind(usfft_plan_t* plan, int t) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (t < 0 || t > plan->t || (size_t)t >= plan->hist.size()) return fail(plan, USFFT_EINVAL, "t out of range");
+    const Snapshot& s = plan->hist[(size_t)t];
+    plan->t = s.t;
+    plan->Ipre = s.Ipre;
+    plan->nIpre = s.nIpre;
+    plan->I1d = s.I1d;
+    plan->theta = s.theta;
+    plan->A = s.A;
+    plan->theta_set = s.theta_set;
+    plan->hist.resize((size_t)t + 1);
+    plan->replay_valid = false;
+    return USFFT_OK;
+}
+
+usfft_status usfft_get_set(const usfft_plan_t* plan, int8_t* freqs, int64_t n_capacity, int64_t* n, int32_t* t) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (n) *n = plan->nIpre;
+    if (t) *t = plan->t;
+    if (freqs) {
+        if (n_capacity < plan->nIpre) return fail(const_cast<usfft_plan_t*>(plan), USFFT_EINVAL, "freqs too small");
+        memcpy(freqs, plan->Ipre.data(), plan->Ipre.size());
+    }
+    return USFFT_OK;
+}
+
+usfft_status usfft_get_lattice(const usfft_plan_t* plan, int64_t* z, int64_t* M, int32_t* t) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    const int tt = plan->last_coupled ? plan->last_t : 1;
+    if (t) *t = tt;
+    if (M) *M = plan->last_coupled ? plan->M : plan->K;
+    if (z) for (int j = 0; j < tt; ++j) z[j] = plan->last_coupled ? plan->z[(size_t)j] : 1;
+    return USFFT_OK;
+}
+
+usfft_status usfft_get_candidates(const usfft_plan_t* plan, int8_t* J, int64_t* n, int64_t* m) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (n) *n = plan->nJ;
+    if (J) memcpy(J, plan->J.data(), plan->J.size());
+    if (m) for (int64_t k = 0; k < plan->nJ; ++k) m[k] = plan->m[(size_t)k];
+    return USFFT_OK;
+}
+
+usfft_status usfft_get_samples(const usfft_plan_t* plan_c, double* U, int64_t* M, int64_t* G) {
+    usfft_plan_t* plan = const_cast<usfft_plan_t*>(plan_c);
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (M) *M = plan->M;
+    if (G) *G = plan->G;
+    if (U && plan->M > 0) {
+        CK(cudaMemcpyAsync(U, plan->U.p, sizeof(double) * (size_t)plan->M * plan->G, cudaMemcpyDeviceToHost,
+                           plan->stream));
+        return wait_stream(plan);
+    }
+    return USFFT_OK;
+}
+
+usfft_status usfft_get_coefficients(const usfft_plan_t* plan_c, double* C, int64_t* G, int64_t* n) {
+    usfft_plan_t* plan = const_cast<usfft_plan_t*>(plan_c);
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (G) *G = plan->G;
+    if (n) *n = plan->nJ;
+    if (C && plan->nJ > 0) {
+        CK(cudaMemcpyAsync(C, plan->C.p, sizeof(double2) * (size_t)plan->nJ * plan->G, cudaMemcpyDeviceToHost,
+                           plan->stream));
+        return wait_stream(plan);
+    }
+    return USFFT_OK;
+}
+
+usfft_status usfft_get_selection(const usfft_plan_t* plan_c, uint32_t* bitmap, int64_t* n) {
+    usfft_plan_t* plan = const_cast<usfft_plan_t*>(plan_c);
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (n) *n = plan->nJ;
+    if (bitmap && plan->nJ > 0) {
+        CK(cudaMemcpyAsync(bitmap, plan->bitmap.p, sizeof(uint32_t) * (size_t)((plan->nJ + 31) / 32),
+                           cudaMemcpyDeviceToHost, plan->stream));
+        return wait_stream(plan);
+    }
+    return USFFT_OK;
+}
+
+usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, double* coefs, int coefs_on_device) {
+    (void)freqs;
+    (void)coefs;
+    (void)coefs_on_device;
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (n) *n = plan->nIpre;
+    return fail(plan, USFFT_ESTATE, "usfft_reconstruct is not available in this version");
+}
+
+usfft_status usfft_search_lattice(const int8_t* J, int64_t n, int t, uint64_t seed, int trials, int max_sizes,
+                                  int64_t* z, int64_t* M) {
+    if (t < 1 || n < 0 || (n > 0 && !J) || !z || !M || trials < 1 || max_sizes < 1)
+        return fail(nullptr, USFFT_EINVAL, "usfft_search_lattice: invalid argument");
+    std::vector<int64_t> zz;
+    int64_t mm = 0;
+    if (!lattice_search(J, n, t, seed, trials, max_sizes, zz, mm))
+        return fail(nullptr, USFFT_ELATTICE, "no reconstructing rank-1 lattice found");
+    for (int j = 0; j < t; ++j) z[j] = zz[(size_t)j];
+    *M = mm;
+    return USFFT_OK;
+}
+
+uint64_t usfft_draw_key(uint64_t seed, const uint64_t* fields, int nfields) {
+    return rng_key(seed, fields, nfields);
+}
+
+double usfft_draw_uniform(uint64_t seed, const uint64_t* fields, int nfields) {
+    return rng_uniform(seed, fields, nfields);
+}
+
+void usfft_destroy(usfft_plan_t* plan) {
+    if (!plan) return;
+    cudaStreamSynchronize(plan->stream);
+    Buf* bufs[] = {&plan->psi, &plan->U, &plan->C, &plan->bitmap, &plan->twid, &plan->goff, &plan->gk, &plan->gm2,
+                   &plan->fftscr, &plan->cgscr, &plan->iters, &plan->failc, &plan->scal, &plan->tpf, &plan->tpc,
+                   &plan->tpaux};
+    for (Buf* b : bufs) buf_free(plan, *b);
+    if (plan->pinned) cudaFreeHost(plan->pinned);
+    if (plan->ev0) cudaEventDestroy(plan->ev0);
+    if (plan->ev1) cudaEventDestroy(plan->ev1);
+    if (plan->evs) cudaEventDestroy(plan->evs);
+    delete plan;
+}
+
+}  // extern "C"

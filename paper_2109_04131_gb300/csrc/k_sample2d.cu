@@ -1,0 +1,489 @@
+// Black-box sampler, part 2: the 2-D FE solve at every lattice node (Eq. (1.1) on the
+// unit square; the paper's FE black box, Sec. 2.1), fused with the coefficient assembly.
+//
+// Discretisation (the same reading as the oracle): n*n interior nodes, h = 1/(n+1), each
+// square split along its "/" diagonal, P1 elements, element coefficient a_T at the
+// centroid, f constant (load h^2 f per node).  On right isosceles triangles the P1
+// coupling across the hypotenuse vanishes, so the stiffness matrix is the 5-point
+// operator whose off-diagonal entry on an axis-parallel edge is -w_e,
+// w_e = (a_T1 + a_T2)/2 over the two triangles sharing the edge, and whose diagonal is
+// the sum of the four edge weights.  The matrix is never stored: one CTA assembles the
+// edge weights of its system in shared memory (one pattern for all systems).
+//
+// Solver: conjugate gradients on the symmetrically Jacobi-scaled system
+//   (D^-1/2 K D^-1/2) x~ = D^-1/2 b,  x = D^-1/2 x~,
+// which produces the iterates of Jacobi-preconditioned CG with fewer fp64 operations
+// per node and iteration (unit diagonal, z = r).  Stopping: ||r~|| <= tol ||b~||.
+//   FP64:  the whole CG in fp64.
+//   MIXED: fp32 CG inner solves on the scaled operator and fp64 iterative refinement:
+//          r~ = b~ - K~ x~ is formed in fp64 with the fp64 edge weights, the correction
+//          solves K~ d = r~ / ||r~|| in fp32, x~ += ||r~|| d in fp64.
+// One CTA owns one system at a time (persistent grid); node g = tid + k*T, k < NPT.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "usfft_internal.h"
+
+namespace usfft {
+
+__device__ __forceinline__ double node_sin2(const NodeSpec& ns, int j, int64_t i) {
+    int64_t zj = ns.z[j];
+    if (zj >= 0) {
+        int64_t nn = (i * zj) % ns.M;
+        return sinpi(2.0 * (double)nn / (double)ns.M);
+    }
+    return sinpi(2.0 * ns.tail[j]);
+}
+
+struct Pcg2dArgs {
+    NodeSpec ns;
+    int n, coef_model, max_iters;
+    double rhs;            // h^2 f
+    double tol;            // relative residual target (fp64 / refinement)
+    double tol_inner;      // relative residual target of an fp32 inner solve
+    const double* psi;     // [d][2(n+1)^2]
+    int64_t i0, count;
+    double* U;             // [count][n*n]
+    int* iters_out;
+    unsigned int* fail_count;
+    double* scratch;       // MIXED: per CTA 2 n (n+1) fp64 scaled weights
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum; `buf` holds 33 doubles; the result is returned to every thread.
+__device__ __forceinline__ double block_sum(double v, double* buf) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) buf[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double w = lane < nw ? buf[lane] : 0.0;
+        w = warp_sum(w);
+        if (lane == 0) buf[32] = w;
+    }
+    __syncthreads();
+    return buf[32];
+}
+
+// Shared-memory layout (doubles): ph[(n+2)^2] | wx[n(n+1)] | wy[(n+1)n] | sj[d] | red[2*33]
+// wx[qq(n+1)+P]: edge (P,qq+1)-(P+1,qq+1) (global node coords), P = 0..n
+// wy[Q n + pp]:  edge (pp+1,Q)-(pp+1,Q+1),                       Q = 0..n
+__device__ void assemble_scaled(const Pcg2dArgs& a, int64_t i, double* ph, double* wx, double* wy, double* sj) {
+    const int n = a.n, d = a.ns.d;
+    const int n1 = n + 1, W = n + 2;
+    const int sq = n1 * n1;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) sj[j] = node_sin2(a.ns, j, i);
+    __syncthreads();
+    const bool logn = a.coef_model == USFFT_COEF_LOGNORMAL_SIN;
+    // phase 1: lower-triangle coefficients of every square into ph (temporary)
+    for (int e = threadIdx.x; e < sq; e += blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < d; ++j) acc = fma(__ldg(a.psi + (size_t)j * 2 * sq + e), sj[j], acc);
+        ph[e] = logn ? exp(acc) : 1.0 + acc;
+    }
+    __syncthreads();
+    // phase 2: upper-triangle coefficient of square (P,Q) closes the horizontal edge above
+    // it and the vertical edge on its left
+    for (int e = threadIdx.x; e < sq; e += blockDim.x) {
+        const int P = e % n1, Q = e / n1;
+        double acc = 0.0;
+        for (int j = 0; j < d; ++j) acc = fma(__ldg(a.psi + (size_t)j * 2 * sq + sq + e), sj[j], acc);
+        const double au = logn ? exp(acc) : 1.0 + acc;
+        if (Q < n) wx[Q * n1 + P] = 0.5 * (ph[(Q + 1) * n1 + P] + au);
+        if (P >= 1) wy[Q * n + (P - 1)] = 0.5 * (au + ph[Q * n1 + (P - 1)]);
+    }
+    __syncthreads();
+    // D^-1/2 into the halo array (zero on the boundary), then scale every edge
+    for (int e = threadIdx.x; e < W * W; e += blockDim.x) ph[e] = 0.0;
+    __syncthreads();
+    for (int g = threadIdx.x; g < n * n; g += blockDim.x) {
+        const int pp = g % n, qq = g / n;
+        const double dg = wx[qq * n1 + pp] + wx[qq * n1 + pp + 1] + wy[qq * n + pp] + wy[(qq + 1) * n + pp];
+        ph[(qq + 1) * W + pp + 1] = 1.0 / sqrt(dg);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n1; e += blockDim.x) {
+        const int qq = e / n1, P = e % n1;          // horizontal: (P,qq+1)-(P+1,qq+1)
+        wx[e] *= ph[(qq + 1) * W + P] * ph[(qq + 1) * W + P + 1];
+    }
+    for (int e = threadIdx.x; e < n1 * n; e += blockDim.x) {
+        const int Q = e / n, pp = e % n;            // vertical: (pp+1,Q)-(pp+1,Q+1)
+        wy[e] *= ph[Q * W + pp + 1] * ph[(Q + 1) * W + pp + 1];
+    }
+    __syncthreads();
+}
+
+// y = K~ v at node (pp,qq) from a halo array vh (unit diagonal)
+template <typename T, typename WT>
+__device__ __forceinline__ T apply_scaled(const T* vh, const WT* wx, const WT* wy, int n, int pp, int qq) {
+    const int n1 = n + 1, W = n + 2;
+    const int h = (qq + 1) * W + pp + 1;
+    T acc = (T)wx[qq * n1 + pp] * vh[h - 1];
+    acc = fma((T)wx[qq * n1 + pp + 1], vh[h + 1], acc);
+    acc = fma((T)wy[qq * n + pp], vh[h - W], acc);
+    acc = fma((T)wy[(qq + 1) * n + pp], vh[h + W], acc);
+    return vh[h] - acc;
+}
+
+template <int NPT>
+__global__ void __launch_bounds__(1024) pcg2d_fp64_kernel(const __grid_constant__ Pcg2dArgs a) {
+    extern __shared__ double sm[];
+    const int n = a.n, G = n * n, W = n + 2, n1 = n + 1;
+    double* ph = sm;
+    double* wx = ph + W * W;
+    double* wy = wx + n * n1;
+    double* sj = wy + n1 * n;
+    double* red = sj + a.ns.d;
+    const int T = blockDim.x, tid = threadIdx.x;
+
+    for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
+        const int64_t i = a.i0 + sys;
+        assemble_scaled(a, i, ph, wx, wy, sj);
+        // D^-1/2 is parked in the output row until the solution is scaled back
+        double* out = a.U + (size_t)sys * G;
+        double x[NPT], r[NPT], p[NPT], q[NPT];
+        double rr_l = 0.0;
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int g = tid + k * T;
+            if (g < G) {
+                const double dg = ph[((g / n) + 1) * W + (g % n) + 1];
+                out[g] = dg;
+                x[k] = 0.0;
+                r[k] = a.rhs * dg;
+                p[k] = r[k];
+                rr_l = fma(r[k], r[k], rr_l);
+            } else {
+                x[k] = r[k] = p[k] = 0.0;
+            }
+        }
+        __syncthreads();                     // every D^-1/2 read before ph is reused
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int g = tid + k * T;
+            if (g < G) ph[((g / n) + 1) * W + (g % n) + 1] = p[k];
+        }
+        double rr = block_sum(rr_l, red);
+        const double stop = a.tol * a.tol * rr;
+        int it = 0;
+        while (rr > stop && it < a.max_iters) {
+            double pq_l = 0.0;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int g = tid + k * T;
+                q[k] = 0.0;
+                if (g < G) {
+                    q[k] = apply_scaled<double, double>(ph, wx, wy, n, g % n, g / n);
+                    pq_l = fma(p[k], q[k], pq_l);
+                }
+            }
+            const double pq = block_sum(pq_l, red);
+            const double alpha = rr / pq;
+            double rn_l = 0.0;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                x[k] = fma(alpha, p[k], x[k]);
+                r[k] = fma(-alpha, q[k], r[k]);
+                rn_l = fma(r[k], r[k], rn_l);
+            }
+            const double rn = block_sum(rn_l, red + 33);
+            const double beta = rn / rr;
+            rr = rn;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int g = tid + k * T;
+                p[k] = fma(beta, p[k], r[k]);
+                if (g < G) ph[((g / n) + 1) * W + (g % n) + 1] = p[k];
+            }
+            __syncthreads();
+            ++it;
+        }
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int g = tid + k * T;
+            if (g < G) out[g] = x[k] * out[g];
+        }
+        if (tid == 0) {
+            if (a.iters_out) a.iters_out[sys] = it;
+            if (rr > stop && a.fail_count) atomicAdd(a.fail_count, 1u);
+        }
+        __syncthreads();
+    }
+}
+
+// MIXED layout (bytes, inside the same dynamic allocation as the fp64 assembly arrays):
+//   [0, 8 W^2)            fp64 halo xh (residual operator input)  -- aliases ph of assembly
+//   [8 W^2, +4 n(n+1))    fp32 wx32                              -- aliases wx of assembly
+//   [.., +4 n(n+1))       fp32 wy32
+//   [.., +4 W^2)          fp32 halo ph32
+//   sj and red as in the fp64 layout (after wy of the assembly layout)
+template <int NPT>
+__global__ void __launch_bounds__(1024) pcg2d_mixed_kernel(const __grid_constant__ Pcg2dArgs a) {
+    extern __shared__ double sm[];
+    const int n = a.n, G = n * n, W = n + 2, n1 = n + 1;
+    double* ph = sm;
+    double* wx = ph + W * W;
+    double* wy = wx + n * n1;
+    double* sj = wy + n1 * n;
+    double* red = sj + a.ns.d;
+    double* xh = sm;                                            // fp64 halo
+    float* wx32 = reinterpret_cast<float*>(wx);
+    float* wy32 = wx32 + n * n1;
+    float* ph32 = wy32 + n1 * n;
+    const int T = blockDim.x, tid = threadIdx.x;
+    double* w64x = a.scratch + (size_t)blockIdx.x * 2 * n * n1;
+    double* w64y = w64x + n * n1;
+
+    for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
+        const int64_t i = a.i0 + sys;
+        assemble_scaled(a, i, ph, wx, wy, sj);
+        double* out = a.U + (size_t)sys * G;     // holds D^-1/2 until the end
+        double x[NPT], bt[NPT];
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int g = tid + k * T;
+            const double dg = (g < G) ? ph[((g / n) + 1) * W + (g % n) + 1] : 0.0;
+            if (g < G) out[g] = dg;
+            bt[k] = a.rhs * dg;
+            x[k] = 0.0;
+        }
+        // fp64 scaled weights to this CTA's scratch slot, fp32 copies to shared memory
+        for (int e = tid; e < n * n1; e += T) {
+            w64x[e] = wx[e];
+            w64y[e] = wy[e];
+        }
+        __syncthreads();
+        for (int e = tid; e < n * n1; e += T) {
+            wx32[e] = (float)__ldcg(w64x + e);
+            wy32[e] = (float)__ldcg(w64y + e);
+        }
+        for (int e = tid; e < W * W; e += T) {
+            ph32[e] = 0.0f;
+            xh[e] = 0.0;
+        }
+        __syncthreads();
+        double rr0_l = 0.0;
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) rr0_l = fma(bt[k], bt[k], rr0_l);
+        const double rr0 = block_sum(rr0_l, red);
+        const double stop = a.tol * a.tol * rr0;
+        double rr64 = rr0;
+        double r64[NPT];
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) r64[k] = bt[k];
+        int total = 0, outer = 0;
+        while (rr64 > stop && outer < 16) {
+            // ---- fp32 inner solve of K~ d = r64 / ||r64|| ----
+            const double nr = sqrt(rr64);
+            const float inv = (float)(1.0 / nr);
+            float d32[NPT], r32[NPT], p32[NPT], q32[NPT];
+            float rr_l = 0.0f;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int g = tid + k * T;
+                d32[k] = 0.0f;
+                r32[k] = (float)r64[k] * inv;
+                p32[k] = r32[k];
+                rr_l = fmaf(r32[k], r32[k], rr_l);
+                if (g < G) ph32[((g / n) + 1) * W + (g % n) + 1] = p32[k];
+            }
+            double rr = block_sum((double)rr_l, red);
+            const double istop = a.tol_inner * a.tol_inner * rr;
+            int it = 0;
+            while (rr > istop && it < a.max_iters) {
+                float pq_l = 0.0f;
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    const int g = tid + k * T;
+                    q32[k] = 0.0f;
+                    if (g < G) {
+                        q32[k] = apply_scaled<float, float>(ph32, wx32, wy32, n, g % n, g / n);
+                        pq_l = fmaf(p32[k], q32[k], pq_l);
+                    }
+                }
+                const double pq = block_sum((double)pq_l, red);
+                const float alpha = (float)(rr / pq);
+                float rn_l = 0.0f;
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    d32[k] = fmaf(alpha, p32[k], d32[k]);
+                    r32[k] = fmaf(-alpha, q32[k], r32[k]);
+                    rn_l = fmaf(r32[k], r32[k], rn_l);
+                }
+                const double rn = block_sum((double)rn_l, red + 33);
+                const float beta = (float)(rn / rr);
+                rr = rn;
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    const int g = tid + k * T;
+                    p32[k] = fmaf(beta, p32[k], r32[k]);
+                    if (g < G) ph32[((g / n) + 1) * W + (g % n) + 1] = p32[k];
+                }
+                __syncthreads();
+                ++it;
+            }
+            total += it;
+            // ---- fp64 update and residual r64 = b~ - K~ x ----
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int g = tid + k * T;
+                x[k] = fma(nr, (double)d32[k], x[k]);
+                if (g < G) xh[((g / n) + 1) * W + (g % n) + 1] = x[k];
+            }
+            __syncthreads();
+            double rl = 0.0;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int g = tid + k * T;
+                r64[k] = 0.0;
+                if (g < G) {
+                    const int pp = g % n, qq = g / n, h = (qq + 1) * W + pp + 1;
+                    double acc = __ldcg(w64x + qq * n1 + pp) * xh[h - 1];
+                    acc = fma(__ldcg(w64x + qq * n1 + pp + 1), xh[h + 1], acc);
+                    acc = fma(__ldcg(w64y + qq * n + pp), xh[h - W], acc);
+                    acc = fma(__ldcg(w64y + (qq + 1) * n + pp), xh[h + W], acc);
+                    r64[k] = bt[k] - (xh[h] - acc);
+                    rl = fma(r64[k], r64[k], rl);
+                }
+            }
+            rr64 = block_sum(rl, red + 33);
+            ++outer;
+        }
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int g = tid + k * T;
+            if (g < G) out[g] = x[k] * out[g];
+        }
+        if (tid == 0) {
+            if (a.iters_out) a.iters_out[sys] = total;
+            if (rr64 > stop && a.fail_count) atomicAdd(a.fail_count, 1u);
+        }
+        __syncthreads();
+    }
+}
+
+// smallest nodes-per-thread count that fits the system into one CTA of <= 1024 threads
+static int pick_npt(int G) {
+    int npt = 1;
+    while ((G + npt - 1) / npt > 1024) npt *= 2;
+    return npt;
+}
+
+static size_t smem_bytes(int n, int d) {
+    const size_t W = (size_t)n + 2;
+    return sizeof(double) * (W * W + 2 * (size_t)n * (n + 1) + (size_t)d + 66);
+}
+
+template <int NPT>
+static int resident_blocks(int precision, int threads, size_t smem) {
+    int per_sm = 0;
+    cudaError_t e;
+    if (precision == USFFT_MIXED) {
+        e = cudaFuncSetAttribute(pcg2d_mixed_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg2d_mixed_kernel<NPT>, threads, smem);
+    } else {
+        e = cudaFuncSetAttribute(pcg2d_fp64_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg2d_fp64_kernel<NPT>, threads, smem);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm < 1 ? 1 : per_sm;
+}
+
+// persistent grid: one wave of resident CTAs on every SM
+int sample_2d_default_blocks(int n, int precision) {
+    const int G = n * n;
+    const int npt = pick_npt(G);
+    const int threads = ((G + npt - 1) / npt + 31) / 32 * 32;
+    const size_t smem = smem_bytes(n, USFFT_MAX_D);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    int per_sm;
+    switch (npt) {
+        case 1: per_sm = resident_blocks<1>(precision, threads, smem); break;
+        case 2: per_sm = resident_blocks<2>(precision, threads, smem); break;
+        case 4: per_sm = resident_blocks<4>(precision, threads, smem); break;
+        case 8: per_sm = resident_blocks<8>(precision, threads, smem); break;
+        default: per_sm = resident_blocks<16>(precision, threads, smem); break;
+    }
+    return sms * per_sm;
+}
+
+size_t sample_2d_scratch_bytes(int n, int precision, int blocks) {
+    if (precision != USFFT_MIXED) return 0;
+    return sizeof(double) * 2 * (size_t)n * (n + 1) * (size_t)blocks;
+}
+
+template <int NPT>
+static cudaError_t launch_npt(const Pcg2dArgs& a, int precision, int blocks, int threads, size_t smem,
+                              cudaStream_t s) {
+    cudaError_t e;
+    if (precision == USFFT_MIXED) {
+        e = cudaFuncSetAttribute(pcg2d_mixed_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        pcg2d_mixed_kernel<NPT><<<blocks, threads, smem, s>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(pcg2d_fp64_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        pcg2d_fp64_kernel<NPT><<<blocks, threads, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f, const double* psi,
+                             const CgConfig& cg, int64_t i0, int64_t count, double* U, int* iters_out,
+                             unsigned int* fail_count, double* scratch, size_t scratch_bytes,
+                             cudaStream_t s, int* launches) {
+    if (count <= 0) return cudaSuccess;
+    Pcg2dArgs a;
+    a.ns = ns;
+    a.n = n;
+    a.coef_model = coef_model;
+    a.max_iters = cg.max_iters;
+    const double h = 1.0 / (double)(n + 1);
+    a.rhs = h * h * f;
+    a.tol = cg.tol;
+    a.tol_inner = 1e-4;
+    a.psi = psi;
+    a.i0 = i0;
+    a.count = count;
+    a.U = U;
+    a.iters_out = iters_out;
+    a.fail_count = fail_count;
+    a.scratch = scratch;
+    const int G = n * n;
+    const int npt = pick_npt(G);
+    int threads = ((G + npt - 1) / npt + 31) / 32 * 32;
+    if (threads > 1024) return cudaErrorInvalidValue;
+    int blocks = cg.blocks > 0 ? cg.blocks : sample_2d_default_blocks(n, cg.precision);
+    if (blocks > count) blocks = (int)count;
+    if (cg.precision == USFFT_MIXED &&
+        scratch_bytes < sample_2d_scratch_bytes(n, USFFT_MIXED, blocks))
+        return cudaErrorInvalidValue;
+    const size_t smem = smem_bytes(n, ns.d);
+    cudaError_t e;
+    switch (npt) {
+        case 1: e = launch_npt<1>(a, cg.precision, blocks, threads, smem, s); break;
+        case 2: e = launch_npt<2>(a, cg.precision, blocks, threads, smem, s); break;
+        case 4: e = launch_npt<4>(a, cg.precision, blocks, threads, smem, s); break;
+        case 8: e = launch_npt<8>(a, cg.precision, blocks, threads, smem, s); break;
+        default: e = launch_npt<16>(a, cg.precision, blocks, threads, smem, s); break;
+    }
+    if (launches) ++*launches;
+    return e;
+}
+
+}  // namespace usfft

@@ -1,0 +1,159 @@
+// Per-node thresholding and union of the detected sets (Algorithm 1, steps 1/2a and 2d-2e).
+//
+// Node g keeps the indices of the at most s~ largest |C[g][k]| that are >= theta; the
+// union over nodes (and detection iterations) is an OR into one bitmap over the
+// candidates.  Readings shared with the oracle: |c|^2 = re*re + im*im with every
+// operation rounded separately (no FMA), compared with theta*theta; equal magnitudes
+// are ordered by the smaller candidate index.
+//
+// One CTA per node.  If at most s~ candidates pass the threshold they are all taken.
+// Otherwise the s~-th largest magnitude is found exactly by an MSB-first radix select
+// over the bit patterns of |c|^2 (non-negative doubles order like their bits), eight
+// 8-bit digits with a 256-bin shared histogram; then every key above it is taken and the
+// remaining quota of keys equal to it goes to the smallest indices (warp ballots and
+// prefix counts over index-ordered chunks).
+#include <cuda_runtime.h>
+
+#include "usfft_internal.h"
+
+namespace usfft {
+
+static const int kSelThreads = 256;
+
+__device__ __forceinline__ double mag2_rn(double2 c) {
+    return __dadd_rn(__dmul_rn(c.x, c.x), __dmul_rn(c.y, c.y));
+}
+
+__device__ __forceinline__ void set_bit(uint32_t* bitmap, int64_t k) {
+    atomicOr(bitmap + (k >> 5), 1u << (k & 31));
+}
+
+__global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2* C, int G, int64_t nJ,
+                                                                     double theta2, int s_tilde, uint32_t* bitmap) {
+    __shared__ unsigned int hist[256];
+    __shared__ unsigned long long sh_prefix;
+    __shared__ unsigned int sh_want;
+    __shared__ unsigned int warp_cnt[kSelThreads / 32];
+    __shared__ unsigned int sh_total;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = blockDim.x >> 5;
+
+    for (int g = blockIdx.x; g < G; g += gridDim.x) {
+        const double2* row = C + (int64_t)g * nJ;
+        // count the candidates above the threshold
+        unsigned int cnt = 0;
+        for (int64_t k = tid; k < nJ; k += blockDim.x) cnt += mag2_rn(row[k]) >= theta2 ? 1u : 0u;
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (lane == 0) warp_cnt[warp] = cnt;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned int t = 0;
+            for (int w = 0; w < nw; ++w) t += warp_cnt[w];
+            sh_total = t;
+        }
+        __syncthreads();
+        const unsigned int total = sh_total;
+        if (total <= (unsigned int)s_tilde) {
+            for (int64_t k = tid; k < nJ; k += blockDim.x)
+                if (mag2_rn(row[k]) >= theta2) set_bit(bitmap, k);
+            __syncthreads();
+            continue;
+        }
+        // exact s~-th largest key among the eligible ones
+        if (tid == 0) {
+            sh_prefix = 0ull;
+            sh_want = (unsigned int)s_tilde;
+        }
+        __syncthreads();
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            hist[tid] = 0u;     // blockDim.x == 256
+            __syncthreads();
+            const unsigned long long prefix = sh_prefix;
+            const unsigned long long himask = (shift == 56) ? 0ull : ~((1ull << (shift + 8)) - 1ull);
+            for (int64_t k = tid; k < nJ; k += blockDim.x) {
+                const double m2 = mag2_rn(row[k]);
+                if (!(m2 >= theta2)) continue;
+                const unsigned long long key = (unsigned long long)__double_as_longlong(m2);
+                if ((key & himask) == prefix) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                unsigned int want = sh_want, cum = 0;
+                int dsel = 0;
+                for (int dg = 255; dg >= 0; --dg) {
+                    if (cum + hist[dg] >= want) {
+                        dsel = dg;
+                        break;
+                    }
+                    cum += hist[dg];
+                }
+                sh_want = want - cum;
+                sh_prefix = prefix | ((unsigned long long)dsel << shift);
+            }
+            __syncthreads();
+        }
+        const unsigned long long tau = sh_prefix;
+        const unsigned int take_eq = sh_want;        // how many keys == tau to take
+        for (int64_t k = tid; k < nJ; k += blockDim.x) {
+            const double m2 = mag2_rn(row[k]);
+            if (m2 >= theta2 && (unsigned long long)__double_as_longlong(m2) > tau) set_bit(bitmap, k);
+        }
+        // keys equal to tau: the first take_eq in index order
+        unsigned int taken = 0;
+        for (int64_t base = 0; base < nJ && taken < take_eq; base += blockDim.x) {
+            const int64_t k = base + tid;
+            bool eq = false;
+            if (k < nJ) {
+                const double m2 = mag2_rn(row[k]);
+                eq = (m2 >= theta2) && ((unsigned long long)__double_as_longlong(m2) == tau);
+            }
+            const unsigned int ball = __ballot_sync(0xffffffffu, eq);
+            if (lane == 0) warp_cnt[warp] = __popc(ball);
+            __syncthreads();
+            unsigned int before = taken;
+            for (int w = 0; w < warp; ++w) before += warp_cnt[w];
+            before += __popc(ball & ((1u << lane) - 1u));
+            if (eq && before < take_eq) set_bit(bitmap, k);
+            unsigned int chunk = 0;
+            for (int w = 0; w < nw; ++w) chunk += warp_cnt[w];
+            __syncthreads();
+            taken += chunk;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_select_union(const double2* C, int G, int64_t nJ, double theta, int s_tilde, uint32_t* bitmap,
+                                cudaStream_t s, int* launches) {
+    if (G <= 0 || nJ <= 0) return cudaSuccess;
+    int blocks = G < 152 * 8 ? G : 152 * 8;
+    select_union_kernel<<<blocks, kSelThreads, 0, s>>>(C, G, nJ, theta * theta, s_tilde, bitmap);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+__global__ void absmax_column_kernel(const double2* C, int G, int64_t nJ, int64_t col, double* out) {
+    __shared__ double red[32];
+    double m = 0.0;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        const double2 c = C[(int64_t)g * nJ + col];
+        m = fmax(m, hypot(c.x, c.y));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+        *out = t;
+    }
+}
+
+cudaError_t launch_absmax_column(const double2* C, int G, int64_t nJ, int64_t col, double* out, cudaStream_t s,
+                                 int* launches) {
+    absmax_column_kernel<<<1, 1024, 0, s>>>(C, G, nJ, col, out);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace usfft

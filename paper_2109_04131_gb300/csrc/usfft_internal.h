@@ -1,0 +1,106 @@
+// Internal declarations of the usFFT GB300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "usfft.h"
+
+#define USFFT_MAX_D 64
+
+// ---------------------------------------------------------------------------------
+// Host planner (host_plan.cpp)
+// ---------------------------------------------------------------------------------
+namespace usfft {
+
+// Counter-based SplitMix64 draws (Steele, Lea, Flood 2014): key(seed, f1, f2, ...)
+// folds one SplitMix64 step per field, h <- mix64((h ^ f) + golden gamma).
+enum Phase : uint64_t { PHASE_1D_TAIL = 1, PHASE_TAIL = 2, PHASE_LATTICE = 3 };
+uint64_t rng_key(uint64_t seed, const uint64_t* fields, int nfields);
+double rng_uniform(uint64_t seed, const uint64_t* fields, int nfields);                 // [0,1)
+int64_t rng_uniform_int(int64_t lo, int64_t hi, uint64_t seed, const uint64_t* fields, int nfields);
+
+bool is_smooth7(int64_t m);
+int64_t next_admissible(int64_t x);
+
+// Reconstructing rank-1 lattice search: J is [n][t] int8 row-major.  Returns false if
+// none is found within max_sizes sizes; z receives t entries.
+bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials, int max_sizes,
+                    std::vector<int64_t>& z, int64_t& M);
+
+// Candidate set J_t = I_prev x I_t within [-N,N]^t (lexicographic in the positions).
+void candidate_set(const int8_t* I_prev, int64_t n_prev, int t_prev, const std::vector<int>& I_t, int N,
+                   std::vector<int8_t>& J, int64_t& nJ);
+
+// ---------------------------------------------------------------------------------
+// Device-side descriptions passed to kernels by value
+// ---------------------------------------------------------------------------------
+struct NodeSpec {          // M sampling nodes: lattice coordinates and fixed tails
+    int64_t M;
+    int d;
+    int64_t z[USFFT_MAX_D];      // >= 0: lattice coordinate with multiplier z_j; -1: tail
+    double tail[USFFT_MAX_D];    // y'_j for tail coordinates
+};
+
+struct FftPlan {           // M = L1 * L2 (L2 == 1: single pass of length L1)
+    int64_t M;
+    int L1, L2;
+};
+
+// ---------------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files); all return cudaGetLastError()
+// ---------------------------------------------------------------------------------
+// psi[j][e] = c j^-mu psi_j(centroid_e), j < d, e < E (E = n+1 in 1-D, 2(n+1)^2 in 2-D)
+cudaError_t launch_psi_table(int kind, int n, int d, double scale, double decay, double* psi,
+                             cudaStream_t s);
+
+// 1-D: fused coefficient assembly + cyclic reduction; U[i][g], i < M, g < n
+cudaError_t launch_sample_1d(const NodeSpec& ns, int n, int coef_model, double f, const double* psi,
+                             int64_t i0, int64_t count, double* U, cudaStream_t s, int* launches);
+
+// 2-D: fused coefficient assembly + Jacobi-PCG (fp64) or fp32-PCG with fp64-residual
+// refinement (mixed); iters_out[i] receives the CG iterations of system i (may be NULL);
+// fail_count gets +1 for every system that hit max_iters.
+struct CgConfig {
+    int precision;
+    int max_iters;
+    double tol;
+    int blocks;            // 0 = auto
+};
+cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f, const double* psi,
+                             const CgConfig& cg, int64_t i0, int64_t count, double* U, int* iters_out,
+                             unsigned int* fail_count, double* scratch, size_t scratch_bytes,
+                             cudaStream_t s, int* launches);
+size_t sample_2d_scratch_bytes(int n, int precision, int blocks);
+int sample_2d_default_blocks(int n, int precision);
+
+// TRIGPOLY black box: U[i][g] = Re sum_s c_{g,s} exp(2 pi i h_{g,s} . y_i)
+cudaError_t launch_sample_trigpoly(const NodeSpec& ns, int G, int nterms, const int8_t* freqs,
+                                   const double* coefs, double* aux /* [G*nterms*3] */, double* U,
+                                   cudaStream_t s, int* launches);
+
+// FFT along the lattice axis with the gather at the DFT indices of the candidates:
+// C[g][k] = (1/M) sum_i U[i][g] exp(-2 pi i i m_k / M).
+struct GatherPlan {        // buckets of candidates by m mod L1 (CSR), entries (k, m div L1)
+    const int* offsets;    // [L1 + 1]
+    const int* k;          // [nJ]
+    const int* m2;         // [nJ]
+};
+FftPlan make_fft_plan(int64_t M);
+size_t fft_scratch_bytes(const FftPlan& p, int G);
+cudaError_t launch_twiddles(int64_t M, double2* W, cudaStream_t s, int* launches);
+cudaError_t launch_fft_gather(const FftPlan& p, int G, const double* U, const double2* W,
+                              const GatherPlan& gp, int64_t nJ, double2* scratch, double2* C,
+                              cudaStream_t s, int* launches);
+
+// Per-node selection of the <= s~ largest |C[g][k]| >= theta and the union (bitmap OR).
+cudaError_t launch_select_union(const double2* C, int G, int64_t nJ, double theta, int s_tilde,
+                                uint32_t* bitmap, cudaStream_t s, int* launches);
+// out = max_g |C[g][col]|
+cudaError_t launch_absmax_column(const double2* C, int G, int64_t nJ, int64_t col, double* out,
+                                 cudaStream_t s, int* launches);
+
+}  // namespace usfft

@@ -1,0 +1,197 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars: lattice (z, M), candidate lists, DFT indices and detected sets bit-exact;
+samples U and coefficients C within 1e-10 relative on the fp64 path and the mixed path,
+in the per-node norm max_k |C_gpu - C_orc| / max_k |C_orc| (the reading of "1e-10
+relative" that ignores noise-level coefficients)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.usfft import OracleRun
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2109_04131_gb300 import binding
+    binding.load_library()
+    return binding
+
+
+def node_rel(Cg, Co):
+    """max over nodes of max_k |Cg - Co| / max_k |Co|."""
+    den = np.max(np.abs(Co), axis=1)
+    den[den == 0] = 1.0
+    return float(np.max(np.max(np.abs(Cg - Co), axis=1) / den))
+
+
+def compare_increment(plan, run, ctx):
+    want = run.increment()
+    info = plan.increment()
+    got = plan.get_set()
+    assert info["t"] == run.t
+    assert got.shape == want.shape and np.array_equal(got, want), f"{ctx}: detected sets differ at t={run.t}"
+    z, M = plan.get_lattice()
+    last = run.records[-1]
+    assert M == last.M and np.array_equal(z, last.z), ctx
+    J, m = plan.get_candidates()
+    if last.coupled:
+        assert np.array_equal(J, run.J), ctx
+    assert np.array_equal(m, last.m), ctx
+    if last.U is not None:
+        U = plan.get_samples()
+        assert U.shape == last.U.shape
+        err = np.max(np.abs(U - last.U)) / np.max(np.abs(last.U))
+        assert err < TOL, f"{ctx}: samples rel err {err:.2e}"
+        C = plan.get_coefficients()
+        assert C.shape == last.C.shape
+        e = node_rel(C, last.C)
+        assert e < TOL, f"{ctx}: coefficient rel err {e:.2e}"
+    return info
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_1d_workload_full_run(B, seed):
+    w = W.c1(seed)
+    plan = B.Plan(w.problem, w.params)
+    run = OracleRun(w.problem, w.params, keep=True)
+    for t in range(1, w.problem.d + 1):
+        info = compare_increment(plan, run, f"c1 seed {seed}")
+        assert info["kernel_launches"] > 0
+    plan.close()
+
+
+@pytest.mark.parametrize("G,seed", [(1, 3), (12, 4), (37, 9)])
+def test_trigpoly_exact_recovery(B, G, seed):
+    d, N = 4, 5
+    prob = W.trigpoly(G=G, d=d, N=N, seed=seed, base_terms=5, node_terms=2, kmax=3, mag_lo=1e-4)
+    params = W.Params(N=N, s=40, s_local=40, delta=1e-9, delta_is_relative=False, r=1, seed=seed)
+    plan = B.Plan(prob, params)
+    run = OracleRun(prob, params, keep=True)
+    union = set()
+    for g in range(G):
+        for f, c in zip(prob.tp_freqs[g], prob.tp_coefs[g]):
+            if c != 0:
+                union.add(tuple(int(v) for v in f))
+    for t in range(1, d + 1):
+        compare_increment(plan, run, f"trigpoly G={G}")
+        got = {tuple(int(v) for v in row) for row in plan.get_set()}
+        assert got == {k[:t] for k in union}
+    # t = d: the coefficients are the polynomial's own
+    C = plan.get_coefficients()
+    J, _ = plan.get_candidates()
+    for g in range(G):
+        truth = {tuple(int(v) for v in f): c for f, c in zip(prob.tp_freqs[g], prob.tp_coefs[g]) if c != 0}
+        want = np.array([truth.get(tuple(int(v) for v in k), 0.0) for k in J])
+        assert np.max(np.abs(C[g] - want)) < 1e-13
+    plan.close()
+
+
+def test_trigpoly_two_pass_fft(B):
+    # full-grid support [-40,40]^2: |J| = 81^2 = 6561 > 4096 needs the two-pass FFT
+    prob = W.trigpoly_grid(G=3, d=2, K=40, seed=5)
+    params = W.Params(N=45, s=20000, s_local=20000, delta=1e-9, delta_is_relative=False, r=1, seed=3)
+    plan = B.Plan(prob, params)
+    run = OracleRun(prob, params, keep=True)
+    compare_increment(plan, run, "grid t=1")
+    info = compare_increment(plan, run, "grid t=2")
+    assert info["M"] > 4096 and info["n_candidates"] == 81 * 81
+    assert len(plan.get_set()) == 81 * 81
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED])
+def test_small_2d_matches_oracle(B, precision):
+    w = W.with_precision(W.small_2d(n=15, d=4, seed=2, N=6, s=30), precision)
+    plan = B.Plan(w.problem, w.params)
+    run = OracleRun(w.problem, w.params, keep=True)
+    for t in range(1, 4):
+        info = compare_increment(plan, run, f"2-D n=15 precision={precision}")
+        assert info["cg_iters_max"] > 0
+    plan.close()
+
+
+def test_2d_ragged_mesh_sizes(B):
+    # n = 9 (81 nodes: one partial warp) and n = 33 (1089 nodes: two nodes per thread, ragged)
+    for n in (9, 33):
+        w = W.small_2d(n=n, d=3, seed=5, N=4, s=20)
+        plan = B.Plan(w.problem, w.params)
+        run = OracleRun(w.problem, w.params, keep=True)
+        for t in range(1, 3):
+            compare_increment(plan, run, f"2-D n={n}")
+        plan.close()
+
+
+def test_c2_shape_first_increments(B):
+    # the 2-D workload at full mesh size (63x63 interior, d = 10): increment 1 in full,
+    # increment 2 in full (about 1000 oracle solves)
+    w = W.c2(1)
+    plan = B.Plan(w.problem, w.params)
+    run = OracleRun(w.problem, w.params, keep=True)
+    compare_increment(plan, run, "c2 t=1")
+    compare_increment(plan, run, "c2 t=2")
+    plan.close()
+
+
+def test_replay_and_rewind_reproduce_the_increment(B):
+    w = W.small_2d(n=15, d=4, seed=3, N=6, s=30)
+    plan = B.Plan(w.problem, w.params)
+    for _ in range(3):
+        plan.increment()
+    S = plan.get_set()
+    C = plan.get_coefficients()
+    sel = plan.get_selection()
+    n = plan.replay(sync=True)
+    assert n > 0
+    assert np.array_equal(plan.get_selection(), sel)
+    assert np.array_equal(plan.get_coefficients(), C)
+    plan.rewind(2)
+    plan.increment()
+    assert np.array_equal(plan.get_set(), S)
+    plan.close()
+
+
+def test_host_injected_failures(B):
+    # invalid coefficient (a_min <= 0), an HBM budget that is too small, and a CG iteration
+    # cap that cannot be met; all are reported as status codes, nothing faults
+    w = W.c1(1)
+    bad = W.Problem(kind=W.PDE_1D, n=31, d=4, coef_scale=2.0)
+    with pytest.raises(B.UsfftError) as e:
+        B.Plan(bad, w.params)
+    assert e.value.status == 1
+    import dataclasses
+    tiny = dataclasses.replace(w.params, hbm_budget_bytes=4096)
+    with pytest.raises(B.UsfftError) as e:
+        p = B.Plan(w.problem, tiny)
+        p.increment()
+    assert e.value.status == 2
+    w2 = W.small_2d(n=15, d=3, seed=1, N=4, s=10)
+    capped = dataclasses.replace(w2.params, max_cg_iters=3)
+    p = B.Plan(w2.problem, capped)
+    with pytest.raises(B.UsfftError) as e:
+        p.increment()
+    assert e.value.status == 4
+    p.close()
+    # the context is still usable afterwards
+    p = B.Plan(w.problem, w.params)
+    p.increment()
+    p.close()
+
+
+def test_increment_after_last_is_a_state_error(B):
+    prob = W.trigpoly(G=2, d=2, N=3, seed=1, base_terms=2, node_terms=1, kmax=2, mag_lo=1e-2)
+    params = W.Params(N=3, s=10, s_local=10, delta=1e-9, delta_is_relative=False, r=1, seed=1)
+    p = B.Plan(prob, params)
+    p.increment()
+    p.increment()
+    with pytest.raises(B.UsfftError) as e:
+        p.increment()
+    assert e.value.status == 7
+    p.close()

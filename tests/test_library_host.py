@@ -1,0 +1,115 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol include/usfft.h declares,
+its struct layouts match the binding, and its host planner (draws, lattice search) agrees
+bit for bit with the oracle.  No device work is started here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lattice, rng
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "usfft.h")
+
+
+@pytest.fixture(scope="module")
+def binding():
+    from paper_2109_04131_gb300 import binding as b
+    if not os.path.exists(b.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    b.load_library()
+    return b
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(usfft_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(binding):
+    lib = binding.load_library()
+    names = _declared_functions()
+    assert "usfft_plan" in names and "usfft_increment" in names and "usfft_reconstruct" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) <= set(binding.SIGNATURES)
+    assert lib.usfft_version().decode().startswith("usfft sm_103a")
+
+
+def test_struct_layouts_match_the_header(binding, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "usfft.h"
+#define P(T, f) printf(#T " " #f " %zu\\n", offsetof(T, f));
+int main(void) {
+  printf("usfft_problem size %zu\\n", sizeof(usfft_problem));
+  printf("usfft_params size %zu\\n", sizeof(usfft_params));
+  printf("usfft_increment_info size %zu\\n", sizeof(usfft_increment_info));
+  P(usfft_problem, tp_freqs) P(usfft_problem, tp_coefs) P(usfft_problem, coef_scale)
+  P(usfft_params, seed) P(usfft_params, hbm_budget_bytes) P(usfft_params, cg_tol) P(usfft_params, alloc_ctx)
+  P(usfft_increment_info, M) P(usfft_increment_info, kernel_launches) P(usfft_increment_info, ms_host_plan)
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    S = {"usfft_problem": binding.UsfftProblem, "usfft_params": binding.UsfftParams,
+         "usfft_increment_info": binding.UsfftIncrementInfo}
+    for (tname, field), val in got.items():
+        if field == "size":
+            assert ctypes.sizeof(S[tname]) == val, tname
+        else:
+            assert getattr(S[tname], field).offset == val, (tname, field)
+
+
+def test_draws_match_the_oracle(binding):
+    for seed in (0, 1, 42, 2**63 + 5):
+        for fields in ((1, 2, 3, 4), (3, 5, 97, 0, 2), (2,), ()):
+            assert binding.usfft_draw_key(seed, *fields) == rng.key(seed, *fields)
+            assert binding.usfft_draw_uniform(seed, *fields) == rng.uniform(seed, *fields)
+
+
+@pytest.mark.parametrize("seed", [1, 7, 123])
+def test_lattice_search_is_bit_exact_with_the_oracle(binding, seed):
+    r = np.random.default_rng(seed)
+    for t in (2, 3, 4):
+        prev = np.unique(r.integers(-5, 6, size=(int(r.integers(5, 80)), t - 1)), axis=0)
+        J = lattice.candidate_set(prev, np.arange(-4, 5), N=8)
+        z0, M0 = lattice.search(J, t, seed)
+        z1, M1 = binding.usfft_search_lattice(J, t, seed)
+        assert M1 == M0 and np.array_equal(z1, z0)
+
+
+def test_lattice_search_on_the_c1_increments(binding):
+    # the candidate sets the oracle builds for the 1-D workload (increments 2..4)
+    from oracle.usfft import OracleRun
+    w = W.c1(3)
+    run = OracleRun(w.problem, w.params)
+    run.increment()
+    for t in range(2, w.problem.d + 1):
+        run.increment()
+        z, M = binding.usfft_search_lattice(run.J, t, w.params.seed)
+        assert M == run.M and np.array_equal(z, run.z)
+
+
+def test_lattice_search_edge_cases(binding):
+    z, M = binding.usfft_search_lattice(np.zeros((0, 2), np.int8), 2, 1)
+    assert M == 0
+    z, M = binding.usfft_search_lattice(np.array([[3, -2]], np.int8), 2, 1)
+    assert M == 1
+    with pytest.raises(binding.UsfftError):
+        binding.usfft_search_lattice(np.zeros((4, 2), np.int8), 2, 1)   # duplicates never separate

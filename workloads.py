@@ -180,3 +180,26 @@ def trigpoly(G: int, d: int, N: int, seed: int, base_terms: int = 6, node_terms:
 
 def with_precision(w: Workload, precision: int) -> Workload:
     return replace(w, params=replace(w.params, precision=precision))
+
+
+def trigpoly_grid(G: int, d: int, K: int, seed: int, mag_lo: float = 1e-3) -> Problem:
+    """Real trigonometric polynomials whose support is the full grid [-K,K]^d (every node
+    shares it), with Hermitian log-uniform coefficients: a dense test black box whose
+    candidate sets are large enough to need the two-pass lattice FFT."""
+    rng = np.random.default_rng(seed)
+    axes = [np.arange(-K, K + 1)] * d
+    grid = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, d)
+    T = grid.shape[0]
+    freqs = np.broadcast_to(grid.astype(np.int8), (G, T, d)).copy()
+    coefs = np.zeros((G, T), dtype=np.complex128)
+    index = {tuple(k): n for n, k in enumerate(grid.tolist())}
+    for g in range(G):
+        for n, k in enumerate(grid.tolist()):
+            m = index[tuple(-v for v in k)]
+            if m < n:
+                coefs[g, n] = np.conj(coefs[g, m])
+                continue
+            mag = math.exp(rng.uniform(math.log(mag_lo), 0.0))
+            ph = 0.0 if m == n else rng.uniform(0.0, 2.0 * math.pi)
+            coefs[g, n] = mag * complex(math.cos(ph), math.sin(ph))
+    return Problem(kind=TRIGPOLY, n=0, d=d, tp_freqs=freqs, tp_coefs=coefs)
