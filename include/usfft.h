@@ -151,6 +151,13 @@ usfft_status usfft_replay(usfft_plan_t* plan, int sync, int32_t* launches);
  * detected set, so a later usfft_increment recomputes increment t+1 exactly. */
 usfft_status usfft_rewind(usfft_plan_t* plan, int t);
 
+/* Resume from a checkpoint: set the state after increment t (0 <= t < d) to the detected
+ * set I^(1..t) ([n][t] int8 rows, host) and the absolute threshold theta (> 0; ignored
+ * when t == 0).  The next usfft_increment runs increment t+1 from this state exactly as it
+ * would have after the increments 1..t (Algorithm 1 needs only I^(1..t) and theta to
+ * continue; every draw is keyed by (phase, t, i, j)).  Earlier history is discarded. */
+usfft_status usfft_resume(usfft_plan_t* plan, int t, const int8_t* I, int64_t n, double theta);
+
 /* Current detected set I^(1..t): *n receives |I|; if freqs is non-NULL it receives
  * |I| rows of t int8 values (capacity *n_capacity rows; EINVAL if too small). */
 usfft_status usfft_get_set(const usfft_plan_t* plan, int8_t* freqs, int64_t n_capacity,

@@ -168,6 +168,14 @@ class OracleRun:
         idx = sorted(found)
         self.I_prefix = J[idx] if len(idx) else np.zeros((0, t), dtype=np.int64)
 
+    def resume(self, t: int, I_prefix: np.ndarray, theta: float):
+        """Continue from the state after increment t: I^(1..t) and theta (checkpoint)."""
+        self.t = t
+        self.I_prefix = np.array(I_prefix, dtype=np.int64).reshape(-1, t) if t > 0 else np.zeros((0, 0), np.int64)
+        if t > 0:
+            self.theta = theta
+        self.I1d = {}
+
     def increment(self):
         self.t += 1
         t = self.t

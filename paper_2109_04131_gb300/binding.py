@@ -6,7 +6,7 @@ allocator (through the allocator hook of usfft_params) and its work runs on the
 current PyTorch stream unless another stream is given.
 
 Module-level functions carry the C names (usfft_plan, usfft_increment, usfft_replay,
-usfft_rewind, usfft_get_set, usfft_reconstruct, usfft_get_lattice, usfft_get_candidates,
+usfft_rewind, usfft_resume, usfft_get_set, usfft_reconstruct, usfft_get_lattice, usfft_get_candidates,
 usfft_get_samples, usfft_get_coefficients, usfft_get_selection, usfft_last_error,
 usfft_destroy); ``Plan`` wraps them.
 """
@@ -56,6 +56,7 @@ SIGNATURES = {
     "usfft_increment": (ctypes.c_int, [_P, ctypes.POINTER(UsfftIncrementInfo)]),
     "usfft_replay": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]),
     "usfft_rewind": (ctypes.c_int, [_P, ctypes.c_int]),
+    "usfft_resume": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_double]),
     "usfft_get_set": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int32)]),
     "usfft_reconstruct": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), _P, _P, ctypes.c_int]),
@@ -179,6 +180,10 @@ def usfft_rewind(plan, t):
     return plan.rewind(t)
 
 
+def usfft_resume(plan, t, I, theta):
+    return plan.resume(t, I, theta)
+
+
 def usfft_get_set(plan):
     return plan.get_set()
 
@@ -284,6 +289,12 @@ class Plan:
 
     def rewind(self, t: int) -> None:
         self._ck(self._lib.usfft_rewind(self.handle, int(t)))
+
+    def resume(self, t: int, I, theta: float) -> None:
+        """Continue from the checkpoint (t, I^(1..t), theta)."""
+        rows = np.ascontiguousarray(np.asarray(I, dtype=np.int8).reshape(-1, max(t, 1)))
+        n = len(rows) if t > 0 else 0
+        self._ck(self._lib.usfft_resume(self.handle, int(t), rows.ctypes.data if n else None, n, float(theta)))
 
     def get_set(self) -> np.ndarray:
         n = ctypes.c_int64(0)

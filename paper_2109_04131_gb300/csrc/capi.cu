@@ -592,6 +592,34 @@ usfft_status usfft_rewind(usfft_plan_t* plan, int t) {
     return USFFT_OK;
 }
 
+usfft_status usfft_resume(usfft_plan_t* plan, int t, const int8_t* I, int64_t n, double theta) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (t < 0 || t >= plan->d || n < 0 || (n > 0 && !I)) return fail(plan, USFFT_EINVAL, "usfft_resume: invalid argument");
+    if (t > 0 && !(theta > 0.0)) return fail(plan, USFFT_EINVAL, "usfft_resume: theta must be > 0");
+    plan->t = t;
+    plan->nIpre = t > 0 ? n : 0;
+    plan->Ipre.assign(I, I + (t > 0 ? n * t : 0));
+    for (auto& v : plan->I1d) v.clear();
+    if (t > 0) {
+        plan->theta = theta;
+        plan->theta_set = true;
+    } else if (plan->par.delta_is_relative) {
+        plan->theta_set = false;
+    }
+    plan->hist.clear();
+    plan->replay_valid = false;
+    Snapshot s;
+    s.t = t;
+    s.Ipre = plan->Ipre;
+    s.nIpre = plan->nIpre;
+    s.I1d = plan->I1d;
+    s.theta = plan->theta;
+    s.A = plan->A;
+    s.theta_set = plan->theta_set;
+    plan->hist.assign((size_t)t + 1, s);
+    return USFFT_OK;
+}
+
 usfft_status usfft_get_set(const usfft_plan_t* plan, int8_t* freqs, int64_t n_capacity, int64_t* n, int32_t* t) {
     if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
     if (n) *n = plan->nIpre;
