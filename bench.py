@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Benchmark of the usFFT sampling-and-detection increment on GB300.
+
+Workload (the 2-D configuration): P1 FE on the unit square with 63x63 interior nodes
+(G = 3969), affine periodic coefficient with d = 10, search domain [-32,32]^10, s = 500,
+delta = 1e-10 relative, r = 2.  One step = one pass of the hot path for the coupled
+increment t (default t = 3): for each of the r~ = 2 detection iterations, FE solves at all
+M lattice nodes, one length-M FFT per mesh node with the gather at k.z mod M, per-node
+selection and the union.  Increments 1..t-1 run untimed beforehand.
+
+Metric: lattice samples/s (one sample = one FE solve at a lattice node, all G nodes), for
+the mixed-precision path (fp32 CG + fp64 residual refinement) and for the fp64 path, both
+at the 1e-10 accuracy bar; `value` is the mixed path, `fp64` holds the fp64 path.
+
+Timing: CUDA events on the plan's stream around each step, a 256 MB L2 flush between
+steps (outside the events), barrier + synchronize around the timed region, max over
+ranks.  `e2e` times the public call usfft_increment (after usfft_rewind) end to end,
+host planning and host<->device copies included.  `--impl reference` times the CPU
+oracle on bounded samples of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "usFFT lattice samples/s (FE solve+FFT) mixed vs FP64 @1e-10; p50/p99 latency"
+UNIT = "lattice samples/s"
+FLUSH_BYTES = 256 << 20
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# ALU peaks from unit counts and the maximum SM clock: FP32 128 FMA/clk/SM; FP64 2 DFMA/clk/SM
+# (the recipe's nominal 1.25 TFLOP/s fp64 over 152 SMs at 2.07 GHz).
+PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FLOPS_PER_CG_ITER_PER_NODE = 21      # Jacobi-PCG: SpMV 9 + two dots 4 + three AXPY 6 + scaling 2
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        for r in self.rows:
+            for name, flag in zip(self.NAMES, r[4:8]):
+                if "Active" in flag and "Not" not in flag:
+                    reasons.add(name)
+        pw = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows),
+                "power_w_max": max(pw) if pw else None}
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q / 100.0
+    f, c = math.floor(k), math.ceil(k)
+    return xs[f] if f == c else xs[f] + (xs[c] - xs[f]) * (k - f)
+
+
+def workload_config(w, t, info=None):
+    p = w.params
+    cfg = {"workload": f"2-D P1 FE {w.problem.n}x{w.problem.n} interior (G={w.problem.G}), affine periodic "
+                       f"coefficient, d={w.problem.d}, Gamma=[-{p.N},{p.N}]^{w.problem.d}, s={p.s}, "
+                       f"delta={p.delta:g} relative, r={p.r}; coupled increment t={t}",
+           "G": w.problem.G, "d": w.problem.d, "N": p.N, "s": p.s, "r": p.r, "t": t,
+           "l2": "inputs larger than L2 (samples M*G*8 B) and a 256 MB L2 flush between steps",
+           "parallelism": "independent instances, one per GPU"}
+    if info is not None:
+        cfg.update({"M": int(info["M"]), "n_candidates": int(info["n_candidates"]),
+                    "samples_per_step": int(info["M"]) * (p.r if t < w.problem.d else 1)})
+    return cfg
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle on bounded samples (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------------------------
+def oracle_shape(w, t):
+    """Oracle-only setup: increments 1..t-1, then J_t, (z, M) of increment t."""
+    from oracle import lattice
+    from oracle.usfft import OracleRun
+    run = OracleRun(w.problem, w.params)
+    for _ in range(t - 1):
+        run.increment()
+    run.detect_1d(t)
+    J = lattice.candidate_set(run.I_prefix, np.array(run.I1d[t], dtype=np.int64), w.params.N)
+    z, M = lattice.search(J, t, w.params.seed)
+    return run, J, z, M
+
+
+def oracle_sample_time(w, t, J, z, M, rows):
+    """Seconds for the oracle's sampler and DFT on `rows` lattice nodes of iteration 1."""
+    from oracle import dft, fe, lattice, rng
+    from oracle.usfft import NodeSet, sample_rows
+    d = w.problem.d
+    tails = {j - 1: rng.uniform(w.params.seed, rng.PHASE_TAIL, t, 1, j) for j in range(t + 1, d + 1)}
+    nodes = NodeSet(d, list(range(t)), z, M, tails)
+    mesh = fe.make_mesh(w.problem.kind, w.problem.n)
+    m = lattice.lattice_indices(J, z, M)
+    t0 = time.perf_counter()
+    U = sample_rows(w.problem, nodes, rows, mesh)
+    t1 = time.perf_counter()
+    dft.partial_coefficients(U, np.asarray(rows), m, M)
+    t2 = time.perf_counter()
+    return t2 - t0, t1 - t0, t2 - t1
+
+
+def cpu_baseline(w, t, rows_n=96):
+    t0 = time.perf_counter()
+    run, J, z, M = oracle_shape(w, t)
+    setup = time.perf_counter() - t0
+    rows = np.linspace(0, M - 1, rows_n).astype(np.int64)
+    tot, ts, td = oracle_sample_time(w, t, J, z, M, rows)
+    return {"value": rows_n / tot, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{rows_n} of the M={M} lattice nodes of increment t={t}, iteration 1 (|J|={len(J)}): "
+                      f"banded-Cholesky FE solves ({ts:.2f} s, one thread) + naive DFT of those rows at all "
+                      f"|J| indices ({td:.2f} s, numpy BLAS on all cores); oracle setup (increments 1..{t - 1}) "
+                      f"untimed ({setup:.1f} s)",
+            "seconds": tot}
+
+
+def run_reference(args, rank, world):
+    import torch.distributed as dist  # noqa: F401
+    if rank != 0:
+        return
+    w = W.c2(1)
+    t = args.t
+    _, J, z, M = oracle_shape(w, t)
+    rows_n = args.ref_rows
+    rng_ = np.random.default_rng(0)
+    times = []
+    for k in range(args.warmup + args.steps):
+        rows = np.sort(rng_.choice(M, size=rows_n, replace=False))
+        tot, _, _ = oracle_sample_time(w, t, J, z, M, rows)
+        if k >= args.warmup:
+            times.append(tot)
+    per = [rows_n / x for x in times]
+    value = rows_n * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, t) | {"M": int(M), "n_candidates": int(len(J))},
+            "latency_ms": {"p50": 1e3 * percentile(times, 50), "p99": 1e3 * percentile(times, 99)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step: {rows_n} random lattice nodes of increment t={t} "
+                                       f"(M={M}, |J|={len(J)}): FE solves + naive DFT rows"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2109_04131_gb300 import binding
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream(dev)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = W.c2(1 + rank)
+    t = args.t
+    # setup: increments 1..t-1 in fp64; both precisions then run increment t from that state
+    p64 = binding.Plan(w.problem, W.with_precision(w, W.PRECISION_FP64).params)
+    for _ in range(t - 1):
+        p64.increment()
+    I_prev = p64.get_set()
+    info64 = p64.increment()
+    pmx = binding.Plan(w.problem, W.with_precision(w, W.PRECISION_MIXED).params)
+    pmx.resume(t - 1, I_prev, info64["theta"])
+    info_mx = pmx.increment()
+    plans = {"mixed": pmx, "fp64": p64}
+    infos = {"mixed": info_mx, "fp64": info64}
+
+    # accuracy of both precisions against the oracle on sampled lattice nodes
+    accuracy = sampled_accuracy(w, t, plans, rows=4) if rank == 0 and not args.skip_accuracy else None
+
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    results = {}
+    for name in ("mixed", "fp64"):
+        plan = plans[name]
+        info = infos[name]
+        samples_per_step = int(info["M"]) * (w.params.r if t < w.problem.d else 1)
+        for _ in range(args.warmup):
+            plan.replay(sync=True)
+        plan.set_timing(True)
+        launches = 0
+        evs = []
+        barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(uuid) if rank == 0 else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        t_wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launches += plan.replay(sync=False)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall0
+        barrier()
+        if clocks:
+            clocks.stop()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        stages = plan.stage_times()
+        plan.set_timing(False)
+        tot_ms = sum(step_ms)
+        if world > 1:
+            tt = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            tot_ms = float(tt.item())
+        results[name] = {"samples_per_step": samples_per_step, "step_ms": step_ms, "tot_ms": tot_ms,
+                         "wall_s": wall, "launches": launches, "stages": stages,
+                         "clocks": clocks.summary() if clocks else None, "info": info}
+
+    # end to end through the public call (rewind + usfft_increment), mixed precision
+    e2e = e2e_measure(plans["mixed"], t, args.e2e_steps, barrier, world, dev)
+
+    if rank != 0:
+        for p in plans.values():
+            p.close()
+        return
+    peaks, peak_kind = measured_peaks()
+    G = w.problem.G
+    mx, f64 = results["mixed"], results["fp64"]
+    value = world * mx["samples_per_step"] * args.steps / (mx["tot_ms"] / 1e3)
+    value64 = world * f64["samples_per_step"] * args.steps / (f64["tot_ms"] / 1e3)
+
+    def alu_roofline(res, peak, prec):
+        st = res["stages"]
+        n = max(1, st["launches"]["sample"])
+        flops = FLOPS_PER_CG_ITER_PER_NODE * G * st["cg_iters_total"] / n
+        dur = st["ms"]["sample"] / n / 1e3
+        ach = flops / dur / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": f"pcg2d_{prec}_kernel (assembly + CG, {n} launches timed)",
+                "flops_per_launch": flops, "ms_per_launch": dur * 1e3,
+                "cg_iters_per_solve": st["cg_iters_total"] / max(1, res["samples_per_step"] * args.steps),
+                "peak_note": f"{prec} peak from unit counts at {SM_MAX_MHZ:.0f} MHz"}
+
+    def fft_roofline(res):
+        st = res["stages"]
+        n = max(1, st["launches"]["fft"])
+        M = int(res["info"]["M"])
+        nJ = int(res["info"]["n_candidates"])
+        algo = 8.0 * M * G + 16.0 * nJ * G          # read the samples once, write the gathered coefficients
+        dur = st["ms"]["fft"] / n / 1e3
+        ach = algo / dur / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "fft_pass_kernel (all passes)",
+                "bytes_per_launch": algo, "ms_per_launch": dur * 1e3,
+                "peak_note": f"{peak_kind} hbm_gbs (burst)"}
+
+    roof = alu_roofline(mx, PEAK_FP32_TFLOPS, "mixed")
+    clocks = mx["clocks"] or {}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mx["tot_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": workload_config(w, t, mx["info"]),
+        "fe_node_samples_per_s": value * G,
+        "latency_ms": {"p50": percentile(mx["step_ms"], 50), "p99": percentile(mx["step_ms"], 99)},
+        "fp64": {"value": value64, "unit": UNIT, "dtype": "f64", "ms_per_step": f64["tot_ms"] / args.steps,
+                 "latency_ms": {"p50": percentile(f64["step_ms"], 50), "p99": percentile(f64["step_ms"], 99)},
+                 "roofline": alu_roofline(f64, PEAK_FP64_TFLOPS, "fp64"), "clocks": f64["clocks"]},
+        "speedup_mixed_vs_fp64": value / value64,
+        "accuracy": accuracy,
+        "roofline": roof,
+        "roofline_fft": fft_roofline(mx),
+        "stage_ms_per_step": {k: v / args.steps for k, v in mx["stages"]["ms"].items()},
+        "gpu_launches": mx["launches"],
+        "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
+                   "reasons": clocks.get("reasons"), "samples": clocks.get("samples"),
+                   "power_w_max": clocks.get("power_w_max")},
+        "e2e": e2e,
+    }
+    if not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, t)
+    print(json.dumps(line), flush=True)
+    for p in plans.values():
+        p.close()
+
+
+def e2e_measure(plan, t, steps, barrier, world, dev):
+    import torch
+    import torch.distributed as dist
+    times, samples, h2d, d2h = [], [], [], []
+    plan.rewind(t - 1)
+    plan.increment()                              # warm
+    barrier()
+    for _ in range(steps):
+        plan.rewind(t - 1)
+        t0 = time.perf_counter()
+        info = plan.increment()
+        times.append(time.perf_counter() - t0)
+        samples.append(info["samples"])
+        h2d.append(info["h2d_bytes"])
+        d2h.append(info["d2h_bytes"])
+    tot = sum(times)
+    if world > 1:
+        tt = torch.tensor([tot], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot = float(tt.item())
+    return {"value": world * sum(samples) / tot, "unit": UNIT, "h2d_bytes_per_step": int(np.mean(h2d)),
+            "d2h_bytes_per_step": int(np.mean(d2h)), "steps": steps,
+            "ms_per_step": 1e3 * tot / steps,
+            "latency_ms": {"p50": 1e3 * percentile(times, 50), "p99": 1e3 * percentile(times, 99)},
+            "call": "usfft_rewind(t-1) + usfft_increment (1-D detections of dimension t, J_t, lattice "
+                    "search, both detection iterations, host copies)"}
+
+
+def sampled_accuracy(w, t, plans, rows=4):
+    """Max relative error of the last iteration's samples on `rows` lattice nodes, against
+    the oracle's banded-Cholesky solves at the same nodes (fp64 and mixed)."""
+    from oracle import fe, rng
+    from oracle.usfft import NodeSet, sample_rows
+    out = {}
+    mesh = fe.make_mesh(w.problem.kind, w.problem.n)
+    d = w.problem.d
+    for name, plan in plans.items():
+        z, M = plan.get_lattice()
+        it = w.params.r if t < d else 1
+        tails = {j - 1: rng.uniform(w.params.seed, rng.PHASE_TAIL, t, it, j) for j in range(t + 1, d + 1)}
+        nodes = NodeSet(d, list(range(t)), np.asarray(z), M, tails)
+        idx = np.linspace(0, M - 1, rows).astype(np.int64)
+        U = plan.get_samples()
+        Uo = sample_rows(w.problem, nodes, idx, mesh)
+        out[name + "_samples_rel_err"] = float(np.max(np.abs(U[idx] - Uo)) / np.max(np.abs(Uo)))
+    out["rows"] = rows
+    out["bar"] = 1e-10
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--t", type=int, default=3, help="coupled increment timed as one step")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-rows", type=int, default=24)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-accuracy", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" and torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -125,6 +125,8 @@ typedef struct {
     double theta;             /* absolute threshold in use */
     double ms_device;         /* device time of the increment's kernels (CUDA events) */
     double ms_host_plan;      /* host time of J_t construction + lattice search */
+    int64_t h2d_bytes;        /* host-to-device bytes copied by this increment */
+    int64_t d2h_bytes;        /* device-to-host bytes copied by this increment */
 } usfft_increment_info;
 
 typedef struct usfft_plan_s usfft_plan_t;
@@ -157,6 +159,22 @@ usfft_status usfft_rewind(usfft_plan_t* plan, int t);
  * would have after the increments 1..t (Algorithm 1 needs only I^(1..t) and theta to
  * continue; every draw is keyed by (phase, t, i, j)).  Earlier history is discarded. */
 usfft_status usfft_resume(usfft_plan_t* plan, int t, const int8_t* I, int64_t n, double theta);
+
+/* Stage timing for measurement.  usfft_set_timing(plan, on) resets the accumulators; with
+ * timing on, every later increment or replay records a CUDA event pair (on the plan's
+ * stream) around each stage launch.  usfft_get_stage_times synchronises the stream and
+ * returns, accumulated since the reset, the device time and launch count per stage and
+ * the total CG iterations of the 2-D solves. */
+#define USFFT_STAGE_SAMPLE 0   /* coefficient assembly + FE solve (the black-box sampler) */
+#define USFFT_STAGE_FFT 1      /* lattice FFT + gather at k.z mod M */
+#define USFFT_STAGE_SELECT 2   /* threshold / top-s~ selection + union */
+typedef struct {
+    double ms[3];
+    int32_t launches[3];
+    int64_t cg_iters_total;
+} usfft_stage_times;
+usfft_status usfft_set_timing(usfft_plan_t* plan, int on);
+usfft_status usfft_get_stage_times(usfft_plan_t* plan, usfft_stage_times* out);
 
 /* Current detected set I^(1..t): *n receives |I|; if freqs is non-NULL it receives
  * |I| rows of t int8 values (capacity *n_capacity rows; EINVAL if too small). */

@@ -29,3 +29,19 @@ def coefficients(U: np.ndarray, m: np.ndarray, M: int, chunk: int = 256) -> np.n
         im = -(U.T @ np.sin(ang))
         out[:, c0:c0 + chunk] = (re + 1j * im) / M
     return out
+
+
+def partial_coefficients(U_rows: np.ndarray, rows: np.ndarray, m: np.ndarray, M: int,
+                         chunk: int = 256) -> np.ndarray:
+    """The contribution of the lattice nodes `rows` (samples U_rows [len(rows), G]) to
+    coefficients(): (1/M) sum_{i in rows} U[i][g] exp(-2 pi i (i m_k)/M).  Summed over a
+    partition of 0..M-1 it gives coefficients(); the cost per row is the same."""
+    U_rows = np.asarray(U_rows, dtype=np.float64)
+    G = U_rows.shape[1]
+    out = np.zeros((G, len(m)), dtype=np.complex128)
+    i = np.asarray(rows, dtype=np.int64)
+    for c0 in range(0, len(m), chunk):
+        mk = np.asarray(m[c0:c0 + chunk], dtype=np.int64)
+        ang = (2.0 * np.pi / M) * np.mod(np.outer(i, mk), M).astype(np.float64)
+        out[:, c0:c0 + chunk] = (U_rows.T @ np.cos(ang) - 1j * (U_rows.T @ np.sin(ang))) / M
+    return out

@@ -63,6 +63,23 @@ def sample(prob, nodes: NodeSet, mesh=None) -> np.ndarray:
     return U
 
 
+def sample_rows(prob, nodes: NodeSet, rows, mesh=None) -> np.ndarray:
+    """The PDE samples of the lattice nodes listed in `rows` only (a bounded subset of
+    sample(); used to time the oracle on part of a large workload)."""
+    if mesh is None:
+        mesh = fe.make_mesh(prob.kind, prob.n)
+    n_int = nodes.lattice_ints()
+    U = np.zeros((len(rows), mesh.G))
+    sin_y = np.zeros(nodes.d)
+    for j, yv in nodes.tails.items():
+        sin_y[j] = math.sin(2.0 * math.pi * yv)
+    for r, i in enumerate(rows):
+        for c, j in enumerate(nodes.lat):
+            sin_y[j] = math.sin(2.0 * math.pi * n_int[i, c] / nodes.M)
+        U[r] = fe.solve(prob, mesh, sin_y)
+    return U
+
+
 def _trigpoly_samples(prob, nodes: NodeSet, n_int: np.ndarray) -> np.ndarray:
     F = prob.tp_freqs.astype(np.int64)        # [G, T, d]
     Cf = prob.tp_coefs                        # [G, T]

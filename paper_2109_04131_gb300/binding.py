@@ -46,7 +46,11 @@ class UsfftIncrementInfo(ctypes.Structure):
                 ("n_detected", ctypes.c_int64), ("n_1d", ctypes.c_int64), ("samples", ctypes.c_int64),
                 ("cg_iters_total", ctypes.c_int64), ("cg_iters_max", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int32), ("theta", ctypes.c_double), ("ms_device", ctypes.c_double),
-                ("ms_host_plan", ctypes.c_double)]
+                ("ms_host_plan", ctypes.c_double), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+
+
+class UsfftStageTimes(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 3), ("launches", ctypes.c_int32 * 3), ("cg_iters_total", ctypes.c_int64)]
 
 
 # exported symbols and their signatures (restype, argtypes)
@@ -57,6 +61,8 @@ SIGNATURES = {
     "usfft_replay": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]),
     "usfft_rewind": (ctypes.c_int, [_P, ctypes.c_int]),
     "usfft_resume": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_double]),
+    "usfft_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "usfft_get_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(UsfftStageTimes)]),
     "usfft_get_set": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int32)]),
     "usfft_reconstruct": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), _P, _P, ctypes.c_int]),
@@ -295,6 +301,17 @@ class Plan:
         rows = np.ascontiguousarray(np.asarray(I, dtype=np.int8).reshape(-1, max(t, 1)))
         n = len(rows) if t > 0 else 0
         self._ck(self._lib.usfft_resume(self.handle, int(t), rows.ctypes.data if n else None, n, float(theta)))
+
+    def set_timing(self, on: bool) -> None:
+        self._ck(self._lib.usfft_set_timing(self.handle, int(bool(on))))
+
+    def stage_times(self) -> dict:
+        st = UsfftStageTimes()
+        self._ck(self._lib.usfft_get_stage_times(self.handle, ctypes.byref(st)))
+        names = ("sample", "fft", "select")
+        return {"ms": {n: st.ms[i] for i, n in enumerate(names)},
+                "launches": {n: st.launches[i] for i, n in enumerate(names)},
+                "cg_iters_total": st.cg_iters_total}
 
     def get_set(self) -> np.ndarray:
         n = ctypes.c_int64(0)

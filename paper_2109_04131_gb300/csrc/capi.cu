@@ -72,7 +72,13 @@ struct usfft_plan_s {
     int launches = 0;
     int64_t cg_iters_total = 0;
     int cg_iters_max = 0;
+    int64_t h2d = 0, d2h = 0;
     bool replay_valid = false;
+    // stage timing (usfft_set_timing): event pairs per stage launch
+    bool timing = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
     double* pinned = nullptr;   // small pinned staging area
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs = nullptr;
     std::string err;
@@ -196,9 +202,40 @@ NodeSpec spec_coupled(const usfft_plan_t* p, int t, int i) {
     return ns;
 }
 
+cudaEvent_t pool_event(usfft_plan_t* plan) {
+    if (plan->ev_used == plan->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        plan->ev_pool.push_back(e);
+    }
+    return plan->ev_pool[plan->ev_used++];
+}
+
+// Records an event pair around one stage launch when timing is on.
+struct StageTimer {
+    usfft_plan_t* plan;
+    int stage;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageTimer(usfft_plan_t* p, int st) : plan(p), stage(st) {
+        if (!plan->timing) return;
+        a = pool_event(plan);
+        b = pool_event(plan);
+        if (a && b) cudaEventRecord(a, plan->stream);
+    }
+    ~StageTimer() {
+        if (!plan->timing || !a || !b) return;
+        cudaEventRecord(b, plan->stream);
+        plan->tev.push_back({stage, {a, b}});
+    }
+};
+
 // sampler dispatch: U[0..M)[G] for the node set
 usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns) {
     const int kind = plan->prob.kind;
+    StageTimer timer(plan, USFFT_STAGE_SAMPLE);
     if (kind == USFFT_PDE_1D) {
         CK(launch_sample_1d(ns, plan->prob.n, plan->prob.coef_model, plan->prob.f_const, (const double*)plan->psi.p,
                             0, ns.M, (double*)plan->U.p, plan->stream, &plan->launches));
@@ -210,7 +247,8 @@ usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns) {
         cg.blocks = plan->cg_blocks;
         CK(launch_sample_2d(ns, plan->prob.n, plan->prob.coef_model, plan->prob.f_const, (const double*)plan->psi.p, cg,
                             0, ns.M, (double*)plan->U.p, (int*)plan->iters.p, (unsigned int*)plan->failc.p,
-                            (double*)plan->cgscr.p, plan->cgscr.bytes, plan->stream, &plan->launches));
+                            (unsigned long long*)((char*)plan->failc.p + 8), (double*)plan->cgscr.p,
+                            plan->cgscr.bytes, plan->stream, &plan->launches));
     } else {
         CK(launch_sample_trigpoly(ns, plan->G, plan->prob.tp_nterms, (const int8_t*)plan->tpf.p,
                                   (const double*)plan->tpc.p, (double*)plan->tpaux.p, (double*)plan->U.p,
@@ -247,9 +285,11 @@ usfft_status prepare_step(usfft_plan_t* plan, int64_t M, const std::vector<int64
     if ((st = ensure(plan, plan->gk, sizeof(int) * (size_t)std::max<int64_t>(nJ, 1), "gather k")) != USFFT_OK) return st;
     if ((st = ensure(plan, plan->gm2, sizeof(int) * (size_t)std::max<int64_t>(nJ, 1), "gather m2")) != USFFT_OK) return st;
     CK(cudaMemcpyAsync(plan->goff.p, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, plan->stream));
+    plan->h2d += (int64_t)(sizeof(int) * off.size());
     if (nJ) {
         CK(cudaMemcpyAsync(plan->gk.p, bk.data(), sizeof(int) * (size_t)nJ, cudaMemcpyHostToDevice, plan->stream));
         CK(cudaMemcpyAsync(plan->gm2.p, bm2.data(), sizeof(int) * (size_t)nJ, cudaMemcpyHostToDevice, plan->stream));
+        plan->h2d += (int64_t)(2 * sizeof(int) * (size_t)nJ);
     }
     // host vectors must outlive the asynchronous copies
     CK(cudaStreamSynchronize(plan->stream));
@@ -269,22 +309,28 @@ usfft_status run_step_device(usfft_plan_t* plan, bool first_1d_sets_theta) {
     for (size_t it = 0; it < plan->specs.size(); ++it) {
         usfft_status st = run_sampler(plan, plan->specs[it]);
         if (st != USFFT_OK) return st;
-        CK(launch_fft_gather(plan->fp, plan->G, (const double*)plan->U.p, (const double2*)plan->twid.p, gp, nJ,
-                             (double2*)plan->fftscr.p, (double2*)plan->C.p, plan->stream, &plan->launches));
+        {
+            StageTimer timer(plan, USFFT_STAGE_FFT);
+            CK(launch_fft_gather(plan->fp, plan->G, (const double*)plan->U.p, (const double2*)plan->twid.p, gp, nJ,
+                                 (double2*)plan->fftscr.p, (double2*)plan->C.p, plan->stream, &plan->launches));
+        }
         if (first_1d_sets_theta && it == 0 && !plan->theta_set) {
             // relative threshold: theta = delta * max_g |c_{g,0}| of the first 1-D detection
             CK(launch_absmax_column((const double2*)plan->C.p, plan->G, nJ, plan->N, (double*)plan->scal.p,
                                     plan->stream, &plan->launches));
             CK(cudaMemcpyAsync(plan->pinned, plan->scal.p, sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
+            plan->d2h += (int64_t)sizeof(double);
             usfft_status w = wait_stream(plan);
             if (w != USFFT_OK) return w;
             plan->A = plan->pinned[0];
             plan->theta = plan->par.delta * plan->A;
             plan->theta_set = true;
         }
-        if (plan->s_tilde > 0)
+        if (plan->s_tilde > 0) {
+            StageTimer timer(plan, USFFT_STAGE_SELECT);
             CK(launch_select_union((const double2*)plan->C.p, plan->G, nJ, plan->theta, plan->s_tilde,
                                    (uint32_t*)plan->bitmap.p, plan->stream, &plan->launches));
+        }
     }
     return USFFT_OK;
 }
@@ -293,6 +339,7 @@ usfft_status read_bitmap(usfft_plan_t* plan, std::vector<uint32_t>& bits) {
     const size_t words = (size_t)((plan->nJ + 31) / 32);
     bits.assign(words, 0u);
     if (words) CK(cudaMemcpyAsync(bits.data(), plan->bitmap.p, 4 * words, cudaMemcpyDeviceToHost, plan->stream));
+    plan->d2h += (int64_t)(4 * words);
     return wait_stream(plan);
 }
 
@@ -302,6 +349,7 @@ usfft_status read_cg_stats(usfft_plan_t* plan, int64_t count) {
     unsigned int fails = 0;
     CK(cudaMemcpyAsync(it.data(), plan->iters.p, sizeof(int) * (size_t)count, cudaMemcpyDeviceToHost, plan->stream));
     CK(cudaMemcpyAsync(&fails, plan->failc.p, sizeof(unsigned), cudaMemcpyDeviceToHost, plan->stream));
+    plan->d2h += (int64_t)(sizeof(int) * (size_t)count + sizeof(unsigned));
     usfft_status st = wait_stream(plan);
     if (st != USFFT_OK) return st;
     for (int v : it) {
@@ -461,6 +509,7 @@ usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
     plan->launches = 0;
     plan->cg_iters_total = 0;
     plan->cg_iters_max = 0;
+    plan->h2d = plan->d2h = 0;
     double ms_host = 0.0;
     usfft_status st;
     CK(cudaMemsetAsync(plan->failc.p, 0, sizeof(unsigned), plan->stream));
@@ -561,6 +610,8 @@ usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
         cudaEventElapsedTime(&ms, plan->ev0, plan->ev1);
         info->ms_device = ms;
         info->ms_host_plan = ms_host;
+        info->h2d_bytes = plan->h2d;
+        info->d2h_bytes = plan->d2h;
     }
     return USFFT_OK;
 }
@@ -617,6 +668,39 @@ usfft_status usfft_resume(usfft_plan_t* plan, int t, const int8_t* I, int64_t n,
     s.A = plan->A;
     s.theta_set = plan->theta_set;
     plan->hist.assign((size_t)t + 1, s);
+    return USFFT_OK;
+}
+
+usfft_status usfft_set_timing(usfft_plan_t* plan, int on) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    usfft_status st = wait_stream(plan);
+    if (st != USFFT_OK) return st;
+    plan->timing = on != 0;
+    plan->tev.clear();
+    plan->ev_used = 0;
+    CK(cudaMemsetAsync((char*)plan->failc.p + 8, 0, 8, plan->stream));
+    return USFFT_OK;
+}
+
+usfft_status usfft_get_stage_times(usfft_plan_t* plan, usfft_stage_times* out) {
+    if (!plan || !out) return fail(plan, USFFT_EINVAL, "plan or out is NULL");
+    usfft_status st = wait_stream(plan);
+    if (st != USFFT_OK) return st;
+    memset(out, 0, sizeof *out);
+    for (auto& e : plan->tev) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.second.first, e.second.second) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (e.first >= 0 && e.first < 3) {
+            out->ms[e.first] += ms;
+            out->launches[e.first] += 1;
+        }
+    }
+    unsigned long long it = 0;
+    CK(cudaMemcpy(&it, (char*)plan->failc.p + 8, 8, cudaMemcpyDeviceToHost));
+    out->cg_iters_total = (int64_t)it;
     return USFFT_OK;
 }
 
@@ -727,6 +811,7 @@ void usfft_destroy(usfft_plan_t* plan) {
     if (plan->ev0) cudaEventDestroy(plan->ev0);
     if (plan->ev1) cudaEventDestroy(plan->ev1);
     if (plan->evs) cudaEventDestroy(plan->evs);
+    for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
     delete plan;
 }
 

@@ -46,6 +46,7 @@ struct Pcg2dArgs {
     double* U;             // [count][n*n]
     int* iters_out;
     unsigned int* fail_count;
+    unsigned long long* iters_sum;   // total CG iterations of the launch (may be NULL)
     double* scratch;       // MIXED: per CTA 2 n (n+1) fp64 scaled weights
 };
 
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(1024) pcg2d_fp64_kernel(const __grid_constant_
         }
         if (tid == 0) {
             if (a.iters_out) a.iters_out[sys] = it;
+            if (a.iters_sum) atomicAdd(a.iters_sum, (unsigned long long)it);
             if (rr > stop && a.fail_count) atomicAdd(a.fail_count, 1u);
         }
         __syncthreads();
@@ -362,6 +364,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_kernel(const __grid_constant
         }
         if (tid == 0) {
             if (a.iters_out) a.iters_out[sys] = total;
+            if (a.iters_sum) atomicAdd(a.iters_sum, (unsigned long long)total);
             if (rr64 > stop && a.fail_count) atomicAdd(a.fail_count, 1u);
         }
         __syncthreads();
@@ -445,8 +448,8 @@ static cudaError_t launch_npt(const Pcg2dArgs& a, int precision, int blocks, int
 
 cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f, const double* psi,
                              const CgConfig& cg, int64_t i0, int64_t count, double* U, int* iters_out,
-                             unsigned int* fail_count, double* scratch, size_t scratch_bytes,
-                             cudaStream_t s, int* launches) {
+                             unsigned int* fail_count, unsigned long long* iters_sum, double* scratch,
+                             size_t scratch_bytes, cudaStream_t s, int* launches) {
     if (count <= 0) return cudaSuccess;
     Pcg2dArgs a;
     a.ns = ns;
@@ -463,6 +466,7 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
     a.U = U;
     a.iters_out = iters_out;
     a.fail_count = fail_count;
+    a.iters_sum = iters_sum;
     a.scratch = scratch;
     const int G = n * n;
     const int npt = pick_npt(G);

@@ -72,8 +72,8 @@ struct CgConfig {
 };
 cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f, const double* psi,
                              const CgConfig& cg, int64_t i0, int64_t count, double* U, int* iters_out,
-                             unsigned int* fail_count, double* scratch, size_t scratch_bytes,
-                             cudaStream_t s, int* launches);
+                             unsigned int* fail_count, unsigned long long* iters_sum, double* scratch,
+                             size_t scratch_bytes, cudaStream_t s, int* launches);
 size_t sample_2d_scratch_bytes(int n, int precision, int blocks);
 int sample_2d_default_blocks(int n, int precision);
 

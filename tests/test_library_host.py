@@ -56,6 +56,7 @@ int main(void) {
   P(usfft_problem, tp_freqs) P(usfft_problem, tp_coefs) P(usfft_problem, coef_scale)
   P(usfft_params, seed) P(usfft_params, hbm_budget_bytes) P(usfft_params, cg_tol) P(usfft_params, alloc_ctx)
   P(usfft_increment_info, M) P(usfft_increment_info, kernel_launches) P(usfft_increment_info, ms_host_plan)
+  P(usfft_increment_info, d2h_bytes)
   return 0;
 }
 """)

@@ -131,3 +131,13 @@ def test_union_invariants():
     for g in range(7):
         assert set(detect.select(C[g], theta, s).tolist()) <= U
     assert len(U) <= sum(min(s, c) for c in counts)
+
+
+def test_partial_coefficients_sum_to_the_full_dft():
+    r = np.random.default_rng(12)
+    M, G = 60, 4
+    U = r.standard_normal((M, G))
+    m = np.array([0, 7, 59, 31])
+    parts = [np.arange(0, 25), np.arange(25, 60)]
+    tot = sum(dft.partial_coefficients(U[p], p, m, M) for p in parts)
+    assert np.max(np.abs(tot - dft.coefficients(U, m, M))) < 1e-15
