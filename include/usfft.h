@@ -65,9 +65,12 @@ typedef enum {
 #define USFFT_COEF_LOGNORMAL_SIN 2
 
 /* precision of the sampler */
-#define USFFT_FP64 0          /* fp64 everywhere */
-#define USFFT_MIXED 1         /* 2-D: fp32 CG inner solves + fp64-residual iterative refinement;
-                                 1-D: fp64; FFT, gather and selection stay fp64 */
+#define USFFT_FP64 0          /* fp64 everywhere; 2-D solves by Jacobi-preconditioned CG */
+#define USFFT_MIXED 1         /* 2-D: fp64-residual iterative refinement around fp32 flexible CG
+                                 preconditioned by the constant-coefficient operator (2-D sine
+                                 transform on the tensor cores, TF32); 1-D: fp64; FFT, gather and
+                                 selection stay fp64 */
+#define USFFT_MIXED_JACOBI 2  /* 2-D: the same refinement around fp32 Jacobi-CG (for comparison) */
 
 typedef struct {
     int kind;                 /* USFFT_PDE_1D | USFFT_PDE_2D | USFFT_TRIGPOLY */

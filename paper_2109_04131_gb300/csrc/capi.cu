@@ -401,7 +401,8 @@ usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params
     if (pa.N < 1 || pa.N > 127) return fail(nullptr, USFFT_EINVAL, "N must lie in [1, 127] (int8 frequencies)");
     if (pa.r < 1 || pa.s < 0 || pa.s_local < 0) return fail(nullptr, USFFT_EINVAL, "r >= 1, s >= 0, s_local >= 0");
     if (!(pa.delta >= 0.0)) return fail(nullptr, USFFT_EINVAL, "delta must be >= 0");
-    if (pa.precision != USFFT_FP64 && pa.precision != USFFT_MIXED) return fail(nullptr, USFFT_EINVAL, "precision");
+    if (pa.precision != USFFT_FP64 && pa.precision != USFFT_MIXED && pa.precision != USFFT_MIXED_JACOBI)
+        return fail(nullptr, USFFT_EINVAL, "precision");
     int G = 0, E = 0;
     if (pr.kind == USFFT_PDE_1D) {
         if (pr.n < 1 || pr.n > 1023) return fail(nullptr, USFFT_EINVAL, "1-D: n must lie in [1, 1023]");
@@ -409,7 +410,7 @@ usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params
         E = pr.n + 1;
     } else if (pr.kind == USFFT_PDE_2D) {
         if (pr.n < 1 || pr.n > 63) return fail(nullptr, USFFT_EINVAL, "2-D: n must lie in [1, 63] in this version");
-        if (pa.precision == USFFT_MIXED && pr.n < 4) return fail(nullptr, USFFT_EINVAL, "2-D mixed: n >= 4");
+        if (pa.precision == USFFT_MIXED_JACOBI && pr.n < 4) return fail(nullptr, USFFT_EINVAL, "2-D mixed: n >= 4");
         G = pr.n * pr.n;
         E = 2 * (pr.n + 1) * (pr.n + 1);
     } else if (pr.kind == USFFT_TRIGPOLY) {

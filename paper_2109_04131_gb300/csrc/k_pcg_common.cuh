@@ -1,0 +1,80 @@
+// Device helpers shared by the 2-D sampler kernels (k_sample2d.cu, k_sample2d_dst.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "usfft_internal.h"
+
+namespace usfft {
+
+__device__ __forceinline__ double node_sin2(const NodeSpec& ns, int j, int64_t i) {
+    int64_t zj = ns.z[j];
+    if (zj >= 0) {
+        int64_t nn = (i * zj) % ns.M;
+        return sinpi(2.0 * (double)nn / (double)ns.M);
+    }
+    return sinpi(2.0 * ns.tail[j]);
+}
+
+struct Pcg2dArgs {
+    NodeSpec ns;
+    int n, coef_model, max_iters;
+    double rhs;            // h^2 f
+    double tol;            // relative residual target (fp64 / refinement)
+    double tol_inner;      // relative residual target of an fp32 inner solve
+    const double* psi;     // [d][2(n+1)^2]
+    int64_t i0, count;
+    double* U;             // [count][n*n]
+    int* iters_out;
+    unsigned int* fail_count;
+    unsigned long long* iters_sum;   // total CG iterations of the launch (may be NULL)
+    double* scratch;       // MIXED: per CTA 2 n (n+1) fp64 scaled weights
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum plus one scalar ratio, computed once by thread 0 and broadcast:
+// ratio = num / sum (NUM_OVER_SUM) or sum / den (SUM_OVER_DEN).  `buf` holds 34 values.
+// Every thread of the block must call it (two barriers).
+enum { NUM_OVER_SUM = 0, SUM_OVER_DEN = 1 };
+template <typename T, int MODE>
+__device__ __forceinline__ void block_sum_ratio(T v, T other, T* buf, T& sum, T& ratio) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) buf[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nw ? buf[lane] : (T)0;
+        w = warp_sum(w);
+        if (lane == 0) {
+            buf[32] = w;
+            buf[33] = (MODE == NUM_OVER_SUM) ? other / w : w / other;
+        }
+    }
+    __syncthreads();
+    sum = buf[32];
+    ratio = buf[33];
+}
+
+// Block-wide sum; `buf` holds 33 doubles; the result is returned to every thread.
+__device__ __forceinline__ double block_sum(double v, double* buf) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) buf[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double w = lane < nw ? buf[lane] : 0.0;
+        w = warp_sum(w);
+        if (lane == 0) buf[32] = w;
+    }
+    __syncthreads();
+    return buf[32];
+}
+
+
+}  // namespace usfft

@@ -23,56 +23,18 @@
 #include <math.h>
 
 #include "usfft_internal.h"
+#include "k_pcg_common.cuh"
 
 namespace usfft {
 
-__device__ __forceinline__ double node_sin2(const NodeSpec& ns, int j, int64_t i) {
-    int64_t zj = ns.z[j];
-    if (zj >= 0) {
-        int64_t nn = (i * zj) % ns.M;
-        return sinpi(2.0 * (double)nn / (double)ns.M);
-    }
-    return sinpi(2.0 * ns.tail[j]);
-}
+// DST-preconditioned mixed kernel (k_sample2d_dst.cu)
+size_t dst_smem_bytes(int n, int d);
+template <int NPT>
+cudaError_t launch_dst_npt(const Pcg2dArgs& a, int blocks, int threads, cudaStream_t s);
+template <int NPT>
+int dst_resident_blocks(int threads, int d, int n);
 
-struct Pcg2dArgs {
-    NodeSpec ns;
-    int n, coef_model, max_iters;
-    double rhs;            // h^2 f
-    double tol;            // relative residual target (fp64 / refinement)
-    double tol_inner;      // relative residual target of an fp32 inner solve
-    const double* psi;     // [d][2(n+1)^2]
-    int64_t i0, count;
-    double* U;             // [count][n*n]
-    int* iters_out;
-    unsigned int* fail_count;
-    unsigned long long* iters_sum;   // total CG iterations of the launch (may be NULL)
-    double* scratch;       // MIXED: per CTA 2 n (n+1) fp64 scaled weights
-};
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Block-wide sum; `buf` holds 33 doubles; the result is returned to every thread.
-__device__ __forceinline__ double block_sum(double v, double* buf) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) buf[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        double w = lane < nw ? buf[lane] : 0.0;
-        w = warp_sum(w);
-        if (lane == 0) buf[32] = w;
-    }
-    __syncthreads();
-    return buf[32];
-}
-
-// Shared-memory layout (doubles): ph[(n+2)^2] | wx[n(n+1)] | wy[(n+1)n] | sj[d] | red[2*33]
+// Shared-memory layout (doubles): ph[(n+2)^2] | wx[n(n+1)] | wy[(n+1)n] | sj[d] | red[2*34]
 // wx[qq(n+1)+P]: edge (P,qq+1)-(P+1,qq+1) (global node coords), P = 0..n
 // wy[Q n + pp]:  edge (pp+1,Q)-(pp+1,Q+1),                       Q = 0..n
 __device__ void assemble_scaled(const Pcg2dArgs& a, int64_t i, double* ph, double* wx, double* wy, double* sj) {
@@ -184,8 +146,8 @@ __global__ void __launch_bounds__(1024) pcg2d_fp64_kernel(const __grid_constant_
                     pq_l = fma(p[k], q[k], pq_l);
                 }
             }
-            const double pq = block_sum(pq_l, red);
-            const double alpha = rr / pq;
+            double pq, alpha;
+            block_sum_ratio<double, NUM_OVER_SUM>(pq_l, rr, red, pq, alpha);      // alpha = rr / (p, Kp)
             double rn_l = 0.0;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
@@ -193,8 +155,8 @@ __global__ void __launch_bounds__(1024) pcg2d_fp64_kernel(const __grid_constant_
                 r[k] = fma(-alpha, q[k], r[k]);
                 rn_l = fma(r[k], r[k], rn_l);
             }
-            const double rn = block_sum(rn_l, red + 33);
-            const double beta = rn / rr;
+            double rn, beta;
+            block_sum_ratio<double, SUM_OVER_DEN>(rn_l, rr, red + 34, rn, beta);  // beta = rn / rr
             rr = rn;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
@@ -234,6 +196,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_kernel(const __grid_constant
     double* wy = wx + n * n1;
     double* sj = wy + n1 * n;
     double* red = sj + a.ns.d;
+    float* red32 = reinterpret_cast<float*>(red);               // fp32 reduction scratch (68 floats)
     double* xh = sm;                                            // fp64 halo
     float* wx32 = reinterpret_cast<float*>(wx);
     float* wy32 = wx32 + n * n1;
@@ -295,8 +258,9 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_kernel(const __grid_constant
                 rr_l = fmaf(r32[k], r32[k], rr_l);
                 if (g < G) ph32[((g / n) + 1) * W + (g % n) + 1] = p32[k];
             }
-            double rr = block_sum((double)rr_l, red);
-            const double istop = a.tol_inner * a.tol_inner * rr;
+            float rr, unused;
+            block_sum_ratio<float, SUM_OVER_DEN>(rr_l, 1.0f, red32, rr, unused);
+            const float istop = (float)(a.tol_inner * a.tol_inner) * rr;
             int it = 0;
             while (rr > istop && it < a.max_iters) {
                 float pq_l = 0.0f;
@@ -309,8 +273,8 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_kernel(const __grid_constant
                         pq_l = fmaf(p32[k], q32[k], pq_l);
                     }
                 }
-                const double pq = block_sum((double)pq_l, red);
-                const float alpha = (float)(rr / pq);
+                float pq, alpha;
+                block_sum_ratio<float, NUM_OVER_SUM>(pq_l, rr, red32, pq, alpha);
                 float rn_l = 0.0f;
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
@@ -318,8 +282,8 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_kernel(const __grid_constant
                     r32[k] = fmaf(-alpha, q32[k], r32[k]);
                     rn_l = fmaf(r32[k], r32[k], rn_l);
                 }
-                const double rn = block_sum((double)rn_l, red + 33);
-                const float beta = (float)(rn / rr);
+                float rn, beta;
+                block_sum_ratio<float, SUM_OVER_DEN>(rn_l, rr, red32 + 34, rn, beta);
                 rr = rn;
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
@@ -380,14 +344,16 @@ static int pick_npt(int G) {
 
 static size_t smem_bytes(int n, int d) {
     const size_t W = (size_t)n + 2;
-    return sizeof(double) * (W * W + 2 * (size_t)n * (n + 1) + (size_t)d + 66);
+    return sizeof(double) * (W * W + 2 * (size_t)n * (n + 1) + (size_t)d + 68);
 }
 
 template <int NPT>
-static int resident_blocks(int precision, int threads, size_t smem) {
+static int resident_blocks(int precision, int threads, int n) {
+    if (precision == USFFT_MIXED) return dst_resident_blocks<NPT>(threads, USFFT_MAX_D, n);
+    const size_t smem = smem_bytes(n, USFFT_MAX_D);
     int per_sm = 0;
     cudaError_t e;
-    if (precision == USFFT_MIXED) {
+    if (precision == USFFT_MIXED_JACOBI) {
         e = cudaFuncSetAttribute(pcg2d_mixed_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg2d_mixed_kernel<NPT>, threads, smem);
@@ -408,33 +374,32 @@ int sample_2d_default_blocks(int n, int precision) {
     const int G = n * n;
     const int npt = pick_npt(G);
     const int threads = ((G + npt - 1) / npt + 31) / 32 * 32;
-    const size_t smem = smem_bytes(n, USFFT_MAX_D);
     int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         sms = 152;
     }
     int per_sm;
     switch (npt) {
-        case 1: per_sm = resident_blocks<1>(precision, threads, smem); break;
-        case 2: per_sm = resident_blocks<2>(precision, threads, smem); break;
-        case 4: per_sm = resident_blocks<4>(precision, threads, smem); break;
-        case 8: per_sm = resident_blocks<8>(precision, threads, smem); break;
-        default: per_sm = resident_blocks<16>(precision, threads, smem); break;
+        case 1: per_sm = resident_blocks<1>(precision, threads, n); break;
+        case 2: per_sm = resident_blocks<2>(precision, threads, n); break;
+        default: per_sm = resident_blocks<4>(precision, threads, n); break;
     }
     return sms * per_sm;
 }
 
 size_t sample_2d_scratch_bytes(int n, int precision, int blocks) {
-    if (precision != USFFT_MIXED) return 0;
+    if (precision == USFFT_FP64) return 0;
     return sizeof(double) * 2 * (size_t)n * (n + 1) * (size_t)blocks;
 }
 
 template <int NPT>
-static cudaError_t launch_npt(const Pcg2dArgs& a, int precision, int blocks, int threads, size_t smem,
-                              cudaStream_t s) {
+static cudaError_t launch_npt(const Pcg2dArgs& a, int precision, int blocks, int threads, cudaStream_t s) {
+    if (precision == USFFT_MIXED) return launch_dst_npt<NPT>(a, blocks, threads, s);
+    const size_t smem = smem_bytes(a.n, a.ns.d);
     cudaError_t e;
-    if (precision == USFFT_MIXED) {
+    if (precision == USFFT_MIXED_JACOBI) {
         e = cudaFuncSetAttribute(pcg2d_mixed_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         pcg2d_mixed_kernel<NPT><<<blocks, threads, smem, s>>>(a);
@@ -451,6 +416,7 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
                              unsigned int* fail_count, unsigned long long* iters_sum, double* scratch,
                              size_t scratch_bytes, cudaStream_t s, int* launches) {
     if (count <= 0) return cudaSuccess;
+    if (n < 1 || n > 63) return cudaErrorInvalidValue;
     Pcg2dArgs a;
     a.ns = ns;
     a.n = n;
@@ -459,7 +425,7 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
     const double h = 1.0 / (double)(n + 1);
     a.rhs = h * h * f;
     a.tol = cg.tol;
-    a.tol_inner = 1e-4;
+    a.tol_inner = cg.precision == USFFT_MIXED ? 1e-5 : 1e-4;
     a.psi = psi;
     a.i0 = i0;
     a.count = count;
@@ -470,21 +436,16 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
     a.scratch = scratch;
     const int G = n * n;
     const int npt = pick_npt(G);
-    int threads = ((G + npt - 1) / npt + 31) / 32 * 32;
-    if (threads > 1024) return cudaErrorInvalidValue;
+    const int threads = ((G + npt - 1) / npt + 31) / 32 * 32;
     int blocks = cg.blocks > 0 ? cg.blocks : sample_2d_default_blocks(n, cg.precision);
     if (blocks > count) blocks = (int)count;
-    if (cg.precision == USFFT_MIXED &&
-        scratch_bytes < sample_2d_scratch_bytes(n, USFFT_MIXED, blocks))
+    if (cg.precision != USFFT_FP64 && scratch_bytes < sample_2d_scratch_bytes(n, cg.precision, blocks))
         return cudaErrorInvalidValue;
-    const size_t smem = smem_bytes(n, ns.d);
     cudaError_t e;
     switch (npt) {
-        case 1: e = launch_npt<1>(a, cg.precision, blocks, threads, smem, s); break;
-        case 2: e = launch_npt<2>(a, cg.precision, blocks, threads, smem, s); break;
-        case 4: e = launch_npt<4>(a, cg.precision, blocks, threads, smem, s); break;
-        case 8: e = launch_npt<8>(a, cg.precision, blocks, threads, smem, s); break;
-        default: e = launch_npt<16>(a, cg.precision, blocks, threads, smem, s); break;
+        case 1: e = launch_npt<1>(a, cg.precision, blocks, threads, s); break;
+        case 2: e = launch_npt<2>(a, cg.precision, blocks, threads, s); break;
+        default: e = launch_npt<4>(a, cg.precision, blocks, threads, s); break;
     }
     if (launches) ++*launches;
     return e;

@@ -1,0 +1,394 @@
+// 2-D sampler, mixed precision with a fast-Poisson preconditioner (the MIXED precision mode).
+//
+// Same discretisation and assembly as k_sample2d.cu (5-point P1 operator K with edge
+// weights w_e = mean of the two adjacent triangle coefficients).  The solve is fp64
+// iterative refinement around an fp32 flexible preconditioned CG:
+//   x = 0, r = b;  repeat:  solve K d = r / ||r|| in fp32 to tol_inner,
+//                           x += ||r|| d (fp64),  r = b - K x with fp64 weights,
+//   until ||r|| <= tol ||b||.
+// Preconditioner: the inverse of the constant-coefficient operator K_0 (w_e = 1), applied
+// exactly through its eigenbasis, the 2-D sine transform (DST-I):
+//   K_0^-1 r = c^2 S ((S R S) o L) S,  S_jk = sin(pi (j+1)(k+1)/(n+1)),  c = 2/(n+1),
+//   L_qp = 1 / (mu_p + mu_q),  mu_k = 2 - 2 cos(pi (k+1)/(n+1)),
+// with R the residual on the n x n grid.  Because every edge weight lies in
+// [min_e w_e, max_e w_e], the preconditioned operator has condition number at most
+// max w / min w, independent of the mesh width, so a handful of iterations reduce the
+// residual by 1e-5 (Jacobi-PCG needs hundreds).  The four n x n matrix products run on
+// the tensor cores (mma.sync m16n8k8, TF32 operands, fp32 accumulation) from shared
+// memory; the preconditioner is then slightly non-symmetric, which the flexible
+// (Polak-Ribiere) beta tolerates.  One CTA owns one system at a time (persistent grid).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "k_pcg_common.cuh"
+#include "usfft_internal.h"
+
+namespace usfft {
+
+struct DstLayout {
+    int n, W, P, LD;
+    size_t o_xh, o_S, o_L, o_Ta, o_Tb, o_wx, o_wy, o_ph, o_sj, o_r64, o_r32, total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline DstLayout dst_layout(int n, int d) {
+    DstLayout L;
+    L.n = n;
+    L.W = n + 2;
+    L.P = (n + 15) / 16 * 16;
+    L.LD = L.P + 4;   // row stride: conflict-free TF32 fragment loads
+    size_t o = 0;
+    L.o_xh = o;  o = align16(o + sizeof(double) * (size_t)L.W * L.W);
+    L.o_S = o;   o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
+    L.o_L = o;   o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
+    L.o_Ta = o;  o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
+    L.o_Tb = o;  o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
+    L.o_wx = o;  o = align16(o + sizeof(float) * (size_t)n * (n + 1));
+    L.o_wy = o;  o = align16(o + sizeof(float) * (size_t)n * (n + 1));
+    L.o_ph = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
+    L.o_sj = o;  o = align16(o + sizeof(double) * (size_t)d);
+    L.o_r64 = o; o = align16(o + sizeof(double) * 36);
+    L.o_r32 = o; o = align16(o + sizeof(float) * 4 * 36);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// C = A B (P x P, row-major, stride LD) on the tensor cores; C o= Lsc if Lsc != nullptr.
+// Each warp takes 16x8 output tiles; fragment layouts of mma.m16n8k8 (TF32):
+//   a0 (g, t) a1 (g+8, t) a2 (g, t+4) a3 (g+8, t+4); b0 (t, g) b1 (t+4, g);
+//   c0 (g, 2t) c1 (g, 2t+1) c2 (g+8, 2t) c3 (g+8, 2t+1),   g = lane/4, t = lane%4.
+__device__ __forceinline__ void gemm_tf32(const float* __restrict__ A, const float* __restrict__ B,
+                                          float* __restrict__ C, const float* __restrict__ Lsc, int P, int LD) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int nt = P / 8, tiles = (P / 16) * nt;
+    for (int tile = warp; tile < tiles; tile += nwarps) {
+        const int m0 = (tile / nt) * 16, n0 = (tile % nt) * 8;
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+        for (int k0 = 0; k0 < P; k0 += 8) {
+            const uint32_t a0 = to_tf32(A[(m0 + g) * LD + k0 + t]);
+            const uint32_t a1 = to_tf32(A[(m0 + g + 8) * LD + k0 + t]);
+            const uint32_t a2 = to_tf32(A[(m0 + g) * LD + k0 + t + 4]);
+            const uint32_t a3 = to_tf32(A[(m0 + g + 8) * LD + k0 + t + 4]);
+            const uint32_t b0 = to_tf32(B[(k0 + t) * LD + n0 + g]);
+            const uint32_t b1 = to_tf32(B[(k0 + t + 4) * LD + n0 + g]);
+            asm volatile(
+                "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+                "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+        const int r0 = (m0 + g) * LD + n0 + 2 * t, r1 = r0 + 8 * LD;
+        if (Lsc) {
+            c0 *= Lsc[r0];
+            c1 *= Lsc[r0 + 1];
+            c2 *= Lsc[r1];
+            c3 *= Lsc[r1 + 1];
+        }
+        C[r0] = c0;
+        C[r0 + 1] = c1;
+        C[r1] = c2;
+        C[r1 + 1] = c3;
+    }
+}
+
+// z = K_0^-1 r for the NPT nodes of this thread (r written into Ta first).
+template <int NPT>
+__device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[NPT], float* Ta, float* Tb,
+                                              const float* S, const float* Li, int n, int P, int LD) {
+    const int G = n * n, T = blockDim.x, tid = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int g = tid + k * T;
+        if (g < G) Ta[(g / n) * LD + (g % n)] = r[k];
+    }
+    __syncthreads();
+    gemm_tf32(S, Ta, Tb, nullptr, P, LD);
+    __syncthreads();
+    gemm_tf32(Tb, S, Ta, Li, P, LD);
+    __syncthreads();
+    gemm_tf32(S, Ta, Tb, nullptr, P, LD);
+    __syncthreads();
+    gemm_tf32(Tb, S, Ta, nullptr, P, LD);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int g = tid + k * T;
+        z[k] = (g < G) ? Ta[(g / n) * LD + (g % n)] : 0.f;
+    }
+}
+
+// three block sums in one pass; thread 0 also forms ratio = (s0 - s1) / den
+__device__ __forceinline__ void block_sum3(float v0, float v1, float v2, float den, float* buf, float& s0,
+                                           float& s2, float& ratio) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    if (lane == 0) {
+        buf[warp] = v0;
+        buf[36 + warp] = v1;
+        buf[72 + warp] = v2;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float a = lane < nw ? buf[lane] : 0.f;
+        float b = lane < nw ? buf[36 + lane] : 0.f;
+        float c = lane < nw ? buf[72 + lane] : 0.f;
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_sum(c);
+        if (lane == 0) {
+            buf[32] = a;
+            buf[33] = c;
+            buf[34] = (a - b) / den;
+        }
+    }
+    __syncthreads();
+    s0 = buf[32];
+    s2 = buf[33];
+    ratio = buf[34];
+}
+
+template <int NPT>
+__global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_constant__ Pcg2dArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = a.n, G = n * n, n1 = n + 1;
+    const DstLayout Lo = dst_layout(n, a.ns.d);
+    const int W = Lo.W, P = Lo.P, LD = Lo.LD;
+    double* xh = reinterpret_cast<double*>(smraw + Lo.o_xh);
+    float* S = reinterpret_cast<float*>(smraw + Lo.o_S);
+    float* Li = reinterpret_cast<float*>(smraw + Lo.o_L);
+    float* Ta = reinterpret_cast<float*>(smraw + Lo.o_Ta);
+    float* Tb = reinterpret_cast<float*>(smraw + Lo.o_Tb);
+    float* wx = reinterpret_cast<float*>(smraw + Lo.o_wx);
+    float* wy = reinterpret_cast<float*>(smraw + Lo.o_wy);
+    float* ph = reinterpret_cast<float*>(smraw + Lo.o_ph);
+    double* sj = reinterpret_cast<double*>(smraw + Lo.o_sj);
+    double* red64 = reinterpret_cast<double*>(smraw + Lo.o_r64);
+    float* red32 = reinterpret_cast<float*>(smraw + Lo.o_r32);
+    const int T = blockDim.x, tid = threadIdx.x;
+    double* w64x = a.scratch + (size_t)blockIdx.x * 2 * n * n1;
+    double* w64y = w64x + n * n1;
+
+    // per CTA: the sine matrix and the scaled inverse eigenvalues, zero padded to P x P
+    const double c2 = 4.0 / ((double)n1 * n1);
+    for (int e = tid; e < P * LD; e += T) {
+        const int j = e / LD, k = e % LD;
+        float sv = 0.f, lv = 0.f;
+        if (j < n && k < n) {
+            sv = (float)sinpi((double)((j + 1) * (k + 1)) / (double)n1);
+            const double sj1 = sinpi((double)(k + 1) / (2.0 * n1)), sj2 = sinpi((double)(j + 1) / (2.0 * n1));
+            lv = (float)(c2 / (4.0 * sj1 * sj1 + 4.0 * sj2 * sj2));
+        }
+        S[e] = sv;
+        Li[e] = lv;
+        Ta[e] = 0.f;
+        Tb[e] = 0.f;
+    }
+    __syncthreads();
+
+    for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
+        const int64_t i = a.i0 + sys;
+        // ---- assembly: fp64 weights to the CTA's scratch slot, fp32 copies to shared memory ----
+        for (int j = tid; j < a.ns.d; j += T) sj[j] = node_sin2(a.ns, j, i);
+        __syncthreads();
+        const bool logn = a.coef_model == USFFT_COEF_LOGNORMAL_SIN;
+        const int sq = n1 * n1, d = a.ns.d;
+        double* low = xh;                       // lower-triangle coefficients (temporary)
+        for (int e = tid; e < sq; e += T) {
+            double acc = 0.0;
+            for (int j = 0; j < d; ++j) acc = fma(__ldg(a.psi + (size_t)j * 2 * sq + e), sj[j], acc);
+            low[e] = logn ? exp(acc) : 1.0 + acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < sq; e += T) {
+            const int Pp = e % n1, Q = e / n1;
+            double acc = 0.0;
+            for (int j = 0; j < d; ++j) acc = fma(__ldg(a.psi + (size_t)j * 2 * sq + sq + e), sj[j], acc);
+            const double au = logn ? exp(acc) : 1.0 + acc;
+            if (Q < n) {
+                const double w = 0.5 * (low[(Q + 1) * n1 + Pp] + au);
+                w64x[Q * n1 + Pp] = w;
+                wx[Q * n1 + Pp] = (float)w;
+            }
+            if (Pp >= 1) {
+                const double w = 0.5 * (au + low[Q * n1 + (Pp - 1)]);
+                w64y[Q * n + (Pp - 1)] = w;
+                wy[Q * n + (Pp - 1)] = (float)w;
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < W * W; e += T) {
+            xh[e] = 0.0;
+            ph[e] = 0.f;
+        }
+        __syncthreads();
+
+        // ---- fp64 iterative refinement around fp32 flexible PCG ----
+        const double b = a.rhs;
+        const double rr0 = (double)G * b * b;
+        const double stop = a.tol * a.tol * rr0;
+        double r64[NPT];
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) r64[k] = (tid + k * T < G) ? b : 0.0;
+        double rr64 = rr0;
+        int total = 0, outer = 0;
+        while (rr64 > stop && outer < 16) {
+            const double nr = sqrt(rr64);
+            const float inv = (float)(1.0 / nr);
+            float d32[NPT], r32[NPT], p32[NPT], z32[NPT], q32[NPT];
+            float rl = 0.f;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                d32[k] = 0.f;
+                r32[k] = (float)r64[k] * inv;
+                rl = fmaf(r32[k], r32[k], rl);
+            }
+            apply_precond<NPT>(r32, z32, Ta, Tb, S, Li, n, P, LD);
+            float rz_l = 0.f;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int g = tid + k * T;
+                p32[k] = z32[k];
+                rz_l = fmaf(r32[k], z32[k], rz_l);
+                if (g < G) ph[((g / n) + 1) * W + (g % n) + 1] = p32[k];
+            }
+            float rz, rr, unused;
+            block_sum3(rz_l, 0.f, rl, 1.f, red32, rz, rr, unused);
+            const float istop = (float)(a.tol_inner * a.tol_inner) * rr;
+            int it = 0;
+            while (rr > istop && it < a.max_iters) {
+                float pq_l = 0.f;
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    const int g = tid + k * T;
+                    q32[k] = 0.f;
+                    if (g < G) {
+                        const int pp = g % n, qq = g / n, h = (qq + 1) * W + pp + 1;
+                        const float wl = wx[qq * n1 + pp], wr = wx[qq * n1 + pp + 1];
+                        const float wd = wy[qq * n + pp], wu = wy[(qq + 1) * n + pp];
+                        float acc = wl * ph[h - 1];
+                        acc = fmaf(wr, ph[h + 1], acc);
+                        acc = fmaf(wd, ph[h - W], acc);
+                        acc = fmaf(wu, ph[h + W], acc);
+                        q32[k] = fmaf(wl + wr + wd + wu, p32[k], -acc);
+                        pq_l = fmaf(p32[k], q32[k], pq_l);
+                    }
+                }
+                float pq, alpha;
+                block_sum_ratio<float, NUM_OVER_SUM>(pq_l, rz, red32 + 108, pq, alpha);
+                float rold[NPT];
+                float rn_l = 0.f;
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    d32[k] = fmaf(alpha, p32[k], d32[k]);
+                    rold[k] = r32[k];
+                    r32[k] = fmaf(-alpha, q32[k], r32[k]);
+                    rn_l = fmaf(r32[k], r32[k], rn_l);
+                }
+                apply_precond<NPT>(r32, z32, Ta, Tb, S, Li, n, P, LD);
+                float zr_l = 0.f, zro_l = 0.f;
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    zr_l = fmaf(z32[k], r32[k], zr_l);
+                    zro_l = fmaf(z32[k], rold[k], zro_l);
+                }
+                float rz_new, beta;
+                block_sum3(zr_l, zro_l, rn_l, rz, red32, rz_new, rr, beta);   // flexible beta
+                rz = rz_new;
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    const int g = tid + k * T;
+                    p32[k] = fmaf(beta, p32[k], z32[k]);
+                    if (g < G) ph[((g / n) + 1) * W + (g % n) + 1] = p32[k];
+                }
+                __syncthreads();
+                ++it;
+            }
+            total += it;
+            // x += ||r|| d in fp64, then the fp64 residual with the fp64 weights
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int g = tid + k * T;
+                if (g < G) {
+                    const int h = ((g / n) + 1) * W + (g % n) + 1;
+                    xh[h] = fma(nr, (double)d32[k], xh[h]);
+                }
+            }
+            __syncthreads();
+            double rl64 = 0.0;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int g = tid + k * T;
+                r64[k] = 0.0;
+                if (g < G) {
+                    const int pp = g % n, qq = g / n, h = (qq + 1) * W + pp + 1;
+                    const double wl = __ldcg(w64x + qq * n1 + pp), wr = __ldcg(w64x + qq * n1 + pp + 1);
+                    const double wd = __ldcg(w64y + qq * n + pp), wu = __ldcg(w64y + (qq + 1) * n + pp);
+                    double acc = wl * xh[h - 1];
+                    acc = fma(wr, xh[h + 1], acc);
+                    acc = fma(wd, xh[h - W], acc);
+                    acc = fma(wu, xh[h + W], acc);
+                    r64[k] = b - fma(wl + wr + wd + wu, xh[h], -acc);
+                    rl64 = fma(r64[k], r64[k], rl64);
+                }
+            }
+            double unused64;
+            block_sum_ratio<double, SUM_OVER_DEN>(rl64, 1.0, red64, rr64, unused64);
+            ++outer;
+        }
+        double* out = a.U + (size_t)sys * G;
+        for (int g = tid; g < G; g += T) out[g] = xh[((g / n) + 1) * W + (g % n) + 1];
+        if (tid == 0) {
+            if (a.iters_out) a.iters_out[sys] = total;
+            if (a.iters_sum) atomicAdd(a.iters_sum, (unsigned long long)total);
+            if (rr64 > stop && a.fail_count) atomicAdd(a.fail_count, 1u);
+        }
+        __syncthreads();
+    }
+}
+
+size_t dst_smem_bytes(int n, int d) { return dst_layout(n, d).total; }
+
+template <int NPT>
+cudaError_t launch_dst_npt(const Pcg2dArgs& a, int blocks, int threads, cudaStream_t s) {
+    const size_t smem = dst_smem_bytes(a.n, a.ns.d);
+    cudaError_t e = cudaFuncSetAttribute(pcg2d_mixed_dst_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    pcg2d_mixed_dst_kernel<NPT><<<blocks, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NPT>
+int dst_resident_blocks(int threads, int d, int n) {
+    const size_t smem = dst_smem_bytes(n, d);
+    int per_sm = 0;
+    cudaError_t e = cudaFuncSetAttribute(pcg2d_mixed_dst_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg2d_mixed_dst_kernel<NPT>,
+                                                                            threads, smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm < 1 ? 1 : per_sm;
+}
+
+template cudaError_t launch_dst_npt<1>(const Pcg2dArgs&, int, int, cudaStream_t);
+template cudaError_t launch_dst_npt<2>(const Pcg2dArgs&, int, int, cudaStream_t);
+template cudaError_t launch_dst_npt<4>(const Pcg2dArgs&, int, int, cudaStream_t);
+template int dst_resident_blocks<1>(int, int, int);
+template int dst_resident_blocks<2>(int, int, int);
+template int dst_resident_blocks<4>(int, int, int);
+
+}  // namespace usfft

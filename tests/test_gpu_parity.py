@@ -141,7 +141,7 @@ def test_trigpoly_two_pass_fft(B):
     plan.close()
 
 
-@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED])
+@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED, W.PRECISION_MIXED_JACOBI])
 def test_small_2d_matches_oracle(B, precision):
     w = W.with_precision(W.small_2d(n=15, d=4, seed=2, N=6, s=30), precision)
     plan = B.Plan(w.problem, w.params)
@@ -153,9 +153,10 @@ def test_small_2d_matches_oracle(B, precision):
 
 
 def test_2d_ragged_mesh_sizes(B):
-    # n = 9 (81 nodes: one partial warp) and n = 33 (1089 nodes: two nodes per thread, ragged)
-    for n in (9, 33):
-        w = W.small_2d(n=n, d=3, seed=5, N=4, s=20)
+    # n = 9 (81 nodes: one partial warp) and n = 33 (1089 nodes: two nodes per thread, ragged;
+    # DST tiles padded from 33 to 48), both precisions
+    for n, prec in ((9, W.PRECISION_FP64), (33, W.PRECISION_FP64), (9, W.PRECISION_MIXED), (33, W.PRECISION_MIXED)):
+        w = W.with_precision(W.small_2d(n=n, d=3, seed=5, N=4, s=20), prec)
         plan = B.Plan(w.problem, w.params)
         run = OracleRun(w.problem, w.params, keep=True)
         for t in range(1, 3):
@@ -163,10 +164,11 @@ def test_2d_ragged_mesh_sizes(B):
         plan.close()
 
 
-def test_c2_shape_first_increments(B):
+@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED])
+def test_c2_shape_first_increments(B, precision):
     # the 2-D workload at full mesh size (63x63 interior, d = 10): increment 1 in full,
     # increment 2 in full (about 1000 oracle solves)
-    w = W.c2(1)
+    w = W.with_precision(W.c2(1), precision)
     plan = B.Plan(w.problem, w.params)
     run = OracleRun(w.problem, w.params, keep=True)
     compare_increment(plan, run, "c2 t=1", exact=False)

@@ -29,6 +29,7 @@ COEF_LOGNORMAL_SIN = 2  # a = exp(sum_j c j^-mu psi_j(x) sin(2 pi y_j))
 
 PRECISION_FP64 = 0
 PRECISION_MIXED = 1
+PRECISION_MIXED_JACOBI = 2
 
 
 @dataclass
