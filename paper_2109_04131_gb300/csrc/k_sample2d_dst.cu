@@ -45,8 +45,8 @@ __host__ __device__ inline DstLayout dst_layout(int n, int d) {
     L.o_L = o;   o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
     L.o_Ta = o;  o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
     L.o_Tb = o;  o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
-    L.o_wx = o;  o = align16(o + sizeof(float) * (size_t)n * (n + 1));
-    L.o_wy = o;  o = align16(o + sizeof(float) * (size_t)n * (n + 1));
+    L.o_wx = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
+    L.o_wy = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
     L.o_ph = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
     L.o_sj = o;  o = align16(o + sizeof(double) * (size_t)d);
     L.o_r64 = o; o = align16(o + sizeof(double) * 36);
@@ -55,11 +55,9 @@ __host__ __device__ inline DstLayout dst_layout(int n, int d) {
     return L;
 }
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
+// TF32 operand: the fp32 bit pattern itself (the tensor core ignores the low 13 mantissa
+// bits, i.e. truncates), which is accurate enough for a preconditioner.
+__device__ __forceinline__ uint32_t to_tf32(float x) { return __float_as_uint(x); }
 
 // C = A B (P x P, row-major, stride LD) on the tensor cores; C o= Lsc if Lsc != nullptr.
 // Each warp takes 16x8 output tiles; fragment layouts of mma.m16n8k8 (TF32):
@@ -100,16 +98,14 @@ __device__ __forceinline__ void gemm_tf32(const float* __restrict__ A, const flo
     }
 }
 
-// z = K_0^-1 r for the NPT nodes of this thread (r written into Ta first).
+// z = K_0^-1 r for the NPT nodes of this thread (r written into Ta first).  ti[k] is the
+// node's position in the P x LD transform grid (-1: no node).
 template <int NPT>
-__device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[NPT], float* Ta, float* Tb,
-                                              const float* S, const float* Li, int n, int P, int LD) {
-    const int G = n * n, T = blockDim.x, tid = threadIdx.x;
+__device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[NPT], const int (&ti)[NPT],
+                                              float* Ta, float* Tb, const float* S, const float* Li, int P, int LD) {
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const int g = tid + k * T;
-        if (g < G) Ta[(g / n) * LD + (g % n)] = r[k];
-    }
+    for (int k = 0; k < NPT; ++k)
+        if (ti[k] >= 0) Ta[ti[k]] = r[k];
     __syncthreads();
     gemm_tf32(S, Ta, Tb, nullptr, P, LD);
     __syncthreads();
@@ -120,10 +116,7 @@ __device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[
     gemm_tf32(Tb, S, Ta, nullptr, P, LD);
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const int g = tid + k * T;
-        z[k] = (g < G) ? Ta[(g / n) * LD + (g % n)] : 0.f;
-    }
+    for (int k = 0; k < NPT; ++k) z[k] = (ti[k] >= 0) ? Ta[ti[k]] : 0.f;
 }
 
 // three block sums in one pass; thread 0 also forms ratio = (s0 - s1) / den
@@ -158,6 +151,25 @@ __device__ __forceinline__ void block_sum3(float v0, float v1, float v2, float d
     ratio = buf[34];
 }
 
+// block-wide fp64 sum; thread 0 also takes its square root (both broadcast)
+__device__ __forceinline__ void block_sum_sqrt(double v, double* buf, double& sum, double& root) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) buf[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double w = lane < nw ? buf[lane] : 0.0;
+        w = warp_sum(w);
+        if (lane == 0) {
+            buf[32] = w;
+            buf[33] = sqrt(w);
+        }
+    }
+    __syncthreads();
+    sum = buf[32];
+    root = buf[33];
+}
+
 template <int NPT>
 __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_constant__ Pcg2dArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -169,31 +181,53 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
     float* Li = reinterpret_cast<float*>(smraw + Lo.o_L);
     float* Ta = reinterpret_cast<float*>(smraw + Lo.o_Ta);
     float* Tb = reinterpret_cast<float*>(smraw + Lo.o_Tb);
-    float* wx = reinterpret_cast<float*>(smraw + Lo.o_wx);
-    float* wy = reinterpret_cast<float*>(smraw + Lo.o_wy);
+    float* wl = reinterpret_cast<float*>(smraw + Lo.o_wx);   // weight of the edge to the left of halo node h
+    float* wd = reinterpret_cast<float*>(smraw + Lo.o_wy);   // weight of the edge below halo node h
     float* ph = reinterpret_cast<float*>(smraw + Lo.o_ph);
     double* sj = reinterpret_cast<double*>(smraw + Lo.o_sj);
     double* red64 = reinterpret_cast<double*>(smraw + Lo.o_r64);
     float* red32 = reinterpret_cast<float*>(smraw + Lo.o_r32);
     const int T = blockDim.x, tid = threadIdx.x;
-    double* w64x = a.scratch + (size_t)blockIdx.x * 2 * n * n1;
-    double* w64y = w64x + n * n1;
+    double* w64l = a.scratch + (size_t)blockIdx.x * 2 * W * W;   // fp64 weights, same halo layout
+    double* w64d = w64l + W * W;
 
-    // per CTA: the sine matrix and the scaled inverse eigenvalues, zero padded to P x P
-    const double c2 = 4.0 / ((double)n1 * n1);
+    // per-thread node indices: halo position hi[k], transform-grid position ti[k]
+    int hi[NPT], ti[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int g = tid + k * T;
+        hi[k] = ti[k] = -1;
+        if (g < G) {
+            const int pp = g % n, qq = g / n;
+            hi[k] = (qq + 1) * W + pp + 1;
+            ti[k] = qq * LD + pp;
+        }
+    }
+    // per CTA: the sine matrix and the scaled inverse eigenvalues (fp32), zero padded
+    const float c2 = 4.0f / ((float)n1 * (float)n1);
     for (int e = tid; e < P * LD; e += T) {
         const int j = e / LD, k = e % LD;
         float sv = 0.f, lv = 0.f;
         if (j < n && k < n) {
-            sv = (float)sinpi((double)((j + 1) * (k + 1)) / (double)n1);
-            const double sj1 = sinpi((double)(k + 1) / (2.0 * n1)), sj2 = sinpi((double)(j + 1) / (2.0 * n1));
-            lv = (float)(c2 / (4.0 * sj1 * sj1 + 4.0 * sj2 * sj2));
+            sv = sinpif((float)((j + 1) * (k + 1)) / (float)n1);
+            const float s1 = sinpif((float)(k + 1) / (2.0f * n1)), s2 = sinpif((float)(j + 1) / (2.0f * n1));
+            lv = c2 / (4.0f * s1 * s1 + 4.0f * s2 * s2);
         }
         S[e] = sv;
         Li[e] = lv;
         Ta[e] = 0.f;
         Tb[e] = 0.f;
     }
+    for (int e = tid; e < W * W; e += T) {
+        wl[e] = 0.f;
+        wd[e] = 0.f;
+        w64l[e] = 0.0;
+        w64d[e] = 0.0;
+    }
+    const double b = a.rhs;
+    const double rr0 = (double)G * b * b;
+    const double stop = a.tol * a.tol * rr0;
+    const double nr0 = sqrt(rr0);
     __syncthreads();
 
     for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
@@ -215,15 +249,17 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
             double acc = 0.0;
             for (int j = 0; j < d; ++j) acc = fma(__ldg(a.psi + (size_t)j * 2 * sq + sq + e), sj[j], acc);
             const double au = logn ? exp(acc) : 1.0 + acc;
-            if (Q < n) {
+            if (Q < n) {            // edge (Pp,Q+1)-(Pp+1,Q+1): left of node (Pp+1,Q+1)
                 const double w = 0.5 * (low[(Q + 1) * n1 + Pp] + au);
-                w64x[Q * n1 + Pp] = w;
-                wx[Q * n1 + Pp] = (float)w;
+                const int h = (Q + 1) * W + Pp + 1;
+                w64l[h] = w;
+                wl[h] = (float)w;
             }
-            if (Pp >= 1) {
+            if (Pp >= 1) {          // edge (Pp,Q)-(Pp,Q+1): below node (Pp,Q+1)
                 const double w = 0.5 * (au + low[Q * n1 + (Pp - 1)]);
-                w64y[Q * n + (Pp - 1)] = w;
-                wy[Q * n + (Pp - 1)] = (float)w;
+                const int h = (Q + 1) * W + Pp;
+                w64d[h] = w;
+                wd[h] = (float)w;
             }
         }
         __syncthreads();
@@ -231,19 +267,19 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
             xh[e] = 0.0;
             ph[e] = 0.f;
         }
+        float dg[NPT];
+#pragma unroll
+        for (int k = 0; k < NPT; ++k)
+            dg[k] = (hi[k] >= 0) ? wl[hi[k]] + wl[hi[k] + 1] + wd[hi[k]] + wd[hi[k] + W] : 0.f;
         __syncthreads();
 
         // ---- fp64 iterative refinement around fp32 flexible PCG ----
-        const double b = a.rhs;
-        const double rr0 = (double)G * b * b;
-        const double stop = a.tol * a.tol * rr0;
         double r64[NPT];
 #pragma unroll
-        for (int k = 0; k < NPT; ++k) r64[k] = (tid + k * T < G) ? b : 0.0;
-        double rr64 = rr0;
+        for (int k = 0; k < NPT; ++k) r64[k] = (hi[k] >= 0) ? b : 0.0;
+        double rr64 = rr0, nr = nr0;
         int total = 0, outer = 0;
         while (rr64 > stop && outer < 16) {
-            const double nr = sqrt(rr64);
             const float inv = (float)(1.0 / nr);
             float d32[NPT], r32[NPT], p32[NPT], z32[NPT], q32[NPT];
             float rl = 0.f;
@@ -253,14 +289,13 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                 r32[k] = (float)r64[k] * inv;
                 rl = fmaf(r32[k], r32[k], rl);
             }
-            apply_precond<NPT>(r32, z32, Ta, Tb, S, Li, n, P, LD);
+            apply_precond<NPT>(r32, z32, ti, Ta, Tb, S, Li, P, LD);
             float rz_l = 0.f;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
-                const int g = tid + k * T;
                 p32[k] = z32[k];
                 rz_l = fmaf(r32[k], z32[k], rz_l);
-                if (g < G) ph[((g / n) + 1) * W + (g % n) + 1] = p32[k];
+                if (hi[k] >= 0) ph[hi[k]] = p32[k];
             }
             float rz, rr, unused;
             block_sum3(rz_l, 0.f, rl, 1.f, red32, rz, rr, unused);
@@ -270,17 +305,14 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                 float pq_l = 0.f;
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
-                    const int g = tid + k * T;
                     q32[k] = 0.f;
-                    if (g < G) {
-                        const int pp = g % n, qq = g / n, h = (qq + 1) * W + pp + 1;
-                        const float wl = wx[qq * n1 + pp], wr = wx[qq * n1 + pp + 1];
-                        const float wd = wy[qq * n + pp], wu = wy[(qq + 1) * n + pp];
-                        float acc = wl * ph[h - 1];
-                        acc = fmaf(wr, ph[h + 1], acc);
-                        acc = fmaf(wd, ph[h - W], acc);
-                        acc = fmaf(wu, ph[h + W], acc);
-                        q32[k] = fmaf(wl + wr + wd + wu, p32[k], -acc);
+                    const int h = hi[k];
+                    if (h >= 0) {
+                        float acc = wl[h] * ph[h - 1];
+                        acc = fmaf(wl[h + 1], ph[h + 1], acc);
+                        acc = fmaf(wd[h], ph[h - W], acc);
+                        acc = fmaf(wd[h + W], ph[h + W], acc);
+                        q32[k] = fmaf(dg[k], p32[k], -acc);
                         pq_l = fmaf(p32[k], q32[k], pq_l);
                     }
                 }
@@ -295,7 +327,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                     r32[k] = fmaf(-alpha, q32[k], r32[k]);
                     rn_l = fmaf(r32[k], r32[k], rn_l);
                 }
-                apply_precond<NPT>(r32, z32, Ta, Tb, S, Li, n, P, LD);
+                apply_precond<NPT>(r32, z32, ti, Ta, Tb, S, Li, P, LD);
                 float zr_l = 0.f, zro_l = 0.f;
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
@@ -307,9 +339,8 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                 rz = rz_new;
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
-                    const int g = tid + k * T;
                     p32[k] = fmaf(beta, p32[k], z32[k]);
-                    if (g < G) ph[((g / n) + 1) * W + (g % n) + 1] = p32[k];
+                    if (hi[k] >= 0) ph[hi[k]] = p32[k];
                 }
                 __syncthreads();
                 ++it;
@@ -317,33 +348,26 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
             total += it;
             // x += ||r|| d in fp64, then the fp64 residual with the fp64 weights
 #pragma unroll
-            for (int k = 0; k < NPT; ++k) {
-                const int g = tid + k * T;
-                if (g < G) {
-                    const int h = ((g / n) + 1) * W + (g % n) + 1;
-                    xh[h] = fma(nr, (double)d32[k], xh[h]);
-                }
-            }
+            for (int k = 0; k < NPT; ++k)
+                if (hi[k] >= 0) xh[hi[k]] = fma(nr, (double)d32[k], xh[hi[k]]);
             __syncthreads();
             double rl64 = 0.0;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
-                const int g = tid + k * T;
                 r64[k] = 0.0;
-                if (g < G) {
-                    const int pp = g % n, qq = g / n, h = (qq + 1) * W + pp + 1;
-                    const double wl = __ldcg(w64x + qq * n1 + pp), wr = __ldcg(w64x + qq * n1 + pp + 1);
-                    const double wd = __ldcg(w64y + qq * n + pp), wu = __ldcg(w64y + (qq + 1) * n + pp);
-                    double acc = wl * xh[h - 1];
-                    acc = fma(wr, xh[h + 1], acc);
-                    acc = fma(wd, xh[h - W], acc);
-                    acc = fma(wu, xh[h + W], acc);
-                    r64[k] = b - fma(wl + wr + wd + wu, xh[h], -acc);
+                const int h = hi[k];
+                if (h >= 0) {
+                    const double w0 = __ldcg(w64l + h), w1 = __ldcg(w64l + h + 1);
+                    const double w2 = __ldcg(w64d + h), w3 = __ldcg(w64d + h + W);
+                    double acc = w0 * xh[h - 1];
+                    acc = fma(w1, xh[h + 1], acc);
+                    acc = fma(w2, xh[h - W], acc);
+                    acc = fma(w3, xh[h + W], acc);
+                    r64[k] = b - fma(w0 + w1 + w2 + w3, xh[h], -acc);
                     rl64 = fma(r64[k], r64[k], rl64);
                 }
             }
-            double unused64;
-            block_sum_ratio<double, SUM_OVER_DEN>(rl64, 1.0, red64, rr64, unused64);
+            block_sum_sqrt(rl64, red64, rr64, nr);
             ++outer;
         }
         double* out = a.U + (size_t)sys * G;
