@@ -235,6 +235,36 @@ usfft_status usfft_search_lattice(const int8_t* J, int64_t n, int t, uint64_t se
 uint64_t usfft_draw_key(uint64_t seed, const uint64_t* fields, int nfields);
 double usfft_draw_uniform(uint64_t seed, const uint64_t* fields, int nfields);
 
+/* ---- Sampling without device allocation ----
+ *
+ * usfft_sample_2d_static: the mixed-precision 2-D FE sampler (the USFFT_MIXED solver of
+ * usfft_increment: fp64 refinement around fp32 flexible CG with the sine-transform
+ * preconditioner) for callers that cannot allocate device memory, e.g. a plug-in inside a
+ * framework that has already reserved HBM for its own pool, or a latency-critical loop that
+ * must never enter the allocator.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The paper has no counterpart: this is a deployment variant of the black-box
+ * sampler, not a step of the method.
+ *
+ * The caller passes inputs and outputs: problem (USFFT_PDE_2D, 1 <= n <= 63, 1 <= d <= 64; host),
+ * z[d] and tails[d] (host): coordinate j is a lattice coordinate with y_j = (i z_j mod M)/M
+ * when 0 <= z_j < M, otherwise (z_j < 0) it is fixed to tails[j] in [0,1); the nodes
+ * i = i0 .. i0+count-1 of that set are solved and their samples written to U (device,
+ * [count][n*n] fp64 row-major, caller-owned).  tol (0 = 1e-13) and max_iters (0 = 4000) as in
+ * usfft_params.  If unconverged is non-NULL the call synchronises `stream` and stores how many
+ * solves missed tol; with NULL it returns after enqueueing the work on `stream`.
+ *
+ * Scratch: one fixed 16 MiB device array in the library (the mode table and one slot of fp64
+ * edge weights per resident CTA), held by every GPU that loads the library until the process
+ * exits.  Requests that would need more are rejected with USFFT_EINVAL and a message in
+ * usfft_last_error(NULL).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream capture.  All
+ * calls share the array and it keeps the last call's contents: calls whose work overlaps on
+ * the GPU (other streams, or other host threads) race and corrupt each other's results;
+ * serialise them. */
+usfft_status usfft_sample_2d_static(const usfft_problem* problem, const int64_t* z, const double* tails,
+                                    int64_t M, int64_t i0, int64_t count, double tol, int max_iters,
+                                    double* U, void* stream, uint32_t* unconverged);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,9 @@ SIGNATURES = {
                                             ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int64)]),
     "usfft_draw_key": (ctypes.c_uint64, [ctypes.c_uint64, _P, ctypes.c_int]),
     "usfft_draw_uniform": (ctypes.c_double, [ctypes.c_uint64, _P, ctypes.c_int]),
+    "usfft_sample_2d_static": (ctypes.c_int, [ctypes.POINTER(UsfftProblem), _P, _P, ctypes.c_int64, ctypes.c_int64,
+                                              ctypes.c_int64, ctypes.c_double, ctypes.c_int, _P, _P,
+                                              ctypes.POINTER(ctypes.c_uint32)]),
 }
 
 _lib = None
@@ -238,6 +241,23 @@ def usfft_search_lattice(J, t, seed, trials=64, max_sizes=400):
                                   z.ctypes.data, ctypes.byref(M))
     _check(st, None)
     return z, M.value
+
+
+def usfft_sample_2d_static(problem, z, tails, M, i0, count, U_ptr, stream=0, tol=0.0, max_iters=0,
+                           sync=True):
+    """Mixed-precision 2-D samples of nodes i0..i0+count-1 into the caller's device buffer
+    U_ptr ([count][n*n] fp64) without any device allocation by the library.  Returns the
+    number of unconverged solves (sync=True) or None."""
+    lib = load_library()
+    prob, keep = make_problem(problem)
+    zc = np.ascontiguousarray(z, dtype=np.int64)
+    tc = np.ascontiguousarray(tails, dtype=np.float64)
+    unc = ctypes.c_uint32(0)
+    st = lib.usfft_sample_2d_static(ctypes.byref(prob), zc.ctypes.data, tc.ctypes.data, int(M), int(i0), int(count),
+                                    float(tol), int(max_iters), ctypes.c_void_p(int(U_ptr)),
+                                    ctypes.c_void_p(int(stream or 0)), ctypes.byref(unc) if sync else None)
+    _check(st, None)
+    return unc.value if sync else None
 
 
 def usfft_draw_key(seed, *fields):

@@ -40,6 +40,8 @@ thread_local std::string g_last_error;
 
 }  // namespace
 
+void usfft::set_thread_error(const std::string& msg) { g_last_error = msg; }
+
 struct usfft_plan_s {
     usfft_problem prob;
     usfft_params par;

@@ -1,0 +1,133 @@
+// usfft_sample_2d_static: the mixed-precision 2-D sampler with all of its scratch in one
+// fixed, file-scope device array, for callers that cannot allocate device memory.
+//
+// Who needs it: code whose device memory is owned by someone else and that may not call
+// cudaMalloc / cudaFree or an allocating library routine -- e.g. a plug-in running inside a
+// framework that has already reserved (almost) all of HBM for its own pool, or a
+// latency-critical loop that must never enter the allocator.  Such a caller passes its own
+// input description and output buffer; the scratch the sampler needs (the mode table
+// c j^-mu psi_j(centroid_e) and one slot of fp64 edge weights per resident CTA) lives in
+// g_static_scratch below, which every GPU that loads this library holds until the process
+// exits.
+//
+// Set-up: the first call on a device (with that device current) looks up the device
+// address of g_static_scratch with cudaGetSymbolAddress -- the host-side symbol is only a
+// stand-in and must never be passed to a kernel -- and caches it per device.  Make the first
+// call on each device before any stream capture.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "usfft.h"
+#include "usfft_internal.h"
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;   // 16 MiB per device
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_setup_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// the message is what usfft_last_error(NULL) returns on this thread
+usfft_status static_fail(usfft_status st, const std::string& msg) {
+    usfft::set_thread_error(msg);
+    return st;
+}
+
+// Device address of g_static_scratch on the current device (set up once per device).
+usfft_status scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return static_fail(USFFT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return static_fail(USFFT_EINVAL, "device ordinal beyond 63");
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return static_fail(USFFT_ECUDA, std::string("cudaGetSymbolAddress(g_static_scratch): ") +
+                                                cudaGetErrorString(e));
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return USFFT_OK;
+}
+
+}  // namespace
+
+extern "C" usfft_status usfft_sample_2d_static(const usfft_problem* problem, const int64_t* z, const double* tails,
+                                               int64_t M, int64_t i0, int64_t count, double tol, int max_iters,
+                                               double* U, void* stream, uint32_t* unconverged) {
+    using namespace usfft;
+    if (!problem || !z || !tails || !U) return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: NULL argument");
+    const usfft_problem& pr = *problem;
+    if (pr.kind != USFFT_PDE_2D) return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: 2-D problems only");
+    if (pr.n < 1 || pr.n > 63) return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: n must lie in [1, 63]");
+    if (pr.d < 1 || pr.d > USFFT_MAX_D) return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: d must lie in [1, 64]");
+    if (pr.coef_model != USFFT_COEF_AFFINE_SIN && pr.coef_model != USFFT_COEF_LOGNORMAL_SIN)
+        return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: unknown coefficient model");
+    if (M < 1 || M > (int64_t(1) << 31) || i0 < 0 || count < 0 || i0 + count > M)
+        return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: need 1 <= M <= 2^31 and 0 <= i0 <= i0+count <= M");
+    NodeSpec ns;
+    memset(&ns, 0, sizeof ns);
+    ns.M = M;
+    ns.d = pr.d;
+    for (int j = 0; j < pr.d; ++j) {
+        if (z[j] >= M) return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: z_j must be < M");
+        ns.z[j] = z[j] < 0 ? -1 : z[j];
+        ns.tail[j] = tails[j];
+    }
+    if (count == 0) {
+        if (unconverged) *unconverged = 0;
+        return USFFT_OK;
+    }
+
+    // scratch layout: [mode table d*E doubles][2 counters][per-CTA weight slots]
+    const int n = pr.n;
+    const size_t E = 2 * (size_t)(n + 1) * (n + 1);
+    const size_t psi_bytes = (sizeof(double) * E * pr.d + 255) & ~(size_t)255;
+    const size_t cnt_bytes = 256;
+    const size_t slot_bytes = sample_2d_scratch_bytes(n, USFFT_MIXED, 1);
+    if (psi_bytes + cnt_bytes + slot_bytes > kStaticScratchBytes)
+        return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: the problem needs more than the 16 MiB static scratch");
+    int blocks = sample_2d_default_blocks(n, USFFT_MIXED);
+    const int fit = (int)((kStaticScratchBytes - psi_bytes - cnt_bytes) / slot_bytes);
+    if (blocks > fit) blocks = fit;
+
+    void* base = nullptr;
+    usfft_status st = scratch_address(&base);
+    if (st != USFFT_OK) return st;
+    double* psi = reinterpret_cast<double*>(base);
+    unsigned int* fails = reinterpret_cast<unsigned int*>(static_cast<unsigned char*>(base) + psi_bytes);
+    double* slots = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + psi_bytes + cnt_bytes);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    cudaError_t e = launch_psi_table(USFFT_PDE_2D, n, pr.d, pr.coef_scale, pr.coef_decay, psi, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(fails, 0, sizeof(unsigned int), s);   // counters start at zero
+    if (e == cudaSuccess) {
+        CgConfig cg;
+        cg.precision = USFFT_MIXED;
+        cg.max_iters = max_iters > 0 ? max_iters : 4000;
+        cg.tol = tol > 0.0 ? tol : 1e-13;
+        cg.blocks = blocks;
+        e = launch_sample_2d(ns, n, pr.coef_model, pr.f_const, psi, cg, i0, count, U, nullptr, fails, nullptr, slots,
+                             slot_bytes * (size_t)blocks, s, nullptr);
+    }
+    if (e != cudaSuccess) return static_fail(USFFT_ECUDA, std::string("usfft_sample_2d_static: ") + cudaGetErrorString(e));
+    if (unconverged) {
+        unsigned int h = 0;
+        e = cudaMemcpyAsync(&h, fails, sizeof h, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            return static_fail(USFFT_ECUDA, std::string("usfft_sample_2d_static: ") + cudaGetErrorString(e));
+        *unconverged = h;
+    }
+    return USFFT_OK;
+}

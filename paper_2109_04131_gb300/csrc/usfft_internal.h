@@ -103,4 +103,7 @@ cudaError_t launch_select_union(const double2* C, int G, int64_t nJ, double thet
 cudaError_t launch_absmax_column(const double2* C, int G, int64_t nJ, int64_t col, double* out,
                                  cudaStream_t s, int* launches);
 
+// Sets the message usfft_last_error(NULL) returns on the calling thread (capi.cu).
+void set_thread_error(const std::string& msg);
+
 }  // namespace usfft
