@@ -166,15 +166,16 @@ usfft_status usfft_resume(usfft_plan_t* plan, int t, const int8_t* I, int64_t n,
 /* Stage timing for measurement.  usfft_set_timing(plan, on) resets the accumulators; with
  * timing on, every later increment or replay records a CUDA event pair (on the plan's
  * stream) around each stage launch.  usfft_get_stage_times synchronises the stream and
- * returns, accumulated since the reset, the device time and launch count per stage and
- * the total CG iterations of the 2-D solves. */
+ * returns, accumulated since the reset, the device time and launch count per stage, the
+ * total CG iterations and the total refinement steps of the 2-D solves. */
 #define USFFT_STAGE_SAMPLE 0   /* coefficient assembly + FE solve (the black-box sampler) */
 #define USFFT_STAGE_FFT 1      /* lattice FFT + gather at k.z mod M */
 #define USFFT_STAGE_SELECT 2   /* threshold / top-s~ selection + union */
 typedef struct {
     double ms[3];
     int32_t launches[3];
-    int64_t cg_iters_total;
+    int64_t cg_iters_total;       /* CG iterations (inner iterations in the refinement modes) */
+    int64_t refine_steps_total;   /* fp64 refinement steps (USFFT_MIXED, USFFT_MIXED_JACOBI) */
 } usfft_stage_times;
 usfft_status usfft_set_timing(usfft_plan_t* plan, int on);
 usfft_status usfft_get_stage_times(usfft_plan_t* plan, usfft_stage_times* out);

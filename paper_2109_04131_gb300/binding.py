@@ -50,7 +50,8 @@ class UsfftIncrementInfo(ctypes.Structure):
 
 
 class UsfftStageTimes(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 3), ("launches", ctypes.c_int32 * 3), ("cg_iters_total", ctypes.c_int64)]
+    _fields_ = [("ms", ctypes.c_double * 3), ("launches", ctypes.c_int32 * 3), ("cg_iters_total", ctypes.c_int64),
+                ("refine_steps_total", ctypes.c_int64)]
 
 
 # exported symbols and their signatures (restype, argtypes)
@@ -331,7 +332,7 @@ class Plan:
         names = ("sample", "fft", "select")
         return {"ms": {n: st.ms[i] for i, n in enumerate(names)},
                 "launches": {n: st.launches[i] for i, n in enumerate(names)},
-                "cg_iters_total": st.cg_iters_total}
+                "cg_iters_total": st.cg_iters_total, "refine_steps_total": st.refine_steps_total}
 
     def get_set(self) -> np.ndarray:
         n = ctypes.c_int64(0)

@@ -681,7 +681,7 @@ usfft_status usfft_set_timing(usfft_plan_t* plan, int on) {
     plan->timing = on != 0;
     plan->tev.clear();
     plan->ev_used = 0;
-    CK(cudaMemsetAsync((char*)plan->failc.p + 8, 0, 8, plan->stream));
+    CK(cudaMemsetAsync((char*)plan->failc.p + 8, 0, 16, plan->stream));
     return USFFT_OK;
 }
 
@@ -701,9 +701,10 @@ usfft_status usfft_get_stage_times(usfft_plan_t* plan, usfft_stage_times* out) {
             out->launches[e.first] += 1;
         }
     }
-    unsigned long long it = 0;
-    CK(cudaMemcpy(&it, (char*)plan->failc.p + 8, 8, cudaMemcpyDeviceToHost));
-    out->cg_iters_total = (int64_t)it;
+    unsigned long long it[2] = {0, 0};
+    CK(cudaMemcpy(it, (char*)plan->failc.p + 8, 16, cudaMemcpyDeviceToHost));
+    out->cg_iters_total = (int64_t)it[0];
+    out->refine_steps_total = (int64_t)it[1];
     return USFFT_OK;
 }
 

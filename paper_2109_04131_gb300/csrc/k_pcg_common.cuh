@@ -28,6 +28,7 @@ struct Pcg2dArgs {
     int* iters_out;
     unsigned int* fail_count;
     unsigned long long* iters_sum;   // total CG iterations of the launch (may be NULL)
+    unsigned long long* outer_sum;   // total refinement steps of the launch (mixed; may be NULL)
     double* scratch;       // MIXED: per CTA 2 n (n+1) fp64 scaled weights
 };
 

@@ -329,6 +329,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_kernel(const __grid_constant
         if (tid == 0) {
             if (a.iters_out) a.iters_out[sys] = total;
             if (a.iters_sum) atomicAdd(a.iters_sum, (unsigned long long)total);
+            if (a.outer_sum) atomicAdd(a.outer_sum, (unsigned long long)outer);
             if (rr64 > stop && a.fail_count) atomicAdd(a.fail_count, 1u);
         }
         __syncthreads();
@@ -435,6 +436,7 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
     a.iters_out = iters_out;
     a.fail_count = fail_count;
     a.iters_sum = iters_sum;
+    a.outer_sum = iters_sum ? iters_sum + 1 : nullptr;
     a.scratch = scratch;
     const int G = n * n;
     const int npt = pick_npt(G);

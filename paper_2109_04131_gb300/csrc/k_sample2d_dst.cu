@@ -59,64 +59,91 @@ __host__ __device__ inline DstLayout dst_layout(int n, int d) {
 // bits, i.e. truncates), which is accurate enough for a preconditioner.
 __device__ __forceinline__ uint32_t to_tf32(float x) { return __float_as_uint(x); }
 
-// C = A B (P x P, row-major, stride LD) on the tensor cores; C o= Lsc if Lsc != nullptr.
-// Each warp takes 16x8 output tiles; fragment layouts of mma.m16n8k8 (TF32):
-//   a0 (g, t) a1 (g+8, t) a2 (g, t+4) a3 (g+8, t+4); b0 (t, g) b1 (t+4, g);
-//   c0 (g, 2t) c1 (g, 2t+1) c2 (g+8, 2t) c3 (g+8, 2t+1),   g = lane/4, t = lane%4.
-__device__ __forceinline__ void gemm_tf32(const float* __restrict__ A, const float* __restrict__ B,
+// C = A B on the tensor cores (P x P, stride LD, P a multiple of 16).  A is stored row-major;
+// B is stored TRANSPOSED (Bt[n][k] = B[k][n]) so that the B-fragment loads, like the A loads,
+// hit bank (4 row + col) mod 32 with LD = 4 mod 32 (conflict-free).  C is written row-major
+// (TRANSPOSE_OUT = false) or transposed (true); C o= Lsc (symmetric) if SCALE.
+// Warp tiles are 16 x (8 NC) (one A fragment feeds NC n8 MMAs); fragment layouts of
+// mma.m16n8k8 (TF32): a0 (g, t) a1 (g+8, t) a2 (g, t+4) a3 (g+8, t+4); b0 (k=t, n=g)
+// b1 (k=t+4, n=g); c0 (g, 2t) c1 (g, 2t+1) c2 (g+8, 2t) c3 (g+8, 2t+1); g = lane/4, t = lane%4.
+constexpr int NC = 1;   // n8 tiles per warp tile
+template <bool TRANSPOSE_OUT, bool SCALE>
+__device__ __forceinline__ void gemm_tf32(const float* __restrict__ A, const float* __restrict__ Bt,
                                           float* __restrict__ C, const float* __restrict__ Lsc, int P, int LD) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int nt = P / 8, tiles = (P / 16) * nt;
+    const int nwt = P / (8 * NC);                   // P is a multiple of 16 and of 8 NC
+    const int tiles = (P / 16) * nwt;
     for (int tile = warp; tile < tiles; tile += nwarps) {
-        const int m0 = (tile / nt) * 16, n0 = (tile % nt) * 8;
-        float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+        const int m0 = (tile / nwt) * 16, nb = (tile % nwt) * (8 * NC);
+        float acc[NC][4];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
         for (int k0 = 0; k0 < P; k0 += 8) {
             const uint32_t a0 = to_tf32(A[(m0 + g) * LD + k0 + t]);
             const uint32_t a1 = to_tf32(A[(m0 + g + 8) * LD + k0 + t]);
             const uint32_t a2 = to_tf32(A[(m0 + g) * LD + k0 + t + 4]);
             const uint32_t a3 = to_tf32(A[(m0 + g + 8) * LD + k0 + t + 4]);
-            const uint32_t b0 = to_tf32(B[(k0 + t) * LD + n0 + g]);
-            const uint32_t b1 = to_tf32(B[(k0 + t + 4) * LD + n0 + g]);
-            asm volatile(
-                "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
-                "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
-                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                {
+                    const int n0 = nb + 8 * c;
+                    const uint32_t b0 = to_tf32(Bt[(n0 + g) * LD + k0 + t]);
+                    const uint32_t b1 = to_tf32(Bt[(n0 + g) * LD + k0 + t + 4]);
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+                        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                        : "+f"(acc[c][0]), "+f"(acc[c][1]), "+f"(acc[c][2]), "+f"(acc[c][3])
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+                }
+            }
         }
-        const int r0 = (m0 + g) * LD + n0 + 2 * t, r1 = r0 + 8 * LD;
-        if (Lsc) {
-            c0 *= Lsc[r0];
-            c1 *= Lsc[r0 + 1];
-            c2 *= Lsc[r1];
-            c3 *= Lsc[r1 + 1];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int n0 = nb + 8 * c;
+            const int row0 = m0 + g, row1 = m0 + g + 8, col0 = n0 + 2 * t, col1 = col0 + 1;
+            float v0 = acc[c][0], v1 = acc[c][1], v2 = acc[c][2], v3 = acc[c][3];
+            if (SCALE) {
+                v0 *= Lsc[row0 * LD + col0];
+                v1 *= Lsc[row0 * LD + col1];
+                v2 *= Lsc[row1 * LD + col0];
+                v3 *= Lsc[row1 * LD + col1];
+            }
+            if (TRANSPOSE_OUT) {
+                C[col0 * LD + row0] = v0;
+                C[col1 * LD + row0] = v1;
+                C[col0 * LD + row1] = v2;
+                C[col1 * LD + row1] = v3;
+            } else {
+                C[row0 * LD + col0] = v0;
+                C[row0 * LD + col1] = v1;
+                C[row1 * LD + col0] = v2;
+                C[row1 * LD + col1] = v3;
+            }
         }
-        C[r0] = c0;
-        C[r0 + 1] = c1;
-        C[r1] = c2;
-        C[r1 + 1] = c3;
     }
 }
 
-// z = K_0^-1 r for the NPT nodes of this thread (r written into Ta first).  ti[k] is the
-// node's position in the P x LD transform grid (-1: no node).
+// z = K_0^-1 r for the NPT nodes of this thread.  The transform grid X (rows q, columns p)
+// is kept transposed in Ta (Ta[p][q]), the layout the B operand wants; nid[k] >> 16 = p LD + q
+// of the node (nid[k] = -1: no node).  S is symmetric, so it serves as A and as transposed B alike.
 template <int NPT>
-__device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[NPT], const int (&ti)[NPT],
+__device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[NPT], const int (&nid)[NPT],
                                               float* Ta, float* Tb, const float* S, const float* Li, int P, int LD) {
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
-        if (ti[k] >= 0) Ta[ti[k]] = r[k];
+        if (nid[k] >= 0) Ta[nid[k] >> 16] = r[k];
     __syncthreads();
-    gemm_tf32(S, Ta, Tb, nullptr, P, LD);
+    gemm_tf32<false, false>(S, Ta, Tb, nullptr, P, LD);     // Tb = S X
     __syncthreads();
-    gemm_tf32(Tb, S, Ta, Li, P, LD);
+    gemm_tf32<true, true>(Tb, S, Ta, Li, P, LD);            // Ta = ((S X S) o L)^T
     __syncthreads();
-    gemm_tf32(S, Ta, Tb, nullptr, P, LD);
+    gemm_tf32<false, false>(S, Ta, Tb, nullptr, P, LD);     // Tb = S ((S X S) o L)
     __syncthreads();
-    gemm_tf32(Tb, S, Ta, nullptr, P, LD);
+    gemm_tf32<true, false>(Tb, S, Ta, nullptr, P, LD);      // Ta = Z^T
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) z[k] = (ti[k] >= 0) ? Ta[ti[k]] : 0.f;
+    for (int k = 0; k < NPT; ++k) z[k] = (nid[k] >= 0) ? Ta[nid[k] >> 16] : 0.f;
 }
 
 // three block sums in one pass; thread 0 also forms ratio = (s0 - s1) / den
@@ -191,16 +218,16 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
     double* w64l = a.scratch + (size_t)blockIdx.x * 2 * W * W;   // fp64 weights, same halo layout
     double* w64d = w64l + W * W;
 
-    // per-thread node indices: halo position hi[k], transform-grid position ti[k]
-    int hi[NPT], ti[NPT];
+    // per-thread node indices, packed: halo position (low 16 bits) | transform-grid position
+    // (high 16 bits); -1 marks a thread slot without a node (W^2, P LD < 2^15 for n <= 63)
+    int nid[NPT];
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
         const int g = tid + k * T;
-        hi[k] = ti[k] = -1;
+        nid[k] = -1;
         if (g < G) {
             const int pp = g % n, qq = g / n;
-            hi[k] = (qq + 1) * W + pp + 1;
-            ti[k] = qq * LD + pp;
+            nid[k] = ((qq + 1) * W + pp + 1) | ((pp * LD + qq) << 16);
         }
     }
     // per CTA: the sine matrix and the scaled inverse eigenvalues (fp32), zero padded
@@ -267,16 +294,12 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
             xh[e] = 0.0;
             ph[e] = 0.f;
         }
-        float dg[NPT];
-#pragma unroll
-        for (int k = 0; k < NPT; ++k)
-            dg[k] = (hi[k] >= 0) ? wl[hi[k]] + wl[hi[k] + 1] + wd[hi[k]] + wd[hi[k] + W] : 0.f;
         __syncthreads();
 
         // ---- fp64 iterative refinement around fp32 flexible PCG ----
         double r64[NPT];
 #pragma unroll
-        for (int k = 0; k < NPT; ++k) r64[k] = (hi[k] >= 0) ? b : 0.0;
+        for (int k = 0; k < NPT; ++k) r64[k] = (nid[k] >= 0) ? b : 0.0;
         double rr64 = rr0, nr = nr0;
         int total = 0, outer = 0;
         while (rr64 > stop && outer < 16) {
@@ -289,13 +312,13 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                 r32[k] = (float)r64[k] * inv;
                 rl = fmaf(r32[k], r32[k], rl);
             }
-            apply_precond<NPT>(r32, z32, ti, Ta, Tb, S, Li, P, LD);
+            apply_precond<NPT>(r32, z32, nid, Ta, Tb, S, Li, P, LD);
             float rz_l = 0.f;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
                 p32[k] = z32[k];
                 rz_l = fmaf(r32[k], z32[k], rz_l);
-                if (hi[k] >= 0) ph[hi[k]] = p32[k];
+                if (nid[k] >= 0) ph[nid[k] & 0xffff] = p32[k];
             }
             float rz, rr, unused;
             block_sum3(rz_l, 0.f, rl, 1.f, red32, rz, rr, unused);
@@ -306,13 +329,14 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
                     q32[k] = 0.f;
-                    const int h = hi[k];
-                    if (h >= 0) {
-                        float acc = wl[h] * ph[h - 1];
-                        acc = fmaf(wl[h + 1], ph[h + 1], acc);
-                        acc = fmaf(wd[h], ph[h - W], acc);
-                        acc = fmaf(wd[h + W], ph[h + W], acc);
-                        q32[k] = fmaf(dg[k], p32[k], -acc);
+                    if (nid[k] >= 0) {
+                        const int h = nid[k] & 0xffff;
+                        const float w0 = wl[h], w1 = wl[h + 1], w2 = wd[h], w3 = wd[h + W];
+                        float acc = w0 * ph[h - 1];
+                        acc = fmaf(w1, ph[h + 1], acc);
+                        acc = fmaf(w2, ph[h - W], acc);
+                        acc = fmaf(w3, ph[h + W], acc);
+                        q32[k] = fmaf((w0 + w1) + (w2 + w3), p32[k], -acc);
                         pq_l = fmaf(p32[k], q32[k], pq_l);
                     }
                 }
@@ -327,7 +351,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                     r32[k] = fmaf(-alpha, q32[k], r32[k]);
                     rn_l = fmaf(r32[k], r32[k], rn_l);
                 }
-                apply_precond<NPT>(r32, z32, ti, Ta, Tb, S, Li, P, LD);
+                apply_precond<NPT>(r32, z32, nid, Ta, Tb, S, Li, P, LD);
                 float zr_l = 0.f, zro_l = 0.f;
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
@@ -340,7 +364,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
                     p32[k] = fmaf(beta, p32[k], z32[k]);
-                    if (hi[k] >= 0) ph[hi[k]] = p32[k];
+                    if (nid[k] >= 0) ph[nid[k] & 0xffff] = p32[k];
                 }
                 __syncthreads();
                 ++it;
@@ -349,14 +373,14 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
             // x += ||r|| d in fp64, then the fp64 residual with the fp64 weights
 #pragma unroll
             for (int k = 0; k < NPT; ++k)
-                if (hi[k] >= 0) xh[hi[k]] = fma(nr, (double)d32[k], xh[hi[k]]);
+                if (nid[k] >= 0) xh[nid[k] & 0xffff] = fma(nr, (double)d32[k], xh[nid[k] & 0xffff]);
             __syncthreads();
             double rl64 = 0.0;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
                 r64[k] = 0.0;
-                const int h = hi[k];
-                if (h >= 0) {
+                if (nid[k] >= 0) {
+                    const int h = nid[k] & 0xffff;
                     const double w0 = __ldcg(w64l + h), w1 = __ldcg(w64l + h + 1);
                     const double w2 = __ldcg(w64d + h), w3 = __ldcg(w64d + h + W);
                     double acc = w0 * xh[h - 1];
@@ -375,6 +399,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
         if (tid == 0) {
             if (a.iters_out) a.iters_out[sys] = total;
             if (a.iters_sum) atomicAdd(a.iters_sum, (unsigned long long)total);
+            if (a.outer_sum) atomicAdd(a.outer_sum, (unsigned long long)outer);
             if (rr64 > stop && a.fail_count) atomicAdd(a.fail_count, 1u);
         }
         __syncthreads();

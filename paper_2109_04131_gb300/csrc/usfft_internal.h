@@ -63,7 +63,8 @@ cudaError_t launch_sample_1d(const NodeSpec& ns, int n, int coef_model, double f
 
 // 2-D: fused coefficient assembly + Jacobi-PCG (fp64) or fp32-PCG with fp64-residual
 // refinement (mixed); iters_out[i] receives the CG iterations of system i (may be NULL);
-// fail_count gets +1 for every system that hit max_iters.
+// fail_count gets +1 for every system that hit max_iters; iters_sum[0] accumulates the CG
+// iterations and, for the refinement kernels, iters_sum[1] the refinement steps.
 struct CgConfig {
     int precision;
     int max_iters;
