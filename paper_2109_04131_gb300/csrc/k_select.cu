@@ -28,8 +28,15 @@ __device__ __forceinline__ void set_bit(uint32_t* bitmap, int64_t k) {
     atomicOr(bitmap + (k >> 5), 1u << (k & 31));
 }
 
+// Keys: 1 + bit pattern of |c|^2 for candidates >= theta, 0 for the others (the bit patterns
+// of non-negative doubles are ordered like the values; +1 keeps a zero magnitude eligible
+// when theta = 0).  With KEYS_IN_SMEM the keys of a node are computed once (three fp64
+// operations per candidate) into shared memory and every radix pass is integer work;
+// otherwise (more candidates than fit) they are recomputed from C in every pass.
+template <bool KEYS_IN_SMEM>
 __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2* C, int G, int64_t nJ,
                                                                      double theta2, int s_tilde, uint32_t* bitmap) {
+    extern __shared__ unsigned long long skeys[];
     __shared__ unsigned int hist[256];
     __shared__ unsigned long long sh_prefix;
     __shared__ unsigned int sh_want;
@@ -40,9 +47,19 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
 
     for (int g = blockIdx.x; g < G; g += gridDim.x) {
         const double2* row = C + (int64_t)g * nJ;
-        // count the candidates above the threshold
+        auto key_of = [&](int64_t k) -> unsigned long long {
+            if (KEYS_IN_SMEM) return skeys[k];
+            const double m2 = mag2_rn(row[k]);
+            return m2 >= theta2 ? (unsigned long long)__double_as_longlong(m2) + 1ull : 0ull;
+        };
+        // pass 0: keys and the count of candidates above the threshold
         unsigned int cnt = 0;
-        for (int64_t k = tid; k < nJ; k += blockDim.x) cnt += mag2_rn(row[k]) >= theta2 ? 1u : 0u;
+        for (int64_t k = tid; k < nJ; k += blockDim.x) {
+            const double m2 = mag2_rn(row[k]);
+            const unsigned long long key = m2 >= theta2 ? (unsigned long long)__double_as_longlong(m2) + 1ull : 0ull;
+            if (KEYS_IN_SMEM) skeys[k] = key;
+            cnt += key ? 1u : 0u;
+        }
         cnt = __reduce_add_sync(0xffffffffu, cnt);
         if (lane == 0) warp_cnt[warp] = cnt;
         __syncthreads();
@@ -50,31 +67,26 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
             unsigned int t = 0;
             for (int w = 0; w < nw; ++w) t += warp_cnt[w];
             sh_total = t;
+            sh_prefix = 0ull;
+            sh_want = (unsigned int)s_tilde;
         }
         __syncthreads();
         const unsigned int total = sh_total;
         if (total <= (unsigned int)s_tilde) {
             for (int64_t k = tid; k < nJ; k += blockDim.x)
-                if (mag2_rn(row[k]) >= theta2) set_bit(bitmap, k);
+                if (key_of(k)) set_bit(bitmap, k);
             __syncthreads();
             continue;
         }
-        // exact s~-th largest key among the eligible ones
-        if (tid == 0) {
-            sh_prefix = 0ull;
-            sh_want = (unsigned int)s_tilde;
-        }
-        __syncthreads();
+        // exact s~-th largest key: MSB-first radix select, 8-bit digits
         for (int shift = 56; shift >= 0; shift -= 8) {
             hist[tid] = 0u;     // blockDim.x == 256
             __syncthreads();
             const unsigned long long prefix = sh_prefix;
             const unsigned long long himask = (shift == 56) ? 0ull : ~((1ull << (shift + 8)) - 1ull);
             for (int64_t k = tid; k < nJ; k += blockDim.x) {
-                const double m2 = mag2_rn(row[k]);
-                if (!(m2 >= theta2)) continue;
-                const unsigned long long key = (unsigned long long)__double_as_longlong(m2);
-                if ((key & himask) == prefix) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
+                const unsigned long long key = key_of(k);
+                if (key && (key & himask) == prefix) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
             }
             __syncthreads();
             if (tid == 0) {
@@ -94,19 +106,13 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
         }
         const unsigned long long tau = sh_prefix;
         const unsigned int take_eq = sh_want;        // how many keys == tau to take
-        for (int64_t k = tid; k < nJ; k += blockDim.x) {
-            const double m2 = mag2_rn(row[k]);
-            if (m2 >= theta2 && (unsigned long long)__double_as_longlong(m2) > tau) set_bit(bitmap, k);
-        }
+        for (int64_t k = tid; k < nJ; k += blockDim.x)
+            if (key_of(k) > tau) set_bit(bitmap, k);
         // keys equal to tau: the first take_eq in index order
         unsigned int taken = 0;
         for (int64_t base = 0; base < nJ && taken < take_eq; base += blockDim.x) {
             const int64_t k = base + tid;
-            bool eq = false;
-            if (k < nJ) {
-                const double m2 = mag2_rn(row[k]);
-                eq = (m2 >= theta2) && ((unsigned long long)__double_as_longlong(m2) == tau);
-            }
+            const bool eq = (k < nJ) && key_of(k) == tau;
             const unsigned int ball = __ballot_sync(0xffffffffu, eq);
             if (lane == 0) warp_cnt[warp] = __popc(ball);
             __syncthreads();
@@ -123,11 +129,29 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
     }
 }
 
+static const int64_t kMaxSmemKeys = 24576;   // 192 KB of keys per CTA
+
 cudaError_t launch_select_union(const double2* C, int G, int64_t nJ, double theta, int s_tilde, uint32_t* bitmap,
                                 cudaStream_t s, int* launches) {
     if (G <= 0 || nJ <= 0) return cudaSuccess;
-    int blocks = G < 152 * 8 ? G : 152 * 8;
-    select_union_kernel<<<blocks, kSelThreads, 0, s>>>(C, G, nJ, theta * theta, s_tilde, bitmap);
+    cudaError_t e;
+    if (nJ <= kMaxSmemKeys) {
+        const size_t smem = sizeof(unsigned long long) * (size_t)nJ;
+        e = cudaFuncSetAttribute(select_union_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_union_kernel<true>, kSelThreads, smem);
+        if (e != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        int blocks = 152 * per_sm;
+        if (blocks > G) blocks = G;
+        select_union_kernel<true><<<blocks, kSelThreads, smem, s>>>(C, G, nJ, theta * theta, s_tilde, bitmap);
+    } else {
+        int blocks = G < 152 * 8 ? G : 152 * 8;
+        select_union_kernel<false><<<blocks, kSelThreads, 0, s>>>(C, G, nJ, theta * theta, s_tilde, bitmap);
+    }
     if (launches) ++*launches;
     return cudaGetLastError();
 }
