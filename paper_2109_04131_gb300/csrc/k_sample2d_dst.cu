@@ -14,9 +14,12 @@
 // [min_e w_e, max_e w_e], the preconditioned operator has condition number at most
 // max w / min w, independent of the mesh width, so a handful of iterations reduce the
 // residual by 1e-5 (Jacobi-PCG needs hundreds).  The four n x n matrix products run on
-// the tensor cores (mma.sync m16n8k8, TF32 operands, fp32 accumulation) from shared
-// memory; the preconditioner is then slightly non-symmetric, which the flexible
-// (Polak-Ribiere) beta tolerates.  One CTA owns one system at a time (persistent grid).
+// the tensor cores (mma.sync m16n8k16, BF16 operands in shared memory, fp32
+// accumulation); the rounded preconditioner is slightly non-symmetric, which the
+// flexible (Polak-Ribiere) beta tolerates -- only the convergence rate depends on it, the
+// solution accuracy comes from the fp64 refinement.  One CTA owns one system at a time
+// (persistent grid).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -38,13 +41,13 @@ __host__ __device__ inline DstLayout dst_layout(int n, int d) {
     L.n = n;
     L.W = n + 2;
     L.P = (n + 15) / 16 * 16;
-    L.LD = L.P + 4;   // row stride: conflict-free TF32 fragment loads
+    L.LD = L.P + 8;   // row stride in elements: 4 mod 32 words, conflict-free BF16 fragment loads
     size_t o = 0;
     L.o_xh = o;  o = align16(o + sizeof(double) * (size_t)L.W * L.W);
-    L.o_S = o;   o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
+    L.o_S = o;   o = align16(o + sizeof(__nv_bfloat16) * (size_t)L.P * L.LD);
     L.o_L = o;   o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
-    L.o_Ta = o;  o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
-    L.o_Tb = o;  o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
+    L.o_Ta = o;  o = align16(o + sizeof(__nv_bfloat16) * (size_t)L.P * L.LD);
+    L.o_Tb = o;  o = align16(o + sizeof(__nv_bfloat16) * (size_t)L.P * L.LD);
     L.o_wx = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
     L.o_wy = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
     L.o_ph = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
@@ -55,95 +58,81 @@ __host__ __device__ inline DstLayout dst_layout(int n, int d) {
     return L;
 }
 
-// TF32 operand: the fp32 bit pattern itself (the tensor core ignores the low 13 mantissa
-// bits, i.e. truncates), which is accurate enough for a preconditioner.
-__device__ __forceinline__ uint32_t to_tf32(float x) { return __float_as_uint(x); }
+typedef __nv_bfloat16 bf16;
 
-// C = A B on the tensor cores (P x P, stride LD, P a multiple of 16).  A is stored row-major;
-// B is stored TRANSPOSED (Bt[n][k] = B[k][n]) so that the B-fragment loads, like the A loads,
-// hit bank (4 row + col) mod 32 with LD = 4 mod 32 (conflict-free).  C is written row-major
-// (TRANSPOSE_OUT = false) or transposed (true); C o= Lsc (symmetric) if SCALE.
-// Warp tiles are 16 x (8 NC) (one A fragment feeds NC n8 MMAs); fragment layouts of
-// mma.m16n8k8 (TF32): a0 (g, t) a1 (g+8, t) a2 (g, t+4) a3 (g+8, t+4); b0 (k=t, n=g)
-// b1 (k=t+4, n=g); c0 (g, 2t) c1 (g, 2t+1) c2 (g+8, 2t) c3 (g+8, 2t+1); g = lane/4, t = lane%4.
-constexpr int NC = 1;   // n8 tiles per warp tile
+// C = A B on the tensor cores (P x P, row stride LD elements, P a multiple of 16), BF16
+// operands, fp32 accumulation.  A is stored row-major; B is stored TRANSPOSED
+// (Bt[n][k] = B[k][n]) so that both operand loads read 32-bit words at bank
+// (4 row + col) mod 32 (LD/2 = 4 mod 32 words: conflict-free).  C is written row-major
+// (TRANSPOSE_OUT = false) or transposed (true), as BF16; before rounding it is multiplied
+// elementwise by Lsc (fp32, symmetric, stride LD) if SCALE.  Fragment layouts of
+// mma.m16n8k16 (BF16): a0 (g, 2t..2t+1) a1 (g+8, 2t..) a2 (g, 2t+8..) a3 (g+8, 2t+8..);
+// b0 (k = 2t..2t+1, n = g) b1 (k = 2t+8.., n = g); c0 (g, 2t) c1 (g, 2t+1) c2 (g+8, 2t)
+// c3 (g+8, 2t+1); g = lane/4, t = lane%4.  Each warp takes 16x8 output tiles.
 template <bool TRANSPOSE_OUT, bool SCALE>
-__device__ __forceinline__ void gemm_tf32(const float* __restrict__ A, const float* __restrict__ Bt,
-                                          float* __restrict__ C, const float* __restrict__ Lsc, int P, int LD) {
+__device__ __forceinline__ void gemm_bf16(const bf16* __restrict__ A, const bf16* __restrict__ Bt,
+                                          bf16* __restrict__ C, const float* __restrict__ Lsc, int P, int LD) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int nwt = P / (8 * NC);                   // P is a multiple of 16 and of 8 NC
-    const int tiles = (P / 16) * nwt;
+    const int nt = P / 8, tiles = (P / 16) * nt;
     for (int tile = warp; tile < tiles; tile += nwarps) {
-        const int m0 = (tile / nwt) * 16, nb = (tile % nwt) * (8 * NC);
-        float acc[NC][4];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
-        for (int k0 = 0; k0 < P; k0 += 8) {
-            const uint32_t a0 = to_tf32(A[(m0 + g) * LD + k0 + t]);
-            const uint32_t a1 = to_tf32(A[(m0 + g + 8) * LD + k0 + t]);
-            const uint32_t a2 = to_tf32(A[(m0 + g) * LD + k0 + t + 4]);
-            const uint32_t a3 = to_tf32(A[(m0 + g + 8) * LD + k0 + t + 4]);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                {
-                    const int n0 = nb + 8 * c;
-                    const uint32_t b0 = to_tf32(Bt[(n0 + g) * LD + k0 + t]);
-                    const uint32_t b1 = to_tf32(Bt[(n0 + g) * LD + k0 + t + 4]);
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
-                        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                        : "+f"(acc[c][0]), "+f"(acc[c][1]), "+f"(acc[c][2]), "+f"(acc[c][3])
-                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-                }
-            }
+        const int m0 = (tile / nt) * 16, n0 = (tile % nt) * 8;
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+        const bf16* Ar0 = A + (m0 + g) * LD + 2 * t;
+        const bf16* Ar1 = Ar0 + 8 * LD;
+        const bf16* Br = Bt + (n0 + g) * LD + 2 * t;
+        for (int k0 = 0; k0 < P; k0 += 16) {
+            const uint32_t a0 = *reinterpret_cast<const uint32_t*>(Ar0 + k0);
+            const uint32_t a1 = *reinterpret_cast<const uint32_t*>(Ar1 + k0);
+            const uint32_t a2 = *reinterpret_cast<const uint32_t*>(Ar0 + k0 + 8);
+            const uint32_t a3 = *reinterpret_cast<const uint32_t*>(Ar1 + k0 + 8);
+            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(Br + k0);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(Br + k0 + 8);
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
         }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int n0 = nb + 8 * c;
-            const int row0 = m0 + g, row1 = m0 + g + 8, col0 = n0 + 2 * t, col1 = col0 + 1;
-            float v0 = acc[c][0], v1 = acc[c][1], v2 = acc[c][2], v3 = acc[c][3];
-            if (SCALE) {
-                v0 *= Lsc[row0 * LD + col0];
-                v1 *= Lsc[row0 * LD + col1];
-                v2 *= Lsc[row1 * LD + col0];
-                v3 *= Lsc[row1 * LD + col1];
-            }
-            if (TRANSPOSE_OUT) {
-                C[col0 * LD + row0] = v0;
-                C[col1 * LD + row0] = v1;
-                C[col0 * LD + row1] = v2;
-                C[col1 * LD + row1] = v3;
-            } else {
-                C[row0 * LD + col0] = v0;
-                C[row0 * LD + col1] = v1;
-                C[row1 * LD + col0] = v2;
-                C[row1 * LD + col1] = v3;
-            }
+        const int row0 = m0 + g, row1 = m0 + g + 8, col0 = n0 + 2 * t, col1 = col0 + 1;
+        if (SCALE) {
+            c0 *= Lsc[row0 * LD + col0];
+            c1 *= Lsc[row0 * LD + col1];
+            c2 *= Lsc[row1 * LD + col0];
+            c3 *= Lsc[row1 * LD + col1];
+        }
+        if (TRANSPOSE_OUT) {
+            C[col0 * LD + row0] = __float2bfloat16_rn(c0);
+            C[col1 * LD + row0] = __float2bfloat16_rn(c1);
+            C[col0 * LD + row1] = __float2bfloat16_rn(c2);
+            C[col1 * LD + row1] = __float2bfloat16_rn(c3);
+        } else {
+            *reinterpret_cast<__nv_bfloat162*>(C + row0 * LD + col0) = __floats2bfloat162_rn(c0, c1);
+            *reinterpret_cast<__nv_bfloat162*>(C + row1 * LD + col0) = __floats2bfloat162_rn(c2, c3);
         }
     }
 }
 
 // z = K_0^-1 r for the NPT nodes of this thread.  The transform grid X (rows q, columns p)
 // is kept transposed in Ta (Ta[p][q]), the layout the B operand wants; nid[k] >> 16 = p LD + q
-// of the node (nid[k] = -1: no node).  S is symmetric, so it serves as A and as transposed B alike.
+// of the node (nid[k] = -1: no node).  S is symmetric, so it serves as A and as transposed B.
 template <int NPT>
 __device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[NPT], const int (&nid)[NPT],
-                                              float* Ta, float* Tb, const float* S, const float* Li, int P, int LD) {
+                                              bf16* Ta, bf16* Tb, const bf16* S, const float* Li, int P, int LD) {
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
-        if (nid[k] >= 0) Ta[nid[k] >> 16] = r[k];
+        if (nid[k] >= 0) Ta[nid[k] >> 16] = __float2bfloat16_rn(r[k]);
     __syncthreads();
-    gemm_tf32<false, false>(S, Ta, Tb, nullptr, P, LD);     // Tb = S X
+    gemm_bf16<false, false>(S, Ta, Tb, nullptr, P, LD);     // Tb = S X
     __syncthreads();
-    gemm_tf32<true, true>(Tb, S, Ta, Li, P, LD);            // Ta = ((S X S) o L)^T
+    gemm_bf16<true, true>(Tb, S, Ta, Li, P, LD);            // Ta = ((S X S) o L)^T
     __syncthreads();
-    gemm_tf32<false, false>(S, Ta, Tb, nullptr, P, LD);     // Tb = S ((S X S) o L)
+    gemm_bf16<false, false>(S, Ta, Tb, nullptr, P, LD);     // Tb = S ((S X S) o L)
     __syncthreads();
-    gemm_tf32<true, false>(Tb, S, Ta, nullptr, P, LD);      // Ta = Z^T
+    gemm_bf16<true, false>(Tb, S, Ta, nullptr, P, LD);      // Ta = Z^T
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) z[k] = (nid[k] >= 0) ? Ta[nid[k] >> 16] : 0.f;
+    for (int k = 0; k < NPT; ++k) z[k] = (nid[k] >= 0) ? __bfloat162float(Ta[nid[k] >> 16]) : 0.f;
 }
 
 // three block sums in one pass; thread 0 also forms ratio = (s0 - s1) / den
@@ -204,10 +193,10 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
     const DstLayout Lo = dst_layout(n, a.ns.d);
     const int W = Lo.W, P = Lo.P, LD = Lo.LD;
     double* xh = reinterpret_cast<double*>(smraw + Lo.o_xh);
-    float* S = reinterpret_cast<float*>(smraw + Lo.o_S);
+    bf16* S = reinterpret_cast<bf16*>(smraw + Lo.o_S);
     float* Li = reinterpret_cast<float*>(smraw + Lo.o_L);
-    float* Ta = reinterpret_cast<float*>(smraw + Lo.o_Ta);
-    float* Tb = reinterpret_cast<float*>(smraw + Lo.o_Tb);
+    bf16* Ta = reinterpret_cast<bf16*>(smraw + Lo.o_Ta);
+    bf16* Tb = reinterpret_cast<bf16*>(smraw + Lo.o_Tb);
     float* wl = reinterpret_cast<float*>(smraw + Lo.o_wx);   // weight of the edge to the left of halo node h
     float* wd = reinterpret_cast<float*>(smraw + Lo.o_wy);   // weight of the edge below halo node h
     float* ph = reinterpret_cast<float*>(smraw + Lo.o_ph);
@@ -240,10 +229,10 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
             const float s1 = sinpif((float)(k + 1) / (2.0f * n1)), s2 = sinpif((float)(j + 1) / (2.0f * n1));
             lv = c2 / (4.0f * s1 * s1 + 4.0f * s2 * s2);
         }
-        S[e] = sv;
+        S[e] = __float2bfloat16_rn(sv);
         Li[e] = lv;
-        Ta[e] = 0.f;
-        Tb[e] = 0.f;
+        Ta[e] = __float2bfloat16_rn(0.f);
+        Tb[e] = __float2bfloat16_rn(0.f);
     }
     for (int e = tid; e < W * W; e += T) {
         wl[e] = 0.f;
