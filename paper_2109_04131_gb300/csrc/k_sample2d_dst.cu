@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
     float* Li = reinterpret_cast<float*>(smraw + Lo.o_L);
     bf16* Ta = reinterpret_cast<bf16*>(smraw + Lo.o_Ta);
     bf16* Tb = reinterpret_cast<bf16*>(smraw + Lo.o_Tb);
-    float* wl = reinterpret_cast<float*>(smraw + Lo.o_wx);   // weight of the edge to the left of halo node h
-    float* wd = reinterpret_cast<float*>(smraw + Lo.o_wy);   // weight of the edge below halo node h
+    float* wl = reinterpret_cast<float*>(smraw + Lo.o_wx);   // weight of the edge to the left of halo node h (x - h)
+    float* wd = reinterpret_cast<float*>(smraw + Lo.o_wy);   // weight of the edge below halo node h (y - h)
     float* ph = reinterpret_cast<float*>(smraw + Lo.o_ph);
     double* sj = reinterpret_cast<double*>(smraw + Lo.o_sj);
     double* red64 = reinterpret_cast<double*>(smraw + Lo.o_r64);
@@ -208,15 +208,18 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
     double* w64d = w64l + W * W;
 
     // per-thread node indices, packed: halo position (low 16 bits) | transform-grid position
-    // (high 16 bits); -1 marks a thread slot without a node (W^2, P LD < 2^15 for n <= 63)
+    // (high 16 bits); -1 marks a thread slot without a node (W^2, P LD < 2^15 for n <= 63).
+    // Threads walk the nodes column by column (consecutive threads: consecutive y), and the
+    // halo arrays are stored column-major, h = (p+1) W + (q+1): every per-node shared access
+    // and the transposed transform grid (p LD + q) are then contiguous across a warp.
     int nid[NPT];
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
         const int g = tid + k * T;
         nid[k] = -1;
         if (g < G) {
-            const int pp = g % n, qq = g / n;
-            nid[k] = ((qq + 1) * W + pp + 1) | ((pp * LD + qq) << 16);
+            const int pp = g / n, qq = g % n;
+            nid[k] = ((pp + 1) * W + qq + 1) | ((pp * LD + qq) << 16);
         }
     }
     // per CTA: the sine matrix and the scaled inverse eigenvalues (fp32), zero padded
@@ -267,13 +270,13 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
             const double au = logn ? exp(acc) : 1.0 + acc;
             if (Q < n) {            // edge (Pp,Q+1)-(Pp+1,Q+1): left of node (Pp+1,Q+1)
                 const double w = 0.5 * (low[(Q + 1) * n1 + Pp] + au);
-                const int h = (Q + 1) * W + Pp + 1;
+                const int h = (Pp + 1) * W + Q + 1;
                 w64l[h] = w;
                 wl[h] = (float)w;
             }
             if (Pp >= 1) {          // edge (Pp,Q)-(Pp,Q+1): below node (Pp,Q+1)
                 const double w = 0.5 * (au + low[Q * n1 + (Pp - 1)]);
-                const int h = (Q + 1) * W + Pp;
+                const int h = Pp * W + Q + 1;
                 w64d[h] = w;
                 wd[h] = (float)w;
             }
@@ -320,11 +323,11 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                     q32[k] = 0.f;
                     if (nid[k] >= 0) {
                         const int h = nid[k] & 0xffff;
-                        const float w0 = wl[h], w1 = wl[h + 1], w2 = wd[h], w3 = wd[h + W];
-                        float acc = w0 * ph[h - 1];
-                        acc = fmaf(w1, ph[h + 1], acc);
-                        acc = fmaf(w2, ph[h - W], acc);
-                        acc = fmaf(w3, ph[h + W], acc);
+                        const float w0 = wl[h], w1 = wl[h + W], w2 = wd[h], w3 = wd[h + 1];
+                        float acc = w0 * ph[h - W];
+                        acc = fmaf(w1, ph[h + W], acc);
+                        acc = fmaf(w2, ph[h - 1], acc);
+                        acc = fmaf(w3, ph[h + 1], acc);
                         q32[k] = fmaf((w0 + w1) + (w2 + w3), p32[k], -acc);
                         pq_l = fmaf(p32[k], q32[k], pq_l);
                     }
@@ -370,12 +373,12 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                 r64[k] = 0.0;
                 if (nid[k] >= 0) {
                     const int h = nid[k] & 0xffff;
-                    const double w0 = __ldcg(w64l + h), w1 = __ldcg(w64l + h + 1);
-                    const double w2 = __ldcg(w64d + h), w3 = __ldcg(w64d + h + W);
-                    double acc = w0 * xh[h - 1];
-                    acc = fma(w1, xh[h + 1], acc);
-                    acc = fma(w2, xh[h - W], acc);
-                    acc = fma(w3, xh[h + W], acc);
+                    const double w0 = __ldcg(w64l + h), w1 = __ldcg(w64l + h + W);
+                    const double w2 = __ldcg(w64d + h), w3 = __ldcg(w64d + h + 1);
+                    double acc = w0 * xh[h - W];
+                    acc = fma(w1, xh[h + W], acc);
+                    acc = fma(w2, xh[h - 1], acc);
+                    acc = fma(w3, xh[h + 1], acc);
                     r64[k] = b - fma(w0 + w1 + w2 + w3, xh[h], -acc);
                     rl64 = fma(r64[k], r64[k], rl64);
                 }
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
             ++outer;
         }
         double* out = a.U + (size_t)sys * G;
-        for (int g = tid; g < G; g += T) out[g] = xh[((g / n) + 1) * W + (g % n) + 1];
+        for (int g = tid; g < G; g += T) out[g] = xh[((g % n) + 1) * W + (g / n) + 1];   // g = q n + p
         if (tid == 0) {
             if (a.iters_out) a.iters_out[sys] = total;
             if (a.iters_sum) atomicAdd(a.iters_sum, (unsigned long long)total);
