@@ -247,6 +247,8 @@ usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns) {
         cg.max_iters = plan->par.max_cg_iters;
         cg.tol = plan->par.cg_tol;
         cg.blocks = plan->cg_blocks;
+        cg.coef_scale = plan->prob.coef_scale;
+        cg.coef_decay = plan->prob.coef_decay;
         CK(launch_sample_2d(ns, plan->prob.n, plan->prob.coef_model, plan->prob.f_const, (const double*)plan->psi.p, cg,
                             0, ns.M, (double*)plan->U.p, (int*)plan->iters.p, (unsigned int*)plan->failc.p,
                             (unsigned long long*)((char*)plan->failc.p + 8), (double*)plan->cgscr.p,

@@ -117,6 +117,8 @@ extern "C" usfft_status usfft_sample_2d_static(const usfft_problem* problem, con
         cg.max_iters = max_iters > 0 ? max_iters : 4000;
         cg.tol = tol > 0.0 ? tol : 1e-13;
         cg.blocks = blocks;
+        cg.coef_scale = pr.coef_scale;
+        cg.coef_decay = pr.coef_decay;
         e = launch_sample_2d(ns, n, pr.coef_model, pr.f_const, psi, cg, i0, count, U, nullptr, fails, nullptr, slots,
                              slot_bytes * (size_t)blocks, s, nullptr);
     }

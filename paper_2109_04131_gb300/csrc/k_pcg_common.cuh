@@ -29,8 +29,21 @@ struct Pcg2dArgs {
     unsigned int* fail_count;
     unsigned long long* iters_sum;   // total CG iterations of the launch (may be NULL)
     unsigned long long* outer_sum;   // total refinement steps of the launch (mixed; may be NULL)
-    double* scratch;       // MIXED: per CTA 2 n (n+1) fp64 scaled weights
+    double* scratch;       // refinement kernels: per-CTA fp64 weight slots
+    double coef_scale;     // c, mu (separable assembly of the MIXED kernel)
+    double coef_decay;
 };
+
+// Spatial mode of the 2-D coefficient: (j1, j2) = (m1(j-1)+1, m2(j-1)+1) with the diagonal
+// enumeration of Sec. 4.2 / Table 4.2.
+__host__ __device__ inline void mode_pair(int j, int& j1, int& j2) {
+    const int jm = j - 1;
+    int k = 0;
+    while ((k + 1) * (k + 2) / 2 <= jm) ++k;
+    const int m1 = jm - k * (k + 1) / 2;
+    j1 = m1 + 1;
+    j2 = (k - m1) + 1;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

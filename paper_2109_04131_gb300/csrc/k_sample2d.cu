@@ -393,7 +393,7 @@ int sample_2d_default_blocks(int n, int precision) {
 size_t sample_2d_scratch_bytes(int n, int precision, int blocks) {
     if (precision == USFFT_FP64) return 0;
     const size_t W = (size_t)n + 2;
-    if (precision == USFFT_MIXED) return sizeof(double) * 2 * W * W * (size_t)blocks;
+    if (precision == USFFT_MIXED) return sizeof(double) * 3 * W * W * (size_t)blocks;
     return sizeof(double) * 2 * (size_t)n * (n + 1) * (size_t)blocks;
 }
 
@@ -438,6 +438,8 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
     a.iters_sum = iters_sum;
     a.outer_sum = iters_sum ? iters_sum + 1 : nullptr;
     a.scratch = scratch;
+    a.coef_scale = cg.coef_scale;
+    a.coef_decay = cg.coef_decay;
     const int G = n * n;
     const int npt = pick_npt(G);
     const int threads = ((G + npt - 1) / npt + 31) / 32 * 32;

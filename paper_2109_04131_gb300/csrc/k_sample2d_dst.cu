@@ -30,8 +30,8 @@
 namespace usfft {
 
 struct DstLayout {
-    int n, W, P, LD;
-    size_t o_xh, o_S, o_L, o_Ta, o_Tb, o_wx, o_wy, o_ph, o_sj, o_r64, o_r32, total;
+    int n, W, P, LD, J1, JA;
+    size_t o_xh, o_S, o_L, o_Ta, o_Tb, o_wx, o_wy, o_ph, o_sj, o_r64, o_r32, o_A, o_Tr, o_md, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -54,6 +54,19 @@ __host__ __device__ inline DstLayout dst_layout(int n, int d) {
     L.o_sj = o;  o = align16(o + sizeof(double) * (size_t)d);
     L.o_r64 = o; o = align16(o + sizeof(double) * 36);
     L.o_r32 = o; o = align16(o + sizeof(float) * 4 * 36);
+    // separable assembly: J1 = largest first mode index, JA = largest index of either factor
+    L.J1 = 1;
+    L.JA = 1;
+    for (int j = 1; j <= d; ++j) {
+        int j1, j2;
+        mode_pair(j, j1, j2);
+        if (j1 > L.J1) L.J1 = j1;
+        if (j1 > L.JA) L.JA = j1;
+        if (j2 > L.JA) L.JA = j2;
+    }
+    L.o_A = o;   o = align16(o + sizeof(double) * (size_t)L.JA * 2 * (n + 1));   // sin(j pi (P + o/3) h)
+    L.o_Tr = o;  o = align16(o + sizeof(double) * (size_t)L.J1 * 2 * (n + 1));   // per-row partial sums
+    L.o_md = o;  o = align16(o + sizeof(double) * (size_t)d + sizeof(int) * 2 * (size_t)d);   // amplitudes, modes
     L.total = o;
     return L;
 }
@@ -203,9 +216,16 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
     double* sj = reinterpret_cast<double*>(smraw + Lo.o_sj);
     double* red64 = reinterpret_cast<double*>(smraw + Lo.o_r64);
     float* red32 = reinterpret_cast<float*>(smraw + Lo.o_r32);
+    double* At = reinterpret_cast<double*>(smraw + Lo.o_A);     // At[(j-1)][o-1][P] = sin(j pi (P + o/3) h)
+    double* Tr = reinterpret_cast<double*>(smraw + Lo.o_Tr);    // Tr[(j1-1)][o-1][Q]
+    double* amp = reinterpret_cast<double*>(smraw + Lo.o_md);   // c j^-mu
+    int* mj1 = reinterpret_cast<int*>(amp + a.ns.d);
+    int* mj2 = mj1 + a.ns.d;
+    const int J1 = Lo.J1, JA = Lo.JA;
     const int T = blockDim.x, tid = threadIdx.x;
-    double* w64l = a.scratch + (size_t)blockIdx.x * 2 * W * W;   // fp64 weights, same halo layout
+    double* w64l = a.scratch + (size_t)blockIdx.x * 3 * W * W;   // fp64 weights and diagonal, same halo layout
     double* w64d = w64l + W * W;
+    double* d64 = w64d + W * W;
 
     // per-thread node indices, packed: halo position (low 16 bits) | transform-grid position
     // (high 16 bits); -1 marks a thread slot without a node (W^2, P LD < 2^15 for n <= 63).
@@ -242,6 +262,23 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
         wd[e] = 0.f;
         w64l[e] = 0.0;
         w64d[e] = 0.0;
+        d64[e] = 0.0;
+    }
+    // separable coefficient: psi_j(centroid) = sin(j1 pi x1) sin(j2 pi x2); the centroids of
+    // square (P,Q) are ((P+2/3)h, (Q+1/3)h) (lower triangle) and ((P+1/3)h, (Q+2/3)h) (upper)
+    {
+        const double hh = 1.0 / (double)n1;
+        for (int e = tid; e < JA * 2 * n1; e += T) {
+            const int jj = e / (2 * n1) + 1, o = (e / n1) % 2 + 1, Pp = e % n1;
+            At[e] = sinpi((double)jj * (((double)Pp + (double)o / 3.0) * hh));
+        }
+        for (int j = tid; j < a.ns.d; j += T) {
+            int j1, j2;
+            mode_pair(j + 1, j1, j2);
+            mj1[j] = j1;
+            mj2[j] = j2;
+            amp[j] = a.coef_scale * pow((double)(j + 1), -a.coef_decay);
+        }
     }
     const double b = a.rhs;
     const double rr0 = (double)G * b * b;
@@ -256,17 +293,27 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
         __syncthreads();
         const bool logn = a.coef_model == USFFT_COEF_LOGNORMAL_SIN;
         const int sq = n1 * n1, d = a.ns.d;
+        // per-row partial sums Tr[j1][o][Q] = sum_{j: j1(j) = j1} c j^-mu sin(2 pi y_j) At[j2(j)][o][Q]
+        for (int e = tid; e < J1 * 2 * n1; e += T) {
+            const int j1 = e / (2 * n1) + 1, o = (e / n1) % 2, Q = e % n1;
+            double acc = 0.0;
+            for (int j = 0; j < d; ++j)
+                if (mj1[j] == j1) acc = fma(amp[j] * sj[j], At[((mj2[j] - 1) * 2 + o) * n1 + Q], acc);
+            Tr[e] = acc;
+        }
+        __syncthreads();
         double* low = xh;                       // lower-triangle coefficients (temporary)
         for (int e = tid; e < sq; e += T) {
+            const int Pp = e % n1, Q = e / n1;
             double acc = 0.0;
-            for (int j = 0; j < d; ++j) acc = fma(__ldg(a.psi + (size_t)j * 2 * sq + e), sj[j], acc);
+            for (int j1 = 0; j1 < J1; ++j1) acc = fma(At[(j1 * 2 + 1) * n1 + Pp], Tr[(j1 * 2 + 0) * n1 + Q], acc);
             low[e] = logn ? exp(acc) : 1.0 + acc;
         }
         __syncthreads();
         for (int e = tid; e < sq; e += T) {
             const int Pp = e % n1, Q = e / n1;
             double acc = 0.0;
-            for (int j = 0; j < d; ++j) acc = fma(__ldg(a.psi + (size_t)j * 2 * sq + sq + e), sj[j], acc);
+            for (int j1 = 0; j1 < J1; ++j1) acc = fma(At[(j1 * 2 + 0) * n1 + Pp], Tr[(j1 * 2 + 1) * n1 + Q], acc);
             const double au = logn ? exp(acc) : 1.0 + acc;
             if (Q < n) {            // edge (Pp,Q+1)-(Pp+1,Q+1): left of node (Pp+1,Q+1)
                 const double w = 0.5 * (low[(Q + 1) * n1 + Pp] + au);
@@ -279,6 +326,15 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                 const int h = Pp * W + Q + 1;
                 w64d[h] = w;
                 wd[h] = (float)w;
+            }
+        }
+        __syncthreads();
+        // fp64 diagonal of every node (sum of its four edge weights) for the refinement residual
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            if (nid[k] >= 0) {
+                const int h = nid[k] & 0xffff;
+                d64[h] = (w64l[h] + w64l[h + W]) + (w64d[h] + w64d[h + 1]);
             }
         }
         __syncthreads();
@@ -379,7 +435,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                     acc = fma(w1, xh[h + W], acc);
                     acc = fma(w2, xh[h - 1], acc);
                     acc = fma(w3, xh[h + 1], acc);
-                    r64[k] = b - fma(w0 + w1 + w2 + w3, xh[h], -acc);
+                    r64[k] = b - fma(__ldcg(d64 + h), xh[h], -acc);
                     rl64 = fma(r64[k], r64[k], rl64);
                 }
             }

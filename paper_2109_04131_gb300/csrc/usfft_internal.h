@@ -70,6 +70,8 @@ struct CgConfig {
     int max_iters;
     double tol;
     int blocks;            // 0 = auto
+    double coef_scale;     // c and mu of the coefficient (the MIXED kernel assembles from them
+    double coef_decay;     // directly, in separable form, instead of reading the mode table)
 };
 cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f, const double* psi,
                              const CgConfig& cg, int64_t i0, int64_t count, double* U, int* iters_out,
