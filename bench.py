@@ -443,6 +443,18 @@ def sampled_accuracy(w, t, plans, rows=4):
     return out
 
 
+def alu_probe():
+    """Measured FMA throughput of the GPU (the ALU peaks of the roofline are derived from the
+    unit counts; this checks them on the device)."""
+    src = os.path.join(ROOT, "paper_2109_04131_gb300", "probe", "alu_probe.cu")
+    exe = os.path.join(ROOT, "paper_2109_04131_gb300", "_build", "alu_probe")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    subprocess.run([nvcc if os.path.exists(nvcc) else "nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                    "-o", exe, src], check=True)
+    print(subprocess.run([exe], capture_output=True, text=True, check=True).stdout.strip(), flush=True)
+
+
 def profile_case(args):
     """A short, fixed run for ncu: increments 1..K of the 2-D workload in one precision."""
     import torch
@@ -471,7 +483,12 @@ def main():
     ap.add_argument("--profile-increments", type=int, default=0,
                     help="profiling mode: only run this many increments of the 2-D workload (no timing)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--alu-probe", action="store_true",
+                    help="build and run the FP64/FP32 FMA throughput probe (paper_2109_04131_gb300/probe)")
     args = ap.parse_args()
+    if args.alu_probe:
+        alu_probe()
+        return
     if args.profile_increments:
         profile_case(args)
         return
