@@ -47,6 +47,28 @@ PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 FLOPS_PER_CG_ITER_PER_NODE = 21      # Jacobi-PCG: SpMV 9 + two dots 4 + three AXPY 6 + scaling 2
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
+# kernel, with a hash of the kernel source it was taken on; a changed source makes it null.
+PROFILE_TRAFFIC = {
+    "mixed": {"bytes": 263168 + 177223680, "files": ["k_sample2d_dst.cu", "k_pcg_common.cuh"],
+              "sha": "4b72ca9fa20f6d9c", "profile": "profiles/pcg2d_mixed_dst_c2_t3.md"},
+    "fp64": {"bytes": 7748608 + 169484288, "files": ["k_sample2d.cu", "k_pcg_common.cuh"],
+             "sha": "543258ce85e18805", "profile": "profiles/pcg2d_fp64_c2_t3.md"},
+    "fft": {"bytes": 221549312 + 159785728 + 747531008 + 557830144, "files": ["k_fft.cu"],
+            "sha": "7b4ea64a052c6718", "profile": "profiles/fft_c2_t3.md"},
+}
+
+
+def profiled_traffic(kind):
+    import hashlib
+    rec = PROFILE_TRAFFIC[kind]
+    h = hashlib.sha256()
+    for f in rec["files"]:
+        with open(os.path.join(ROOT, "paper_2109_04131_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes"] if h.hexdigest()[:16] == rec["sha"] else None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -310,7 +332,7 @@ def run_ours(args, rank, world):
 
     d_, E_ = w.problem.d, 2 * (w.problem.n + 1) ** 2
     P_ = (w.problem.n + 15) // 16 * 16
-    peak_tf32 = peaks.get("bf16_tflops", 1921.8) * 1.1 / 2.25      # the recipe's nominal tf32:bf16 ratio
+    peak_bf16 = peaks.get("bf16_tflops", 1921.8)
 
     def fp64_roofline(res):
         # FP64 path: 21 G flops per Jacobi-PCG iteration + 2 d E flops of coefficient assembly per solve
@@ -321,7 +343,7 @@ def run_ours(args, rank, world):
         dur = st["ms"]["sample"] / n / 1e3
         ach = flops / dur / 1e12
         return {"bound": "alu", "achieved": ach, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / PEAK_FP64_TFLOPS, "traffic": None,
+                "frac": ach / PEAK_FP64_TFLOPS, "traffic": profiled_traffic("fp64"),
                 "kernel": f"pcg2d_fp64_kernel (assembly + Jacobi-PCG, {n} launches timed)",
                 "flops_per_launch": flops, "ms_per_launch": dur * 1e3,
                 "cg_iters_per_solve": st["cg_iters_total"] / max(1, solves),
@@ -329,7 +351,7 @@ def run_ours(args, rank, world):
 
     def mixed_roofline(res):
         # MIXED path: fp64 work (assembly 2 d E per solve, refinement residual + update 17 G per step)
-        # is the binding roof at peak; fp32 CG (21 G per inner iteration) and the TF32 sine
+        # is the binding roof at peak; fp32 CG (21 G per inner iteration) and the BF16 sine
         # transforms (4 x 2 P^3 per preconditioner application) are listed beside it.
         st = res["stages"]
         n = max(1, st["launches"]["sample"])
@@ -337,18 +359,18 @@ def run_ours(args, rank, world):
         inner, outer = st["cg_iters_total"], st["refine_steps_total"]
         f64 = (2.0 * d_ * E_ * solves + 17.0 * G * outer) / n
         f32 = FLOPS_PER_CG_ITER_PER_NODE * G * inner / n
-        ftc = 4 * 2.0 * P_ ** 3 * (inner + outer) / n
+        ftc = 4 * 2.0 * P_ ** 3 * (inner + outer) / n          # BF16 tensor flops of the sine transforms
         dur = st["ms"]["sample"] / n / 1e3
         ach = f64 / dur / 1e12
         return {"bound": "alu", "achieved": ach, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / PEAK_FP64_TFLOPS, "traffic": None,
-                "kernel": f"pcg2d_mixed_dst_kernel (assembly + refinement + fp32 PCG + TF32 DST, {n} launches timed)",
+                "frac": ach / PEAK_FP64_TFLOPS, "traffic": profiled_traffic("mixed"),
+                "kernel": f"pcg2d_mixed_dst_kernel (assembly + refinement + fp32 PCG + BF16 DST, {n} launches timed)",
                 "flops_per_launch": f64, "ms_per_launch": dur * 1e3,
                 "units": {"fp64": {"tflops": ach, "frac": ach / PEAK_FP64_TFLOPS},
                           "fp32": {"tflops": f32 / dur / 1e12, "frac": f32 / dur / 1e12 / PEAK_FP32_TFLOPS},
-                          "tensor_tf32": {"tflops": ftc / dur / 1e12, "frac": ftc / dur / 1e12 / peak_tf32}},
+                          "tensor_bf16": {"tflops": ftc / dur / 1e12, "frac": ftc / dur / 1e12 / peak_bf16}},
                 "inner_iters_per_solve": inner / max(1, solves), "refine_steps_per_solve": outer / max(1, solves),
-                "peak_note": f"fp64 peak from unit counts at {SM_MAX_MHZ:.0f} MHz; tf32 peak = measured bf16 x 1.1/2.25"}
+                "peak_note": f"fp64 peak from unit counts at {SM_MAX_MHZ:.0f} MHz; bf16 peak measured (cuBLAS)"}
 
     def fft_roofline(res):
         st = res["stages"]
@@ -359,7 +381,8 @@ def run_ours(args, rank, world):
         dur = st["ms"]["fft"] / n / 1e3
         ach = algo / dur / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "fft_pass_kernel (all passes)",
+                "frac": ach / peaks["hbm_gbs"], "traffic": profiled_traffic("fft"),
+                "kernel": "fft_pass1_kernel + fft_final_kernel (one iteration)",
                 "bytes_per_launch": algo, "ms_per_launch": dur * 1e3,
                 "peak_note": f"{peak_kind} hbm_gbs (burst)"}
 
