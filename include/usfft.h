@@ -156,11 +156,12 @@ usfft_status usfft_replay(usfft_plan_t* plan, int sync, int32_t* launches);
  * detected set, so a later usfft_increment recomputes increment t+1 exactly. */
 usfft_status usfft_rewind(usfft_plan_t* plan, int t);
 
-/* Resume from a checkpoint: set the state after increment t (0 <= t < d) to the detected
+/* Resume from a checkpoint: set the state after increment t (0 <= t <= d) to the detected
  * set I^(1..t) ([n][t] int8 rows, host) and the absolute threshold theta (> 0; ignored
  * when t == 0).  The next usfft_increment runs increment t+1 from this state exactly as it
  * would have after the increments 1..t (Algorithm 1 needs only I^(1..t) and theta to
- * continue; every draw is keyed by (phase, t, i, j)).  Earlier history is discarded. */
+ * continue; every draw is keyed by (phase, t, i, j)); with t == d the next call is
+ * usfft_reconstruct.  Earlier history is discarded. */
 usfft_status usfft_resume(usfft_plan_t* plan, int t, const int8_t* I, int64_t n, double theta);
 
 /* Stage timing for measurement.  usfft_set_timing(plan, on) resets the accumulators; with
@@ -185,10 +186,17 @@ usfft_status usfft_get_stage_times(usfft_plan_t* plan, usfft_stage_times* out);
 usfft_status usfft_get_set(const usfft_plan_t* plan, int8_t* freqs, int64_t n_capacity,
                            int64_t* n, int32_t* t);
 
-/* Final coefficients (Algorithm 1, step 3) on the current set I with one reconstructing
- * rank-1 lattice for I (no threshold): coefs receives [G][|I|][2] (re, im) fp64, host or
- * device pointer (coefs_on_device != 0).  freqs (may be NULL) receives [|I|][t] int8.
- * With coefs == NULL only *n is set. */
+/* Final coefficients (Algorithm 1, step 3) on the detected set I = I^(1..d), after all d
+ * increments (USFFT_ESTATE before): a reconstructing rank-1 lattice for I is searched with
+ * the rule of usfft_search_lattice, its draws keyed by phase 4 instead of 3; the FE problem
+ * is solved at its M nodes (all d coordinates on the lattice, no random tails) and each
+ * node's length-M FFT is read at k.z mod M, without a threshold.  The paper uses multiple
+ * rank-1 lattices here; one reconstructing lattice computes the same coefficients exactly
+ * for trigonometric polynomials supported in I (Appendix A).
+ * *n receives |I|; freqs (may be NULL) receives [|I|][d] int8; coefs (may be NULL: only the
+ * sizes are returned) receives [G][|I|][2] (re, im) fp64 through a host pointer, or a device
+ * pointer when coefs_on_device != 0.  The last-step inspection calls then describe this
+ * step (lattice, candidates = I, samples, coefficients). */
 usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, double* coefs,
                                int coefs_on_device);
 

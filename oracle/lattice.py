@@ -75,8 +75,9 @@ def is_reconstructing(J: np.ndarray, z: np.ndarray, M: int) -> bool:
     return len(np.unique(m)) == len(m)
 
 
-def search(J: np.ndarray, t: int, seed: int, trials: int = 64, max_sizes: int = 400):
-    """(z, M) of the first reconstructing lattice under the rule in the module header."""
+def search(J: np.ndarray, t: int, seed: int, trials: int = 64, max_sizes: int = 400, phase: int = rng.PHASE_LATTICE):
+    """(z, M) of the first reconstructing lattice under the rule in the module header; the
+    draws are keyed by `phase` (PHASE_LATTICE in the coupled steps, PHASE_RECON in step 3)."""
     if len(J) == 0:
         return np.zeros(t, dtype=np.int64), 0
     if len(np.unique(J, axis=0)) < len(J):
@@ -88,7 +89,7 @@ def search(J: np.ndarray, t: int, seed: int, trials: int = 64, max_sizes: int = 
         for tr in range(trials):
             z = np.ones(t, dtype=np.int64)
             for j in range(2, t + 1):
-                z[j - 1] = rng.uniform_int(1, M - 1, seed, rng.PHASE_LATTICE, t, M, tr, j) if M > 1 else 0
+                z[j - 1] = rng.uniform_int(1, M - 1, seed, phase, t, M, tr, j) if M > 1 else 0
             if is_reconstructing(J, z, M):
                 return z, M
         M = next_admissible((105 * M + 99) // 100)

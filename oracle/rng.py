@@ -24,7 +24,8 @@ GOLDEN_GAMMA = 0x9E3779B97F4A7C15
 # phases of the counter key
 PHASE_1D_TAIL = 1      # tails y'_j, j != t, of the 1-D detections (steps 1 & 2a)
 PHASE_TAIL = 2         # tails y'_{t+1..d} of the coupled step t (step 2b)
-PHASE_LATTICE = 3      # generating-vector components of the lattice search
+PHASE_LATTICE = 3      # generating-vector components of the lattice search (coupled steps)
+PHASE_RECON = 4        # generating-vector components of the step-3 lattice
 
 
 def mix64(z: int) -> int:

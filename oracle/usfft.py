@@ -19,6 +19,11 @@ of positions in J_t; I^(1..t) keeps J_t's order.
 
 Sampling uses exact lattice integers: sin(2 pi y_j) = sin(2 pi n/M) with
 n = i z_j mod M for lattice coordinates.
+
+Step 3 (reconstruct): one reconstructing rank-1 lattice for I^(1..d) (the search rule
+of oracle.lattice with draws keyed by PHASE_RECON; the paper uses multiple lattices
+here, a single reconstructing lattice gives the same coefficients exactly for
+polynomials supported in I), samples at its nodes, DFT at k.z mod M, no threshold.
 """
 import math
 from dataclasses import dataclass, field
@@ -184,6 +189,22 @@ class OracleRun:
                                            sel if self.keep else []))
         idx = sorted(found)
         self.I_prefix = J[idx] if len(idx) else np.zeros((0, t), dtype=np.int64)
+
+    # ---- Algorithm 1, step 3 ----------------------------------------------------------
+    def reconstruct(self):
+        """Coefficients of every node on I = I^(1..d) from one reconstructing rank-1 lattice
+        (draws keyed by PHASE_RECON), no tails, no threshold: (I, z, M, C [G, |I|])."""
+        assert self.t == self.prob.d
+        I = self.I_prefix
+        d = self.prob.d
+        z, M = lattice.search(I, d, self.p.seed, self.p.max_lattice_trials, phase=rng.PHASE_RECON)
+        if len(I) == 0:
+            return I, z, M, np.zeros((0, 0), dtype=np.complex128)
+        m = lattice.lattice_indices(I, z, M)
+        nodes = NodeSet(d, list(range(d)), z, M, {})
+        U = sample(self.prob, nodes, self.mesh)
+        self.samples_used += M
+        return I, z, M, dft.coefficients(U, m, M)
 
     def resume(self, t: int, I_prefix: np.ndarray, theta: float):
         """Continue from the state after increment t: I^(1..t) and theta (checkpoint)."""

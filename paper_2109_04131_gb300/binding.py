@@ -344,9 +344,15 @@ class Plan:
         return out.astype(np.int64)
 
     def reconstruct(self):
+        """(I [n][d] int64, C [G][n] complex128): step 3 on the detected set."""
         n = ctypes.c_int64(0)
         self._ck(self._lib.usfft_reconstruct(self.handle, ctypes.byref(n), None, None, 0))
-        return n.value
+        d = self.problem.d
+        I = np.zeros((n.value, d), dtype=np.int8)
+        C = np.zeros((self.problem.G if self.problem.kind != 3 else self.problem.tp_freqs.shape[0], n.value, 2))
+        if n.value:
+            self._ck(self._lib.usfft_reconstruct(self.handle, ctypes.byref(n), I.ctypes.data, C.ctypes.data, 0))
+        return I.astype(np.int64), C[..., 0] + 1j * C[..., 1]
 
     def get_lattice(self):
         M = ctypes.c_int64(0)

@@ -650,7 +650,7 @@ usfft_status usfft_rewind(usfft_plan_t* plan, int t) {
 
 usfft_status usfft_resume(usfft_plan_t* plan, int t, const int8_t* I, int64_t n, double theta) {
     if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
-    if (t < 0 || t >= plan->d || n < 0 || (n > 0 && !I)) return fail(plan, USFFT_EINVAL, "usfft_resume: invalid argument");
+    if (t < 0 || t > plan->d || n < 0 || (n > 0 && !I)) return fail(plan, USFFT_EINVAL, "usfft_resume: invalid argument");
     if (t > 0 && !(theta > 0.0)) return fail(plan, USFFT_EINVAL, "usfft_resume: theta must be > 0");
     plan->t = t;
     plan->nIpre = t > 0 ? n : 0;
@@ -777,12 +777,48 @@ usfft_status usfft_get_selection(const usfft_plan_t* plan_c, uint32_t* bitmap, i
 }
 
 usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, double* coefs, int coefs_on_device) {
-    (void)freqs;
-    (void)coefs;
-    (void)coefs_on_device;
     if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (plan->t != plan->d) return fail(plan, USFFT_ESTATE, "usfft_reconstruct needs all d increments done");
     if (n) *n = plan->nIpre;
-    return fail(plan, USFFT_ESTATE, "usfft_reconstruct is not available in this version");
+    if (freqs) memcpy(freqs, plan->Ipre.data(), plan->Ipre.size());
+    if (!coefs) return USFFT_OK;
+    const int d = plan->d;
+    const int64_t nI = plan->nIpre;
+    if (nI == 0) return USFFT_OK;
+    // one reconstructing rank-1 lattice for I (Algorithm 1, step 3; single-lattice reading)
+    std::vector<int64_t> z;
+    int64_t M = 0;
+    if (!lattice_search(plan->Ipre.data(), nI, d, plan->par.seed, plan->par.max_lattice_trials, 400, z, M,
+                        PHASE_RECON))
+        return fail(plan, USFFT_ELATTICE, "no reconstructing rank-1 lattice for the detected set");
+    std::vector<int64_t> m((size_t)nI);
+    for (int64_t a = 0; a < nI; ++a) {
+        int64_t acc = 0;
+        for (int j = 0; j < d; ++j) acc += (int64_t)plan->Ipre[(size_t)(a * d + j)] * z[(size_t)j];
+        int64_t mm = acc % M;
+        m[(size_t)a] = mm < 0 ? mm + M : mm;
+    }
+    plan->launches = 0;
+    usfft_status st = prepare_step(plan, M, m);
+    if (st != USFFT_OK) return st;
+    plan->J = plan->Ipre;
+    plan->z = z;
+    plan->last_coupled = true;
+    plan->last_t = d;
+    plan->replay_valid = false;
+    NodeSpec ns;
+    memset(&ns, 0, sizeof ns);
+    ns.M = M;
+    ns.d = d;
+    for (int j = 0; j < d; ++j) ns.z[j] = z[(size_t)j];
+    plan->specs.assign(1, ns);
+    plan->s_tilde = 0;                       // no threshold in step 3
+    if ((st = run_step_device(plan, false)) != USFFT_OK) return st;
+    if ((st = read_cg_stats(plan, M)) != USFFT_OK) return st;
+    const size_t bytes = sizeof(double2) * (size_t)nI * plan->G;
+    CK(cudaMemcpyAsync(coefs, plan->C.p, bytes, coefs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       plan->stream));
+    return wait_stream(plan);
 }
 
 usfft_status usfft_search_lattice(const int8_t* J, int64_t n, int t, uint64_t seed, int trials, int max_sizes,

@@ -12,6 +12,8 @@
 //     k -> k.z mod M is injective on J is taken;
 //   - the search gives up on a repeated candidate, after 400 sizes or beyond
 //     M = 4096^2 (the largest two-pass FFT).
+// Step 3 (the final coefficients on I) uses the same rule with the draws keyed by
+// PHASE_RECON instead of PHASE_LATTICE.
 #include <stdint.h>
 
 #include <algorithm>
@@ -103,7 +105,7 @@ static bool injective(const int8_t* J, int64_t n, int t, const int64_t* z, int64
 }
 
 bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials, int max_sizes,
-                    std::vector<int64_t>& z, int64_t& M) {
+                    std::vector<int64_t>& z, int64_t& M, uint64_t phase) {
     z.assign((size_t)t, 0);
     if (n == 0) {
         M = 0;
@@ -130,7 +132,7 @@ bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials
             z[0] = 1;
             for (int j = 2; j <= t; ++j) {
                 if (m > 1) {
-                    uint64_t f[5] = {PHASE_LATTICE, (uint64_t)t, (uint64_t)m, (uint64_t)tr, (uint64_t)j};
+                    uint64_t f[5] = {phase, (uint64_t)t, (uint64_t)m, (uint64_t)tr, (uint64_t)j};
                     z[(size_t)(j - 1)] = rng_uniform_int(1, m - 1, seed, f, 5);
                 } else {
                     z[(size_t)(j - 1)] = 0;

@@ -89,18 +89,37 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
                 if (key && (key & himask) == prefix) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
             }
             __syncthreads();
-            if (tid == 0) {
-                unsigned int want = sh_want, cum = 0;
-                int dsel = 0;
-                for (int dg = 255; dg >= 0; --dg) {
-                    if (cum + hist[dg] >= want) {
-                        dsel = dg;
-                        break;
-                    }
-                    cum += hist[dg];
+            if (warp == 0) {
+                // warp-parallel scan from the top digit: lane l owns digits 255-8l .. 248-8l
+                const unsigned int want = sh_want;
+                unsigned int c[8], own = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    c[q] = hist[255 - 8 * lane - q];
+                    own += c[q];
                 }
-                sh_want = want - cum;
-                sh_prefix = prefix | ((unsigned long long)dsel << shift);
+                unsigned int incl = own;             // inclusive prefix over lanes 0..lane
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const unsigned int excl = incl - own;   // keys with a larger digit than this lane's range
+                const bool hit = excl < want && want <= incl;
+                if (hit) {
+                    unsigned int cum = excl;
+                    int dsel = 255 - 8 * lane;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (cum + c[q] >= want) {
+                            dsel = 255 - 8 * lane - q;
+                            break;
+                        }
+                        cum += c[q];
+                    }
+                    sh_want = want - cum;
+                    sh_prefix = prefix | ((unsigned long long)dsel << shift);
+                }
             }
             __syncthreads();
         }

@@ -18,7 +18,7 @@ namespace usfft {
 
 // Counter-based SplitMix64 draws (Steele, Lea, Flood 2014): key(seed, f1, f2, ...)
 // folds one SplitMix64 step per field, h <- mix64((h ^ f) + golden gamma).
-enum Phase : uint64_t { PHASE_1D_TAIL = 1, PHASE_TAIL = 2, PHASE_LATTICE = 3 };
+enum Phase : uint64_t { PHASE_1D_TAIL = 1, PHASE_TAIL = 2, PHASE_LATTICE = 3, PHASE_RECON = 4 };
 uint64_t rng_key(uint64_t seed, const uint64_t* fields, int nfields);
 double rng_uniform(uint64_t seed, const uint64_t* fields, int nfields);                 // [0,1)
 int64_t rng_uniform_int(int64_t lo, int64_t hi, uint64_t seed, const uint64_t* fields, int nfields);
@@ -27,9 +27,10 @@ bool is_smooth7(int64_t m);
 int64_t next_admissible(int64_t x);
 
 // Reconstructing rank-1 lattice search: J is [n][t] int8 row-major.  Returns false if
-// none is found within max_sizes sizes; z receives t entries.
+// none is found within max_sizes sizes; z receives t entries.  `phase` keys the draws
+// (PHASE_LATTICE for the coupled steps, PHASE_RECON for step 3).
 bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials, int max_sizes,
-                    std::vector<int64_t>& z, int64_t& M);
+                    std::vector<int64_t>& z, int64_t& M, uint64_t phase = PHASE_LATTICE);
 
 // Candidate set J_t = I_prev x I_t within [-N,N]^t (lexicographic in the positions).
 void candidate_set(const int8_t* I_prev, int64_t n_prev, int t_prev, const std::vector<int>& I_t, int N,

@@ -231,3 +231,48 @@ def test_increment_after_last_is_a_state_error(B):
         p.increment()
     assert e.value.status == 7
     p.close()
+
+
+def _reconstruct_both(B, prob, params):
+    plan = B.Plan(prob, params)
+    run = OracleRun(prob, params, keep=True)
+    for _ in range(prob.d):
+        if run.t > 0:
+            plan.resume(run.t, run.I_prefix, run.theta)
+        run.increment()
+        plan.increment()
+    plan.resume(run.t, run.I_prefix, run.theta)
+    I_o, z_o, M_o, C_o = run.reconstruct()
+    I_g, C_g = plan.reconstruct()
+    assert np.array_equal(I_g, I_o)
+    z, M = plan.get_lattice()
+    assert M == M_o and np.array_equal(z, z_o)
+    return plan, I_g, C_g, C_o
+
+
+def test_reconstruct_trigpoly_coefficients(B):
+    prob = W.trigpoly(G=9, d=4, N=5, seed=8, base_terms=5, node_terms=2, kmax=3, mag_lo=1e-4)
+    params = W.Params(N=5, s=40, s_local=40, delta=1e-9, delta_is_relative=False, r=1, seed=8)
+    plan, I, C, C_o = _reconstruct_both(B, prob, params)
+    for g in range(prob.G):
+        truth = {tuple(int(v) for v in f): c for f, c in zip(prob.tp_freqs[g], prob.tp_coefs[g]) if c != 0}
+        want = np.array([truth.get(tuple(int(v) for v in k), 0.0) for k in I])
+        assert np.max(np.abs(C[g] - want)) < 1e-13
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED])
+def test_reconstruct_2d_matches_oracle(B, precision):
+    w = W.with_precision(W.small_2d(n=15, d=3, seed=2, N=4, s=20), precision)
+    plan, I, C, C_o = _reconstruct_both(B, w.problem, w.params)
+    assert C.shape == C_o.shape and len(I) > 0
+    assert node_rel(C, C_o) < TOL
+    # the device-pointer variant of the copy gives the same numbers
+    import torch
+    out = torch.empty((w.problem.G, len(I), 2), dtype=torch.float64, device="cuda")
+    n = B.ctypes.c_int64(0)
+    st = plan._lib.usfft_reconstruct(plan.handle, B.ctypes.byref(n), None, B.ctypes.c_void_p(out.data_ptr()), 1)
+    assert st == 0 and n.value == len(I)
+    Cd = out.cpu().numpy()
+    assert np.max(np.abs((Cd[..., 0] + 1j * Cd[..., 1]) - C)) <= 1e-12 * np.max(np.abs(C))
+    plan.close()

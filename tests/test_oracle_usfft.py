@@ -102,3 +102,30 @@ def test_last_increment_uses_one_iteration_and_s():
     assert all(len(s) <= 2 for s in last[0].selected)
     mid = [r for r in run.records if r.coupled and r.t == 2]
     assert len(mid) == 3
+
+
+def test_step3_reconstruction_returns_the_polynomial_coefficients():
+    # Algorithm 1, step 3: on the detected set I (= the union of the supports here) a
+    # reconstructing rank-1 lattice samples the full d-variate function, so the lattice
+    # DFT returns each node's own coefficients (Appendix A; no tails, no threshold)
+    from oracle import lattice
+    d, N, G = 4, 5, 7
+    prob = W.trigpoly(G=G, d=d, N=N, seed=8, base_terms=5, node_terms=2, kmax=3, mag_lo=1e-4)
+    params = W.Params(N=N, s=40, s_local=40, delta=1e-9, delta_is_relative=False, r=1, seed=8)
+    assert _margins_ok(prob, params, params.delta)
+    run = OracleRun(prob, params, keep=True)
+    with pytest.raises(AssertionError):
+        run.reconstruct()                        # only after all d increments
+    for _ in range(d):
+        run.increment()
+    I, z, M, C = run.reconstruct()
+    sup = _support(prob)
+    assert {tuple(int(v) for v in k) for k in I} == set().union(*[set(s) for s in sup])
+    assert lattice.is_reconstructing(I, z, M) and z[0] == 1
+    # the phase-4 draws give a lattice of their own (not the last coupled step's)
+    zs, Ms = lattice.search(I, d, params.seed, params.max_lattice_trials, phase=rng.PHASE_RECON)
+    assert Ms == M and np.array_equal(zs, z)
+    assert C.shape == (G, len(I))
+    for g in range(G):
+        want = np.array([sup[g].get(tuple(int(v) for v in k), 0.0) for k in I])
+        assert np.max(np.abs(C[g] - want)) < 1e-13
