@@ -200,6 +200,34 @@ usfft_status usfft_get_set(const usfft_plan_t* plan, int8_t* freqs, int64_t n_ca
 usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, double* coefs,
                                int coefs_on_device);
 
+/* Evaluation at explicit parameter points (Section 4).  y is [n][d] fp64 row-major (one
+ * point y^(j) per row; coordinates on the torus, any real value is taken mod 1 by the
+ * 1-periodic coefficient model).  With on_device != 0, y and the output are device pointers
+ * (the calls then work in place, in one pass), else host pointers (staged through the plan
+ * in chunks of 8192 points).  Outputs belong to the caller. */
+
+/* The black box at the points: the FE solution u-check(x_g, y^(j)) of Eq. (1.1) for fixed
+ * y^(j) (or the test polynomials' values), samples [n][G] fp64.  USFFT_ENOCONV if a 2-D
+ * solve misses the CG tolerance. */
+usfft_status usfft_sample_points(usfft_plan_t* plan, const double* y, int64_t n, double* samples,
+                                 int on_device);
+
+/* The approximation u^usFFT(x_g, y^(j)) = sum_{k in I} c_{g,k} e^{2 pi i k.y^(j)} with the set
+ * and coefficients of the last usfft_reconstruct (USFFT_ESTATE before one): values
+ * [n][G][2] (re, im) fp64.  The imaginary part is zero up to rounding when I is closed under
+ * k -> -k (the coefficients of a real function are then conjugate pairs). */
+usfft_status usfft_evaluate(usfft_plan_t* plan, const double* y, int64_t n, double* values,
+                            int on_device);
+
+/* The errors of Section 4 over n >= 1 test points, per mesh node g:
+ *   err2[g]   = ( (1/n) sum_j |u-check(x_g, y^(j)) - u^usFFT(x_g, y^(j))|^2 )^(1/2)
+ *   errinf[g] = max_j |u-check(x_g, y^(j)) - u^usFFT(x_g, y^(j))|
+ * (|.| the complex modulus).  y is a host (y_on_device == 0) or device pointer; err2 and
+ * errinf are host arrays of G doubles.  The FE solutions and the approximation are formed
+ * chunk by chunk on the device and never leave it; the sums are reduced in a fixed order. */
+usfft_status usfft_errors(usfft_plan_t* plan, const double* y, int64_t n, int y_on_device,
+                          double* err2, double* errinf);
+
 /* Inspection of the last detection step (the coupled step of the last increment, or the
  * 1-D detection when t = 1): lattice, candidates J_t with their DFT indices k.z mod M,
  * and the samples U [M][G], coefficients C [G][|J|] and union bitmap of its LAST detection

@@ -6,7 +6,8 @@ allocator (through the allocator hook of usfft_params) and its work runs on the
 current PyTorch stream unless another stream is given.
 
 Module-level functions carry the C names (usfft_plan, usfft_increment, usfft_replay,
-usfft_rewind, usfft_resume, usfft_get_set, usfft_reconstruct, usfft_get_lattice, usfft_get_candidates,
+usfft_rewind, usfft_resume, usfft_get_set, usfft_reconstruct, usfft_sample_points, usfft_evaluate,
+usfft_errors, usfft_get_lattice, usfft_get_candidates,
 usfft_get_samples, usfft_get_coefficients, usfft_get_selection, usfft_last_error,
 usfft_destroy); ``Plan`` wraps them.
 """
@@ -67,6 +68,9 @@ SIGNATURES = {
     "usfft_get_set": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int32)]),
     "usfft_reconstruct": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), _P, _P, ctypes.c_int]),
+    "usfft_sample_points": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int]),
+    "usfft_evaluate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int]),
+    "usfft_errors": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, _P, _P]),
     "usfft_get_lattice": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
     "usfft_get_candidates": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), _P]),
     "usfft_get_samples": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
@@ -200,6 +204,18 @@ def usfft_get_set(plan):
 
 def usfft_reconstruct(plan):
     return plan.reconstruct()
+
+
+def usfft_sample_points(plan, Y):
+    return plan.sample_points(Y)
+
+
+def usfft_evaluate(plan, Y):
+    return plan.evaluate(Y)
+
+
+def usfft_errors(plan, Y):
+    return plan.errors(Y)
 
 
 def usfft_get_lattice(plan):
@@ -349,10 +365,36 @@ class Plan:
         self._ck(self._lib.usfft_reconstruct(self.handle, ctypes.byref(n), None, None, 0))
         d = self.problem.d
         I = np.zeros((n.value, d), dtype=np.int8)
-        C = np.zeros((self.problem.G if self.problem.kind != 3 else self.problem.tp_freqs.shape[0], n.value, 2))
+        C = np.zeros((self.problem.G, n.value, 2))
         if n.value:
             self._ck(self._lib.usfft_reconstruct(self.handle, ctypes.byref(n), I.ctypes.data, C.ctypes.data, 0))
         return I.astype(np.int64), C[..., 0] + 1j * C[..., 1]
+
+    def _points(self, Y) -> np.ndarray:
+        Y = np.ascontiguousarray(np.asarray(Y, dtype=np.float64).reshape(-1, self.problem.d))
+        return Y
+
+    def sample_points(self, Y) -> np.ndarray:
+        """FE solutions (the black box) at the rows of Y: [n][G]."""
+        Y = self._points(Y)
+        U = np.zeros((len(Y), self.problem.G))
+        self._ck(self._lib.usfft_sample_points(self.handle, Y.ctypes.data, len(Y), U.ctypes.data, 0))
+        return U
+
+    def evaluate(self, Y) -> np.ndarray:
+        """u^usFFT at the rows of Y with the last reconstruction: complex [n][G]."""
+        Y = self._points(Y)
+        V = np.zeros((len(Y), self.problem.G, 2))
+        self._ck(self._lib.usfft_evaluate(self.handle, Y.ctypes.data, len(Y), V.ctypes.data, 0))
+        return V[..., 0] + 1j * V[..., 1]
+
+    def errors(self, Y):
+        """(err_2 [G], err_inf [G]) of the last reconstruction over the test points Y."""
+        Y = self._points(Y)
+        e2 = np.zeros(self.problem.G)
+        ei = np.zeros(self.problem.G)
+        self._ck(self._lib.usfft_errors(self.handle, Y.ctypes.data, len(Y), 0, e2.ctypes.data, ei.ctypes.data))
+        return e2, ei
 
     def get_lattice(self):
         M = ctypes.c_int64(0)

@@ -69,6 +69,9 @@ struct usfft_plan_s {
     FftPlan fp{};
     // device buffers
     Buf psi, U, C, bitmap, twid, goff, gk, gm2, fftscr, cgscr, iters, failc, scal, tpf, tpc, tpaux;
+    // step 3 result (usfft_reconstruct) and the buffers of point evaluation
+    Buf Crec, Irec, Ypts, Upts, Vpts, epart, etot;
+    int64_t nrec = -1;     // |I| of the stored reconstruction, -1: none
     size_t bytes = 0;
     int cg_blocks = 0;
     int launches = 0;
@@ -234,13 +237,14 @@ struct StageTimer {
     }
 };
 
-// sampler dispatch: U[0..M)[G] for the node set
-usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns) {
+// sampler dispatch: out[0..M)[G] for the node set (out = the plan's sample buffer by default)
+usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns, double* out = nullptr) {
     const int kind = plan->prob.kind;
+    double* U = out ? out : (double*)plan->U.p;
     StageTimer timer(plan, USFFT_STAGE_SAMPLE);
     if (kind == USFFT_PDE_1D) {
         CK(launch_sample_1d(ns, plan->prob.n, plan->prob.coef_model, plan->prob.f_const, (const double*)plan->psi.p,
-                            0, ns.M, (double*)plan->U.p, plan->stream, &plan->launches));
+                            0, ns.M, U, plan->stream, &plan->launches));
     } else if (kind == USFFT_PDE_2D) {
         CgConfig cg;
         cg.precision = plan->par.precision;
@@ -250,12 +254,12 @@ usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns) {
         cg.coef_scale = plan->prob.coef_scale;
         cg.coef_decay = plan->prob.coef_decay;
         CK(launch_sample_2d(ns, plan->prob.n, plan->prob.coef_model, plan->prob.f_const, (const double*)plan->psi.p, cg,
-                            0, ns.M, (double*)plan->U.p, (int*)plan->iters.p, (unsigned int*)plan->failc.p,
+                            0, ns.M, U, (int*)plan->iters.p, (unsigned int*)plan->failc.p,
                             (unsigned long long*)((char*)plan->failc.p + 8), (double*)plan->cgscr.p,
                             plan->cgscr.bytes, plan->stream, &plan->launches));
     } else {
         CK(launch_sample_trigpoly(ns, plan->G, plan->prob.tp_nterms, (const int8_t*)plan->tpf.p,
-                                  (const double*)plan->tpc.p, (double*)plan->tpaux.p, (double*)plan->U.p,
+                                  (const double*)plan->tpc.p, (double*)plan->tpaux.p, U,
                                   plan->stream, &plan->launches));
     }
     return USFFT_OK;
@@ -799,6 +803,10 @@ usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, do
         m[(size_t)a] = mm < 0 ? mm + M : mm;
     }
     plan->launches = 0;
+    plan->cg_iters_total = 0;
+    plan->cg_iters_max = 0;
+    plan->nrec = -1;
+    CK(cudaMemsetAsync(plan->failc.p, 0, sizeof(unsigned), plan->stream));
     usfft_status st = prepare_step(plan, M, m);
     if (st != USFFT_OK) return st;
     plan->J = plan->Ipre;
@@ -816,8 +824,162 @@ usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, do
     if ((st = run_step_device(plan, false)) != USFFT_OK) return st;
     if ((st = read_cg_stats(plan, M)) != USFFT_OK) return st;
     const size_t bytes = sizeof(double2) * (size_t)nI * plan->G;
+    // keep I and the coefficients for usfft_evaluate / usfft_errors
+    if ((st = ensure(plan, plan->Crec, bytes, "reconstruction coefficients")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->Irec, (size_t)nI * d, "reconstruction set")) != USFFT_OK) return st;
+    CK(cudaMemcpyAsync(plan->Crec.p, plan->C.p, bytes, cudaMemcpyDeviceToDevice, plan->stream));
+    CK(cudaMemcpyAsync(plan->Irec.p, plan->Ipre.data(), (size_t)nI * d, cudaMemcpyHostToDevice, plan->stream));
+    plan->h2d += (int64_t)nI * d;
     CK(cudaMemcpyAsync(coefs, plan->C.p, bytes, coefs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        plan->stream));
+    if ((st = wait_stream(plan)) != USFFT_OK) return st;
+    plan->nrec = nI;
+    return USFFT_OK;
+}
+
+// ---- evaluation at given points (Section 4) ----------------------------------------------
+namespace {
+
+const int64_t kPointChunk = 8192;
+
+usfft_status check_points(usfft_plan_t* plan, const double* y, int64_t n, const char* who) {
+    if (n < 0 || (n > 0 && !y)) return fail(plan, USFFT_EINVAL, std::string(who) + ": need n >= 0 and y");
+    return USFFT_OK;
+}
+
+// points [cnt][d] on the device: the caller's (device input) or staged through Ypts
+usfft_status stage_points(usfft_plan_t* plan, const double* y, int64_t off, int64_t cnt, int on_device,
+                          const double** yd) {
+    const int d = plan->d;
+    if (on_device) {
+        *yd = y + off * d;
+        return USFFT_OK;
+    }
+    usfft_status st = ensure(plan, plan->Ypts, sizeof(double) * (size_t)kPointChunk * d, "points");
+    if (st != USFFT_OK) return st;
+    CK(cudaMemcpyAsync(plan->Ypts.p, y + off * d, sizeof(double) * (size_t)cnt * d, cudaMemcpyHostToDevice,
+                       plan->stream));
+    plan->h2d += (int64_t)(sizeof(double) * (size_t)cnt * d);
+    *yd = (const double*)plan->Ypts.p;
+    return USFFT_OK;
+}
+
+// FE solutions (or the test polynomials) at cnt explicit points into out [cnt][G] (device)
+usfft_status sample_at(usfft_plan_t* plan, const double* yd, int64_t cnt, double* out) {
+    usfft_status st = ensure(plan, plan->iters, sizeof(int) * (size_t)cnt, "cg iterations");
+    if (st != USFFT_OK) return st;
+    NodeSpec ns;
+    memset(&ns, 0, sizeof ns);
+    ns.M = cnt;
+    ns.d = plan->d;
+    ns.Y = yd;
+    if ((st = run_sampler(plan, ns, out)) != USFFT_OK) return st;
+    return read_cg_stats(plan, cnt);
+}
+
+void reset_counters(usfft_plan_t* plan) {
+    plan->launches = 0;
+    plan->cg_iters_total = 0;
+    plan->cg_iters_max = 0;
+    plan->h2d = plan->d2h = 0;
+}
+
+}  // namespace
+
+usfft_status usfft_sample_points(usfft_plan_t* plan, const double* y, int64_t n, double* samples, int on_device) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    usfft_status st = check_points(plan, y, n, "usfft_sample_points");
+    if (st != USFFT_OK) return st;
+    if (n > 0 && !samples) return fail(plan, USFFT_EINVAL, "usfft_sample_points: samples is NULL");
+    reset_counters(plan);
+    CK(cudaMemsetAsync(plan->failc.p, 0, sizeof(unsigned), plan->stream));
+    const int G = plan->G;
+    for (int64_t off = 0; off < n; off += kPointChunk) {
+        const int64_t cnt = std::min(kPointChunk, n - off);
+        const double* yd = nullptr;
+        if ((st = stage_points(plan, y, off, cnt, on_device, &yd)) != USFFT_OK) return st;
+        double* out = samples + off * G;
+        if (!on_device) {
+            if ((st = ensure(plan, plan->Upts, sizeof(double) * (size_t)kPointChunk * G, "point samples")) != USFFT_OK)
+                return st;
+            out = (double*)plan->Upts.p;
+        }
+        if ((st = sample_at(plan, yd, cnt, out)) != USFFT_OK) return st;
+        if (!on_device) {
+            CK(cudaMemcpyAsync(samples + off * G, out, sizeof(double) * (size_t)cnt * G, cudaMemcpyDeviceToHost,
+                               plan->stream));
+            plan->d2h += (int64_t)(sizeof(double) * (size_t)cnt * G);
+            if ((st = wait_stream(plan)) != USFFT_OK) return st;
+        }
+    }
+    return wait_stream(plan);
+}
+
+usfft_status usfft_evaluate(usfft_plan_t* plan, const double* y, int64_t n, double* values, int on_device) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (plan->nrec < 0) return fail(plan, USFFT_ESTATE, "usfft_evaluate needs a usfft_reconstruct first");
+    usfft_status st = check_points(plan, y, n, "usfft_evaluate");
+    if (st != USFFT_OK) return st;
+    if (n > 0 && !values) return fail(plan, USFFT_EINVAL, "usfft_evaluate: values is NULL");
+    reset_counters(plan);
+    const int G = plan->G;
+    for (int64_t off = 0; off < n; off += kPointChunk) {
+        const int64_t cnt = std::min(kPointChunk, n - off);
+        const double* yd = nullptr;
+        if ((st = stage_points(plan, y, off, cnt, on_device, &yd)) != USFFT_OK) return st;
+        double2* out = (double2*)values + off * G;
+        if (!on_device) {
+            if ((st = ensure(plan, plan->Vpts, sizeof(double2) * (size_t)kPointChunk * G, "point values")) != USFFT_OK)
+                return st;
+            out = (double2*)plan->Vpts.p;
+        }
+        CK(launch_evaluate(yd, cnt, plan->d, (const int8_t*)plan->Irec.p, plan->nrec, (const double2*)plan->Crec.p,
+                           G, out, nullptr, nullptr, nullptr, plan->stream, &plan->launches));
+        if (!on_device) {
+            CK(cudaMemcpyAsync(values + 2 * off * G, out, sizeof(double2) * (size_t)cnt * G, cudaMemcpyDeviceToHost,
+                               plan->stream));
+            plan->d2h += (int64_t)(sizeof(double2) * (size_t)cnt * G);
+            if ((st = wait_stream(plan)) != USFFT_OK) return st;
+        }
+    }
+    return wait_stream(plan);
+}
+
+usfft_status usfft_errors(usfft_plan_t* plan, const double* y, int64_t n, int y_on_device, double* err2,
+                          double* errinf) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (plan->nrec < 0) return fail(plan, USFFT_ESTATE, "usfft_errors needs a usfft_reconstruct first");
+    if (n < 1 || !y) return fail(plan, USFFT_EINVAL, "usfft_errors: need n >= 1 test points");
+    if (!err2 || !errinf) return fail(plan, USFFT_EINVAL, "usfft_errors: err2 and errinf are required");
+    reset_counters(plan);
+    CK(cudaMemsetAsync(plan->failc.p, 0, sizeof(unsigned), plan->stream));
+    const int G = plan->G;
+    const int64_t tiles_max = (kPointChunk + evaluate_point_tile() - 1) / evaluate_point_tile();
+    usfft_status st;
+    if ((st = ensure(plan, plan->Upts, sizeof(double) * (size_t)kPointChunk * G, "point samples")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->epart, 2 * sizeof(double) * (size_t)tiles_max * G, "error partials")) != USFFT_OK)
+        return st;
+    if ((st = ensure(plan, plan->etot, 2 * sizeof(double) * (size_t)G, "errors")) != USFFT_OK) return st;
+    double* psum = (double*)plan->epart.p;
+    double* pmax = psum + (size_t)tiles_max * G;
+    double* tsum = (double*)plan->etot.p;
+    double* tmax = tsum + G;
+    CK(cudaMemsetAsync(tsum, 0, 2 * sizeof(double) * (size_t)G, plan->stream));
+    for (int64_t off = 0; off < n; off += kPointChunk) {
+        const int64_t cnt = std::min(kPointChunk, n - off);
+        const double* yd = nullptr;
+        if ((st = stage_points(plan, y, off, cnt, y_on_device, &yd)) != USFFT_OK) return st;
+        // the reference values: FE solutions at the test points
+        if ((st = sample_at(plan, yd, cnt, (double*)plan->Upts.p)) != USFFT_OK) return st;
+        CK(launch_evaluate(yd, cnt, plan->d, (const int8_t*)plan->Irec.p, plan->nrec, (const double2*)plan->Crec.p,
+                           G, nullptr, (const double*)plan->Upts.p, psum, pmax, plan->stream, &plan->launches));
+        const int tiles = (int)((cnt + evaluate_point_tile() - 1) / evaluate_point_tile());
+        CK(launch_error_accumulate(psum, pmax, tiles, G, tsum, tmax, plan->stream, &plan->launches));
+    }
+    CK(launch_error_finalize(tsum, G, n, plan->stream, &plan->launches));
+    CK(cudaMemcpyAsync(err2, tsum, sizeof(double) * (size_t)G, cudaMemcpyDeviceToHost, plan->stream));
+    CK(cudaMemcpyAsync(errinf, tmax, sizeof(double) * (size_t)G, cudaMemcpyDeviceToHost, plan->stream));
+    plan->d2h += (int64_t)(2 * sizeof(double) * (size_t)G);
     return wait_stream(plan);
 }
 
@@ -845,9 +1007,10 @@ double usfft_draw_uniform(uint64_t seed, const uint64_t* fields, int nfields) {
 void usfft_destroy(usfft_plan_t* plan) {
     if (!plan) return;
     cudaStreamSynchronize(plan->stream);
-    Buf* bufs[] = {&plan->psi, &plan->U, &plan->C, &plan->bitmap, &plan->twid, &plan->goff, &plan->gk, &plan->gm2,
-                   &plan->fftscr, &plan->cgscr, &plan->iters, &plan->failc, &plan->scal, &plan->tpf, &plan->tpc,
-                   &plan->tpaux};
+    Buf* bufs[] = {&plan->psi,   &plan->U,    &plan->C,    &plan->bitmap, &plan->twid, &plan->goff,
+                   &plan->gk,    &plan->gm2,  &plan->fftscr, &plan->cgscr, &plan->iters, &plan->failc,
+                   &plan->scal,  &plan->tpf,  &plan->tpc,  &plan->tpaux, &plan->Crec, &plan->Irec,
+                   &plan->Ypts,  &plan->Upts, &plan->Vpts, &plan->epart, &plan->etot};
     for (Buf* b : bufs) buf_free(plan, *b);
     if (plan->pinned) cudaFreeHost(plan->pinned);
     if (plan->ev0) cudaEventDestroy(plan->ev0);

@@ -8,6 +8,7 @@
 namespace usfft {
 
 __device__ __forceinline__ double node_sin2(const NodeSpec& ns, int j, int64_t i) {
+    if (ns.Y) return sinpi(2.0 * ns.Y[i * ns.d + j]);
     int64_t zj = ns.z[j];
     if (zj >= 0) {
         int64_t nn = (i * zj) % ns.M;

@@ -72,9 +72,11 @@ cudaError_t launch_psi_table(int kind, int n, int d, double scale, double decay,
     return cudaGetLastError();
 }
 
-// sin(2 pi y_j) of lattice node i: exact integer reduction n = i z_j mod M for lattice
-// coordinates (Eq. (3.4)), the fixed tail value otherwise.
+// sin(2 pi y_j) of node i: the given coordinate for explicit points; on a lattice the exact
+// integer reduction n = i z_j mod M for lattice coordinates (Eq. (3.4)), the fixed tail
+// value otherwise.
 __device__ __forceinline__ double node_sin(const NodeSpec& ns, int j, int64_t i) {
+    if (ns.Y) return sinpi(2.0 * ns.Y[i * ns.d + j]);
     int64_t zj = ns.z[j];
     if (zj >= 0) {
         int64_t nn = (i * zj) % ns.M;

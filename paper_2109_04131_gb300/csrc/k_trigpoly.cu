@@ -1,5 +1,6 @@
 // Test black box: G real trigonometric polynomials p^(g)(y) = Re sum_s c_{g,s} e^{2 pi i h_{g,s}.y}
-// sampled at the nodes of a lattice with fixed tails (the setting of Theorem 1.1).
+// sampled at the nodes of a lattice with fixed tails (the setting of Theorem 1.1), or at
+// explicit points.
 //
 // For lattice coordinates the phase of node i is exact in integers:
 // sum_j h_j (i z_j mod M) = i (h.z) mod M, so each term keeps m_s = (h_lat . z) mod M and the
@@ -62,9 +63,50 @@ __global__ void trigpoly_sample_kernel(int64_t M, int G, int nterms, const doubl
     }
 }
 
+// Explicit points y_i (rows of Y): the phase h.y_i is summed term by term, each product
+// h_j y_ij reduced mod 1 with its rounding error kept (fma), so the phase error stays at the
+// rounding level of numbers in [-1/2, 1/2] whatever |h|.
+__global__ void trigpoly_points_kernel(const double* Y, int64_t count, int d, int G, int nterms,
+                                       const int8_t* freqs, const double* coefs, double* U) {
+    const int64_t total = count * G;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / G;
+        const int g = (int)(idx % G);
+        const double* y = Y + i * d;
+        double acc = 0.0;
+        for (int s = 0; s < nterms; ++s) {
+            const int64_t t = (int64_t)g * nterms + s;
+            const double cr = coefs[2 * t], ci = coefs[2 * t + 1];
+            if (cr == 0.0 && ci == 0.0) continue;
+            const int8_t* h = freqs + t * d;
+            double ph = 0.0;
+            for (int j = 0; j < d; ++j) {
+                if (!h[j]) continue;
+                const double hj = (double)h[j];
+                const double p = hj * y[j];
+                const double e = fma(hj, y[j], -p);
+                ph += (p - rint(p)) + e;
+            }
+            ph -= rint(ph);
+            double sv, cv;
+            sincospi(2.0 * ph, &sv, &cv);
+            acc += cr * cv - ci * sv;
+        }
+        U[idx] = acc;
+    }
+}
+
 cudaError_t launch_sample_trigpoly(const NodeSpec& ns, int G, int nterms, const int8_t* freqs,
                                    const double* coefs, double* aux, double* U, cudaStream_t s, int* launches) {
     if (ns.M <= 0) return cudaSuccess;
+    if (ns.Y) {
+        int64_t b = (ns.M * G + 255) / 256;
+        if (b > 152 * 64) b = 152 * 64;
+        trigpoly_points_kernel<<<(unsigned)b, 256, 0, s>>>(ns.Y, ns.M, ns.d, G, nterms, freqs, coefs, U);
+        if (launches) ++*launches;
+        return cudaGetLastError();
+    }
     int64_t tot = (int64_t)G * nterms;
     int b1 = (int)((tot + 255) / 256);
     trigpoly_setup_kernel<<<b1 > 0 ? b1 : 1, 256, 0, s>>>(ns, G, nterms, freqs, aux);

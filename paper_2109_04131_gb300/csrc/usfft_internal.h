@@ -44,6 +44,8 @@ struct NodeSpec {          // M sampling nodes: lattice coordinates and fixed ta
     int d;
     int64_t z[USFFT_MAX_D];      // >= 0: lattice coordinate with multiplier z_j; -1: tail
     double tail[USFFT_MAX_D];    // y'_j for tail coordinates
+    const double* Y;             // non-NULL: explicit points, node i is Y[i*d .. i*d+d) (device;
+                                 // z and tail unused)
 };
 
 struct FftPlan {           // M = L1 * L2 (L2 == 1: single pass of length L1)
@@ -106,6 +108,20 @@ cudaError_t launch_select_union(const double2* C, int G, int64_t nJ, double thet
 // out = max_g |C[g][col]|
 cudaError_t launch_absmax_column(const double2* C, int G, int64_t nJ, int64_t col, double* out,
                                  cudaStream_t s, int* launches);
+
+// Sparse approximation at explicit points (Section 4): V[j][g] = sum_k C[g][k] e^{2 pi i k.y_j}
+// (V may be NULL); with Uchk, per point tile r of 64 points and node g the partials
+// part_sum[r][g] = sum_j |Uchk[j][g] - V[j][g]|^2 and part_max[r][g] = max_j |...|.
+int64_t evaluate_max_points();
+int evaluate_point_tile();
+cudaError_t launch_evaluate(const double* Y, int64_t n, int d, const int8_t* I, int64_t nI, const double2* C, int G,
+                            double2* V, const double* Uchk, double* part_sum, double* part_max, cudaStream_t s,
+                            int* launches);
+// tot_sum[g] += sum_r part_sum[r][g], tot_max[g] = max(tot_max[g], max_r part_max[r][g])
+cudaError_t launch_error_accumulate(const double* part_sum, const double* part_max, int tiles, int G, double* tot_sum,
+                                    double* tot_max, cudaStream_t s, int* launches);
+// tot_sum[g] <- sqrt(tot_sum[g] / n)
+cudaError_t launch_error_finalize(double* tot_sum, int G, int64_t n, cudaStream_t s, int* launches);
 
 // Sets the message usfft_last_error(NULL) returns on the calling thread (capi.cu).
 void set_thread_error(const std::string& msg);

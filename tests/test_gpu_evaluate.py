@@ -1,0 +1,122 @@
+"""Parity of point sampling, evaluation of the sparse approximation and the errors of
+Section 4 (usfft_sample_points, usfft_evaluate, usfft_errors) with the oracle.
+
+Both sides reach step 3 from the oracle's state.  Bars: FE samples at the points within
+1e-10 of max |U| (the fp64 path and the mixed path); the approximation within 1e-10 of
+sum_k |c_{g,k}| per node (the library evaluates its own coefficients, which agree with
+the oracle's to 1e-10 per node); the errors within the sum of both."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import evaluate as ev
+from oracle.usfft import OracleRun
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2109_04131_gb300 import binding
+    binding.load_library()
+    return binding
+
+
+def _to_step3(B, prob, params):
+    plan = B.Plan(prob, params)
+    run = OracleRun(prob, params, keep=True)
+    for _ in range(prob.d):
+        run.increment()
+    plan.resume(run.t, run.I_prefix, run.theta)
+    I_o, z_o, M_o, C_o = run.reconstruct()
+    I_g, C_g = plan.reconstruct()
+    assert np.array_equal(I_g, I_o)
+    return plan, run, I_o, C_o, C_g
+
+
+def _check(B, plan, prob, run, I_o, C_o, Y):
+    U_o = ev.sample_points(prob, Y, run.mesh)
+    V_o = ev.evaluate(I_o, C_o, Y)
+    U_g = plan.sample_points(Y)
+    scale_u = np.max(np.abs(U_o))
+    assert U_g.shape == U_o.shape
+    assert np.max(np.abs(U_g - U_o)) <= TOL * scale_u
+    V_g = plan.evaluate(Y)
+    l1 = np.sum(np.abs(C_o), axis=1)                  # per node: bound of |V|
+    assert V_g.shape == V_o.shape
+    assert np.all(np.max(np.abs(V_g - V_o), axis=0) <= TOL * l1 + 1e-300)
+    e2_o, ei_o = ev.errors(U_o, V_o)
+    e2_g, ei_g = plan.errors(Y)
+    bar = TOL * (scale_u + l1)
+    assert np.all(np.abs(e2_g - e2_o) <= bar) and np.all(np.abs(ei_g - ei_o) <= bar)
+    assert np.all(e2_g <= ei_g * (1 + 1e-12))
+    return U_g, V_g, e2_g, ei_g
+
+
+def test_trigpoly_points_evaluation_and_errors(B):
+    prob = W.trigpoly(G=9, d=4, N=5, seed=8, base_terms=5, node_terms=2, kmax=3, mag_lo=1e-4)
+    params = W.Params(N=5, s=40, s_local=40, delta=1e-9, delta_is_relative=False, r=1, seed=8)
+    plan, run, I, C_o, C_g = _to_step3(B, prob, params)
+    # 9000 points: two chunks of the host path, a ragged point tile, |I| not a multiple of 16
+    Y = W.test_points(9000, prob.d, seed=1)
+    U, V, e2, ei = _check(B, plan, prob, run, I, C_o, Y)
+    # exact recovery: the approximation is the polynomial, the errors are at rounding level
+    assert np.max(np.abs(V - U)) < 1e-13 and np.max(ei) < 1e-13
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED])
+def test_2d_points_evaluation_and_errors(B, precision):
+    w = W.with_precision(W.small_2d(n=15, d=3, seed=2, N=4, s=20), precision)
+    plan, run, I, C_o, C_g = _to_step3(B, w.problem, w.params)
+    Y = W.test_points(333, w.problem.d, seed=2)
+    U, V, e2, ei = _check(B, plan, w.problem, run, I, C_o, Y)
+    # the detected expansion approximates the solution: errors well below the solution's size
+    assert np.max(ei) < 0.05 * np.max(np.abs(U))
+    plan.close()
+
+
+def test_device_pointer_variants(B):
+    import torch
+    w = W.with_precision(W.small_2d(n=9, d=3, seed=5, N=3, s=10), W.PRECISION_MIXED)
+    plan, run, I, C_o, C_g = _to_step3(B, w.problem, w.params)
+    Y = W.test_points(100, w.problem.d, seed=3)
+    G = w.problem.G
+    Yd = torch.from_numpy(Y).cuda()
+    Ud = torch.empty((100, G), dtype=torch.float64, device="cuda")
+    Vd = torch.empty((100, G, 2), dtype=torch.float64, device="cuda")
+    lib, h = plan._lib, plan.handle
+    assert lib.usfft_sample_points(h, Yd.data_ptr(), 100, Ud.data_ptr(), 1) == 0
+    assert lib.usfft_evaluate(h, Yd.data_ptr(), 100, Vd.data_ptr(), 1) == 0
+    e2 = np.zeros(G)
+    ei = np.zeros(G)
+    assert lib.usfft_errors(h, Yd.data_ptr(), 100, 1, e2.ctypes.data, ei.ctypes.data) == 0
+    U_h = plan.sample_points(Y)
+    V_h = plan.evaluate(Y)
+    e2_h, ei_h = plan.errors(Y)
+    torch.cuda.synchronize()
+    assert np.array_equal(Ud.cpu().numpy(), U_h)
+    Vn = Vd.cpu().numpy()
+    assert np.array_equal(Vn[..., 0] + 1j * Vn[..., 1], V_h)
+    assert np.array_equal(e2, e2_h) and np.array_equal(ei, ei_h)
+    plan.close()
+
+
+def test_evaluation_needs_a_reconstruction(B):
+    w = W.small_2d(n=7, d=2, seed=1, N=3, s=10)
+    plan = B.Plan(w.problem, w.params)
+    Y = W.test_points(4, 2, seed=0)
+    U = plan.sample_points(Y)                       # the black box needs no reconstruction
+    assert U.shape == (4, w.problem.G) and np.all(U > 0)
+    with pytest.raises(B.UsfftError) as e:
+        plan.evaluate(Y)
+    assert e.value.status == 7
+    with pytest.raises(B.UsfftError) as e:
+        plan.errors(Y)
+    assert e.value.status == 7
+    plan.close()

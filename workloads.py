@@ -204,3 +204,9 @@ def trigpoly_grid(G: int, d: int, K: int, seed: int, mag_lo: float = 1e-3) -> Pr
             ph = 0.0 if m == n else rng.uniform(0.0, 2.0 * math.pi)
             coefs[g, n] = mag * complex(math.cos(ph), math.sin(ph))
     return Problem(kind=TRIGPOLY, n=0, d=d, tp_freqs=freqs, tp_coefs=coefs)
+
+
+def test_points(n: int, d: int, seed: int) -> np.ndarray:
+    """n test parameters y^(j) drawn uniformly from the torus [0,1)^d (the distribution of the
+    periodic model's parameters; Section 4 uses such random test points): float64 [n, d]."""
+    return np.random.default_rng(np.random.SeedSequence([seed, 7, d])).random((n, d))
