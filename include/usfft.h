@@ -54,27 +54,43 @@ typedef enum {
 #define USFFT_PDE_2D 2        /* unit square, n*n interior nodes, "/"-split squares of side 1/(n+1) */
 #define USFFT_TRIGPOLY 3      /* test black box: G real trigonometric polynomials (Theorem 1.1)   */
 
-/* coefficient models, periodic in y (Eq. (1.2) with Theta_j(y) = sin(2 pi y_j), Sec. 4.1):
- *   AFFINE_SIN:    a(x,y) = 1 + sum_{j<=d} c j^-mu psi_j(x) sin(2 pi y_j)
- *   LOGNORMAL_SIN: a(x,y) = exp(sum_{j<=d} c j^-mu psi_j(x) sin(2 pi y_j))
+/* coefficient models (Eq. (1.2) and the lognormal form of Sec. 1):
+ *   AFFINE_SIN:    a(x,y) = 1 + sum_{j<=d} c j^-mu psi_j(x) Theta_j(y)
+ *   LOGNORMAL_SIN: a(x,y) = exp(sum_{j<=d} c j^-mu psi_j(x) Theta_j(y))
+ * with Theta_j chosen by the problem's theta_map (below): sin(2 pi y_j) for the periodic
+ * model of Sec. 4.2, else the parameter y_j itself (affine / lognormal models).
  * psi_j(x) = sin(j pi x) in 1-D; sin(j1 pi x1) sin(j2 pi x2) in 2-D with (j1, j2) the
- * j-th pair of the diagonal enumeration of Sec. 4.2 / Table 4.2, shifted by one:
+ * j-th pair of the diagonal enumeration of Sec. 4.3 / Table 4.2, shifted by one:
  * (1,1), (1,2), (2,1), (1,3), (2,2), (3,1), ...  The coefficient of an element is taken
  * at its centroid (midpoint in 1-D). */
 #define USFFT_COEF_AFFINE_SIN 1
 #define USFFT_COEF_LOGNORMAL_SIN 2
 
+/* parameter maps (theta_map; Sec. 3.2).  The library samples on the torus: a sampling node
+ * y~ in [0,1)^d gives Theta_j = sin(2 pi y~_j) (PERIODIC, no periodization), or Theta_j =
+ * phi_j(y~_j) with
+ *   TENT:   phi_j(y~) = beta - |(beta - alpha)(1 - 2 y~)|  (Eq. (3.2); y_j uniform on
+ *           [alpha, beta], affine model), inverse (y - alpha) / (2 (beta - alpha));
+ *   NORMAL: phi_{j,Delta} = tau_1 o tau_{2,Delta} (Eq. (3.3); y_j standard normal, lognormal
+ *           model), tau_1(v) = sqrt(2) erfinv(2 v), tau_{2,Delta} the shifted tent with poles
+ *           at y~ = Delta and 1/2 + Delta; inverse y~ = erf(y / sqrt 2) / 4 + Delta + 1/4.
+ * The detected coefficients are those of u~(x, y~) = u(x, phi(y~)).  Explicit points (the
+ * evaluation calls) are parameters y of the model's own domain. */
+#define USFFT_MAP_PERIODIC 0
+#define USFFT_MAP_TENT 1
+#define USFFT_MAP_NORMAL 2
+
 /* precision of the sampler */
 #define USFFT_FP64 0          /* fp64 everywhere; 2-D solves by Jacobi-preconditioned CG */
 #define USFFT_MIXED 1         /* 2-D: fp64-residual iterative refinement around fp32 flexible CG
                                  preconditioned by the constant-coefficient operator (2-D sine
-                                 transform on the tensor cores, TF32); 1-D: fp64; FFT, gather and
+                                 transform as BF16 tensor-core GEMMs); 1-D: fp64; FFT, gather and
                                  selection stay fp64 */
 #define USFFT_MIXED_JACOBI 2  /* 2-D: the same refinement around fp32 Jacobi-CG (for comparison) */
 
 typedef struct {
     int kind;                 /* USFFT_PDE_1D | USFFT_PDE_2D | USFFT_TRIGPOLY */
-    int n;                    /* PDE: interior nodes per side, 1 <= n <= 1023 (1-D), n <= 127 (2-D) */
+    int n;                    /* PDE: interior nodes per side, 1 <= n <= 1023 (1-D), n <= 63 (2-D) */
     int d;                    /* stochastic dimension, 1 <= d <= 64 */
     int coef_model;           /* USFFT_COEF_* (PDE kinds) */
     double coef_scale;        /* c  */
@@ -90,6 +106,13 @@ typedef struct {
     int tp_nterms;
     const int8_t* tp_freqs;
     const double* tp_coefs;
+    /* parameter map (PDE kinds; TRIGPOLY takes PERIODIC only) */
+    int theta_map;            /* USFFT_MAP_PERIODIC | USFFT_MAP_TENT | USFFT_MAP_NORMAL */
+    double map_alpha;         /* TENT: alpha < beta */
+    double map_beta;
+    double map_shift;         /* NORMAL: Delta in (0, 1/2); a lattice with a node at a pole is
+                                 rejected (USFFT_EINVAL); Lemma 3.1 gives 1/(4M) as the best
+                                 Delta for a single prime-size lattice */
 } usfft_problem;
 
 /* Device allocator hook: alloc(bytes, stream, ctx) returns device memory or NULL;
@@ -227,6 +250,18 @@ usfft_status usfft_evaluate(usfft_plan_t* plan, const double* y, int64_t n, doub
  * chunk by chunk on the device and never leave it; the sums are reduced in a fixed order. */
 usfft_status usfft_errors(usfft_plan_t* plan, const double* y, int64_t n, int y_on_device,
                           double* err2, double* errinf);
+
+/* Quantities of interest of the last usfft_reconstruct (USFFT_ESTATE before one), per mesh
+ * node g (host arrays, each may be NULL):
+ *   mean[g][2]   E(u^usFFT(x_g, .)) = sum_{k in I} c_{g,k} D_k (Sec. 4.1): D_k = prod_j D_{k_j}
+ *                with D_{k_j} = 1 for k_j = 0 and, for k_j != 0, 0 (PERIODIC: the mean is
+ *                c_{g,0}), 2i/(pi k_j) for odd k_j and 0 for even k_j (TENT, Eq. (4.5)), the
+ *                TENT factor times e^{2 pi i k_j Delta} (NORMAL);
+ *   variance[g]  sigma^2 = sum_{k in I, k != 0} |c_{g,k}|^2 (Sec. 4);
+ *   gsi[g][l-1]  the global sensitivity index rho(J_l) (Eq. (4.3)) of J_l = the k in I with
+ *                exactly l non-zero components (Eq. (4.4)), l = 1..d (0 where sigma^2 = 0).
+ * One warp per node reads the node's coefficients once; sums are reduced in a fixed order. */
+usfft_status usfft_statistics(usfft_plan_t* plan, double* mean, double* variance, double* gsi);
 
 /* Inspection of the last detection step (the coupled step of the last increment, or the
  * 1-D detection when t = 1): lattice, candidates J_t with their DFT indices k.z mod M,

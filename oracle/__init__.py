@@ -11,7 +11,7 @@ sparse FFT with application to PDEs with random coefficients"):
 - ``rng``      counter-based SplitMix64 draws for the random tails y' and the
                lattice search (the paper draws them "uniformly at random",
                Algorithm 1, steps 1/2a and 2b).
-- ``model``    the coefficient models (Eq. (1.2), Sec. 4.1, Sec. 4.2 with the
+- ``model``    the coefficient models (Eq. (1.2), Sec. 4.2, Sec. 4.3 with the
                mode ordering of Table 4.2).
 - ``fe``       the black-box sampler: P1 finite elements for Eq. (1.1) in its
                weak form (Sec. 2.1), assembled element by element and solved by

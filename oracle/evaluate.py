@@ -1,10 +1,11 @@
 """Evaluation of the sparse approximation and its errors (oracle side; test infrastructure).
 
-- sample_points: the black box at explicit parameter points, u-check(x_g, y^(j)) -- the FE
-  solution of Eq. (1.1) for the fixed parameter y^(j) (Section 4), or the test polynomial.
-- evaluate: u^usFFT(x_g, y) = sum_{k in I} c_{g,k} e^{2 pi i k.y}, the truncated Fourier
-  series of Section 3 (the evaluation formula of Section 3.2 with the identity as
-  periodization, the periodic model needing none).
+- sample_points: the black box at explicit parameter points of the model's domain,
+  u-check(x_g, y^(j)) -- the FE solution of Eq. (1.1) for the fixed parameter y^(j)
+  (Section 4), or the test polynomial.
+- evaluate: u~^usFFT(x_g, y~) = sum_{k in I} c_{g,k} e^{2 pi i k.y~} at torus points;
+  evaluate_parameters: u^usFFT(x_g, y) = the same at y~ = phi^-1(y) (Eq. (3.1); phi is the
+  identity for the periodic model).
 - errors: err_2 and err_inf of Section 4 per mesh node, over the test points, with |.| the
   complex modulus.
 
@@ -14,11 +15,9 @@ is reproduced at random points; Parseval on the nodes of a reconstructing lattic
 terms against cos/sin; err_2 <= err_inf with equality for a constant difference; the FE
 samples at a lattice node equal the lattice sampler's.
 """
-import math
-
 import numpy as np
 
-from . import fe
+from . import fe, periodization
 
 PDE_1D, PDE_2D, TRIGPOLY = 1, 2, 3
 
@@ -39,8 +38,7 @@ def sample_points(prob, Y: np.ndarray, mesh=None) -> np.ndarray:
         mesh = fe.make_mesh(prob.kind, prob.n)
     U = np.zeros((len(Y), mesh.G))
     for j, y in enumerate(Y):
-        sin_y = np.array([math.sin(2.0 * math.pi * v) for v in y])
-        U[j] = fe.solve(prob, mesh, sin_y)
+        U[j] = fe.solve(prob, mesh, periodization.theta_of_parameter(prob, y))
     return U
 
 
@@ -52,6 +50,11 @@ def evaluate(I: np.ndarray, C: np.ndarray, Y: np.ndarray) -> np.ndarray:
         return np.zeros((len(Y), C.shape[0]), dtype=np.complex128)
     E = np.exp(2j * np.pi * np.mod(Y @ I.T.astype(np.float64), 1.0))     # [n, |I|]
     return E @ C.T
+
+
+def evaluate_parameters(prob, I: np.ndarray, C: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """u^usFFT at parameters Y of the model's own domain: evaluate() at phi^-1(Y) (Eq. (3.1))."""
+    return evaluate(I, C, periodization.to_torus(prob, Y))
 
 
 def errors(U: np.ndarray, V: np.ndarray):

@@ -117,13 +117,13 @@ def assemble_band(mesh, a_elem: np.ndarray, f_const: float):
     return ab, b
 
 
-def element_coefficients(prob, mesh, sin_y: np.ndarray) -> np.ndarray:
+def element_coefficients(prob, mesh, theta: np.ndarray) -> np.ndarray:
     return model.coefficient(prob.coef_model, prob.coef_scale, prob.coef_decay,
-                             mesh.centroids, mesh.dim, sin_y)
+                             mesh.centroids, mesh.dim, theta)
 
 
-def solve(prob, mesh, sin_y: np.ndarray) -> np.ndarray:
-    """u(x_g, y) at all interior nodes for one y, given sin(2 pi y_j), j=1..d."""
-    a = element_coefficients(prob, mesh, sin_y)
+def solve(prob, mesh, theta: np.ndarray) -> np.ndarray:
+    """u(x_g, y) at all interior nodes for one y, given Theta_j(y), j=1..d."""
+    a = element_coefficients(prob, mesh, theta)
     ab, b = assemble_band(mesh, a, prob.f_const)
     return solveh_banded(ab, b, lower=False, check_finite=False)

@@ -25,12 +25,11 @@ of oracle.lattice with draws keyed by PHASE_RECON; the paper uses multiple latti
 here, a single reconstructing lattice gives the same coefficients exactly for
 polynomials supported in I), samples at its nodes, DFT at k.z mod M, no threshold.
 """
-import math
 from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import detect, dft, fe, lattice, rng
+from . import detect, dft, fe, lattice, periodization, rng
 
 PDE_1D, PDE_2D, TRIGPOLY = 1, 2, 3
 
@@ -58,13 +57,13 @@ def sample(prob, nodes: NodeSet, mesh=None) -> np.ndarray:
     if mesh is None:
         mesh = fe.make_mesh(prob.kind, prob.n)
     U = np.zeros((nodes.M, mesh.G))
-    sin_y = np.zeros(nodes.d)
+    theta = np.zeros(nodes.d)
     for j, yv in nodes.tails.items():
-        sin_y[j] = math.sin(2.0 * math.pi * yv)
+        theta[j] = periodization.theta_of_node(prob, yv)
     for i in range(nodes.M):
         for c, j in enumerate(nodes.lat):
-            sin_y[j] = math.sin(2.0 * math.pi * n_int[i, c] / nodes.M)
-        U[i] = fe.solve(prob, mesh, sin_y)
+            theta[j] = periodization.theta_of_node(prob, n_int[i, c] / nodes.M)
+        U[i] = fe.solve(prob, mesh, theta)
     return U
 
 
@@ -75,13 +74,13 @@ def sample_rows(prob, nodes: NodeSet, rows, mesh=None) -> np.ndarray:
         mesh = fe.make_mesh(prob.kind, prob.n)
     n_int = nodes.lattice_ints()
     U = np.zeros((len(rows), mesh.G))
-    sin_y = np.zeros(nodes.d)
+    theta = np.zeros(nodes.d)
     for j, yv in nodes.tails.items():
-        sin_y[j] = math.sin(2.0 * math.pi * yv)
+        theta[j] = periodization.theta_of_node(prob, yv)
     for r, i in enumerate(rows):
         for c, j in enumerate(nodes.lat):
-            sin_y[j] = math.sin(2.0 * math.pi * n_int[i, c] / nodes.M)
-        U[r] = fe.solve(prob, mesh, sin_y)
+            theta[j] = periodization.theta_of_node(prob, n_int[i, c] / nodes.M)
+        U[r] = fe.solve(prob, mesh, theta)
     return U
 
 

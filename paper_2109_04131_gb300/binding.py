@@ -7,7 +7,7 @@ current PyTorch stream unless another stream is given.
 
 Module-level functions carry the C names (usfft_plan, usfft_increment, usfft_replay,
 usfft_rewind, usfft_resume, usfft_get_set, usfft_reconstruct, usfft_sample_points, usfft_evaluate,
-usfft_errors, usfft_get_lattice, usfft_get_candidates,
+usfft_errors, usfft_statistics, usfft_get_lattice, usfft_get_candidates,
 usfft_get_samples, usfft_get_coefficients, usfft_get_selection, usfft_last_error,
 usfft_destroy); ``Plan`` wraps them.
 """
@@ -31,7 +31,9 @@ class UsfftProblem(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("d", ctypes.c_int), ("coef_model", ctypes.c_int),
                 ("coef_scale", ctypes.c_double), ("coef_decay", ctypes.c_double), ("f_const", ctypes.c_double),
                 ("tp_nodes", ctypes.c_int), ("tp_nterms", ctypes.c_int),
-                ("tp_freqs", ctypes.c_void_p), ("tp_coefs", ctypes.c_void_p)]
+                ("tp_freqs", ctypes.c_void_p), ("tp_coefs", ctypes.c_void_p),
+                ("theta_map", ctypes.c_int), ("map_alpha", ctypes.c_double), ("map_beta", ctypes.c_double),
+                ("map_shift", ctypes.c_double)]
 
 
 class UsfftParams(ctypes.Structure):
@@ -71,6 +73,7 @@ SIGNATURES = {
     "usfft_sample_points": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int]),
     "usfft_evaluate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int]),
     "usfft_errors": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, _P, _P]),
+    "usfft_statistics": (ctypes.c_int, [_P, _P, _P, _P]),
     "usfft_get_lattice": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
     "usfft_get_candidates": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), _P]),
     "usfft_get_samples": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
@@ -145,6 +148,10 @@ def make_problem(prob) -> tuple:
     p.coef_scale = prob.coef_scale
     p.coef_decay = prob.coef_decay
     p.f_const = prob.f_const
+    p.theta_map = getattr(prob, "theta_map", 0)
+    p.map_alpha = getattr(prob, "map_alpha", -1.0)
+    p.map_beta = getattr(prob, "map_beta", 1.0)
+    p.map_shift = getattr(prob, "map_shift", 0.0)
     keep = []
     if prob.tp_freqs is not None:
         f = np.ascontiguousarray(prob.tp_freqs, dtype=np.int8)
@@ -216,6 +223,10 @@ def usfft_evaluate(plan, Y):
 
 def usfft_errors(plan, Y):
     return plan.errors(Y)
+
+
+def usfft_statistics(plan):
+    return plan.statistics()
 
 
 def usfft_get_lattice(plan):
@@ -366,9 +377,19 @@ class Plan:
         d = self.problem.d
         I = np.zeros((n.value, d), dtype=np.int8)
         C = np.zeros((self.problem.G, n.value, 2))
-        if n.value:
-            self._ck(self._lib.usfft_reconstruct(self.handle, ctypes.byref(n), I.ctypes.data, C.ctypes.data, 0))
+        out = C if C.size else np.zeros(2)          # an empty set still records the (zero) approximation
+        self._ck(self._lib.usfft_reconstruct(self.handle, ctypes.byref(n), I.ctypes.data if n.value else None,
+                                             out.ctypes.data, 0))
         return I.astype(np.int64), C[..., 0] + 1j * C[..., 1]
+
+    def statistics(self):
+        """(mean complex [G], variance [G], gsi [G][d]) of the last reconstruction."""
+        G, d = self.problem.G, self.problem.d
+        mean = np.zeros((G, 2))
+        var = np.zeros(G)
+        gsi = np.zeros((G, d))
+        self._ck(self._lib.usfft_statistics(self.handle, mean.ctypes.data, var.ctypes.data, gsi.ctypes.data))
+        return mean[:, 0] + 1j * mean[:, 1], var, gsi
 
     def _points(self, Y) -> np.ndarray:
         Y = np.ascontiguousarray(np.asarray(Y, dtype=np.float64).reshape(-1, self.problem.d))

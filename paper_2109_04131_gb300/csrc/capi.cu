@@ -72,6 +72,7 @@ struct usfft_plan_s {
     // step 3 result (usfft_reconstruct) and the buffers of point evaluation
     Buf Crec, Irec, Ypts, Upts, Vpts, epart, etot;
     int64_t nrec = -1;     // |I| of the stored reconstruction, -1: none
+    std::vector<int8_t> Irec_h;
     size_t bytes = 0;
     int cg_blocks = 0;
     int launches = 0;
@@ -173,11 +174,48 @@ usfft_status wait_stream(usfft_plan_t* plan) {
     }
 }
 
+void set_map(NodeSpec& ns, const usfft_problem& pr) {
+    ns.map = pr.kind == USFFT_TRIGPOLY ? USFFT_MAP_PERIODIC : pr.theta_map;
+    ns.map_alpha = pr.map_alpha;
+    ns.map_beta = pr.map_beta;
+    ns.map_shift = pr.map_shift;
+}
+
+ParamMap param_map(const usfft_problem& pr) {
+    ParamMap pm;
+    pm.map = pr.kind == USFFT_TRIGPOLY ? USFFT_MAP_PERIODIC : pr.theta_map;
+    pm.alpha = pr.map_alpha;
+    pm.beta = pr.map_beta;
+    pm.shift = pr.map_shift;
+    return pm;
+}
+
+// tau_{2,Delta} of the lognormal map, evaluated as the kernels do (k_theta.cuh)
+double tau2_host(double yt, double shift) {
+    const double u = yt - shift;
+    return yt < shift ? -0.5 - 2.0 * u : (yt < 0.5 + shift ? -0.5 + 2.0 * u : 1.5 - 2.0 * u);
+}
+
+// Lognormal map: true if a node i/M of a lattice of size M (as the kernels compute it) lands on
+// a pole of tau_1 (tau_{2,Delta} = -1/2 or +1/2), i.e. at y~ = Delta or 1/2 + Delta.
+bool lattice_hits_pole(int64_t M, double shift) {
+    const double cands[2] = {shift, 0.5 + shift};
+    for (double c : cands) {
+        const int64_t base = (int64_t)floor(c * (double)M);
+        for (int64_t nn = base - 1; nn <= base + 2; ++nn) {
+            if (nn < 0 || nn >= M) continue;
+            if (fabs(tau2_host((double)nn / (double)M, shift)) >= 0.5) return true;
+        }
+    }
+    return false;
+}
+
 NodeSpec spec_1d(const usfft_plan_t* p, int t, int i) {
     NodeSpec ns;
     memset(&ns, 0, sizeof ns);
     ns.M = p->K;
     ns.d = p->d;
+    set_map(ns, p->prob);
     for (int j = 1; j <= p->d; ++j) {
         if (j == t) {
             ns.z[j - 1] = 1;
@@ -195,6 +233,7 @@ NodeSpec spec_coupled(const usfft_plan_t* p, int t, int i) {
     memset(&ns, 0, sizeof ns);
     ns.M = p->M;
     ns.d = p->d;
+    set_map(ns, p->prob);
     for (int j = 1; j <= p->d; ++j) {
         if (j <= t) {
             ns.z[j - 1] = p->z[(size_t)(j - 1)];
@@ -269,6 +308,13 @@ usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns, double* out = n
 usfft_status prepare_step(usfft_plan_t* plan, int64_t M, const std::vector<int64_t>& m) {
     const int64_t nJ = (int64_t)m.size();
     usfft_status st;
+    if (plan->prob.kind != USFFT_TRIGPOLY && plan->prob.theta_map == USFFT_MAP_NORMAL &&
+        lattice_hits_pole(M, plan->prob.map_shift)) {
+        char msg[200];
+        snprintf(msg, sizeof msg, "a node of the lattice of size %lld lies on a pole of the lognormal map "
+                 "(Delta = %.17g): choose another map_shift", (long long)M, plan->prob.map_shift);
+        return fail(plan, USFFT_EINVAL, msg);
+    }
     plan->fp = make_fft_plan(M);
     if (plan->fp.L2 <= 0) return fail(plan, USFFT_EINVAL, "lattice size has no factorisation into FFT passes <= 4096");
     const int G = plan->G;
@@ -431,13 +477,26 @@ usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params
     if (pr.kind != USFFT_TRIGPOLY) {
         if (pr.coef_model != USFFT_COEF_AFFINE_SIN && pr.coef_model != USFFT_COEF_LOGNORMAL_SIN)
             return fail(nullptr, USFFT_EINVAL, "unknown coefficient model");
-        // uniform ellipticity (Eq. (2.1)) of the affine model: 1 - c sum_j j^-mu > 0
+        if (pr.theta_map == USFFT_MAP_TENT) {
+            if (!(pr.map_alpha < pr.map_beta)) return fail(nullptr, USFFT_EINVAL, "tent map: need alpha < beta");
+        } else if (pr.theta_map == USFFT_MAP_NORMAL) {
+            if (!(pr.map_shift > 0.0 && pr.map_shift < 0.5))
+                return fail(nullptr, USFFT_EINVAL, "lognormal map: need 0 < map_shift < 1/2");
+            if (pr.coef_model == USFFT_COEF_AFFINE_SIN)
+                return fail(nullptr, USFFT_EINVAL, "lognormal map: Theta_j is unbounded, use the lognormal coefficient");
+        } else if (pr.theta_map != USFFT_MAP_PERIODIC) {
+            return fail(nullptr, USFFT_EINVAL, "unknown parameter map");
+        }
+        // uniform ellipticity (Eq. (2.1)) of the affine model: 1 - c max|Theta| sum_j j^-mu > 0
         if (pr.coef_model == USFFT_COEF_AFFINE_SIN) {
             double sum = 0.0;
             for (int j = 1; j <= pr.d; ++j) sum += pow((double)j, -pr.coef_decay);
-            if (1.0 - fabs(pr.coef_scale) * sum <= 0.0)
+            const double tmax = pr.theta_map == USFFT_MAP_TENT ? fmax(fabs(pr.map_alpha), fabs(pr.map_beta)) : 1.0;
+            if (1.0 - fabs(pr.coef_scale) * tmax * sum <= 0.0)
                 return fail(nullptr, USFFT_EINVAL, "coefficient violates uniform ellipticity: a_min <= 0");
         }
+    } else if (pr.theta_map != USFFT_MAP_PERIODIC) {
+        return fail(nullptr, USFFT_EINVAL, "TRIGPOLY: the test polynomials are periodic (theta_map 0)");
     }
     plan = new usfft_plan_s();
     plan->prob = pr;
@@ -788,7 +847,11 @@ usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, do
     if (!coefs) return USFFT_OK;
     const int d = plan->d;
     const int64_t nI = plan->nIpre;
-    if (nI == 0) return USFFT_OK;
+    if (nI == 0) {             // nothing detected: the approximation is zero
+        plan->nrec = 0;
+        plan->Irec_h.clear();
+        return USFFT_OK;
+    }
     // one reconstructing rank-1 lattice for I (Algorithm 1, step 3; single-lattice reading)
     std::vector<int64_t> z;
     int64_t M = 0;
@@ -818,6 +881,7 @@ usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, do
     memset(&ns, 0, sizeof ns);
     ns.M = M;
     ns.d = d;
+    set_map(ns, plan->prob);
     for (int j = 0; j < d; ++j) ns.z[j] = z[(size_t)j];
     plan->specs.assign(1, ns);
     plan->s_tilde = 0;                       // no threshold in step 3
@@ -834,6 +898,7 @@ usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, do
                        plan->stream));
     if ((st = wait_stream(plan)) != USFFT_OK) return st;
     plan->nrec = nI;
+    plan->Irec_h = plan->Ipre;
     return USFFT_OK;
 }
 
@@ -872,6 +937,7 @@ usfft_status sample_at(usfft_plan_t* plan, const double* yd, int64_t cnt, double
     memset(&ns, 0, sizeof ns);
     ns.M = cnt;
     ns.d = plan->d;
+    set_map(ns, plan->prob);
     ns.Y = yd;
     if ((st = run_sampler(plan, ns, out)) != USFFT_OK) return st;
     return read_cg_stats(plan, cnt);
@@ -933,7 +999,7 @@ usfft_status usfft_evaluate(usfft_plan_t* plan, const double* y, int64_t n, doub
                 return st;
             out = (double2*)plan->Vpts.p;
         }
-        CK(launch_evaluate(yd, cnt, plan->d, (const int8_t*)plan->Irec.p, plan->nrec, (const double2*)plan->Crec.p,
+        CK(launch_evaluate(yd, cnt, plan->d, param_map(plan->prob), (const int8_t*)plan->Irec.p, plan->nrec, (const double2*)plan->Crec.p,
                            G, out, nullptr, nullptr, nullptr, plan->stream, &plan->launches));
         if (!on_device) {
             CK(cudaMemcpyAsync(values + 2 * off * G, out, sizeof(double2) * (size_t)cnt * G, cudaMemcpyDeviceToHost,
@@ -971,7 +1037,7 @@ usfft_status usfft_errors(usfft_plan_t* plan, const double* y, int64_t n, int y_
         if ((st = stage_points(plan, y, off, cnt, y_on_device, &yd)) != USFFT_OK) return st;
         // the reference values: FE solutions at the test points
         if ((st = sample_at(plan, yd, cnt, (double*)plan->Upts.p)) != USFFT_OK) return st;
-        CK(launch_evaluate(yd, cnt, plan->d, (const int8_t*)plan->Irec.p, plan->nrec, (const double2*)plan->Crec.p,
+        CK(launch_evaluate(yd, cnt, plan->d, param_map(plan->prob), (const int8_t*)plan->Irec.p, plan->nrec, (const double2*)plan->Crec.p,
                            G, nullptr, (const double*)plan->Upts.p, psum, pmax, plan->stream, &plan->launches));
         const int tiles = (int)((cnt + evaluate_point_tile() - 1) / evaluate_point_tile());
         CK(launch_error_accumulate(psum, pmax, tiles, G, tsum, tmax, plan->stream, &plan->launches));
@@ -981,6 +1047,57 @@ usfft_status usfft_errors(usfft_plan_t* plan, const double* y, int64_t n, int y_
     CK(cudaMemcpyAsync(errinf, tmax, sizeof(double) * (size_t)G, cudaMemcpyDeviceToHost, plan->stream));
     plan->d2h += (int64_t)(2 * sizeof(double) * (size_t)G);
     return wait_stream(plan);
+}
+
+usfft_status usfft_statistics(usfft_plan_t* plan, double* mean, double* variance, double* gsi) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (plan->nrec < 0) return fail(plan, USFFT_ESTATE, "usfft_statistics needs a usfft_reconstruct first");
+    reset_counters(plan);
+    const int G = plan->G, d = plan->d;
+    const int64_t nI = plan->nrec;
+    // group the frequencies of I by their number of non-zero components (index bookkeeping)
+    std::vector<int64_t> offsets((size_t)d + 2, 0);
+    std::vector<int> order((size_t)nI), perm((size_t)nI);
+    for (int64_t k = 0; k < nI; ++k) {
+        int l = 0;
+        for (int j = 0; j < d; ++j) l += plan->Irec_h[(size_t)(k * d + j)] != 0;
+        order[(size_t)k] = l;
+        offsets[(size_t)l + 1]++;
+    }
+    for (int l = 0; l <= d; ++l) offsets[(size_t)l + 1] += offsets[(size_t)l];
+    {
+        std::vector<int64_t> fill(offsets.begin(), offsets.end() - 1);
+        for (int64_t k = 0; k < nI; ++k) perm[(size_t)fill[(size_t)order[(size_t)k]]++] = (int)k;
+    }
+    usfft_status st;
+    const size_t stat_bytes = sizeof(double2) * (size_t)std::max<int64_t>(nI, 1) + sizeof(int) * (size_t)std::max<int64_t>(nI, 1) +
+                              sizeof(int64_t) * offsets.size() + sizeof(double2) * G + sizeof(double) * G +
+                              sizeof(double) * (size_t)G * d + 256 * 6;
+    if ((st = ensure(plan, plan->epart, stat_bytes, "statistics")) != USFFT_OK) return st;
+    char* base = (char*)plan->epart.p;
+    auto carve = [&](size_t bytes) {
+        char* p = base;
+        base += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    double2* dfac = (double2*)carve(sizeof(double2) * (size_t)std::max<int64_t>(nI, 1));
+    int* dperm = (int*)carve(sizeof(int) * (size_t)std::max<int64_t>(nI, 1));
+    int64_t* doff = (int64_t*)carve(sizeof(int64_t) * offsets.size());
+    double2* dmean = (double2*)carve(sizeof(double2) * G);
+    double* dvar = (double*)carve(sizeof(double) * G);
+    double* dgsi = (double*)carve(sizeof(double) * (size_t)G * d);
+    if (nI) CK(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * (size_t)nI, cudaMemcpyHostToDevice, plan->stream));
+    CK(cudaMemcpyAsync(doff, offsets.data(), sizeof(int64_t) * offsets.size(), cudaMemcpyHostToDevice, plan->stream));
+    plan->h2d += (int64_t)(sizeof(int) * (size_t)nI + sizeof(int64_t) * offsets.size());
+    CK(launch_expectation_factors((const int8_t*)plan->Irec.p, nI, d, param_map(plan->prob), dfac, plan->stream,
+                                  &plan->launches));
+    CK(launch_statistics((const double2*)plan->Crec.p, G, nI, d, dfac, dperm, doff, dmean, dvar, dgsi, plan->stream,
+                         &plan->launches));
+    if (mean) CK(cudaMemcpyAsync(mean, dmean, sizeof(double2) * G, cudaMemcpyDeviceToHost, plan->stream));
+    if (variance) CK(cudaMemcpyAsync(variance, dvar, sizeof(double) * G, cudaMemcpyDeviceToHost, plan->stream));
+    if (gsi) CK(cudaMemcpyAsync(gsi, dgsi, sizeof(double) * (size_t)G * d, cudaMemcpyDeviceToHost, plan->stream));
+    plan->d2h += (int64_t)((mean ? 16 : 0) + (variance ? 8 : 0) + (gsi ? 8 * d : 0)) * G;
+    return wait_stream(plan);   // the host vectors above outlive the copies
 }
 
 usfft_status usfft_search_lattice(const int8_t* J, int64_t n, int t, uint64_t seed, int trials, int max_sizes,

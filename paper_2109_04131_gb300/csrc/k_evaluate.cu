@@ -1,7 +1,8 @@
 // Evaluation of the sparse approximation and its errors (Section 4).
 //
-// u^usFFT(x_g, y) = sum_{k in I} c_{g,k} e^{2 pi i k.y} is a dense complex contraction
-// V[j][g] = sum_k E[j][k] C[g][k] with E[j][k] = e^{2 pi i k.y_j}; with the FE solutions
+// u^usFFT(x_g, y) = sum_{k in I} c_{g,k} e^{2 pi i k.phi^-1(y)} (Eq. (3.1); phi^-1 the inverse
+// parameter map, the identity for the periodic model) is a dense complex contraction
+// V[j][g] = sum_k E[j][k] C[g][k] with E[j][k] = e^{2 pi i k.y~_j}, y~_j = phi^-1(y_j); with the FE solutions
 // U[j][g] at the same points the errors of Section 4 are, per mesh node g,
 //   err_2(x_g)   = ( (1/n) sum_j |U[j][g] - V[j][g]|^2 )^(1/2),
 //   err_inf(x_g) = max_j |U[j][g] - V[j][g]|.
@@ -16,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "k_theta.cuh"
 #include "usfft_internal.h"
 
 namespace usfft {
@@ -25,7 +27,7 @@ namespace {
 constexpr int TJ = 64, TG = 64, TK = 16, NT = 256;
 
 __global__ void __launch_bounds__(NT) evaluate_kernel(const double* __restrict__ Y, int64_t n, int d,
-                                                      const int8_t* __restrict__ I, int64_t nI,
+                                                      const ParamMap pm, const int8_t* __restrict__ I, int64_t nI,
                                                       const double2* __restrict__ C, int G, double2* V,
                                                       const double* __restrict__ Uchk, double* part_sum,
                                                       double* part_max) {
@@ -40,7 +42,7 @@ __global__ void __launch_bounds__(NT) evaluate_kernel(const double* __restrict__
 
     for (int e = tid; e < TJ * d; e += NT) {
         const int jj = e / d;
-        Ys[e] = (j0 + jj < n) ? Y[(j0 + jj) * d + (e - jj * d)] : 0.0;
+        Ys[e] = (j0 + jj < n) ? to_torus(pm, Y[(j0 + jj) * d + (e - jj * d)]) : 0.0;
     }
     double2 acc[4][4];
 #pragma unroll
@@ -173,16 +175,16 @@ size_t eval_smem_bytes(int d) {
 int64_t evaluate_max_points() { return (int64_t)65535 * TJ; }
 int evaluate_point_tile() { return TJ; }
 
-cudaError_t launch_evaluate(const double* Y, int64_t n, int d, const int8_t* I, int64_t nI, const double2* C, int G,
-                            double2* V, const double* Uchk, double* part_sum, double* part_max, cudaStream_t s,
-                            int* launches) {
+cudaError_t launch_evaluate(const double* Y, int64_t n, int d, const ParamMap& pm, const int8_t* I, int64_t nI,
+                            const double2* C, int G, double2* V, const double* Uchk, double* part_sum,
+                            double* part_max, cudaStream_t s, int* launches) {
     if (n <= 0 || G <= 0) return cudaSuccess;
     if (n > evaluate_max_points()) return cudaErrorInvalidValue;
     const size_t smem = eval_smem_bytes(d);
     cudaError_t e = cudaFuncSetAttribute(evaluate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((G + TG - 1) / TG), (unsigned)((n + TJ - 1) / TJ));
-    evaluate_kernel<<<grid, NT, smem, s>>>(Y, n, d, I, nI, C, G, V, Uchk, part_sum, part_max);
+    evaluate_kernel<<<grid, NT, smem, s>>>(Y, n, d, pm, I, nI, C, G, V, Uchk, part_sum, part_max);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

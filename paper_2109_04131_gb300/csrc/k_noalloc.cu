@@ -73,12 +73,18 @@ extern "C" usfft_status usfft_sample_2d_static(const usfft_problem* problem, con
     if (pr.d < 1 || pr.d > USFFT_MAX_D) return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: d must lie in [1, 64]");
     if (pr.coef_model != USFFT_COEF_AFFINE_SIN && pr.coef_model != USFFT_COEF_LOGNORMAL_SIN)
         return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: unknown coefficient model");
+    if (pr.theta_map != USFFT_MAP_PERIODIC && pr.theta_map != USFFT_MAP_TENT && pr.theta_map != USFFT_MAP_NORMAL)
+        return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: unknown parameter map");
     if (M < 1 || M > (int64_t(1) << 31) || i0 < 0 || count < 0 || i0 + count > M)
         return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: need 1 <= M <= 2^31 and 0 <= i0 <= i0+count <= M");
     NodeSpec ns;
     memset(&ns, 0, sizeof ns);
     ns.M = M;
     ns.d = pr.d;
+    ns.map = pr.theta_map;
+    ns.map_alpha = pr.map_alpha;
+    ns.map_beta = pr.map_beta;
+    ns.map_shift = pr.map_shift;
     for (int j = 0; j < pr.d; ++j) {
         if (z[j] >= M) return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: z_j must be < M");
         ns.z[j] = z[j] < 0 ? -1 : z[j];

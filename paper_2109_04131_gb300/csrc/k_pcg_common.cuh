@@ -3,19 +3,10 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "k_theta.cuh"
 #include "usfft_internal.h"
 
 namespace usfft {
-
-__device__ __forceinline__ double node_sin2(const NodeSpec& ns, int j, int64_t i) {
-    if (ns.Y) return sinpi(2.0 * ns.Y[i * ns.d + j]);
-    int64_t zj = ns.z[j];
-    if (zj >= 0) {
-        int64_t nn = (i * zj) % ns.M;
-        return sinpi(2.0 * (double)nn / (double)ns.M);
-    }
-    return sinpi(2.0 * ns.tail[j]);
-}
 
 struct Pcg2dArgs {
     NodeSpec ns;

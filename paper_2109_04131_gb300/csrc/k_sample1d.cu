@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "k_theta.cuh"
 #include "usfft_internal.h"
 
 namespace usfft {
@@ -72,19 +73,6 @@ cudaError_t launch_psi_table(int kind, int n, int d, double scale, double decay,
     return cudaGetLastError();
 }
 
-// sin(2 pi y_j) of node i: the given coordinate for explicit points; on a lattice the exact
-// integer reduction n = i z_j mod M for lattice coordinates (Eq. (3.4)), the fixed tail
-// value otherwise.
-__device__ __forceinline__ double node_sin(const NodeSpec& ns, int j, int64_t i) {
-    if (ns.Y) return sinpi(2.0 * ns.Y[i * ns.d + j]);
-    int64_t zj = ns.z[j];
-    if (zj >= 0) {
-        int64_t nn = (i * zj) % ns.M;
-        return sinpi(2.0 * (double)nn / (double)ns.M);
-    }
-    return sinpi(2.0 * ns.tail[j]);
-}
-
 // ---------------------------------------------------------------------------------
 // 1-D sampler
 // ---------------------------------------------------------------------------------
@@ -117,7 +105,7 @@ __global__ void __launch_bounds__(256) sample_1d_cr_kernel(const __grid_constant
 
     for (int64_t sys = (int64_t)blockIdx.x * warps + warp; sys < a.count; sys += (int64_t)gridDim.x * warps) {
         const int64_t i = a.i0 + sys;
-        for (int j = lane; j < d; j += 32) sj[j] = node_sin(a.ns, j, i);
+        for (int j = lane; j < d; j += 32) sj[j] = node_theta(a.ns, j, i);
         __syncwarp();
         // element coefficients (fused assembly; never stored in HBM)
         for (int e = lane; e <= n; e += 32) {

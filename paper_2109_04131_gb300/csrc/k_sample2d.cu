@@ -41,7 +41,7 @@ __device__ void assemble_scaled(const Pcg2dArgs& a, int64_t i, double* ph, doubl
     const int n = a.n, d = a.ns.d;
     const int n1 = n + 1, W = n + 2;
     const int sq = n1 * n1;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) sj[j] = node_sin2(a.ns, j, i);
+    for (int j = threadIdx.x; j < d; j += blockDim.x) sj[j] = node_theta(a.ns, j, i);
     __syncthreads();
     const bool logn = a.coef_model == USFFT_COEF_LOGNORMAL_SIN;
     // phase 1: lower-triangle coefficients of every square into ph (temporary)

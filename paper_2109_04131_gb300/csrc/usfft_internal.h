@@ -45,7 +45,15 @@ struct NodeSpec {          // M sampling nodes: lattice coordinates and fixed ta
     int64_t z[USFFT_MAX_D];      // >= 0: lattice coordinate with multiplier z_j; -1: tail
     double tail[USFFT_MAX_D];    // y'_j for tail coordinates
     const double* Y;             // non-NULL: explicit points, node i is Y[i*d .. i*d+d) (device;
-                                 // z and tail unused)
+                                 // parameters of the model's domain; z and tail unused)
+    int map;                     // USFFT_MAP_*: Theta_j of a torus coordinate (Sec. 3.2)
+    double map_alpha, map_beta, map_shift;
+};
+
+// Theta_j and the inverse map on the device (k_theta.cuh) take these fields of a problem.
+struct ParamMap {
+    int map;
+    double alpha, beta, shift;
 };
 
 struct FftPlan {           // M = L1 * L2 (L2 == 1: single pass of length L1)
@@ -114,14 +122,25 @@ cudaError_t launch_absmax_column(const double2* C, int G, int64_t nJ, int64_t co
 // part_sum[r][g] = sum_j |Uchk[j][g] - V[j][g]|^2 and part_max[r][g] = max_j |...|.
 int64_t evaluate_max_points();
 int evaluate_point_tile();
-cudaError_t launch_evaluate(const double* Y, int64_t n, int d, const int8_t* I, int64_t nI, const double2* C, int G,
-                            double2* V, const double* Uchk, double* part_sum, double* part_max, cudaStream_t s,
-                            int* launches);
+// Y holds parameters of the model's domain; the kernel maps them to the torus (phi^-1, Eq. (3.1)).
+cudaError_t launch_evaluate(const double* Y, int64_t n, int d, const ParamMap& pm, const int8_t* I, int64_t nI,
+                            const double2* C, int G, double2* V, const double* Uchk, double* part_sum,
+                            double* part_max, cudaStream_t s, int* launches);
 // tot_sum[g] += sum_r part_sum[r][g], tot_max[g] = max(tot_max[g], max_r part_max[r][g])
 cudaError_t launch_error_accumulate(const double* part_sum, const double* part_max, int tiles, int G, double* tot_sum,
                                     double* tot_max, cudaStream_t s, int* launches);
 // tot_sum[g] <- sqrt(tot_sum[g] / n)
 cudaError_t launch_error_finalize(double* tot_sum, int G, int64_t n, cudaStream_t s, int* launches);
+
+// Quantities of interest (Sec. 4, 4.1): dfac[k] = D_k of frequency row k (int8 [nI][d]) under
+// the map; then per node g mean[g] = sum_k C[g][k] D_k, var[g] = sum_{k != 0} |C[g][k]|^2 and
+// gsi[g][l-1] = sum_{k in J_l} |C[g][k]|^2 / var[g], with the rows grouped by order l through
+// perm / offsets (order l = offsets[l] .. offsets[l+1]-1 of perm, l = 0..d).
+cudaError_t launch_expectation_factors(const int8_t* I, int64_t nI, int d, const ParamMap& pm, double2* dfac,
+                                       cudaStream_t s, int* launches);
+cudaError_t launch_statistics(const double2* C, int G, int64_t nI, int d, const double2* dfac, const int* perm,
+                              const int64_t* offsets, double2* mean, double* var, double* gsi, cudaStream_t s,
+                              int* launches);
 
 // Sets the message usfft_last_error(NULL) returns on the calling thread (capi.cu).
 void set_thread_error(const std::string& msg);

@@ -10,6 +10,7 @@ import pytest
 
 import workloads as W
 from oracle import evaluate as ev
+from oracle import periodization as P
 from oracle.usfft import OracleRun
 
 pytestmark = pytest.mark.gpu
@@ -41,7 +42,7 @@ def _to_step3(B, prob, params):
 
 def _check(B, plan, prob, run, I_o, C_o, Y):
     U_o = ev.sample_points(prob, Y, run.mesh)
-    V_o = ev.evaluate(I_o, C_o, Y)
+    V_o = ev.evaluate_parameters(prob, I_o, C_o, Y)
     U_g = plan.sample_points(Y)
     scale_u = np.max(np.abs(U_o))
     assert U_g.shape == U_o.shape
@@ -119,4 +120,47 @@ def test_evaluation_needs_a_reconstruction(B):
     with pytest.raises(B.UsfftError) as e:
         plan.errors(Y)
     assert e.value.status == 7
+    plan.close()
+
+
+MAPS = [(W.MAP_TENT, dict(alpha=-1.0, beta=1.0)), (W.MAP_NORMAL, dict(shift=0.0123456789))]
+
+
+def _statistics_match(plan, prob, I, C_o, C_g):
+    mean, var, gsi = plan.statistics()
+    m_o = P.expectation(I, C_o, prob.theta_map, prob.map_shift)
+    v_o = P.variance(I, C_o)
+    g_o = P.gsi(I, C_o, prob.d)
+    l1 = np.sum(np.abs(C_o), axis=1)
+    assert np.all(np.abs(mean - m_o) <= TOL * l1)
+    assert np.all(np.abs(var - v_o) <= 1e-9 * (v_o + 1e-300) + 1e-20)
+    assert np.max(np.abs(gsi - g_o)) < 1e-8
+    assert np.allclose(gsi.sum(axis=1)[var > 0], 1.0)
+    return mean, var, gsi
+
+
+@pytest.mark.parametrize("theta_map,kw", MAPS)
+@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED])
+def test_periodized_models_reconstruct_evaluate_and_statistics(B, theta_map, kw, precision):
+    base = W.small_2d(n=15, d=3, seed=2, N=4, s=20)
+    if theta_map == W.MAP_NORMAL:
+        base = W.Workload(base.name, W.Problem(kind=W.PDE_2D, n=15, d=3, coef_model=W.COEF_LOGNORMAL_SIN,
+                                               coef_scale=0.5), base.params)
+    w = W.with_precision(W.with_map(base, theta_map, **kw), precision)
+    plan, run, I, C_o, C_g = _to_step3(B, w.problem, w.params)
+    Y = W.parameter_points(w.problem, 200, seed=4)
+    U, V, e2, ei = _check(B, plan, w.problem, run, I, C_o, Y)
+    # a sanity bar only (N = 4 is far from converged, the lognormal map's poles slow the decay)
+    assert np.all(np.isfinite(ei)) and np.max(e2) < 0.05 * np.max(np.abs(U))
+    _statistics_match(plan, w.problem, I, C_o, C_g)
+    plan.close()
+
+
+def test_periodic_statistics_mean_is_c0(B):
+    w = W.with_precision(W.small_2d(n=15, d=3, seed=2, N=4, s=20), W.PRECISION_MIXED)
+    plan, run, I, C_o, C_g = _to_step3(B, w.problem, w.params)
+    mean, var, gsi = _statistics_match(plan, w.problem, I, C_o, C_g)
+    zero = np.nonzero(np.all(I == 0, axis=1))[0]
+    assert len(zero) == 1
+    assert np.array_equal(mean, C_g[:, zero[0]])       # D_k = delta_k0 exactly
     plan.close()

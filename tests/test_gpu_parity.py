@@ -276,3 +276,50 @@ def test_reconstruct_2d_matches_oracle(B, precision):
     Cd = out.cpu().numpy()
     assert np.max(np.abs((Cd[..., 0] + 1j * Cd[..., 1]) - C)) <= 1e-12 * np.max(np.abs(C))
     plan.close()
+
+
+
+@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED])
+def test_tent_and_lognormal_maps_match_oracle(B, precision):
+    tent = W.with_map(W.small_2d(n=15, d=4, seed=3, N=5, s=30), W.MAP_TENT, -1.0, 1.0)
+    logn = W.small_2d(n=15, d=4, seed=3, N=5, s=30)
+    logn = W.with_map(W.Workload(logn.name, W.Problem(kind=W.PDE_2D, n=15, d=4, coef_model=W.COEF_LOGNORMAL_SIN,
+                                                      coef_scale=0.5), logn.params), W.MAP_NORMAL, shift=0.0123456789)
+    for w in (tent, logn):
+        w = W.with_precision(w, precision)
+        plan = B.Plan(w.problem, w.params)
+        run = OracleRun(w.problem, w.params, keep=True)
+        for t in range(1, 4):
+            compare_increment(plan, run, f"map {w.problem.theta_map} precision {precision}", exact=False)
+        plan.close()
+
+
+def test_1d_tent_map_full_run_and_even_coefficients(B):
+    w = W.with_map(W.c1(3), W.MAP_TENT, -1.0, 1.0)
+    plan = B.Plan(w.problem, w.params)
+    run = OracleRun(w.problem, w.params, keep=True)
+    compare_increment(plan, run, "c1 tent t=1", exact=False)
+    # u~ is even about y~ = 1/2 in every coordinate ((A3)): the 1-D coefficients are real and
+    # c_k = c_-k -- a property of the library's own output, independent of the oracle
+    C = plan.get_coefficients()
+    scale = np.max(np.abs(C))
+    assert np.max(np.abs(C - C[:, ::-1])) < 1e-13 * scale and np.max(np.abs(C.imag)) < 1e-13 * scale
+    for t in range(2, w.problem.d + 1):
+        compare_increment(plan, run, f"c1 tent t={t}", exact=False)
+    plan.close()
+
+
+def test_lognormal_map_rejects_a_lattice_node_on_a_pole(B):
+    # K = 2N + 1 = 9: the 1-D detection nodes are i/9; Delta = 1/9 puts node 1 on a pole
+    prob = W.Problem(kind=W.PDE_1D, n=15, d=2, coef_model=W.COEF_LOGNORMAL_SIN, coef_scale=0.5,
+                     theta_map=W.MAP_NORMAL, map_shift=1.0 / 9.0)
+    params = W.Params(N=4, s=10, s_local=10, delta=1e-8, delta_is_relative=True, r=1, seed=1)
+    plan = B.Plan(prob, params)
+    with pytest.raises(B.UsfftError) as e:
+        plan.increment()
+    assert e.value.status == 1 and "pole" in str(e.value)
+    plan.close()
+    # an affine coefficient with the unbounded lognormal parameters is refused at plan time
+    bad = W.Problem(kind=W.PDE_1D, n=15, d=2, theta_map=W.MAP_NORMAL, map_shift=0.01)
+    with pytest.raises(B.UsfftError):
+        B.Plan(bad, params)

@@ -65,7 +65,7 @@ def test_table_4_2_mode_ordering():
     for j, m1, m2, k in (map(int, r) for r in _rows("table_4_2.txt")):
         assert model.diag_k(j) == k
         assert model.diag_m(j) == (m1, m2)
-        # Sec. 4.2 formula k(j) = floor(-1/2 + sqrt(1/4 + 2j)) in floating point agrees
+        # Sec. 4.3 formula k(j) = floor(-1/2 + sqrt(1/4 + 2j)) in floating point agrees
         assert math.floor(-0.5 + math.sqrt(0.25 + 2 * j)) == k
     modes = [model.mode_2d(j) for j in range(1, 11)]
     assert modes[:6] == [(1, 1), (1, 2), (2, 1), (1, 3), (2, 2), (3, 1)]
@@ -77,7 +77,7 @@ def test_printed_ellipticity_bounds():
     for mu, c, amin, amax in (map(float, r) for r in _rows("periodic_example_bounds.txt")):
         lo, hi = model.ellipticity_bounds(model.COEF_AFFINE_SIN, c / math.sqrt(6), mu)
         assert abs(lo - amin) < 6e-6 and abs(hi - amax) < 6e-6
-    # affine example of Sec. 4.2: c = 0.9/zeta(2) gives a_min = 0.1, a_max = 1.9
+    # affine example of Sec. 4.3: c = 0.9/zeta(2) gives a_min = 0.1, a_max = 1.9
     from scipy.special import zeta
     lo, hi = model.ellipticity_bounds(model.COEF_AFFINE_SIN, 0.9 / zeta(2), 2.0)
     assert abs(lo - 0.1) < 1e-14 and abs(hi - 1.9) < 1e-14

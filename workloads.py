@@ -5,7 +5,7 @@ test polynomials.  It contains none of the usFFT arithmetic (no lattice, no
 transform, no solve, no selection), so both the CPU oracle and the CUDA path may
 import it without sharing method code.
 
-The PDE workloads stand in for the paper's numerical examples (Sec. 4.1-4.3,
+The PDE workloads stand in for the paper's numerical examples (Sec. 4.2-4.4,
 Table 4.1): the same stochastic dimensions, search domains, sparsities and
 coefficient families, on uniform meshes instead of the paper's unstructured
 mesh (which is not available).
@@ -27,6 +27,10 @@ TRIGPOLY = 3
 COEF_AFFINE_SIN = 1     # a = 1 + sum_j c j^-mu psi_j(x) sin(2 pi y_j)
 COEF_LOGNORMAL_SIN = 2  # a = exp(sum_j c j^-mu psi_j(x) sin(2 pi y_j))
 
+MAP_PERIODIC = 0        # Theta_j = sin(2 pi y_j), y on the torus
+MAP_TENT = 1            # Theta_j = y_j uniform on [alpha, beta], tent periodization
+MAP_NORMAL = 2          # Theta_j = y_j standard normal, tau_1 o tau_{2,Delta} periodization
+
 PRECISION_FP64 = 0
 PRECISION_MIXED = 1
 PRECISION_MIXED_JACOBI = 2
@@ -39,12 +43,18 @@ class Problem:
     n: int                      # interior nodes per side (PDE); G = n (1-D) or n*n (2-D)
     d: int                      # stochastic dimension
     coef_model: int = COEF_AFFINE_SIN
-    coef_scale: float = 0.9 * 6.0 / math.pi ** 2   # c = 0.9/zeta(2) (Sec. 4.2)
+    coef_scale: float = 0.9 * 6.0 / math.pi ** 2   # c = 0.9/zeta(2) (Sec. 4.3)
     coef_decay: float = 2.0                        # mu
     f_const: float = 1.0
     # TRIGPOLY black box: per node g a list of (frequency, coefficient) terms
     tp_freqs: Optional[np.ndarray] = None   # int8 [G][nterms][d]
     tp_coefs: Optional[np.ndarray] = None   # complex128 [G][nterms] (0 pads unused slots)
+    # parameter map (Sec. 3.2): periodic model (Theta_j = sin 2 pi y_j), affine model with the
+    # tent periodization on [map_alpha, map_beta], lognormal model with tau_1 o tau_{2,Delta}
+    theta_map: int = 0                      # MAP_PERIODIC | MAP_TENT | MAP_NORMAL
+    map_alpha: float = -1.0
+    map_beta: float = 1.0
+    map_shift: float = 0.0                  # Delta of the lognormal periodization
 
     @property
     def G(self) -> int:
@@ -210,3 +220,20 @@ def test_points(n: int, d: int, seed: int) -> np.ndarray:
     """n test parameters y^(j) drawn uniformly from the torus [0,1)^d (the distribution of the
     periodic model's parameters; Section 4 uses such random test points): float64 [n, d]."""
     return np.random.default_rng(np.random.SeedSequence([seed, 7, d])).random((n, d))
+
+
+def parameter_points(prob: "Problem", n: int, seed: int) -> np.ndarray:
+    """n test parameters drawn from the model's own distribution (Section 4): uniform on the
+    torus (periodic model), uniform on [alpha, beta] (affine), standard normal (lognormal)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 11, prob.d, prob.theta_map]))
+    if prob.theta_map == MAP_TENT:
+        return prob.map_alpha + (prob.map_beta - prob.map_alpha) * rng.random((n, prob.d))
+    if prob.theta_map == MAP_NORMAL:
+        return rng.standard_normal((n, prob.d))
+    return rng.random((n, prob.d))
+
+
+def with_map(w: "Workload", theta_map: int, alpha: float = -1.0, beta: float = 1.0, shift: float = 0.0) -> "Workload":
+    """The same workload with another parameter map (Sec. 3.2)."""
+    p = replace(w.problem, theta_map=theta_map, map_alpha=alpha, map_beta=beta, map_shift=shift)
+    return replace(w, problem=p)
