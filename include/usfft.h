@@ -136,6 +136,19 @@ typedef struct {
     usfft_alloc_fn alloc;     /* NULL = cudaMalloc */
     usfft_free_fn free;
     void* alloc_ctx;
+    /* Sampling of the coupled steps (Algorithm A):
+     *   rr_lattices = 0: one reconstructing rank-1 lattice per detection iteration (above);
+     *   rr_lattices = L (odd, <= 31): L random rank-1 lattices per detection iteration, all
+     *   sampling the same projection (the iteration's tails).  Sizes: M_1 = smallest 7-smooth
+     *   size >= ceil(rr_size_factor * max(|I^(1..t-1)|, |I^(t)|, s~)) (at least 2), M_(l+1) the
+     *   next 7-smooth size after M_l; every component of z_l a unit mod M_l drawn from the
+     *   counter RNG (phase 5).  Estimate of c_k: the value of the first lattice in which no
+     *   other candidate shares k's index, else the median over the L lattices of the real
+     *   and, separately, the imaginary parts.  Fewer samples than one reconstructing lattice
+     *   (sizes grow with max(s, N) instead of |J_t|) at the price of a failure probability
+     *   (proof of Theorem 1.1, Appendix B).  Step 3 always uses one reconstructing lattice. */
+    int rr_lattices;
+    double rr_size_factor;    /* 0 = 2.0 */
 } usfft_params;
 
 typedef struct {
@@ -279,6 +292,16 @@ usfft_status usfft_get_coefficients(const usfft_plan_t* plan, double* C /* host 
 usfft_status usfft_get_selection(const usfft_plan_t* plan, uint32_t* bitmap /* host, ceil(|J|/32) */,
                                  int64_t* n);
 
+/* The random rank-1 lattices of the last coupled step when params.rr_lattices > 0: *count
+ * receives r~ * L (0 after a single-lattice step or a 1-D step), *t the number of lattice
+ * coordinates; z (may be NULL) receives [count][t] generating vectors and M (may be NULL)
+ * [count] sizes, lattice q = (i-1)*L + (l-1) of detection iteration i.  With random lattices
+ * the single-lattice inspection calls (usfft_get_lattice, usfft_get_candidates' indices,
+ * usfft_get_samples) describe the last lattice sampled; usfft_get_coefficients returns the
+ * estimate of the last iteration. */
+usfft_status usfft_get_random_lattices(const usfft_plan_t* plan, int64_t* z, int64_t* M, int32_t* count,
+                                       int32_t* t);
+
 /* Message of the last failure of this plan (plan == NULL: of the calling thread). */
 const char* usfft_last_error(const usfft_plan_t* plan);
 
@@ -289,6 +312,13 @@ void usfft_destroy(usfft_plan_t* plan);
 const char* usfft_version(void);
 
 /* ---- Host-only planner utilities (no device work; usable without a GPU) ---- */
+
+/* The random rank-1 lattice rule of params.rr_lattices on the host (no GPU needed): the L
+ * lattices of detection iteration i of the coupled step t, given |I^(1..t-1)| = n_prev,
+ * |I^(t)| = n_t and s~ = s_t; z receives [L][t], M receives [L].  USFFT_EINVAL for t outside
+ * [1, 64], i < 1, L outside [1, 31] or factor outside (0, 1e6). */
+usfft_status usfft_random_lattices(int t, int i, int64_t n_prev, int64_t n_t, int64_t s_t, int L, double factor,
+                                   uint64_t seed, int64_t* z, int64_t* M);
 
 /* The reconstructing rank-1 lattice search used by usfft_increment for the candidate set
  * J ([n][t] int8, row-major): the smallest admissible (7-smooth) size M >= n, then

@@ -28,6 +28,8 @@ Pins (tests/test_oracle_lattice.py): on tiny sets, the injectivity test agrees w
 the definition through the lattice Fourier matrix (its columns for J are orthonormal
 exactly when the lattice reconstructs J), enumerated over every z.
 """
+import math
+
 import numpy as np
 
 from . import rng
@@ -94,3 +96,27 @@ def search(J: np.ndarray, t: int, seed: int, trials: int = 64, max_sizes: int = 
                 return z, M
         M = next_admissible((105 * M + 99) // 100)
     raise RuntimeError("no reconstructing lattice found")
+
+
+def random_lattices(t: int, i: int, n_prev: int, n_t: int, s_t: int, L: int, factor: float, seed: int):
+    """The L random rank-1 lattices of detection iteration i of the coupled step t (the random
+    R1L approach in the role of Algorithm A; sizes from the bound max(s, N_Gamma) of the proof
+    of Theorem 1.1, the rule itself a reading): M_1 is the smallest admissible size >=
+    ceil(factor * max(|I^(1..t-1)|, |I^(t)|, s~)), M_(l+1) the smallest admissible size > M_l;
+    every component of z_l is a unit mod M_l (gcd 1, so that each coordinate alone takes all M_l
+    values): the first of the draws uniform in [1, M_l - 1] keyed (seed, PHASE_RANDOM_R1L, t, i,
+    l, j, a), a = 0, 1, ..., 63, that is coprime to M_l, else 1.  Returns [(z_l, M_l)], l = 1..L."""
+    base = max(int(math.ceil(factor * max(n_prev, n_t, s_t, 1))), 2)
+    M = next_admissible(base)
+    out = []
+    for l in range(1, L + 1):
+        z = np.ones(t, dtype=np.int64)
+        for j in range(1, t + 1):
+            for a in range(64):
+                v = rng.uniform_int(1, M - 1, seed, rng.PHASE_RANDOM_R1L, t, i, l, j, a)
+                if math.gcd(v, M) == 1:
+                    z[j - 1] = v
+                    break
+        out.append((z, M))
+        M = next_admissible(M + 1)
+    return out

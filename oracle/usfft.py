@@ -169,6 +169,8 @@ class OracleRun:
         r_t = p.r if t < d else 1
         s_t = p.s_local if t < d else p.s
         J = lattice.candidate_set(self.I_prefix, np.array(self.I1d[t], dtype=np.int64), p.N)
+        if getattr(p, "rr_lattices", 0) > 0:
+            return self._coupled_random(t, J, r_t, s_t)
         z, M = lattice.search(J, t, p.seed, p.max_lattice_trials)
         self.J, self.z, self.M = J, z, M
         found = set()
@@ -186,6 +188,51 @@ class OracleRun:
                 self.records.append(Record(t, i, True, z, M, tails, m,
                                            U if self.keep else None, C if self.keep else None,
                                            sel if self.keep else []))
+        idx = sorted(found)
+        self.I_prefix = J[idx] if len(idx) else np.zeros((0, t), dtype=np.int64)
+
+    def _coupled_random(self, t: int, J: np.ndarray, r_t: int, s_t: int):
+        """Coupled step t with random rank-1 lattices in the role of Algorithm A: per detection
+        iteration the same t-variate projection (fixed tails) is sampled on L random lattices
+        (oracle.lattice.random_lattices) and c_k is read from the lattice DFTs at k.z_l mod M_l:
+        from the first lattice in which no other candidate of J_t shares k's index (there the
+        value is what a reconstructing lattice gives), else as the median over the L lattices,
+        separately for the real and the imaginary part (a lattice where k shares its index with
+        a large coefficient gives an outlier; the median discards it while most lattices are
+        free of such collisions)."""
+        p = self.p
+        d = self.prob.d
+        L = p.rr_lattices
+        assert L % 2 == 1, "an odd number of lattices (the median is one of the estimates)"
+        self.J = J
+        found = set()
+        n_prev, n_t = len(self.I_prefix), len(self.I1d[t])
+        for i in range(1, r_t + 1):
+            if len(J) == 0:
+                break
+            tails = {j - 1: rng.uniform(p.seed, rng.PHASE_TAIL, t, i, j) for j in range(t + 1, d + 1)}
+            lats = lattice.random_lattices(t, i, n_prev, n_t, s_t, L, p.rr_size_factor, p.seed)
+            est, ms = [], []
+            for z_l, M_l in lats:
+                U = sample(self.prob, NodeSet(d, list(range(t)), z_l, M_l, tails), self.mesh)
+                self.samples_used += M_l
+                m_l = lattice.lattice_indices(J, z_l, M_l)
+                est.append(dft.coefficients(U, m_l, M_l))
+                ms.append(m_l)
+            E = np.stack(est)                                  # [L, G, |J|]
+            C = np.median(E.real, axis=0) + 1j * np.median(E.imag, axis=0)
+            for k in range(len(J)):
+                for l, m_l in enumerate(ms):
+                    if np.count_nonzero(m_l == m_l[k]) == 1:     # k alone at its index
+                        C[:, k] = E[l, :, k]
+                        break
+            sel = [detect.select(C[g], self.theta, s_t) for g in range(C.shape[0])]
+            for sg in sel:
+                found.update(int(x) for x in sg)
+            self.z = [z for z, _ in lats]
+            self.M = [M for _, M in lats]
+            self.records.append(Record(t, i, True, self.z, self.M, tails, ms, None,
+                                       C if self.keep else None, sel if self.keep else []))
         idx = sorted(found)
         self.I_prefix = J[idx] if len(idx) else np.zeros((0, t), dtype=np.int64)
 

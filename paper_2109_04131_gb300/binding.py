@@ -41,7 +41,8 @@ class UsfftParams(ctypes.Structure):
                 ("delta_is_relative", ctypes.c_int), ("r", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
                 ("max_cg_iters", ctypes.c_int), ("max_lattice_trials", ctypes.c_int), ("cg_tol", ctypes.c_double),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("rr_lattices", ctypes.c_int), ("rr_size_factor", ctypes.c_double)]
 
 
 class UsfftIncrementInfo(ctypes.Structure):
@@ -74,6 +75,8 @@ SIGNATURES = {
     "usfft_evaluate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int]),
     "usfft_errors": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, _P, _P]),
     "usfft_statistics": (ctypes.c_int, [_P, _P, _P, _P]),
+    "usfft_get_random_lattices": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int32),
+                                                 ctypes.POINTER(ctypes.c_int32)]),
     "usfft_get_lattice": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
     "usfft_get_candidates": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), _P]),
     "usfft_get_samples": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
@@ -84,6 +87,8 @@ SIGNATURES = {
     "usfft_version": (ctypes.c_char_p, []),
     "usfft_search_lattice": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                             ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "usfft_random_lattices": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int, ctypes.c_double, ctypes.c_uint64, _P, _P]),
     "usfft_draw_key": (ctypes.c_uint64, [ctypes.c_uint64, _P, ctypes.c_int]),
     "usfft_draw_uniform": (ctypes.c_double, [ctypes.c_uint64, _P, ctypes.c_int]),
     "usfft_sample_2d_static": (ctypes.c_int, [ctypes.POINTER(UsfftProblem), _P, _P, ctypes.c_int64, ctypes.c_int64,
@@ -178,6 +183,8 @@ def make_params(par, alloc=None, free=None) -> UsfftParams:
     q.max_cg_iters = par.max_cg_iters
     q.max_lattice_trials = par.max_lattice_trials
     q.cg_tol = par.cg_tol
+    q.rr_lattices = getattr(par, "rr_lattices", 0)
+    q.rr_size_factor = getattr(par, "rr_size_factor", 0.0)
     q.alloc = alloc if alloc is not None else ALLOC_FN()
     q.free = free if free is not None else FREE_FN()
     q.alloc_ctx = None
@@ -269,6 +276,15 @@ def usfft_search_lattice(J, t, seed, trials=64, max_sizes=400):
                                   z.ctypes.data, ctypes.byref(M))
     _check(st, None)
     return z, M.value
+
+
+def usfft_random_lattices(t, i, n_prev, n_t, s_t, L, factor, seed):
+    """Host-only random rank-1 lattice rule of the library: (z [L][t], M [L])."""
+    lib = load_library()
+    z = np.zeros((L, t), dtype=np.int64)
+    M = np.zeros(L, dtype=np.int64)
+    _check(lib.usfft_random_lattices(t, i, n_prev, n_t, s_t, L, factor, seed, z.ctypes.data, M.ctypes.data), None)
+    return z, M
 
 
 def usfft_sample_2d_static(problem, z, tails, M, i0, count, U_ptr, stream=0, tol=0.0, max_iters=0,
@@ -416,6 +432,19 @@ class Plan:
         ei = np.zeros(self.problem.G)
         self._ck(self._lib.usfft_errors(self.handle, Y.ctypes.data, len(Y), 0, e2.ctypes.data, ei.ctypes.data))
         return e2, ei
+
+    def get_random_lattices(self):
+        """([z_q] int64 [count][t], [M_q] int64 [count]) of the last random-lattice step,
+        q = (i-1)*L + l in detection-iteration order (count 0 after a single-lattice step)."""
+        cnt = ctypes.c_int32(0)
+        t = ctypes.c_int32(0)
+        self._ck(self._lib.usfft_get_random_lattices(self.handle, None, None, ctypes.byref(cnt), ctypes.byref(t)))
+        z = np.zeros((cnt.value, t.value), dtype=np.int64)
+        M = np.zeros(cnt.value, dtype=np.int64)
+        if cnt.value:
+            self._ck(self._lib.usfft_get_random_lattices(self.handle, z.ctypes.data, M.ctypes.data, ctypes.byref(cnt),
+                                                         ctypes.byref(t)))
+        return z, M
 
     def get_lattice(self):
         M = ctypes.c_int64(0)

@@ -73,6 +73,14 @@ struct usfft_plan_s {
     Buf Crec, Irec, Ypts, Upts, Vpts, epart, etot;
     int64_t nrec = -1;     // |I| of the stored reconstruction, -1: none
     std::vector<int8_t> Irec_h;
+    // random rank-1 lattice detection of the last coupled step (params.rr_lattices > 0):
+    // lattice q = i*L + l of iteration i, its FFT plan and its slices of the gather/twiddle buffers
+    bool rr_active = false;
+    int rr_L = 0, rr_iters = 0;
+    std::vector<int64_t> rr_M, rr_z;
+    std::vector<FftPlan> rr_fp;
+    std::vector<size_t> rr_goff_at, rr_gk_at, rr_twid_at;
+    Buf rr_goff, rr_gk, rr_gm2, rr_src, rr_twid, rr_C;
     size_t bytes = 0;
     int cg_blocks = 0;
     int launches = 0;
@@ -354,8 +362,149 @@ usfft_status prepare_step(usfft_plan_t* plan, int64_t M, const std::vector<int64
     return USFFT_OK;
 }
 
+// buffers, gather plans, twiddles and estimate sources of a random-lattice step: rt
+// iterations of L lattices each over the nJ candidates J (t columns)
+usfft_status prepare_rr(usfft_plan_t* plan, const std::vector<int8_t>& J, int64_t nJ, int t, int rt, int s_t) {
+    const int L = plan->par.rr_lattices, G = plan->G;
+    const double factor = plan->par.rr_size_factor > 0.0 ? plan->par.rr_size_factor : 2.0;
+    plan->rr_L = L;
+    plan->rr_iters = rt;
+    plan->rr_M.clear();
+    plan->rr_z.clear();
+    plan->rr_fp.clear();
+    plan->rr_goff_at.clear();
+    plan->rr_gk_at.clear();
+    plan->rr_twid_at.clear();
+    std::vector<int> goff_h, gk_h, gm2_h, src_h((size_t)rt * nJ, -1);
+    size_t twid_total = 0, scr_max = 0;
+    int64_t Mmax = 0;
+    std::vector<int64_t> m((size_t)nJ), sorted;
+    for (int i = 1; i <= rt; ++i) {
+        std::vector<int64_t> zi, Mi;
+        random_lattices(t, i, plan->nIpre, (int64_t)plan->I1d[(size_t)t].size(), s_t, L, factor, plan->par.seed, zi, Mi);
+        for (int l = 0; l < L; ++l) {
+            const int64_t M = Mi[(size_t)l];
+            if (M > (int64_t)1 << 24) return fail(plan, USFFT_EINVAL, "random lattice larger than 4096^2");
+            if (plan->prob.kind != USFFT_TRIGPOLY && plan->prob.theta_map == USFFT_MAP_NORMAL &&
+                lattice_hits_pole(M, plan->prob.map_shift))
+                return fail(plan, USFFT_EINVAL, "a random lattice node lies on a pole of the lognormal map");
+            const FftPlan fp = make_fft_plan(M);
+            if (fp.L2 <= 0) return fail(plan, USFFT_EINVAL, "random lattice size has no FFT factorisation");
+            for (int64_t a = 0; a < nJ; ++a) {
+                int64_t acc = 0;
+                for (int j = 0; j < t; ++j) acc += (int64_t)J[(size_t)(a * t + j)] * zi[(size_t)(l * t + j)];
+                const int64_t mm = acc % M;
+                m[(size_t)a] = mm < 0 ? mm + M : mm;
+            }
+            // candidates alone at their index in this lattice
+            sorted = m;
+            std::sort(sorted.begin(), sorted.end());
+            int* src_i = src_h.data() + (size_t)(i - 1) * nJ;
+            for (int64_t a = 0; a < nJ; ++a) {
+                if (src_i[a] >= 0) continue;
+                auto range = std::equal_range(sorted.begin(), sorted.end(), m[(size_t)a]);
+                if (range.second - range.first == 1) src_i[a] = l;
+            }
+            // gather buckets by m mod L1 (as in prepare_step)
+            const int L1 = fp.L1;
+            plan->rr_goff_at.push_back(goff_h.size());
+            plan->rr_gk_at.push_back(gk_h.size());
+            const size_t o0 = goff_h.size(), k0 = gk_h.size();
+            goff_h.resize(o0 + L1 + 1, 0);
+            gk_h.resize(k0 + nJ);
+            gm2_h.resize(k0 + nJ);
+            int* off = goff_h.data() + o0;
+            for (int64_t a = 0; a < nJ; ++a) off[(size_t)(m[(size_t)a] % L1) + 1]++;
+            for (int b = 0; b < L1; ++b) off[b + 1] += off[b];
+            std::vector<int> fill(off, off + L1);
+            for (int64_t a = 0; a < nJ; ++a) {
+                const int b = (int)(m[(size_t)a] % L1);
+                const int e = fill[(size_t)b]++;
+                gk_h[k0 + e] = (int)a;
+                gm2_h[k0 + e] = (int)(m[(size_t)a] / L1);
+            }
+            plan->rr_twid_at.push_back(twid_total);
+            twid_total += (size_t)M;
+            scr_max = std::max(scr_max, fft_scratch_bytes(fp, G));
+            Mmax = std::max(Mmax, M);
+            plan->rr_M.push_back(M);
+            plan->rr_z.insert(plan->rr_z.end(), zi.begin() + (size_t)l * t, zi.begin() + (size_t)(l + 1) * t);
+            plan->rr_fp.push_back(fp);
+        }
+    }
+    usfft_status st;
+    if ((st = ensure(plan, plan->U, sizeof(double) * (size_t)Mmax * G, "samples")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->C, sizeof(double2) * (size_t)nJ * G, "coefficients")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->rr_C, sizeof(double2) * (size_t)L * nJ * G, "lattice coefficients")) != USFFT_OK)
+        return st;
+    if ((st = ensure(plan, plan->rr_twid, sizeof(double2) * twid_total, "twiddles")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->fftscr, scr_max, "fft scratch")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->bitmap, sizeof(uint32_t) * (size_t)((nJ + 31) / 32), "bitmap")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->iters, sizeof(int) * (size_t)Mmax, "cg iterations")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->rr_goff, sizeof(int) * goff_h.size(), "gather offsets")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->rr_gk, sizeof(int) * gk_h.size(), "gather k")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->rr_gm2, sizeof(int) * gm2_h.size(), "gather m2")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->rr_src, sizeof(int) * src_h.size(), "estimate sources")) != USFFT_OK) return st;
+    CK(cudaMemcpyAsync(plan->rr_goff.p, goff_h.data(), sizeof(int) * goff_h.size(), cudaMemcpyHostToDevice, plan->stream));
+    CK(cudaMemcpyAsync(plan->rr_gk.p, gk_h.data(), sizeof(int) * gk_h.size(), cudaMemcpyHostToDevice, plan->stream));
+    CK(cudaMemcpyAsync(plan->rr_gm2.p, gm2_h.data(), sizeof(int) * gm2_h.size(), cudaMemcpyHostToDevice, plan->stream));
+    CK(cudaMemcpyAsync(plan->rr_src.p, src_h.data(), sizeof(int) * src_h.size(), cudaMemcpyHostToDevice, plan->stream));
+    plan->h2d += (int64_t)(sizeof(int) * (goff_h.size() + gk_h.size() + gm2_h.size() + src_h.size()));
+    CK(cudaStreamSynchronize(plan->stream));   // host vectors outlive the copies
+    for (size_t q = 0; q < plan->rr_M.size(); ++q)
+        CK(launch_twiddles(plan->rr_M[q], (double2*)plan->rr_twid.p + plan->rr_twid_at[q], plan->stream,
+                           &plan->launches));
+    // the last lattice stands for the step in the single-lattice inspection calls
+    plan->M = plan->rr_M.back();
+    plan->z.assign(plan->rr_z.end() - t, plan->rr_z.end());
+    plan->m.assign((size_t)nJ, 0);
+    for (int64_t a = 0; a < nJ; ++a) {
+        int64_t acc = 0;
+        for (int j = 0; j < t; ++j) acc += (int64_t)J[(size_t)(a * t + j)] * plan->z[(size_t)j];
+        const int64_t mm = acc % plan->M;
+        plan->m[(size_t)a] = mm < 0 ? mm + plan->M : mm;
+    }
+    plan->nJ = nJ;
+    return USFFT_OK;
+}
+
+// device part of a random-lattice step: per iteration L x (sample -> FFT+gather), the
+// estimate (alias-free lattice or median), select/union
+usfft_status run_rr_device(usfft_plan_t* plan) {
+    const int64_t nJ = plan->nJ;
+    const int G = plan->G, L = plan->rr_L;
+    CK(cudaMemsetAsync(plan->bitmap.p, 0, sizeof(uint32_t) * (size_t)((nJ + 31) / 32), plan->stream));
+    if (nJ == 0) return USFFT_OK;
+    for (int i = 0; i < plan->rr_iters; ++i) {
+        for (int l = 0; l < L; ++l) {
+            const size_t q = (size_t)i * L + l;
+            usfft_status st = run_sampler(plan, plan->specs[q]);
+            if (st != USFFT_OK) return st;
+            StageTimer timer(plan, USFFT_STAGE_FFT);
+            GatherPlan gp{(const int*)plan->rr_goff.p + plan->rr_goff_at[q], (const int*)plan->rr_gk.p + plan->rr_gk_at[q],
+                          (const int*)plan->rr_gm2.p + plan->rr_gk_at[q]};
+            CK(launch_fft_gather(plan->rr_fp[q], G, (const double*)plan->U.p,
+                                 (const double2*)plan->rr_twid.p + plan->rr_twid_at[q], gp, nJ,
+                                 (double2*)plan->fftscr.p, (double2*)plan->rr_C.p + (size_t)l * G * nJ, plan->stream,
+                                 &plan->launches));
+        }
+        {
+            StageTimer timer(plan, USFFT_STAGE_FFT);
+            CK(launch_random_lattice_combine((const double2*)plan->rr_C.p, L, G, nJ, (const int*)plan->rr_src.p + (size_t)i * nJ,
+                                             (double2*)plan->C.p, plan->stream, &plan->launches));
+        }
+        if (plan->s_tilde > 0) {
+            StageTimer timer(plan, USFFT_STAGE_SELECT);
+            CK(launch_select_union((const double2*)plan->C.p, G, nJ, plan->theta, plan->s_tilde, (uint32_t*)plan->bitmap.p,
+                                   plan->stream, &plan->launches));
+        }
+    }
+    return USFFT_OK;
+}
+
 // device part of a detection step: r~ iterations of sample -> FFT+gather -> select/union
 usfft_status run_step_device(usfft_plan_t* plan, bool first_1d_sets_theta) {
+    if (plan->rr_active) return run_rr_device(plan);
     const int64_t nJ = plan->nJ;
     CK(cudaMemsetAsync(plan->bitmap.p, 0, sizeof(uint32_t) * (size_t)((nJ + 31) / 32), plan->stream));
     if (nJ == 0) return USFFT_OK;
@@ -457,6 +606,10 @@ usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params
     if (!(pa.delta >= 0.0)) return fail(nullptr, USFFT_EINVAL, "delta must be >= 0");
     if (pa.precision != USFFT_FP64 && pa.precision != USFFT_MIXED && pa.precision != USFFT_MIXED_JACOBI)
         return fail(nullptr, USFFT_EINVAL, "precision");
+    if (pa.rr_lattices < 0 || pa.rr_lattices > 31 || (pa.rr_lattices > 0 && pa.rr_lattices % 2 == 0))
+        return fail(nullptr, USFFT_EINVAL, "rr_lattices must be 0 or odd in [1, 31]");
+    if (pa.rr_size_factor < 0.0 || !(pa.rr_size_factor < 1e6))
+        return fail(nullptr, USFFT_EINVAL, "rr_size_factor must lie in [0, 1e6)");
     int G = 0, E = 0;
     if (pr.kind == USFFT_PDE_1D) {
         if (pr.n < 1 || pr.n > 1023) return fail(nullptr, USFFT_EINVAL, "1-D: n must lie in [1, 1023]");
@@ -574,6 +727,7 @@ usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
     if (plan->t >= plan->d) return fail(plan, USFFT_ESTATE, "all d increments are done");
     const int t = plan->t + 1;
     const int N = plan->N, K = plan->K;
+    plan->rr_active = false;
     plan->launches = 0;
     plan->cg_iters_total = 0;
     plan->cg_iters_max = 0;
@@ -615,33 +769,58 @@ usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
         std::vector<int8_t> J;
         int64_t nJ = 0;
         candidate_set(plan->Ipre.data(), plan->nIpre, t - 1, plan->I1d[(size_t)t], N, J, nJ);
-        std::vector<int64_t> z;
-        int64_t M = 0;
-        if (!lattice_search(J.data(), nJ, t, plan->par.seed, plan->par.max_lattice_trials, 400, z, M))
-            return fail(plan, USFFT_ELATTICE, "no reconstructing rank-1 lattice found");
-        std::vector<int64_t> m((size_t)nJ);
-        for (int64_t a = 0; a < nJ; ++a) {
-            int64_t acc = 0;
-            for (int j = 0; j < t; ++j) acc += (int64_t)J[(size_t)(a * t + j)] * z[(size_t)j];
-            int64_t mm = acc % M;
-            m[(size_t)a] = mm < 0 ? mm + M : mm;
-        }
-        ms_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
-        plan->J = J;
-        plan->z = z;
-        plan->last_coupled = true;
-        plan->last_t = t;
-        if (nJ > 0) {
-            if ((st = prepare_step(plan, M, m)) != USFFT_OK) return st;
-        } else {
-            plan->M = 0;
-            plan->m.clear();
-            plan->nJ = 0;
-        }
         const int rt = t < plan->d ? plan->par.r : 1;
         plan->s_tilde = t < plan->d ? plan->par.s_local : plan->par.s;
         plan->specs.clear();
-        for (int i = 1; i <= rt && nJ > 0; ++i) plan->specs.push_back(spec_coupled(plan, t, i));
+        if (plan->par.rr_lattices > 0) {
+            // random rank-1 lattices in the role of Algorithm A
+            plan->J = J;
+            plan->last_coupled = true;
+            plan->last_t = t;
+            plan->rr_active = true;
+            if (nJ > 0) {
+                if ((st = prepare_rr(plan, J, nJ, t, rt, plan->s_tilde)) != USFFT_OK) return st;
+                for (int i = 1; i <= rt; ++i)
+                    for (int l = 0; l < plan->rr_L; ++l) {
+                        const size_t q = (size_t)(i - 1) * plan->rr_L + l;
+                        NodeSpec ns = spec_coupled(plan, t, i);      // tails of iteration i
+                        ns.M = plan->rr_M[q];
+                        for (int j = 0; j < t; ++j) ns.z[j] = plan->rr_z[q * t + j];
+                        plan->specs.push_back(ns);
+                    }
+            } else {
+                plan->M = 0;
+                plan->m.clear();
+                plan->nJ = 0;
+                plan->rr_iters = 0;
+            }
+            ms_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
+        } else {
+            std::vector<int64_t> z;
+            int64_t M = 0;
+            if (!lattice_search(J.data(), nJ, t, plan->par.seed, plan->par.max_lattice_trials, 400, z, M))
+                return fail(plan, USFFT_ELATTICE, "no reconstructing rank-1 lattice found");
+            std::vector<int64_t> m((size_t)nJ);
+            for (int64_t a = 0; a < nJ; ++a) {
+                int64_t acc = 0;
+                for (int j = 0; j < t; ++j) acc += (int64_t)J[(size_t)(a * t + j)] * z[(size_t)j];
+                int64_t mm = acc % M;
+                m[(size_t)a] = mm < 0 ? mm + M : mm;
+            }
+            ms_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
+            plan->J = J;
+            plan->z = z;
+            plan->last_coupled = true;
+            plan->last_t = t;
+            if (nJ > 0) {
+                if ((st = prepare_step(plan, M, m)) != USFFT_OK) return st;
+            } else {
+                plan->M = 0;
+                plan->m.clear();
+                plan->nJ = 0;
+            }
+            for (int i = 1; i <= rt && nJ > 0; ++i) plan->specs.push_back(spec_coupled(plan, t, i));
+        }
         if ((st = run_step_device(plan, false)) != USFFT_OK) return st;
         if ((st = read_cg_stats(plan, plan->M)) != USFFT_OK) return st;
         std::vector<uint32_t> bits;
@@ -655,7 +834,7 @@ usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
             }
         plan->Ipre.swap(I);
         plan->nIpre = nI;
-        samples += plan->M * (int64_t)plan->specs.size();
+        for (const NodeSpec& ns : plan->specs) samples += ns.M;
     }
     CK(cudaEventRecord(plan->ev1, plan->stream));
     if ((st = wait_stream(plan)) != USFFT_OK) return st;
@@ -827,6 +1006,20 @@ usfft_status usfft_get_coefficients(const usfft_plan_t* plan_c, double* C, int64
     return USFFT_OK;
 }
 
+usfft_status usfft_get_random_lattices(const usfft_plan_t* plan_c, int64_t* z, int64_t* M, int32_t* count,
+                                       int32_t* t) {
+    const usfft_plan_t* plan = plan_c;
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    const bool on = plan->rr_active && plan->nJ > 0;
+    const int32_t cnt = on ? (int32_t)plan->rr_M.size() : 0;
+    const int32_t tt = on ? (int32_t)(plan->rr_z.size() / std::max<size_t>(plan->rr_M.size(), 1)) : 0;
+    if (count) *count = cnt;
+    if (t) *t = tt;
+    if (cnt && z) memcpy(z, plan->rr_z.data(), sizeof(int64_t) * plan->rr_z.size());
+    if (cnt && M) memcpy(M, plan->rr_M.data(), sizeof(int64_t) * plan->rr_M.size());
+    return USFFT_OK;
+}
+
 usfft_status usfft_get_selection(const usfft_plan_t* plan_c, uint32_t* bitmap, int64_t* n) {
     usfft_plan_t* plan = const_cast<usfft_plan_t*>(plan_c);
     if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
@@ -869,6 +1062,7 @@ usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, do
     plan->cg_iters_total = 0;
     plan->cg_iters_max = 0;
     plan->nrec = -1;
+    plan->rr_active = false;
     CK(cudaMemsetAsync(plan->failc.p, 0, sizeof(unsigned), plan->stream));
     usfft_status st = prepare_step(plan, M, m);
     if (st != USFFT_OK) return st;
@@ -1113,6 +1307,18 @@ usfft_status usfft_search_lattice(const int8_t* J, int64_t n, int t, uint64_t se
     return USFFT_OK;
 }
 
+usfft_status usfft_random_lattices(int t, int i, int64_t n_prev, int64_t n_t, int64_t s_t, int L, double factor,
+                                   uint64_t seed, int64_t* z, int64_t* M) {
+    if (t < 1 || t > USFFT_MAX_D || i < 1 || L < 1 || L > 31 || !(factor > 0.0 && factor < 1e6) || !z || !M ||
+        n_prev < 0 || n_t < 0 || s_t < 0)
+        return fail(nullptr, USFFT_EINVAL, "usfft_random_lattices: invalid argument");
+    std::vector<int64_t> zz, mm;
+    random_lattices(t, i, n_prev, n_t, s_t, L, factor, seed, zz, mm);
+    memcpy(z, zz.data(), sizeof(int64_t) * zz.size());
+    memcpy(M, mm.data(), sizeof(int64_t) * mm.size());
+    return USFFT_OK;
+}
+
 uint64_t usfft_draw_key(uint64_t seed, const uint64_t* fields, int nfields) {
     return rng_key(seed, fields, nfields);
 }
@@ -1127,7 +1333,8 @@ void usfft_destroy(usfft_plan_t* plan) {
     Buf* bufs[] = {&plan->psi,   &plan->U,    &plan->C,    &plan->bitmap, &plan->twid, &plan->goff,
                    &plan->gk,    &plan->gm2,  &plan->fftscr, &plan->cgscr, &plan->iters, &plan->failc,
                    &plan->scal,  &plan->tpf,  &plan->tpc,  &plan->tpaux, &plan->Crec, &plan->Irec,
-                   &plan->Ypts,  &plan->Upts, &plan->Vpts, &plan->epart, &plan->etot};
+                   &plan->Ypts,  &plan->Upts, &plan->Vpts, &plan->epart, &plan->etot, &plan->rr_goff,
+                   &plan->rr_gk, &plan->rr_gm2, &plan->rr_src, &plan->rr_twid, &plan->rr_C};
     for (Buf* b : bufs) buf_free(plan, *b);
     if (plan->pinned) cudaFreeHost(plan->pinned);
     if (plan->ev0) cudaEventDestroy(plan->ev0);

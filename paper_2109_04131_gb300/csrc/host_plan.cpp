@@ -13,7 +13,9 @@
 //   - the search gives up on a repeated candidate, after 400 sizes or beyond
 //     M = 4096^2 (the largest two-pass FFT).
 // Step 3 (the final coefficients on I) uses the same rule with the draws keyed by
-// PHASE_RECON instead of PHASE_LATTICE.
+// PHASE_RECON instead of PHASE_LATTICE.  The random rank-1 lattices of the alternative
+// detection (random_lattices) follow their own rule, stated at its declaration.
+#include <math.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -61,6 +63,39 @@ int64_t next_admissible(int64_t x) {
     int64_t m = x < 1 ? 1 : x;
     while (!is_smooth7(m)) ++m;
     return m;
+}
+
+static int64_t gcd64(int64_t a, int64_t b) {
+    while (b) {
+        const int64_t r = a % b;
+        a = b;
+        b = r;
+    }
+    return a;
+}
+
+void random_lattices(int t, int i, int64_t n_prev, int64_t n_t, int64_t s_t, int L, double factor, uint64_t seed,
+                     std::vector<int64_t>& z, std::vector<int64_t>& M) {
+    z.assign((size_t)L * t, 1);
+    M.assign((size_t)L, 0);
+    int64_t big = std::max<int64_t>(std::max<int64_t>(n_prev, n_t), std::max<int64_t>(s_t, 1));
+    int64_t base = (int64_t)ceil(factor * (double)big);
+    if (base < 2) base = 2;
+    int64_t m = next_admissible(base);
+    for (int l = 1; l <= L; ++l) {
+        M[(size_t)(l - 1)] = m;
+        for (int j = 1; j <= t; ++j) {
+            for (int a = 0; a < 64; ++a) {
+                const uint64_t f[6] = {PHASE_RANDOM_R1L, (uint64_t)t, (uint64_t)i, (uint64_t)l, (uint64_t)j, (uint64_t)a};
+                const int64_t v = rng_uniform_int(1, m - 1, seed, f, 6);
+                if (gcd64(v, m) == 1) {
+                    z[(size_t)((l - 1) * t + (j - 1))] = v;
+                    break;
+                }
+            }
+        }
+        m = next_admissible(m + 1);
+    }
 }
 
 void candidate_set(const int8_t* I_prev, int64_t n_prev, int t_prev, const std::vector<int>& I_t, int N,

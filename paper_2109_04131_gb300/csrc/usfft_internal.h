@@ -18,7 +18,7 @@ namespace usfft {
 
 // Counter-based SplitMix64 draws (Steele, Lea, Flood 2014): key(seed, f1, f2, ...)
 // folds one SplitMix64 step per field, h <- mix64((h ^ f) + golden gamma).
-enum Phase : uint64_t { PHASE_1D_TAIL = 1, PHASE_TAIL = 2, PHASE_LATTICE = 3, PHASE_RECON = 4 };
+enum Phase : uint64_t { PHASE_1D_TAIL = 1, PHASE_TAIL = 2, PHASE_LATTICE = 3, PHASE_RECON = 4, PHASE_RANDOM_R1L = 5 };
 uint64_t rng_key(uint64_t seed, const uint64_t* fields, int nfields);
 double rng_uniform(uint64_t seed, const uint64_t* fields, int nfields);                 // [0,1)
 int64_t rng_uniform_int(int64_t lo, int64_t hi, uint64_t seed, const uint64_t* fields, int nfields);
@@ -31,6 +31,14 @@ int64_t next_admissible(int64_t x);
 // (PHASE_LATTICE for the coupled steps, PHASE_RECON for step 3).
 bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials, int max_sizes,
                     std::vector<int64_t>& z, int64_t& M, uint64_t phase = PHASE_LATTICE);
+
+// The L random rank-1 lattices of detection iteration i of the coupled step t (random R1L
+// approach in the role of Algorithm A): M_1 = smallest admissible size >= ceil(factor *
+// max(n_prev, n_t, s_t)) (at least 2), M_(l+1) = smallest admissible size > M_l; z_l has t
+// components, each the first draw in [1, M_l - 1] keyed (seed, PHASE_RANDOM_R1L, t, i, l, j, a),
+// a = 0..63, that is coprime to M_l (else 1).  z receives L*t entries, M receives L sizes.
+void random_lattices(int t, int i, int64_t n_prev, int64_t n_t, int64_t s_t, int L, double factor, uint64_t seed,
+                     std::vector<int64_t>& z, std::vector<int64_t>& M);
 
 // Candidate set J_t = I_prev x I_t within [-N,N]^t (lexicographic in the positions).
 void candidate_set(const int8_t* I_prev, int64_t n_prev, int t_prev, const std::vector<int>& I_t, int N,
@@ -109,6 +117,12 @@ cudaError_t launch_twiddles(int64_t M, double2* W, cudaStream_t s, int* launches
 cudaError_t launch_fft_gather(const FftPlan& p, int G, const double* U, const double2* W,
                               const GatherPlan& gp, int64_t nJ, double2* scratch, double2* C,
                               cudaStream_t s, int* launches);
+
+// Random-lattice estimate (Algorithm A): C[g][k] = Call[src[k]][g][k] where src[k] >= 0 (the
+// first lattice with k alone at its index), else the median over the L lattices of the real
+// and, separately, the imaginary parts (L odd, <= 31).  Call is [L][G][nJ].
+cudaError_t launch_random_lattice_combine(const double2* Call, int L, int G, int64_t nJ, const int* src, double2* C,
+                                          cudaStream_t s, int* launches);
 
 // Per-node selection of the <= s~ largest |C[g][k]| >= theta and the union (bitmap OR).
 cudaError_t launch_select_union(const double2* C, int G, int64_t nJ, double theta, int s_tilde,

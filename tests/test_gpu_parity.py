@@ -8,6 +8,8 @@ other) and, for PDE samples, bit-exact except at near-ties of the oracle's magni
 samples U and coefficients C within 1e-10 relative on the fp64 path and the mixed path,
 in the per-node norm max_k |C_gpu - C_orc| / max_k |C_orc| (the reading of "1e-10
 relative" that ignores noise-level coefficients)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -323,3 +325,64 @@ def test_lognormal_map_rejects_a_lattice_node_on_a_pole(B):
     bad = W.Problem(kind=W.PDE_1D, n=15, d=2, theta_map=W.MAP_NORMAL, map_shift=0.01)
     with pytest.raises(B.UsfftError):
         B.Plan(bad, params)
+
+
+def compare_random_increment(plan, run, ctx):
+    """Increment t = run.t + 1 with random rank-1 lattices on both sides from the oracle's
+    state: lattices bit-exact, estimates within TOL per node, sets equal up to near-ties."""
+    if run.t > 0:
+        plan.resume(run.t, run.I_prefix, run.theta)
+    first = len(run.records)
+    want = run.increment()
+    info = plan.increment()
+    got = plan.get_set()
+    recs = [r for r in run.records[first:] if r.coupled]
+    if recs:
+        z, M = plan.get_random_lattices()
+        assert np.array_equal(M, np.concatenate([r.M for r in recs])), ctx
+        assert np.array_equal(z, np.concatenate([np.array(r.z) for r in recs])), ctx
+        assert info["samples"] == int(np.sum(M)) + (2 * run.p.N + 1) * run.p.r
+        e = node_rel(plan.get_coefficients(), recs[-1].C)
+        assert e < TOL, f"{ctx}: estimate rel err {e:.2e}"
+    if not (got.shape == want.shape and np.array_equal(got, want)):
+        d = run.prob.d
+        amb = near_ties(recs, run.theta, lambda r: run.p.s_local if r.t < d else run.p.s)
+        diff = {tuple(r) for r in got.tolist()} ^ {tuple(r) for r in want.tolist()}
+        allowed = {tuple(int(v) for v in run.J[k]) for k in amb}
+        assert diff <= allowed, f"{ctx}: t={run.t}: {len(diff - allowed)} differences are not near-ties"
+    return info
+
+
+def test_random_lattices_trigpoly_exact_recovery(B):
+    d, N, G, seed = 4, 5, 9, 12
+    prob = W.trigpoly(G=G, d=d, N=N, seed=seed, base_terms=5, node_terms=2, kmax=3, mag_lo=1e-4)
+    params = W.Params(N=N, s=40, s_local=40, delta=1e-9, delta_is_relative=False, r=1, seed=seed,
+                      rr_lattices=5, rr_size_factor=4.0)
+    plan = B.Plan(prob, params)
+    run = OracleRun(prob, params, keep=True)
+    union = {tuple(int(v) for v in f) for g in range(G) for f, c in zip(prob.tp_freqs[g], prob.tp_coefs[g]) if c != 0}
+    for t in range(1, d + 1):
+        compare_random_increment(plan, run, "trigpoly random lattices")
+        assert {tuple(int(v) for v in row) for row in plan.get_set()} == {k[:t] for k in union}
+    # step 3 keeps the reconstructing lattice: the polynomial's own coefficients
+    I, C = plan.reconstruct()
+    for g in range(G):
+        truth = {tuple(int(v) for v in f): c for f, c in zip(prob.tp_freqs[g], prob.tp_coefs[g]) if c != 0}
+        assert np.max(np.abs(C[g] - np.array([truth.get(tuple(int(v) for v in k), 0.0) for k in I]))) < 1e-13
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED])
+def test_random_lattices_pde_match_oracle(B, precision):
+    for w in (W.c1(2), W.small_2d(n=15, d=4, seed=2, N=6, s=30, r=2)):
+        w = W.with_precision(w, precision)
+        w = W.Workload(w.name, w.problem, dataclasses.replace(w.params, rr_lattices=5, rr_size_factor=2.0))
+        plan = B.Plan(w.problem, w.params)
+        run = OracleRun(w.problem, w.params, keep=True)
+        for t in range(1, min(w.problem.d, 4) + 1):
+            compare_random_increment(plan, run, f"{w.name} random lattices precision {precision}")
+        # replay of a random-lattice step reproduces its estimate
+        C = plan.get_coefficients()
+        plan.replay()
+        assert np.array_equal(plan.get_coefficients(), C)
+        plan.close()

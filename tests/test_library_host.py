@@ -2,6 +2,7 @@
 its struct layouts match the binding, and its host planner (draws, lattice search) agrees
 bit for bit with the oracle.  No device work is started here."""
 import ctypes
+import math
 import os
 import re
 import subprocess
@@ -54,7 +55,9 @@ int main(void) {
   printf("usfft_params size %zu\\n", sizeof(usfft_params));
   printf("usfft_increment_info size %zu\\n", sizeof(usfft_increment_info));
   P(usfft_problem, tp_freqs) P(usfft_problem, tp_coefs) P(usfft_problem, coef_scale)
+  P(usfft_problem, theta_map) P(usfft_problem, map_shift)
   P(usfft_params, seed) P(usfft_params, hbm_budget_bytes) P(usfft_params, cg_tol) P(usfft_params, alloc_ctx)
+  P(usfft_params, rr_lattices) P(usfft_params, rr_size_factor)
   P(usfft_increment_info, M) P(usfft_increment_info, kernel_launches) P(usfft_increment_info, ms_host_plan)
   P(usfft_increment_info, d2h_bytes)
   return 0;
@@ -114,3 +117,18 @@ def test_lattice_search_edge_cases(binding):
     assert M == 1
     with pytest.raises(binding.UsfftError):
         binding.usfft_search_lattice(np.zeros((4, 2), np.int8), 2, 1)   # duplicates never separate
+
+
+@pytest.mark.parametrize("t,i,n_prev,n_t,s_t,L,factor,seed", [
+    (2, 1, 33, 17, 50, 5, 2.0, 1), (5, 2, 1200, 13, 500, 7, 2.0, 3), (3, 1, 1, 1, 0, 1, 0.5, 9),
+    (10, 2, 4000, 30, 1000, 31, 1.5, 12345)])
+def test_random_lattice_rule_is_bit_exact_with_the_oracle(binding, t, i, n_prev, n_t, s_t, L, factor, seed):
+    from oracle import lattice
+    z, M = binding.usfft_random_lattices(t, i, n_prev, n_t, s_t, L, factor, seed)
+    want = lattice.random_lattices(t, i, n_prev, n_t, s_t, L, factor, seed)
+    assert [int(m) for m in M] == [m for _, m in want]
+    assert np.array_equal(z, np.array([zz for zz, _ in want]))
+    assert len(set(M.tolist())) == L and all(lattice.is_smooth7(int(m)) for m in M)
+    assert all(math.gcd(int(v), int(m)) == 1 for row, m in zip(z, M) for v in row)
+    with pytest.raises(binding.UsfftError):
+        binding.usfft_random_lattices(t, i, n_prev, n_t, s_t, 32, factor, seed)

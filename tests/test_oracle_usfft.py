@@ -129,3 +129,38 @@ def test_step3_reconstruction_returns_the_polynomial_coefficients():
     for g in range(G):
         want = np.array([sup[g].get(tuple(int(v) for v in k), 0.0) for k in I])
         assert np.max(np.abs(C[g] - want)) < 1e-13
+
+
+@pytest.mark.parametrize("G,seed", [(3, 5), (9, 12)])
+def test_random_lattices_recover_trigonometric_polynomials(G, seed):
+    # random rank-1 lattices with the median estimate (Algorithm A, reading of the sizes and the
+    # estimator): for sparse polynomials most lattices are free of collisions between non-zero
+    # coefficients, so the median returns every projected coefficient exactly and the detected
+    # sets are the projections of the union of the supports, as with reconstructing lattices
+    from oracle import lattice
+    d, N = 4, 5
+    prob = W.trigpoly(G=G, d=d, N=N, seed=seed, base_terms=5, node_terms=2, kmax=3, mag_lo=1e-4)
+    params = W.Params(N=N, s=40, s_local=40, delta=1e-9, delta_is_relative=False, r=1, seed=seed,
+                      rr_lattices=5, rr_size_factor=4.0)
+    assert _margins_ok(prob, params, params.delta)
+    run = OracleRun(prob, params, keep=True)
+    sup = _support(prob)
+    union = set().union(*[set(s) for s in sup])
+    single = 0
+    for t in range(1, d + 1):
+        I = run.increment()
+        assert {tuple(int(v) for v in row) for row in I} == {k[:t] for k in union}, t
+        if t >= 2:
+            rec = run.records[-1]
+            assert rec.coupled and len(rec.M) == 5 and len(set(rec.M)) == 5
+            assert all(lattice.is_smooth7(M) for M in rec.M)
+            assert rec.M[0] >= 4.0 * max(len(run.J) // max(len(run.I1d[t]), 1), len(run.I1d[t]))
+            assert all(np.all((z >= 1) & (z < M)) for z, M in zip(rec.z, rec.M))
+            single += lattice.search(run.J, t, seed)[1]
+    last = run.records[-1]
+    for g in range(G):
+        for col, k in enumerate(run.J):
+            assert abs(last.C[g, col] - sup[g].get(tuple(int(v) for v in k), 0.0)) < 1e-13
+    # the step-3 reconstruction still uses one reconstructing lattice
+    I, z, M, C = run.reconstruct()
+    assert lattice.is_reconstructing(I, z, M)

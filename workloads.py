@@ -80,6 +80,9 @@ class Params:
     max_cg_iters: int = 4000
     max_lattice_trials: int = 64
     cg_tol: float = 0.0                # 0 = library default
+    rr_lattices: int = 0               # 0: one reconstructing lattice per coupled step; odd L >= 1:
+                                       # L random rank-1 lattices (Algorithm A), median estimate
+    rr_size_factor: float = 2.0        # random lattice size >= factor * max(|I^(1..t-1)|, |I^(t)|, s~)
 
 
 @dataclass
