@@ -319,6 +319,11 @@ def run_ours(args, rank, world):
 
     # end to end through the public call (rewind + usfft_increment), mixed precision
     e2e = e2e_measure(plans["mixed"], t, args.e2e_steps, barrier, world, dev)
+    # the rows past the increment (reconstruction, evaluation, statistics, random lattices)
+    next_rows = None
+    if rank == 0 and not args.skip_next_rows:
+        pk, pkind = measured_peaks()
+        next_rows = next_rows_measure(w, plans["mixed"], t, args.n_test, pk, pkind)
 
     if rank != 0:
         for p in plans.values():
@@ -408,6 +413,7 @@ def run_ours(args, rank, world):
                    "reasons": clocks.get("reasons"), "samples": clocks.get("samples"),
                    "power_w_max": clocks.get("power_w_max")},
         "e2e": e2e,
+        "next_rows": next_rows,
     }
     if not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(w, t)
@@ -442,6 +448,84 @@ def e2e_measure(plan, t, steps, barrier, world, dev):
             "latency_ms": {"p50": 1e3 * percentile(times, 50), "p99": 1e3 * percentile(times, 99)},
             "call": "usfft_rewind(t-1) + usfft_increment (1-D detections of dimension t, J_t, lattice "
                     "search, both detection iterations, host copies)"}
+
+
+def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind):
+    """The rows past the detection increment, on the same workload: the remaining increments
+    t0+1..d of the mixed plan (single reconstructing lattice per step), step 3 (usfft_reconstruct),
+    the quantities of interest (usfft_statistics), FE solves at n_test random parameters and the
+    evaluation of u^usFFT there with the errors (usfft_errors), and the same run with random
+    rank-1 lattices (5 lattices, size factor 2) for the sample counts."""
+    import dataclasses
+    import torch
+    from paper_2109_04131_gb300 import binding
+    d, G = w.problem.d, w.problem.G
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_0 = time.perf_counter()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t_0)
+
+    single = []
+    for _ in range(t0 + 1, d + 1):
+        info = pmx.increment()
+        single.append({"t": info["t"], "M": info["M"], "samples": info["samples"], "n_detected": info["n_detected"],
+                       "ms_device": info["ms_device"]})
+    (I, C), ms_rec, wall_rec = timed(pmx.reconstruct)
+    z_rec, M_rec = pmx.get_lattice()
+    (mean, var, gsi), ms_stat, _ = timed(pmx.statistics)
+    nI = len(I)
+    Y = torch.from_numpy(W.parameter_points(w.problem, n_test, seed=5)).to("cuda")
+    V = torch.empty((n_test, G, 2), dtype=torch.float64, device="cuda")
+    Ud = torch.empty((n_test, G), dtype=torch.float64, device="cuda")
+    lib, h = pmx._lib, pmx.handle
+    _, ms_pts, _ = timed(lambda: lib.usfft_sample_points(h, Y.data_ptr(), n_test, Ud.data_ptr(), 1))
+    timed(lambda: lib.usfft_evaluate(h, Y.data_ptr(), n_test, V.data_ptr(), 1))                # warm
+    st, ms_eval, _ = timed(lambda: lib.usfft_evaluate(h, Y.data_ptr(), n_test, V.data_ptr(), 1))
+    assert st == 0
+    e2 = np.zeros(G)
+    ei = np.zeros(G)
+    st, ms_err, _ = timed(lambda: lib.usfft_errors(h, Y.data_ptr(), n_test, 1, e2.ctypes.data, ei.ctypes.data))
+    assert st == 0
+    flops_eval = 8.0 * n_test * nI * G                  # complex multiply-add per (point, frequency, node)
+    ach = flops_eval / (ms_eval / 1e3) / 1e12
+    stat_bytes = 16.0 * G * nI
+    stat_gbs = stat_bytes / (ms_stat / 1e3) / 1e9
+
+    # random rank-1 lattices on the same workload (increments 1..d)
+    prr = binding.Plan(w.problem, dataclasses.replace(W.with_precision(w, W.PRECISION_MIXED).params, rr_lattices=5,
+                                                      rr_size_factor=2.0))
+    rr = []
+    for _ in range(d):
+        info = prr.increment()
+        rr.append({"t": info["t"], "samples": info["samples"], "n_detected": info["n_detected"],
+                   "ms_device": info["ms_device"]})
+    prr.close()
+    return {
+        "workload": "the 2-D workload above, increments t0+1..d after the timed increment, mixed precision",
+        "increments_single_lattice": single,
+        "samples_single_lattice_t0_plus_1_to_d": int(sum(r["samples"] for r in single)),
+        "reconstruct": {"n_I": nI, "M": int(M_rec), "ms": ms_rec, "wall_ms": wall_rec,
+                        "lattice_samples_per_s": M_rec / (ms_rec / 1e3)},
+        "statistics": {"ms": ms_stat, "bytes": stat_bytes, "achieved_gbs": stat_gbs,
+                       "frac_of_hbm": stat_gbs / peaks["hbm_gbs"], "peak_note": f"{peak_kind} hbm_gbs",
+                       "gsi_l1_min": float(np.min(gsi[:, 0])), "variance_max": float(np.max(var))},
+        "sample_points": {"n": n_test, "ms": ms_pts, "samples_per_s": n_test / (ms_pts / 1e3)},
+        "evaluate": {"n": n_test, "n_I": nI, "ms": ms_eval, "flops": flops_eval, "achieved_tflops": ach,
+                     "frac_of_fp64_peak": ach / PEAK_FP64_TFLOPS, "bound": "alu",
+                     "kernel": "evaluate_kernel (fp64 complex contraction, E formed on chip)"},
+        "errors": {"n": n_test, "ms": ms_err, "err2_max": float(np.max(e2)), "errinf_max": float(np.max(ei)),
+                   "err2_median": float(np.median(e2))},
+        "random_r1l": {"lattices": 5, "size_factor": 2.0, "precision": "mixed", "increments": rr,
+                       "samples_total": int(sum(r["samples"] for r in rr)),
+                       "ms_device_total": float(sum(r["ms_device"] for r in rr))},
+    }
 
 
 def sampled_accuracy(w, t, plans, rows=4):
@@ -503,6 +587,9 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=24)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--skip-next-rows", action="store_true",
+                    help="skip the reconstruction / evaluation / statistics / random-lattice leg")
+    ap.add_argument("--n-test", type=int, default=4096, help="test points of the error evaluation")
     ap.add_argument("--profile-increments", type=int, default=0,
                     help="profiling mode: only run this many increments of the 2-D workload (no timing)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
