@@ -143,6 +143,23 @@ def percentile(xs, q):
     return xs[f] if f == c else xs[f] + (xs[c] - xs[f]) * (k - f)
 
 
+def max_over_ranks(x, world, device=None):
+    """The maximum of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, tot_ms):
+    """Units all ranks processed per second when every rank did units_per_rank in the slowest
+    rank's time tot_ms (independent instances: weak scaling)."""
+    return world * units_per_rank / (tot_ms / 1e3)
+
+
 def workload_config(w, t, info=None):
     p = w.params
     cfg = {"workload": f"2-D P1 FE {w.problem.n}x{w.problem.n} interior (G={w.problem.G}), affine periodic "
@@ -308,11 +325,7 @@ def run_ours(args, rank, world):
         step_ms = [a.elapsed_time(b) for a, b in evs]
         stages = plan.stage_times()
         plan.set_timing(False)
-        tot_ms = sum(step_ms)
-        if world > 1:
-            tt = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            tot_ms = float(tt.item())
+        tot_ms = max_over_ranks(sum(step_ms), world, dev)
         results[name] = {"samples_per_step": samples_per_step, "step_ms": step_ms, "tot_ms": tot_ms,
                          "wall_s": wall, "launches": launches, "stages": stages,
                          "clocks": clocks.summary() if clocks else None, "info": info}
@@ -332,8 +345,8 @@ def run_ours(args, rank, world):
     peaks, peak_kind = measured_peaks()
     G = w.problem.G
     mx, f64 = results["mixed"], results["fp64"]
-    value = world * mx["samples_per_step"] * args.steps / (mx["tot_ms"] / 1e3)
-    value64 = world * f64["samples_per_step"] * args.steps / (f64["tot_ms"] / 1e3)
+    value = whole_job_rate(world, mx["samples_per_step"] * args.steps, mx["tot_ms"])
+    value64 = whole_job_rate(world, f64["samples_per_step"] * args.steps, f64["tot_ms"])
 
     d_, E_ = w.problem.d, 2 * (w.problem.n + 1) ** 2
     P_ = (w.problem.n + 15) // 16 * 16
@@ -423,8 +436,6 @@ def run_ours(args, rank, world):
 
 
 def e2e_measure(plan, t, steps, barrier, world, dev):
-    import torch
-    import torch.distributed as dist
     times, samples, h2d, d2h = [], [], [], []
     plan.rewind(t - 1)
     plan.increment()                              # warm
@@ -437,12 +448,8 @@ def e2e_measure(plan, t, steps, barrier, world, dev):
         samples.append(info["samples"])
         h2d.append(info["h2d_bytes"])
         d2h.append(info["d2h_bytes"])
-    tot = sum(times)
-    if world > 1:
-        tt = torch.tensor([tot], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot = float(tt.item())
-    return {"value": world * sum(samples) / tot, "unit": UNIT, "h2d_bytes_per_step": int(np.mean(h2d)),
+    tot = max_over_ranks(sum(times), world, dev)
+    return {"value": whole_job_rate(world, sum(samples), 1e3 * tot), "unit": UNIT, "h2d_bytes_per_step": int(np.mean(h2d)),
             "d2h_bytes_per_step": int(np.mean(d2h)), "steps": steps,
             "ms_per_step": 1e3 * tot / steps,
             "latency_ms": {"p50": 1e3 * percentile(times, 50), "p99": 1e3 * percentile(times, 99)},
