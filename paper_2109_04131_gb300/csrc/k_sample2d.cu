@@ -428,7 +428,7 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
     const double h = 1.0 / (double)(n + 1);
     a.rhs = h * h * f;
     a.tol = cg.tol;
-    a.tol_inner = cg.precision == USFFT_MIXED ? 1e-5 : 1e-4;
+    a.tol_inner = cg.precision == USFFT_MIXED ? 5e-5 : 1e-4;
     a.psi = psi;
     a.i0 = i0;
     a.count = count;

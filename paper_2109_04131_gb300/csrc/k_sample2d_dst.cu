@@ -6,14 +6,16 @@
 //   x = 0, r = b;  repeat:  solve K d = r / ||r|| in fp32 to tol_inner,
 //                           x += ||r|| d (fp64),  r = b - K x with fp64 weights,
 //   until ||r|| <= tol ||b||.
-// Preconditioner: the inverse of the constant-coefficient operator K_0 (w_e = 1), applied
-// exactly through its eigenbasis, the 2-D sine transform (DST-I):
+// Preconditioner: the inverse of the constant-coefficient operator K_0 (w_e = 1) between two
+// symmetric diagonal scalings, D^-1/2 K_0^-1 D^-1/2 with D = diag(K) / diag(K_0); K_0^-1 is
+// applied exactly through its eigenbasis, the 2-D sine transform (DST-I):
 //   K_0^-1 r = c^2 S ((S R S) o L) S,  S_jk = sin(pi (j+1)(k+1)/(n+1)),  c = 2/(n+1),
 //   L_qp = 1 / (mu_p + mu_q),  mu_k = 2 - 2 cos(pi (k+1)/(n+1)),
-// with R the residual on the n x n grid.  Because every edge weight lies in
-// [min_e w_e, max_e w_e], the preconditioned operator has condition number at most
-// max w / min w, independent of the mesh width, so a handful of iterations reduce the
-// residual by 1e-5 (Jacobi-PCG needs hundreds).  The four n x n matrix products run on
+// with R the residual on the n x n grid.  Without the scaling the preconditioned operator has
+// condition number at most max w / min w (every edge weight lies in [min w, max w]),
+// independent of the mesh width; the scaling removes the pointwise size of the coefficient
+// and leaves its variation, so a handful of iterations reduce the residual by 1e-5
+// (Jacobi-PCG needs hundreds).  The four n x n matrix products run on
 // the tensor cores (mma.sync m16n8k16, BF16 operands in shared memory, fp32
 // accumulation); the rounded preconditioner is slightly non-symmetric, which the
 // flexible (Polak-Ribiere) beta tolerates -- only the convergence rate depends on it, the
@@ -31,7 +33,7 @@ namespace usfft {
 
 struct DstLayout {
     int n, W, P, LD, J1, JA;
-    size_t o_xh, o_S, o_L, o_Ta, o_Tb, o_wx, o_wy, o_ph, o_sj, o_r64, o_r32, o_A, o_Tr, o_md, total;
+    size_t o_xh, o_S, o_L, o_Ta, o_Tb, o_wx, o_wy, o_ph, o_sc, o_sj, o_r64, o_r32, o_A, o_Tr, o_md, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -51,6 +53,7 @@ __host__ __device__ inline DstLayout dst_layout(int n, int d) {
     L.o_wx = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
     L.o_wy = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
     L.o_ph = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
+    L.o_sc = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
     L.o_sj = o;  o = align16(o + sizeof(double) * (size_t)d);
     L.o_r64 = o; o = align16(o + sizeof(double) * 36);
     L.o_r32 = o; o = align16(o + sizeof(float) * 4 * 36);
@@ -126,15 +129,17 @@ __device__ __forceinline__ void gemm_bf16(const bf16* __restrict__ A, const bf16
     }
 }
 
-// z = K_0^-1 r for the NPT nodes of this thread.  The transform grid X (rows q, columns p)
+// z = D^-1/2 K_0^-1 D^-1/2 r for the NPT nodes of this thread (sc = D^-1/2 in the halo layout,
+// D = diag(K) / 4).  The transform grid X (rows q, columns p)
 // is kept transposed in Ta (Ta[p][q]), the layout the B operand wants; nid[k] >> 16 = p LD + q
 // of the node (nid[k] = -1: no node).  S is symmetric, so it serves as A and as transposed B.
 template <int NPT>
 __device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[NPT], const int (&nid)[NPT],
-                                              bf16* Ta, bf16* Tb, const bf16* S, const float* Li, int P, int LD) {
+                                              const float* sc, bf16* Ta, bf16* Tb, const bf16* S,
+                                              const float* Li, int P, int LD) {
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
-        if (nid[k] >= 0) Ta[nid[k] >> 16] = __float2bfloat16_rn(r[k]);
+        if (nid[k] >= 0) Ta[nid[k] >> 16] = __float2bfloat16_rn(sc[nid[k] & 0xffff] * r[k]);
     __syncthreads();
     gemm_bf16<false, false>(S, Ta, Tb, nullptr, P, LD);     // Tb = S X
     __syncthreads();
@@ -145,7 +150,8 @@ __device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[
     gemm_bf16<true, false>(Tb, S, Ta, nullptr, P, LD);      // Ta = Z^T
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) z[k] = (nid[k] >= 0) ? __bfloat162float(Ta[nid[k] >> 16]) : 0.f;
+    for (int k = 0; k < NPT; ++k)
+        z[k] = (nid[k] >= 0) ? sc[nid[k] & 0xffff] * __bfloat162float(Ta[nid[k] >> 16]) : 0.f;
 }
 
 // three block sums in one pass; thread 0 also forms ratio = (s0 - s1) / den
@@ -213,6 +219,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
     float* wl = reinterpret_cast<float*>(smraw + Lo.o_wx);   // weight of the edge to the left of halo node h (x - h)
     float* wd = reinterpret_cast<float*>(smraw + Lo.o_wy);   // weight of the edge below halo node h (y - h)
     float* ph = reinterpret_cast<float*>(smraw + Lo.o_ph);
+    float* scs = reinterpret_cast<float*>(smraw + Lo.o_sc);   // preconditioner scaling, halo layout
     double* sj = reinterpret_cast<double*>(smraw + Lo.o_sj);
     double* red64 = reinterpret_cast<double*>(smraw + Lo.o_r64);
     float* red32 = reinterpret_cast<float*>(smraw + Lo.o_r32);
@@ -284,6 +291,8 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
     const double rr0 = (double)G * b * b;
     const double stop = a.tol * a.tol * rr0;
     const double nr0 = sqrt(rr0);
+    const float nstop = (float)(a.tol * nr0);        // sqrt(stop)
+    const float tol_in = (float)a.tol_inner;
     __syncthreads();
 
     for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
@@ -329,12 +338,15 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
             }
         }
         __syncthreads();
-        // fp64 diagonal of every node (sum of its four edge weights) for the refinement residual
+        // fp64 diagonal of every node (sum of its four edge weights) for the refinement residual;
+        // the symmetric diagonal scaling of the preconditioner, sc = (diag / 4)^-1/2
 #pragma unroll
         for (int k = 0; k < NPT; ++k) {
             if (nid[k] >= 0) {
                 const int h = nid[k] & 0xffff;
-                d64[h] = (w64l[h] + w64l[h + W]) + (w64d[h] + w64d[h + 1]);
+                const double dg = (w64l[h] + w64l[h + W]) + (w64d[h] + w64d[h + 1]);
+                d64[h] = dg;
+                scs[h] = rsqrtf(0.25f * (float)dg);
             }
         }
         __syncthreads();
@@ -360,7 +372,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                 r32[k] = (float)r64[k] * inv;
                 rl = fmaf(r32[k], r32[k], rl);
             }
-            apply_precond<NPT>(r32, z32, nid, Ta, Tb, S, Li, P, LD);
+            apply_precond<NPT>(r32, z32, nid, scs, Ta, Tb, S, Li, P, LD);
             float rz_l = 0.f;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
@@ -370,7 +382,11 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
             }
             float rz, rr, unused;
             block_sum3(rz_l, 0.f, rl, 1.f, red32, rz, rr, unused);
-            const float istop = (float)(a.tol_inner * a.tol_inner) * rr;
+            // inner target: tol_inner, or less when this step only has to close the remaining
+            // gap to the outer tolerance (0.3 x the reduction still missing)
+            const float gap = 0.3f * nstop / (float)nr;
+            const float tin = gap > tol_in ? gap : tol_in;
+            const float istop = tin * tin * rr;
             int it = 0;
             while (rr > istop && it < a.max_iters) {
                 float pq_l = 0.f;
@@ -399,7 +415,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                     r32[k] = fmaf(-alpha, q32[k], r32[k]);
                     rn_l = fmaf(r32[k], r32[k], rn_l);
                 }
-                apply_precond<NPT>(r32, z32, nid, Ta, Tb, S, Li, P, LD);
+                apply_precond<NPT>(r32, z32, nid, scs, Ta, Tb, S, Li, P, LD);
                 float zr_l = 0.f, zro_l = 0.f;
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
