@@ -85,9 +85,9 @@ typedef __nv_bfloat16 bf16;
 // mma.m16n8k16 (BF16): a0 (g, 2t..2t+1) a1 (g+8, 2t..) a2 (g, 2t+8..) a3 (g+8, 2t+8..);
 // b0 (k = 2t..2t+1, n = g) b1 (k = 2t+8.., n = g); c0 (g, 2t) c1 (g, 2t+1) c2 (g+8, 2t)
 // c3 (g+8, 2t+1); g = lane/4, t = lane%4.  Each warp takes 16x8 output tiles.
-template <bool TRANSPOSE_OUT, bool SCALE>
+template <int P, bool TRANSPOSE_OUT, bool SCALE>
 __device__ __forceinline__ void gemm_bf16(const bf16* __restrict__ A, const bf16* __restrict__ Bt,
-                                          bf16* __restrict__ C, const float* __restrict__ Lsc, int P, int LD) {
+                                          bf16* __restrict__ C, const float* __restrict__ Lsc, int LD) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int nt = P / 8, tiles = (P / 16) * nt;
@@ -97,6 +97,7 @@ __device__ __forceinline__ void gemm_bf16(const bf16* __restrict__ A, const bf16
         const bf16* Ar0 = A + (m0 + g) * LD + 2 * t;
         const bf16* Ar1 = Ar0 + 8 * LD;
         const bf16* Br = Bt + (n0 + g) * LD + 2 * t;
+#pragma unroll
         for (int k0 = 0; k0 < P; k0 += 16) {
             const uint32_t a0 = *reinterpret_cast<const uint32_t*>(Ar0 + k0);
             const uint32_t a1 = *reinterpret_cast<const uint32_t*>(Ar1 + k0);
@@ -133,21 +134,21 @@ __device__ __forceinline__ void gemm_bf16(const bf16* __restrict__ A, const bf16
 // D = diag(K) / 4).  The transform grid X (rows q, columns p)
 // is kept transposed in Ta (Ta[p][q]), the layout the B operand wants; nid[k] >> 16 = p LD + q
 // of the node (nid[k] = -1: no node).  S is symmetric, so it serves as A and as transposed B.
-template <int NPT>
+template <int NPT, int P>
 __device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[NPT], const int (&nid)[NPT],
                                               const float* sc, bf16* Ta, bf16* Tb, const bf16* S,
-                                              const float* Li, int P, int LD) {
+                                              const float* Li, int LD) {
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
         if (nid[k] >= 0) Ta[nid[k] >> 16] = __float2bfloat16_rn(sc[nid[k] & 0xffff] * r[k]);
     __syncthreads();
-    gemm_bf16<false, false>(S, Ta, Tb, nullptr, P, LD);     // Tb = S X
+    gemm_bf16<P, false, false>(S, Ta, Tb, nullptr, LD);     // Tb = S X
     __syncthreads();
-    gemm_bf16<true, true>(Tb, S, Ta, Li, P, LD);            // Ta = ((S X S) o L)^T
+    gemm_bf16<P, true, true>(Tb, S, Ta, Li, LD);            // Ta = ((S X S) o L)^T
     __syncthreads();
-    gemm_bf16<false, false>(S, Ta, Tb, nullptr, P, LD);     // Tb = S ((S X S) o L)
+    gemm_bf16<P, false, false>(S, Ta, Tb, nullptr, LD);     // Tb = S ((S X S) o L)
     __syncthreads();
-    gemm_bf16<true, false>(Tb, S, Ta, nullptr, P, LD);      // Ta = Z^T
+    gemm_bf16<P, true, false>(Tb, S, Ta, nullptr, LD);      // Ta = Z^T
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
@@ -205,12 +206,14 @@ __device__ __forceinline__ void block_sum_sqrt(double v, double* buf, double& su
     root = buf[33];
 }
 
-template <int NPT>
+// P = the transform size, n rounded up to a multiple of 16 (a compile-time constant, so the
+// k-loop of the fragment loads and mma unrolls)
+template <int NPT, int P>
 __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_constant__ Pcg2dArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int n = a.n, G = n * n, n1 = n + 1;
     const DstLayout Lo = dst_layout(n, a.ns.d);
-    const int W = Lo.W, P = Lo.P, LD = Lo.LD;
+    const int W = Lo.W, LD = Lo.LD;
     double* xh = reinterpret_cast<double*>(smraw + Lo.o_xh);
     bf16* S = reinterpret_cast<bf16*>(smraw + Lo.o_S);
     float* Li = reinterpret_cast<float*>(smraw + Lo.o_L);
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                 r32[k] = (float)r64[k] * inv;
                 rl = fmaf(r32[k], r32[k], rl);
             }
-            apply_precond<NPT>(r32, z32, nid, scs, Ta, Tb, S, Li, P, LD);
+            apply_precond<NPT, P>(r32, z32, nid, scs, Ta, Tb, S, Li, LD);
             float rz_l = 0.f;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
                     r32[k] = fmaf(-alpha, q32[k], r32[k]);
                     rn_l = fmaf(r32[k], r32[k], rn_l);
                 }
-                apply_precond<NPT>(r32, z32, nid, scs, Ta, Tb, S, Li, P, LD);
+                apply_precond<NPT, P>(r32, z32, nid, scs, Ta, Tb, S, Li, LD);
                 float zr_l = 0.f, zro_l = 0.f;
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
@@ -472,13 +475,30 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_cons
 
 size_t dst_smem_bytes(int n, int d) { return dst_layout(n, d).total; }
 
+// the kernel instance for (NPT, P = n rounded up to 16); nullptr for a pair no n produces
+template <int NPT>
+static void (*dst_kernel_for(int n))(Pcg2dArgs) {
+    const int P = (n + 15) / 16 * 16;
+    if (NPT == 1) {
+        if (P == 16) return pcg2d_mixed_dst_kernel<1, 16>;
+        if (P == 32) return pcg2d_mixed_dst_kernel<1, 32>;
+    } else if (NPT == 2) {
+        if (P == 48) return pcg2d_mixed_dst_kernel<2, 48>;
+    } else if (NPT == 4) {
+        if (P == 48) return pcg2d_mixed_dst_kernel<4, 48>;
+        if (P == 64) return pcg2d_mixed_dst_kernel<4, 64>;
+    }
+    return nullptr;
+}
+
 template <int NPT>
 cudaError_t launch_dst_npt(const Pcg2dArgs& a, int blocks, int threads, cudaStream_t s) {
     const size_t smem = dst_smem_bytes(a.n, a.ns.d);
-    cudaError_t e = cudaFuncSetAttribute(pcg2d_mixed_dst_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    void (*k)(Pcg2dArgs) = dst_kernel_for<NPT>(a.n);
+    if (!k) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    pcg2d_mixed_dst_kernel<NPT><<<blocks, threads, smem, s>>>(a);
+    k<<<blocks, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -486,10 +506,10 @@ template <int NPT>
 int dst_resident_blocks(int threads, int d, int n) {
     const size_t smem = dst_smem_bytes(n, d);
     int per_sm = 0;
-    cudaError_t e = cudaFuncSetAttribute(pcg2d_mixed_dst_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg2d_mixed_dst_kernel<NPT>,
-                                                                            threads, smem);
+    void (*k)(Pcg2dArgs) = dst_kernel_for<NPT>(n);
+    cudaError_t e = k ? cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                      : cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         per_sm = 1;
