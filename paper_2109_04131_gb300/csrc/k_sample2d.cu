@@ -337,9 +337,12 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_kernel(const __grid_constant
 }
 
 // smallest nodes-per-thread count that fits the system into one CTA of <= 1024 threads
-static int pick_npt(int G) {
+// nodes per thread: the smallest power of two with at most 1024 threads per CTA (512 for the
+// MIXED kernel, whose per-thread state then gets up to 128 registers)
+static int pick_npt(int G, int precision) {
+    const int max_threads = precision == USFFT_MIXED ? 512 : 1024;
     int npt = 1;
-    while ((G + npt - 1) / npt > 1024) npt *= 2;
+    while ((G + npt - 1) / npt > max_threads) npt *= 2;
     return npt;
 }
 
@@ -373,7 +376,7 @@ static int resident_blocks(int precision, int threads, int n) {
 // persistent grid: one wave of resident CTAs on every SM
 int sample_2d_default_blocks(int n, int precision) {
     const int G = n * n;
-    const int npt = pick_npt(G);
+    const int npt = pick_npt(G, precision);
     const int threads = ((G + npt - 1) / npt + 31) / 32 * 32;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -385,7 +388,8 @@ int sample_2d_default_blocks(int n, int precision) {
     switch (npt) {
         case 1: per_sm = resident_blocks<1>(precision, threads, n); break;
         case 2: per_sm = resident_blocks<2>(precision, threads, n); break;
-        default: per_sm = resident_blocks<4>(precision, threads, n); break;
+        case 4: per_sm = resident_blocks<4>(precision, threads, n); break;
+        default: per_sm = dst_resident_blocks<8>(threads, USFFT_MAX_D, n); break;   // MIXED only
     }
     return sms * per_sm;
 }
@@ -441,7 +445,7 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
     a.coef_scale = cg.coef_scale;
     a.coef_decay = cg.coef_decay;
     const int G = n * n;
-    const int npt = pick_npt(G);
+    const int npt = pick_npt(G, cg.precision);
     const int threads = ((G + npt - 1) / npt + 31) / 32 * 32;
     int blocks = cg.blocks > 0 ? cg.blocks : sample_2d_default_blocks(n, cg.precision);
     if (blocks > count) blocks = (int)count;
@@ -451,7 +455,8 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
     switch (npt) {
         case 1: e = launch_npt<1>(a, cg.precision, blocks, threads, s); break;
         case 2: e = launch_npt<2>(a, cg.precision, blocks, threads, s); break;
-        default: e = launch_npt<4>(a, cg.precision, blocks, threads, s); break;
+        case 4: e = launch_npt<4>(a, cg.precision, blocks, threads, s); break;
+        default: e = launch_dst_npt<8>(a, blocks, threads, s); break;                 // MIXED only
     }
     if (launches) ++*launches;
     return e;

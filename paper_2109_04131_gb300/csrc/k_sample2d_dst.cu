@@ -84,48 +84,62 @@ typedef __nv_bfloat16 bf16;
 // elementwise by Lsc (fp32, symmetric, stride LD) if SCALE.  Fragment layouts of
 // mma.m16n8k16 (BF16): a0 (g, 2t..2t+1) a1 (g+8, 2t..) a2 (g, 2t+8..) a3 (g+8, 2t+8..);
 // b0 (k = 2t..2t+1, n = g) b1 (k = 2t+8.., n = g); c0 (g, 2t) c1 (g, 2t+1) c2 (g+8, 2t)
-// c3 (g+8, 2t+1); g = lane/4, t = lane%4.  Each warp takes 16x8 output tiles.
+// c3 (g+8, 2t+1); g = lane/4, t = lane%4.  Each warp takes 16x16 output tiles.
 template <int P, bool TRANSPOSE_OUT, bool SCALE>
 __device__ __forceinline__ void gemm_bf16(const bf16* __restrict__ A, const bf16* __restrict__ Bt,
                                           bf16* __restrict__ C, const float* __restrict__ Lsc, int LD) {
+    // warp tiles of 16 x 16 (two mma n-tiles sharing the A fragment): half the fragment bytes
+    // read from shared memory per output of 16 x 8 tiles, the bound of this small GEMM
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int nt = P / 8, tiles = (P / 16) * nt;
-    for (int tile = warp; tile < tiles; tile += nwarps) {
-        const int m0 = (tile / nt) * 16, n0 = (tile % nt) * 8;
-        float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+    constexpr int NT = P / 16, TILES = (P / 16) * NT;
+    for (int tile = warp; tile < TILES; tile += nwarps) {
+        const int m0 = (tile / NT) * 16, n0 = (tile % NT) * 16;
+        float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
         const bf16* Ar0 = A + (m0 + g) * LD + 2 * t;
         const bf16* Ar1 = Ar0 + 8 * LD;
-        const bf16* Br = Bt + (n0 + g) * LD + 2 * t;
+        const bf16* Br0 = Bt + (n0 + g) * LD + 2 * t;
+        const bf16* Br1 = Br0 + 8 * LD;
 #pragma unroll
         for (int k0 = 0; k0 < P; k0 += 16) {
             const uint32_t a0 = *reinterpret_cast<const uint32_t*>(Ar0 + k0);
             const uint32_t a1 = *reinterpret_cast<const uint32_t*>(Ar1 + k0);
             const uint32_t a2 = *reinterpret_cast<const uint32_t*>(Ar0 + k0 + 8);
             const uint32_t a3 = *reinterpret_cast<const uint32_t*>(Ar1 + k0 + 8);
-            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(Br + k0);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(Br + k0 + 8);
+            const uint32_t b00 = *reinterpret_cast<const uint32_t*>(Br0 + k0);
+            const uint32_t b01 = *reinterpret_cast<const uint32_t*>(Br0 + k0 + 8);
+            const uint32_t b10 = *reinterpret_cast<const uint32_t*>(Br1 + k0);
+            const uint32_t b11 = *reinterpret_cast<const uint32_t*>(Br1 + k0 + 8);
             asm volatile(
                 "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
-                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+                : "+f"(c[0][0]), "+f"(c[0][1]), "+f"(c[0][2]), "+f"(c[0][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b00), "r"(b01));
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                : "+f"(c[1][0]), "+f"(c[1][1]), "+f"(c[1][2]), "+f"(c[1][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b10), "r"(b11));
         }
-        const int row0 = m0 + g, row1 = m0 + g + 8, col0 = n0 + 2 * t, col1 = col0 + 1;
-        if (SCALE) {
-            c0 *= Lsc[row0 * LD + col0];
-            c1 *= Lsc[row0 * LD + col1];
-            c2 *= Lsc[row1 * LD + col0];
-            c3 *= Lsc[row1 * LD + col1];
-        }
-        if (TRANSPOSE_OUT) {
-            C[col0 * LD + row0] = __float2bfloat16_rn(c0);
-            C[col1 * LD + row0] = __float2bfloat16_rn(c1);
-            C[col0 * LD + row1] = __float2bfloat16_rn(c2);
-            C[col1 * LD + row1] = __float2bfloat16_rn(c3);
-        } else {
-            *reinterpret_cast<__nv_bfloat162*>(C + row0 * LD + col0) = __floats2bfloat162_rn(c0, c1);
-            *reinterpret_cast<__nv_bfloat162*>(C + row1 * LD + col0) = __floats2bfloat162_rn(c2, c3);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int row0 = m0 + g, row1 = m0 + g + 8, col0 = n0 + 8 * h + 2 * t, col1 = col0 + 1;
+            float c0 = c[h][0], c1 = c[h][1], c2 = c[h][2], c3 = c[h][3];
+            if (SCALE) {
+                c0 *= Lsc[row0 * LD + col0];
+                c1 *= Lsc[row0 * LD + col1];
+                c2 *= Lsc[row1 * LD + col0];
+                c3 *= Lsc[row1 * LD + col1];
+            }
+            if (TRANSPOSE_OUT) {
+                C[col0 * LD + row0] = __float2bfloat16_rn(c0);
+                C[col1 * LD + row0] = __float2bfloat16_rn(c1);
+                C[col0 * LD + row1] = __float2bfloat16_rn(c2);
+                C[col1 * LD + row1] = __float2bfloat16_rn(c3);
+            } else {
+                *reinterpret_cast<__nv_bfloat162*>(C + row0 * LD + col0) = __floats2bfloat162_rn(c0, c1);
+                *reinterpret_cast<__nv_bfloat162*>(C + row1 * LD + col0) = __floats2bfloat162_rn(c2, c3);
+            }
         }
     }
 }
@@ -209,7 +223,7 @@ __device__ __forceinline__ void block_sum_sqrt(double v, double* buf, double& su
 // P = the transform size, n rounded up to a multiple of 16 (a compile-time constant, so the
 // k-loop of the fragment loads and mma unrolls)
 template <int NPT, int P>
-__global__ void __launch_bounds__(1024) pcg2d_mixed_dst_kernel(const __grid_constant__ Pcg2dArgs a) {
+__global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_constant__ Pcg2dArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int n = a.n, G = n * n, n1 = n + 1;
     const DstLayout Lo = dst_layout(n, a.ns.d);
@@ -483,10 +497,12 @@ static void (*dst_kernel_for(int n))(Pcg2dArgs) {
         if (P == 16) return pcg2d_mixed_dst_kernel<1, 16>;
         if (P == 32) return pcg2d_mixed_dst_kernel<1, 32>;
     } else if (NPT == 2) {
-        if (P == 48) return pcg2d_mixed_dst_kernel<2, 48>;
+        if (P == 32) return pcg2d_mixed_dst_kernel<2, 32>;
     } else if (NPT == 4) {
         if (P == 48) return pcg2d_mixed_dst_kernel<4, 48>;
-        if (P == 64) return pcg2d_mixed_dst_kernel<4, 64>;
+    } else if (NPT == 8) {
+        if (P == 48) return pcg2d_mixed_dst_kernel<8, 48>;
+        if (P == 64) return pcg2d_mixed_dst_kernel<8, 64>;
     }
     return nullptr;
 }
@@ -520,8 +536,10 @@ int dst_resident_blocks(int threads, int d, int n) {
 template cudaError_t launch_dst_npt<1>(const Pcg2dArgs&, int, int, cudaStream_t);
 template cudaError_t launch_dst_npt<2>(const Pcg2dArgs&, int, int, cudaStream_t);
 template cudaError_t launch_dst_npt<4>(const Pcg2dArgs&, int, int, cudaStream_t);
+template cudaError_t launch_dst_npt<8>(const Pcg2dArgs&, int, int, cudaStream_t);
 template int dst_resident_blocks<1>(int, int, int);
 template int dst_resident_blocks<2>(int, int, int);
 template int dst_resident_blocks<4>(int, int, int);
+template int dst_resident_blocks<8>(int, int, int);
 
 }  // namespace usfft
