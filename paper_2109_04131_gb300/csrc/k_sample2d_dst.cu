@@ -33,7 +33,7 @@ namespace usfft {
 
 struct DstLayout {
     int n, W, P, LD, J1, JA;
-    size_t o_xh, o_S, o_L, o_Ta, o_Tb, o_wx, o_wy, o_ph, o_sc, o_sj, o_r64, o_r32, o_A, o_Tr, o_md, total;
+    size_t o_xh, o_S, o_L, o_Ta, o_Tb, o_wx, o_wy, o_ph, o_sc, o_sj, o_r64, o_r32, o_A, o_AF, o_Tr, o_md, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -68,13 +68,39 @@ __host__ __device__ inline DstLayout dst_layout(int n, int d) {
         if (j2 > L.JA) L.JA = j2;
     }
     L.o_A = o;   o = align16(o + sizeof(double) * (size_t)L.JA * 2 * (n + 1));   // sin(j pi (P + o/3) h)
-    L.o_Tr = o;  o = align16(o + sizeof(double) * (size_t)L.J1 * 2 * (n + 1));   // per-row partial sums
+    L.o_AF = o;  o = align16(o + sizeof(float2) * (size_t)L.JA * 2 * (n + 1));   // the same as double-float
+    L.o_Tr = o;  o = align16(o + sizeof(float2) * (size_t)L.J1 * 2 * (n + 1));   // per-row partial sums (double-float)
     L.o_md = o;  o = align16(o + sizeof(double) * (size_t)d + sizeof(int) * 2 * (size_t)d);   // amplitudes, modes
     L.total = o;
     return L;
 }
 
 typedef __nv_bfloat16 bf16;
+
+// Double-float arithmetic (a value is hi + lo with |lo| <= ulp(hi)/2, about 48 significant
+// bits) from the error-free transformations of Knuth (TwoSum) and Dekker (the exact product,
+// here with fmaf): the coefficient assembly runs on the FP32 pipe at a precision far below
+// the 1e-10 bar instead of on the 64x slower FP64 pipe.  Every operation is explicitly
+// rounded (__fadd_rn, __fmul_rn) so that no contraction changes the transformations.
+__device__ __forceinline__ float2 df_split(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {          // a + b
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fadd_rn(s, -a.x);
+    const float e = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(s, -bb)), __fadd_rn(b.x, -bb));
+    const float t = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    const float h = __fadd_rn(s, t);
+    return make_float2(h, __fadd_rn(t, -__fadd_rn(h, -s)));
+}
+__device__ __forceinline__ float2 df_fma(float2 acc, float2 a, float2 b) {   // acc + a b
+    const float p = __fmul_rn(a.x, b.x);
+    float pe = __fmaf_rn(a.x, b.x, -p);
+    pe = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, pe));
+    return df_add(acc, make_float2(p, pe));
+}
+__device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
 
 // C = A B on the tensor cores (P x P, row stride LD elements, P a multiple of 16), BF16
 // operands, fp32 accumulation.  A is stored row-major; B is stored TRANSPOSED
@@ -241,7 +267,8 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
     double* red64 = reinterpret_cast<double*>(smraw + Lo.o_r64);
     float* red32 = reinterpret_cast<float*>(smraw + Lo.o_r32);
     double* At = reinterpret_cast<double*>(smraw + Lo.o_A);     // At[(j-1)][o-1][P] = sin(j pi (P + o/3) h)
-    double* Tr = reinterpret_cast<double*>(smraw + Lo.o_Tr);    // Tr[(j1-1)][o-1][Q]
+    float2* AtF = reinterpret_cast<float2*>(smraw + Lo.o_AF);   // At as double-float
+    float2* Tr = reinterpret_cast<float2*>(smraw + Lo.o_Tr);    // Tr[(j1-1)][o-1][Q], double-float
     double* amp = reinterpret_cast<double*>(smraw + Lo.o_md);   // c j^-mu
     int* mj1 = reinterpret_cast<int*>(amp + a.ns.d);
     int* mj2 = mj1 + a.ns.d;
@@ -295,6 +322,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
         for (int e = tid; e < JA * 2 * n1; e += T) {
             const int jj = e / (2 * n1) + 1, o = (e / n1) % 2 + 1, Pp = e % n1;
             At[e] = sinpi((double)jj * (((double)Pp + (double)o / 3.0) * hh));
+            AtF[e] = df_split(At[e]);
         }
         for (int j = tid; j < a.ns.d; j += T) {
             int j1, j2;
@@ -325,33 +353,38 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
             double acc = 0.0;
             for (int j = 0; j < d; ++j)
                 if (mj1[j] == j1) acc = fma(amp[j] * sj[j], At[((mj2[j] - 1) * 2 + o) * n1 + Q], acc);
-            Tr[e] = acc;
+            Tr[e] = df_split(acc);
         }
         __syncthreads();
-        double* low = xh;                       // lower-triangle coefficients (temporary)
+        // triangle coefficients a = 1 + sum_j1 At Tr (affine) or exp(sum_j1 At Tr) (lognormal):
+        // the rank-J1 sums in double-float, the exponential in fp64
+        const float2 one = make_float2(1.f, 0.f);
+        float2* low = reinterpret_cast<float2*>(xh);   // lower-triangle coefficients (temporary)
         for (int e = tid; e < sq; e += T) {
             const int Pp = e % n1, Q = e / n1;
-            double acc = 0.0;
-            for (int j1 = 0; j1 < J1; ++j1) acc = fma(At[(j1 * 2 + 1) * n1 + Pp], Tr[(j1 * 2 + 0) * n1 + Q], acc);
-            low[e] = logn ? exp(acc) : 1.0 + acc;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 1) * n1 + Pp], Tr[(j1 * 2 + 0) * n1 + Q]);
+            low[e] = logn ? df_split(exp(df_to_double(acc))) : df_add(one, acc);
         }
         __syncthreads();
         for (int e = tid; e < sq; e += T) {
             const int Pp = e % n1, Q = e / n1;
-            double acc = 0.0;
-            for (int j1 = 0; j1 < J1; ++j1) acc = fma(At[(j1 * 2 + 0) * n1 + Pp], Tr[(j1 * 2 + 1) * n1 + Q], acc);
-            const double au = logn ? exp(acc) : 1.0 + acc;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 0) * n1 + Pp], Tr[(j1 * 2 + 1) * n1 + Q]);
+            const float2 au = logn ? df_split(exp(df_to_double(acc))) : df_add(one, acc);
             if (Q < n) {            // edge (Pp,Q+1)-(Pp+1,Q+1): left of node (Pp+1,Q+1)
-                const double w = 0.5 * (low[(Q + 1) * n1 + Pp] + au);
+                float2 w = df_add(low[(Q + 1) * n1 + Pp], au);
+                w = make_float2(0.5f * w.x, 0.5f * w.y);              // exact
                 const int h = (Pp + 1) * W + Q + 1;
-                w64l[h] = w;
-                wl[h] = (float)w;
+                w64l[h] = df_to_double(w);
+                wl[h] = w.x;
             }
             if (Pp >= 1) {          // edge (Pp,Q)-(Pp,Q+1): below node (Pp,Q+1)
-                const double w = 0.5 * (au + low[Q * n1 + (Pp - 1)]);
+                float2 w = df_add(au, low[Q * n1 + (Pp - 1)]);
+                w = make_float2(0.5f * w.x, 0.5f * w.y);
                 const int h = Pp * W + Q + 1;
-                w64d[h] = w;
-                wd[h] = (float)w;
+                w64d[h] = df_to_double(w);
+                wd[h] = w.x;
             }
         }
         __syncthreads();
