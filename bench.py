@@ -400,7 +400,7 @@ def run_ours(args, rank, world):
         ach = algo / dur / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": profiled_traffic("fft"),
-                "kernel": "fft_pass1_kernel + fft_final_kernel (one iteration)",
+                "kernel": "fft_pass1_kernel<DF> + fft_final_kernel<DF> (double-float arithmetic, one iteration)",
                 "bytes_per_launch": algo, "ms_per_launch": dur * 1e3,
                 "peak_note": f"{peak_kind} hbm_gbs (burst)"}
 

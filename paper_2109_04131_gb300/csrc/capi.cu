@@ -284,6 +284,10 @@ struct StageTimer {
     }
 };
 
+// the MIXED precision mode runs the lattice FFT in double-float arithmetic (16 bytes per complex
+// value either way, so the twiddle and scratch buffers serve both)
+bool fft_df(const usfft_plan_t* plan) { return plan->par.precision == USFFT_MIXED; }
+
 // sampler dispatch: out[0..M)[G] for the node set (out = the plan's sample buffer by default)
 usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns, double* out = nullptr) {
     const int kind = plan->prob.kind;
@@ -355,7 +359,7 @@ usfft_status prepare_step(usfft_plan_t* plan, int64_t M, const std::vector<int64
     }
     // host vectors must outlive the asynchronous copies
     CK(cudaStreamSynchronize(plan->stream));
-    CK(launch_twiddles(M, (double2*)plan->twid.p, plan->stream, &plan->launches));
+    CK(launch_twiddles(M, plan->twid.p, fft_df(plan), plan->stream, &plan->launches));
     plan->M = M;
     plan->m = m;
     plan->nJ = nJ;
@@ -452,8 +456,8 @@ usfft_status prepare_rr(usfft_plan_t* plan, const std::vector<int8_t>& J, int64_
     plan->h2d += (int64_t)(sizeof(int) * (goff_h.size() + gk_h.size() + gm2_h.size() + src_h.size()));
     CK(cudaStreamSynchronize(plan->stream));   // host vectors outlive the copies
     for (size_t q = 0; q < plan->rr_M.size(); ++q)
-        CK(launch_twiddles(plan->rr_M[q], (double2*)plan->rr_twid.p + plan->rr_twid_at[q], plan->stream,
-                           &plan->launches));
+        CK(launch_twiddles(plan->rr_M[q], (double2*)plan->rr_twid.p + plan->rr_twid_at[q], fft_df(plan),
+                           plan->stream, &plan->launches));
     // the last lattice stands for the step in the single-lattice inspection calls
     plan->M = plan->rr_M.back();
     plan->z.assign(plan->rr_z.end() - t, plan->rr_z.end());
@@ -484,8 +488,8 @@ usfft_status run_rr_device(usfft_plan_t* plan) {
             GatherPlan gp{(const int*)plan->rr_goff.p + plan->rr_goff_at[q], (const int*)plan->rr_gk.p + plan->rr_gk_at[q],
                           (const int*)plan->rr_gm2.p + plan->rr_gk_at[q]};
             CK(launch_fft_gather(plan->rr_fp[q], G, (const double*)plan->U.p,
-                                 (const double2*)plan->rr_twid.p + plan->rr_twid_at[q], gp, nJ,
-                                 (double2*)plan->fftscr.p, (double2*)plan->rr_C.p + (size_t)l * G * nJ, plan->stream,
+                                 (const double2*)plan->rr_twid.p + plan->rr_twid_at[q], fft_df(plan), gp, nJ,
+                                 plan->fftscr.p, (double2*)plan->rr_C.p + (size_t)l * G * nJ, plan->stream,
                                  &plan->launches));
         }
         {
@@ -514,8 +518,8 @@ usfft_status run_step_device(usfft_plan_t* plan, bool first_1d_sets_theta) {
         if (st != USFFT_OK) return st;
         {
             StageTimer timer(plan, USFFT_STAGE_FFT);
-            CK(launch_fft_gather(plan->fp, plan->G, (const double*)plan->U.p, (const double2*)plan->twid.p, gp, nJ,
-                                 (double2*)plan->fftscr.p, (double2*)plan->C.p, plan->stream, &plan->launches));
+            CK(launch_fft_gather(plan->fp, plan->G, (const double*)plan->U.p, plan->twid.p, fft_df(plan), gp, nJ,
+                                 plan->fftscr.p, (double2*)plan->C.p, plan->stream, &plan->launches));
         }
         if (first_1d_sets_theta && it == 0 && !plan->theta_set) {
             // relative threshold: theta = delta * max_g |c_{g,0}| of the first 1-D detection

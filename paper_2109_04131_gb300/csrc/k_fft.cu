@@ -22,7 +22,14 @@
 // Each sub-transform of length L runs in shared memory as a mixed-radix Stockham autosort
 // FFT (radices 8, 4, 2, 3 in registers, every other prime factor by a direct length-R DFT
 // per output), ping-ponging between two buffers, with its twiddles W_L^j (L <= 1024) staged
-// in shared memory from the fp64 table W[j] = e^{-2 pi i j / M} (W_L^j = W[j M / L]).
+// in shared memory from the table W[j] = e^{-2 pi i j / M} (W_L^j = W[j M / L]).
+//
+// Arithmetic.  The kernels are templates over the complex arithmetic: fp64 (double2), or
+// double-float (float4 = re.hi, re.lo, im.hi, im.lo; every real value a pair of floats with
+// about 48 significant bits, from the error-free transformations TwoSum (Knuth) and the fma
+// product (Dekker)).  The double-float transform runs on the FP32 pipe, 64x the FP64 rate of
+// this part, at a rounding error of a few 1e-15 relative to the largest coefficient of a
+// node; both arithmetic kinds store 16 bytes per complex value.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -36,19 +43,30 @@ static const int kTileElems = 2048;   // L * (columns per CTA) complex elements 
 static const int kTwSmem = 1024;      // sub-transform twiddles staged in shared memory up to this L
 static const int kFftThreads = 256;
 
-__global__ void twiddle_kernel(int64_t M, double2* W) {
+// W[j] = e^{-2 pi i j / M} in fp64, or split into double-float (float4) when DFT_DF
+template <bool DFT_DF>
+__global__ void twiddle_kernel(int64_t M, void* Wv) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
         double sv, cv;
         sincospi(2.0 * (double)j / (double)M, &sv, &cv);
-        W[j] = make_double2(cv, -sv);
+        if (DFT_DF) {
+            const float ch = __double2float_rn(cv), sh = __double2float_rn(-sv);
+            reinterpret_cast<float4*>(Wv)[j] =
+                make_float4(ch, __double2float_rn(cv - (double)ch), sh, __double2float_rn(-sv - (double)sh));
+        } else {
+            reinterpret_cast<double2*>(Wv)[j] = make_double2(cv, -sv);
+        }
     }
 }
 
-cudaError_t launch_twiddles(int64_t M, double2* W, cudaStream_t s, int* launches) {
+cudaError_t launch_twiddles(int64_t M, void* W, bool df, cudaStream_t s, int* launches) {
     int64_t b = (M + 255) / 256;
     if (b > 4096) b = 4096;
     if (b < 1) b = 1;
-    twiddle_kernel<<<(unsigned)b, 256, 0, s>>>(M, W);
+    if (df)
+        twiddle_kernel<true><<<(unsigned)b, 256, 0, s>>>(M, W);
+    else
+        twiddle_kernel<false><<<(unsigned)b, 256, 0, s>>>(M, W);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
@@ -64,10 +82,10 @@ struct FftArgs {
     int64_t wstride;    // M / L
     // input rows: row(o, l) = o * in_outer + l * in_step  (o = i2, or the bucket m1)
     const double* Ur;   // real samples [M][G] (pass 1, or the single pass)
-    const double2* Yc;  // packed intermediate [M][Gp] (final pass of two)
+    const void* Yc;     // packed intermediate [M][Gp] (final pass of two), the arithmetic's complex type
     int64_t in_outer, in_step;
     // pass 1 output: Y row m1 * out_m + i2 * out_outer, times W[(i2 m1) mod M]
-    double2* Yo;
+    void* Yo;
     int64_t out_m, out_outer;
     // final pass: gather through the buckets
     const int* boff;
@@ -80,80 +98,167 @@ struct FftArgs {
     int radix[32];
 };
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 mul_mi(double2 a) { return make_double2(a.y, -a.x); }   // * (-i)
+// ---- complex arithmetic: fp64 -----------------------------------------------------------
+struct F64 {
+    typedef double2 C;
+    static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
+    static __device__ __forceinline__ C pair(double x, double y) { return make_double2(x, y); }
+    static __device__ __forceinline__ C add(C a, C b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ C sub(C a, C b) { return make_double2(a.x - b.x, a.y - b.y); }
+    static __device__ __forceinline__ C mul(C a, C b) {
+        return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+    }
+    static __device__ __forceinline__ C mul_mi(C a) { return make_double2(a.y, -a.x); }   // * (-i)
+    static __device__ __forceinline__ C mul_k(C a, double k) { return make_double2(a.x * k, a.y * k); }
+    static __device__ __forceinline__ C half(C a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
+    // (A + conj B) s and (A - conj B) s / i, the unpacked transforms of the two real columns
+    static __device__ __forceinline__ void unpack(C A, C B, double s, double2& even, double2& odd) {
+        even = make_double2((A.x + B.x) * s, (A.y - B.y) * s);
+        odd = make_double2((A.y + B.y) * s, (B.x - A.x) * s);
+    }
+};
 
-__device__ __forceinline__ void dft2(double2* v) {
-    double2 a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
+// ---- complex arithmetic: double-float --------------------------------------------------
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {        // s + e = a + b exactly
+    const float s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    return make_float2(s, __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb)));
 }
-__device__ __forceinline__ void dft3(double2* v) {
-    // w = e^{-2 pi i/3} = -1/2 - i sqrt(3)/2
-    const double s = 0.86602540378443864676;
-    const double2 t1 = cadd(v[1], v[2]);
-    const double2 t2 = make_double2(fma(-0.5, t1.x, v[0].x), fma(-0.5, t1.y, v[0].y));
-    const double2 t3 = make_double2(s * (v[1].x - v[2].x), s * (v[1].y - v[2].y));
-    v[0] = cadd(v[0], t1);
-    v[1] = make_double2(t2.x + t3.y, t2.y - t3.x);     // t2 - i t3
-    v[2] = make_double2(t2.x - t3.y, t2.y + t3.x);     // t2 + i t3
+__device__ __forceinline__ float2 df_norm(float s, float t) {           // fast two-sum, |s| >= |t|
+    const float h = __fadd_rn(s, t);
+    return make_float2(h, __fadd_rn(t, -__fadd_rn(h, -s)));
 }
-__device__ __forceinline__ void dft4(double2* v) {
-    double2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-    double2 s13 = cadd(v[1], v[3]), d13 = mul_mi(csub(v[1], v[3]));
-    v[0] = cadd(s02, s13);
-    v[2] = csub(s02, s13);
-    v[1] = cadd(d02, d13);
-    v[3] = csub(d02, d13);
+__device__ __forceinline__ float2 dfr_add(float hi, float lo, float bhi, float blo) {
+    const float2 se = df_two_sum(hi, bhi);
+    return df_norm(se.x, __fadd_rn(se.y, __fadd_rn(lo, blo)));
 }
-__device__ __forceinline__ void dft8(double2* v) {
+__device__ __forceinline__ float2 dfr_mul(float ahi, float alo, float bhi, float blo) {
+    const float p = __fmul_rn(ahi, bhi);
+    float e = __fmaf_rn(ahi, bhi, -p);
+    e = __fmaf_rn(ahi, blo, __fmaf_rn(alo, bhi, e));
+    return df_norm(p, e);
+}
+struct DF {
+    typedef float4 C;   // re.hi, re.lo, im.hi, im.lo
+    static __device__ __forceinline__ float2 split(double x) {
+        const float h = __double2float_rn(x);
+        return make_float2(h, __double2float_rn(x - (double)h));
+    }
+    static __device__ __forceinline__ C zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    static __device__ __forceinline__ C pair(double x, double y) {
+        const float2 a = split(x), b = split(y);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ C add(C a, C b) {
+        const float2 r = dfr_add(a.x, a.y, b.x, b.y), i = dfr_add(a.z, a.w, b.z, b.w);
+        return make_float4(r.x, r.y, i.x, i.y);
+    }
+    static __device__ __forceinline__ C sub(C a, C b) {
+        const float2 r = dfr_add(a.x, a.y, -b.x, -b.y), i = dfr_add(a.z, a.w, -b.z, -b.w);
+        return make_float4(r.x, r.y, i.x, i.y);
+    }
+    static __device__ __forceinline__ C mul(C a, C b) {
+        const float2 rr = dfr_mul(a.x, a.y, b.x, b.y), ii = dfr_mul(a.z, a.w, b.z, b.w);
+        const float2 ri = dfr_mul(a.x, a.y, b.z, b.w), ir = dfr_mul(a.z, a.w, b.x, b.y);
+        const float2 r = dfr_add(rr.x, rr.y, -ii.x, -ii.y), i = dfr_add(ri.x, ri.y, ir.x, ir.y);
+        return make_float4(r.x, r.y, i.x, i.y);
+    }
+    static __device__ __forceinline__ C mul_mi(C a) { return make_float4(a.z, a.w, -a.x, -a.y); }
+    static __device__ __forceinline__ C mul_k(C a, double k) {
+        const float kh = (float)k, kl = (float)(k - (double)kh);   // folded at compile time for literals
+        const float2 r = dfr_mul(a.x, a.y, kh, kl), i = dfr_mul(a.z, a.w, kh, kl);
+        return make_float4(r.x, r.y, i.x, i.y);
+    }
+    static __device__ __forceinline__ C half(C a) { return make_float4(0.5f * a.x, 0.5f * a.y, 0.5f * a.z, 0.5f * a.w); }
+    static __device__ __forceinline__ void unpack(C A, C B, double s, double2& even, double2& odd) {
+        const float sh = __double2float_rn(s), sl = __double2float_rn(s - (double)sh);
+        const float2 es = dfr_add(A.x, A.y, B.x, B.y);
+        const float2 er = dfr_mul(es.x, es.y, sh, sl);
+        const float2 ad = dfr_add(A.z, A.w, -B.z, -B.w);
+        const float2 ei = dfr_mul(ad.x, ad.y, sh, sl);
+        const float2 os = dfr_add(A.z, A.w, B.z, B.w);
+        const float2 orr = dfr_mul(os.x, os.y, sh, sl);
+        const float2 od = dfr_add(B.x, B.y, -A.x, -A.y);
+        const float2 oi = dfr_mul(od.x, od.y, sh, sl);
+        even = make_double2((double)er.x + (double)er.y, (double)ei.x + (double)ei.y);
+        odd = make_double2((double)orr.x + (double)orr.y, (double)oi.x + (double)oi.y);
+    }
+};
+
+template <class A>
+__device__ __forceinline__ void dft2(typename A::C* v) {
+    const typename A::C a = v[0], b = v[1];
+    v[0] = A::add(a, b);
+    v[1] = A::sub(a, b);
+}
+template <class A>
+__device__ __forceinline__ void dft3(typename A::C* v) {
+    // w = e^{-2 pi i/3} = -1/2 - i sqrt(3)/2:  v1 = t2 - i t3, v2 = t2 + i t3
+    typedef typename A::C C;
+    const C t1 = A::add(v[1], v[2]);
+    const C t2 = A::sub(v[0], A::half(t1));
+    const C t3 = A::mul_k(A::sub(v[1], v[2]), 0.86602540378443864676);
+    v[0] = A::add(v[0], t1);
+    v[1] = A::add(t2, A::mul_mi(t3));
+    v[2] = A::sub(t2, A::mul_mi(t3));
+}
+template <class A>
+__device__ __forceinline__ void dft4(typename A::C* v) {
+    typedef typename A::C C;
+    const C s02 = A::add(v[0], v[2]), d02 = A::sub(v[0], v[2]);
+    const C s13 = A::add(v[1], v[3]), d13 = A::mul_mi(A::sub(v[1], v[3]));
+    v[0] = A::add(s02, s13);
+    v[2] = A::sub(s02, s13);
+    v[1] = A::add(d02, d13);
+    v[3] = A::sub(d02, d13);
+}
+template <class A>
+__device__ __forceinline__ void dft8(typename A::C* v) {
+    typedef typename A::C C;
     const double s = 0.70710678118654752440;
-    double2 e[4] = {v[0], v[2], v[4], v[6]};
-    double2 o[4] = {v[1], v[3], v[5], v[7]};
-    dft4(e);
-    dft4(o);
-    // o[k] *= w8^k, w8 = e^{-2 pi i / 8}
-    double2 o1 = make_double2((o[1].x + o[1].y) * s, (o[1].y - o[1].x) * s);
-    double2 o2 = mul_mi(o[2]);
-    double2 o3 = make_double2((o[3].y - o[3].x) * s, -(o[3].x + o[3].y) * s);
-    v[0] = cadd(e[0], o[0]);
-    v[4] = csub(e[0], o[0]);
-    v[1] = cadd(e[1], o1);
-    v[5] = csub(e[1], o1);
-    v[2] = cadd(e[2], o2);
-    v[6] = csub(e[2], o2);
-    v[3] = cadd(e[3], o3);
-    v[7] = csub(e[3], o3);
+    C e[4] = {v[0], v[2], v[4], v[6]};
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<A>(e);
+    dft4<A>(o);
+    // o[k] *= w8^k, w8 = e^{-2 pi i / 8}:  w8 o = s (o - i o),  w8^3 o = s (-i o - o)
+    const C o1 = A::mul_k(A::add(o[1], A::mul_mi(o[1])), s);
+    const C o2 = A::mul_mi(o[2]);
+    const C o3 = A::mul_k(A::sub(A::mul_mi(o[3]), o[3]), s);
+    v[0] = A::add(e[0], o[0]);
+    v[4] = A::sub(e[0], o[0]);
+    v[1] = A::add(e[1], o1);
+    v[5] = A::sub(e[1], o1);
+    v[2] = A::add(e[2], o2);
+    v[6] = A::sub(e[2], o2);
+    v[3] = A::add(e[3], o3);
+    v[7] = A::sub(e[3], o3);
 }
 
 // twiddle W_L^e from shared memory (tw != null) or from the global table
-__device__ __forceinline__ double2 twid(const double2* tw, const double2* W, int e, int64_t wstride) {
+template <class CT>
+__device__ __forceinline__ CT twid(const CT* tw, const CT* W, int e, int64_t wstride) {
     return tw ? tw[e] : __ldg(W + (int64_t)e * wstride);
 }
 
 // one Stockham stage over `cols` columns (column c of the tile at buf[l * cols + c])
-template <int R>
-__device__ __forceinline__ void stage_reg(const double2* src, double2* dst, const double2* tw, const double2* W,
-                                          int L, int cols, int Ns, int64_t wstride) {
+template <class A, int R>
+__device__ __forceinline__ void stage_reg(const typename A::C* src, typename A::C* dst, const typename A::C* tw,
+                                          const typename A::C* W, int L, int cols, int Ns, int64_t wstride) {
     const int nb = L / R;
     const int tw_unit = L / (Ns * R);
     for (int item = threadIdx.x; item < nb * cols; item += blockDim.x) {
         const int c = item % cols, j = item / cols;
         const int jm = j % Ns;
-        double2 v[R];
+        typename A::C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             v[r] = src[(j + r * nb) * cols + c];
-            if (r > 0 && jm != 0) v[r] = cmul(v[r], twid(tw, W, jm * r * tw_unit, wstride));
+            if (r > 0 && jm != 0) v[r] = A::mul(v[r], twid(tw, W, jm * r * tw_unit, wstride));
         }
-        if (R == 2) dft2(v);
-        if (R == 3) dft3(v);
-        if (R == 4) dft4(v);
-        if (R == 8) dft8(v);
+        if (R == 2) dft2<A>(v);
+        if (R == 3) dft3<A>(v);
+        if (R == 4) dft4<A>(v);
+        if (R == 8) dft8<A>(v);
         const int base = (j / Ns) * Ns * R + jm;
 #pragma unroll
         for (int r = 0; r < R; ++r) dst[(base + r * Ns) * cols + c] = v[r];
@@ -161,8 +266,10 @@ __device__ __forceinline__ void stage_reg(const double2* src, double2* dst, cons
 }
 
 // any radix R: one thread per output element, direct length-R DFT
-__device__ __forceinline__ void stage_generic(const double2* src, double2* dst, const double2* tw, const double2* W,
-                                              int L, int cols, int Ns, int R, int64_t wstride) {
+template <class A>
+__device__ __forceinline__ void stage_generic(const typename A::C* src, typename A::C* dst, const typename A::C* tw,
+                                              const typename A::C* W, int L, int cols, int Ns, int R,
+                                              int64_t wstride) {
     const int nb = L / R;
     const int tw_unit = L / (Ns * R);
     const int unit = L / R;                                   // W_R^1 = W_L^(L/R)
@@ -171,29 +278,30 @@ __device__ __forceinline__ void stage_generic(const double2* src, double2* dst, 
         const int rest = item / cols;
         const int k = rest % R, j = rest / R;
         const int jm = j % Ns;
-        double2 acc = make_double2(0.0, 0.0);
+        typename A::C acc = A::zero();
         for (int r = 0; r < R; ++r) {
-            const double2 v = src[(j + r * nb) * cols + c];
+            const typename A::C v = src[(j + r * nb) * cols + c];
             const int e = (jm * r * tw_unit + ((r * k) % R) * unit) % L;
-            acc = cadd(acc, cmul(v, twid(tw, W, e, wstride)));
+            acc = A::add(acc, A::mul(v, twid(tw, W, e, wstride)));
         }
         dst[((j / Ns) * Ns * R + jm + k * Ns) * cols + c] = acc;
     }
 }
 
 // length-L FFT of `cols` columns held in b0; returns the buffer holding the result
-__device__ double2* fft_tile(double2* b0, double2* b1, const double2* tw, const double2* W, const FftArgs& a,
-                             int cols) {
+template <class A>
+__device__ typename A::C* fft_tile(typename A::C* b0, typename A::C* b1, const typename A::C* tw,
+                                   const typename A::C* W, const FftArgs& a, int cols) {
     int Ns = 1;
     for (int st = 0; st < a.nst; ++st) {
         const int R = a.radix[st];
-        if (R == 8) stage_reg<8>(b0, b1, tw, W, a.L, cols, Ns, a.wstride);
-        else if (R == 4) stage_reg<4>(b0, b1, tw, W, a.L, cols, Ns, a.wstride);
-        else if (R == 2) stage_reg<2>(b0, b1, tw, W, a.L, cols, Ns, a.wstride);
-        else if (R == 3) stage_reg<3>(b0, b1, tw, W, a.L, cols, Ns, a.wstride);
-        else stage_generic(b0, b1, tw, W, a.L, cols, Ns, R, a.wstride);
+        if (R == 8) stage_reg<A, 8>(b0, b1, tw, W, a.L, cols, Ns, a.wstride);
+        else if (R == 4) stage_reg<A, 4>(b0, b1, tw, W, a.L, cols, Ns, a.wstride);
+        else if (R == 2) stage_reg<A, 2>(b0, b1, tw, W, a.L, cols, Ns, a.wstride);
+        else if (R == 3) stage_reg<A, 3>(b0, b1, tw, W, a.L, cols, Ns, a.wstride);
+        else stage_generic<A>(b0, b1, tw, W, a.L, cols, Ns, R, a.wstride);
         __syncthreads();
-        double2* t = b0;
+        typename A::C* t = b0;
         b0 = b1;
         b1 = t;
         Ns *= R;
@@ -201,47 +309,56 @@ __device__ double2* fft_tile(double2* b0, double2* b1, const double2* tw, const 
     return b0;
 }
 
-__device__ __forceinline__ void stage_twiddles(double2* tw, const double2* W, int L, int64_t wstride) {
+template <class CT>
+__device__ __forceinline__ void stage_twiddles(CT* tw, const CT* W, int L, int64_t wstride) {
     for (int j = threadIdx.x; j < L; j += blockDim.x) tw[j] = __ldg(W + (int64_t)j * wstride);
 }
 
 // ---- pass 1 (two-pass plans): length L1 over i1 for a fixed i2 = o, packed column pairs ----
-__global__ void __launch_bounds__(kFftThreads) fft_pass1_kernel(const __grid_constant__ FftArgs a, const double2* W) {
-    extern __shared__ double2 fbuf[];
+template <class A>
+__global__ void __launch_bounds__(kFftThreads) fft_pass1_kernel(const __grid_constant__ FftArgs a,
+                                                                  const typename A::C* W) {
+    typedef typename A::C C;
+    extern __shared__ __align__(16) unsigned char fraw[];
+    C* fbuf = reinterpret_cast<C*>(fraw);
     const int L = a.L, Gt = a.Gt;
     const int ntile = (a.Gp + Gt - 1) / Gt;
     const int o = blockIdx.x / ntile;
     const int c0 = (blockIdx.x % ntile) * Gt;
-    double2* b0 = fbuf;
-    double2* b1 = fbuf + (size_t)L * Gt;
-    double2* tw = (L <= kTwSmem) ? b1 + (size_t)L * Gt : nullptr;      // W_L^j
-    double2* ot = (L <= kTwSmem) ? tw + L : nullptr;                    // W[(o m) mod M], m < L
+    C* b0 = fbuf;
+    C* b1 = fbuf + (size_t)L * Gt;
+    C* tw = (L <= kTwSmem) ? b1 + (size_t)L * Gt : nullptr;            // W_L^j
+    C* ot = (L <= kTwSmem) ? tw + L : nullptr;                          // W[(o m) mod M], m < L
     if (tw) {
         stage_twiddles(tw, W, L, a.wstride);
         for (int m = threadIdx.x; m < L; m += blockDim.x) ot[m] = __ldg(W + ((int64_t)o * m) % a.M);
     }
     for (int idx = threadIdx.x; idx < L * Gt; idx += blockDim.x) {
         const int l = idx / Gt, c = idx % Gt, g = 2 * (c0 + c);
-        double2 v = make_double2(0.0, 0.0);
         const int64_t row = (int64_t)o * a.in_outer + (int64_t)l * a.in_step;
-        if (g < a.G) v.x = __ldcs(a.Ur + row * a.G + g);
-        if (g + 1 < a.G) v.y = __ldcs(a.Ur + row * a.G + g + 1);
-        b0[idx] = v;
+        const double x = g < a.G ? __ldcs(a.Ur + row * a.G + g) : 0.0;
+        const double y = g + 1 < a.G ? __ldcs(a.Ur + row * a.G + g + 1) : 0.0;
+        b0[idx] = A::pair(x, y);
     }
     __syncthreads();
-    const double2* res = fft_tile(b0, b1, tw, W, a, Gt);
+    const C* res = fft_tile<A>(b0, b1, tw, W, a, Gt);
+    C* Yo = reinterpret_cast<C*>(a.Yo);
     for (int idx = threadIdx.x; idx < L * Gt; idx += blockDim.x) {
         const int m = idx / Gt, c = idx % Gt;
         if (c0 + c >= a.Gp) continue;
-        double2 v = res[idx];
-        if (m) v = cmul(v, ot ? ot[m] : __ldg(W + ((int64_t)o * m) % a.M));
-        a.Yo[((int64_t)m * a.out_m + (int64_t)o * a.out_outer) * a.Gp + c0 + c] = v;
+        C v = res[idx];
+        if (m) v = A::mul(v, ot ? ot[m] : __ldg(W + ((int64_t)o * m) % a.M));
+        Yo[((int64_t)m * a.out_m + (int64_t)o * a.out_outer) * a.Gp + c0 + c] = v;
     }
 }
 
 // ---- final pass: buckets m1 and L1-m1 (length L2 over i2), unpack, gather ----
-__global__ void __launch_bounds__(kFftThreads) fft_final_kernel(const __grid_constant__ FftArgs a, const double2* W) {
-    extern __shared__ double2 fbuf[];
+template <class A>
+__global__ void __launch_bounds__(kFftThreads) fft_final_kernel(const __grid_constant__ FftArgs a,
+                                                                  const typename A::C* W) {
+    typedef typename A::C C;
+    extern __shared__ __align__(16) unsigned char fraw[];
+    C* fbuf = reinterpret_cast<C*>(fraw);
     const int L = a.L, Gt = a.Gt;
     const int ntile = (a.Gp + Gt - 1) / Gt;
     const int m1 = blockIdx.x / ntile;                  // 0 <= m1 <= L1/2
@@ -250,27 +367,29 @@ __global__ void __launch_bounds__(kFftThreads) fft_final_kernel(const __grid_con
     const int m1p = (L1 - m1) % L1;                     // partner bucket
     const int nb = (m1p == m1) ? 1 : 2;                 // transforms in this CTA
     const int cols = nb * Gt;                           // column c of bucket b at b * Gt + c
-    double2* b0 = fbuf;
-    double2* b1 = fbuf + (size_t)L * cols;
-    double2* tw = (L <= kTwSmem) ? b1 + (size_t)L * cols : nullptr;
+    C* b0 = fbuf;
+    C* b1 = fbuf + (size_t)L * cols;
+    C* tw = (L <= kTwSmem) ? b1 + (size_t)L * cols : nullptr;
     if (tw) stage_twiddles(tw, W, L, a.wstride);
+    const C* Yc = reinterpret_cast<const C*>(a.Yc);
     for (int idx = threadIdx.x; idx < L * cols; idx += blockDim.x) {
         const int l = idx / cols, cc = idx % cols;
         const int b = cc / Gt, c = cc % Gt;
         const int bucket = b ? m1p : m1;
-        double2 v = make_double2(0.0, 0.0);
         const int64_t row = (int64_t)bucket * a.in_outer + (int64_t)l * a.in_step;
-        if (a.Yc) {
-            if (c0 + c < a.Gp) v = __ldcs(a.Yc + row * a.Gp + c0 + c);
+        C v = A::zero();
+        if (Yc) {
+            if (c0 + c < a.Gp) v = __ldcs(Yc + row * a.Gp + c0 + c);
         } else {
             const int g = 2 * (c0 + c);
-            if (g < a.G) v.x = __ldcs(a.Ur + row * a.G + g);
-            if (g + 1 < a.G) v.y = __ldcs(a.Ur + row * a.G + g + 1);
+            const double x = g < a.G ? __ldcs(a.Ur + row * a.G + g) : 0.0;
+            const double y = g + 1 < a.G ? __ldcs(a.Ur + row * a.G + g + 1) : 0.0;
+            v = A::pair(x, y);
         }
         b0[idx] = v;
     }
     __syncthreads();
-    const double2* Z = fft_tile(b0, b1, tw, W, a, cols);
+    const C* Z = fft_tile<A>(b0, b1, tw, W, a, cols);
     // gather: candidates of bucket m1 (partner transform m1p) and, if distinct, of bucket m1p
     for (int b = 0; b < nb; ++b) {
         const int bucket = b ? m1p : m1;
@@ -281,11 +400,10 @@ __global__ void __launch_bounds__(kFftThreads) fft_final_kernel(const __grid_con
             if (c0 + c >= a.Gp) continue;
             const int m2 = a.bm2[e];
             const int m2p = (bucket == 0) ? (L - m2) % L : L - 1 - m2;
-            const double2 A = Z[m2 * cols + b * Gt + c];
-            const double2 Bc = Z[m2p * cols + pb * Gt + c];      // Z[M - m], conjugated below
-            const double s = 0.5 * a.scale;
-            const double2 even = make_double2((A.x + Bc.x) * s, (A.y - Bc.y) * s);
-            const double2 odd = make_double2((A.y + Bc.y) * s, (Bc.x - A.x) * s);
+            const C Za = Z[m2 * cols + b * Gt + c];
+            const C Zb = Z[m2p * cols + pb * Gt + c];         // Z[M - m], conjugated in the unpack
+            double2 even, odd;
+            A::unpack(Za, Zb, 0.5 * a.scale, even, odd);
             const int g = 2 * (c0 + c);
             const int64_t k = a.bk[e];
             a.C[(int64_t)g * a.nJ + k] = even;
@@ -344,8 +462,10 @@ static size_t pass_smem(int L, int cols) {
     return s;
 }
 
-cudaError_t launch_fft_gather(const FftPlan& p, int G, const double* U, const double2* W, const GatherPlan& gp,
-                              int64_t nJ, double2* scratch, double2* C, cudaStream_t s, int* launches) {
+template <class A>
+static cudaError_t launch_fft_impl(const FftPlan& p, int G, const double* U, const typename A::C* W,
+                                   const GatherPlan& gp, int64_t nJ, void* scratch, double2* C, cudaStream_t s,
+                                   int* launches) {
     if (p.M <= 0 || nJ <= 0) return cudaSuccess;
     if (p.L2 <= 0) return cudaErrorInvalidValue;
     FftArgs a;
@@ -371,10 +491,10 @@ cudaError_t launch_fft_gather(const FftPlan& p, int G, const double* U, const do
         a.out_outer = 1;
         a.nst = factorize(a.L, a.radix);
         const size_t smem = pass_smem(a.L, a.Gt);
-        e = cudaFuncSetAttribute(fft_pass1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(fft_pass1_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int ntile = (a.Gp + a.Gt - 1) / a.Gt;
-        fft_pass1_kernel<<<(unsigned)((int64_t)a.nOuter * ntile), kFftThreads, smem, s>>>(a, W);
+        fft_pass1_kernel<A><<<(unsigned)((int64_t)a.nOuter * ntile), kFftThreads, smem, s>>>(a, W);
         if (launches) ++*launches;
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -397,12 +517,19 @@ cudaError_t launch_fft_gather(const FftPlan& p, int G, const double* U, const do
     b.C = C;
     b.nst = factorize(b.L, b.radix);
     const size_t smem = pass_smem(b.L, (b.L1 > 2 ? 2 : 1) * b.Gt);
-    e = cudaFuncSetAttribute(fft_final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(fft_final_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int ntile = (b.Gp + b.Gt - 1) / b.Gt;
-    fft_final_kernel<<<(unsigned)((int64_t)b.nOuter * ntile), kFftThreads, smem, s>>>(b, W);
+    fft_final_kernel<A><<<(unsigned)((int64_t)b.nOuter * ntile), kFftThreads, smem, s>>>(b, W);
     if (launches) ++*launches;
     return cudaGetLastError();
+}
+
+cudaError_t launch_fft_gather(const FftPlan& p, int G, const double* U, const void* W, bool df, const GatherPlan& gp,
+                              int64_t nJ, void* scratch, double2* C, cudaStream_t s, int* launches) {
+    if (df)
+        return launch_fft_impl<DF>(p, G, U, reinterpret_cast<const float4*>(W), gp, nJ, scratch, C, s, launches);
+    return launch_fft_impl<F64>(p, G, U, reinterpret_cast<const double2*>(W), gp, nJ, scratch, C, s, launches);
 }
 
 }  // namespace usfft

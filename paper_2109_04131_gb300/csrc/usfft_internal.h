@@ -113,9 +113,12 @@ struct GatherPlan {        // buckets of candidates by m mod L1 (CSR), entries (
 };
 FftPlan make_fft_plan(int64_t M);
 size_t fft_scratch_bytes(const FftPlan& p, int G);
-cudaError_t launch_twiddles(int64_t M, double2* W, cudaStream_t s, int* launches);
-cudaError_t launch_fft_gather(const FftPlan& p, int G, const double* U, const double2* W,
-                              const GatherPlan& gp, int64_t nJ, double2* scratch, double2* C,
+// W[j] = e^{-2 pi i j / M}: fp64 (double2) or double-float (float4 = re.hi, re.lo, im.hi, im.lo)
+cudaError_t launch_twiddles(int64_t M, void* W, bool df, cudaStream_t s, int* launches);
+// df selects double-float arithmetic for the transform (W must then be the float4 table);
+// the scratch holds [M][ceil(G/2)] 16-byte complex values of the same arithmetic.
+cudaError_t launch_fft_gather(const FftPlan& p, int G, const double* U, const void* W, bool df,
+                              const GatherPlan& gp, int64_t nJ, void* scratch, double2* C,
                               cudaStream_t s, int* launches);
 
 // Random-lattice estimate (Algorithm A): C[g][k] = Call[src[k]][g][k] where src[k] >= 0 (the
