@@ -112,7 +112,7 @@ struct F64 {
     static __device__ __forceinline__ C mul_k(C a, double k) { return make_double2(a.x * k, a.y * k); }
     static __device__ __forceinline__ C half(C a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
     // (A + conj B) s and (A - conj B) s / i, the unpacked transforms of the two real columns
-    static __device__ __forceinline__ void unpack(C A, C B, double s, double2& even, double2& odd) {
+    static __device__ __forceinline__ void unpack(C A, C B, double s, float, float, double2& even, double2& odd) {
         even = make_double2((A.x + B.x) * s, (A.y - B.y) * s);
         odd = make_double2((A.y + B.y) * s, (B.x - A.x) * s);
     }
@@ -170,8 +170,8 @@ struct DF {
         return make_float4(r.x, r.y, i.x, i.y);
     }
     static __device__ __forceinline__ C half(C a) { return make_float4(0.5f * a.x, 0.5f * a.y, 0.5f * a.z, 0.5f * a.w); }
-    static __device__ __forceinline__ void unpack(C A, C B, double s, double2& even, double2& odd) {
-        const float sh = __double2float_rn(s), sl = __double2float_rn(s - (double)sh);
+    // s given as (sh, sl), the split of the fp64 scale (formed once per kernel)
+    static __device__ __forceinline__ void unpack(C A, C B, double, float sh, float sl, double2& even, double2& odd) {
         const float2 es = dfr_add(A.x, A.y, B.x, B.y);
         const float2 er = dfr_mul(es.x, es.y, sh, sl);
         const float2 ad = dfr_add(A.z, A.w, -B.z, -B.w);
@@ -390,6 +390,10 @@ __global__ void __launch_bounds__(kFftThreads) fft_final_kernel(const __grid_con
     }
     __syncthreads();
     const C* Z = fft_tile<A>(b0, b1, tw, W, a, cols);
+    // the output scale 1 / (2M): fp64, and its split for the double-float unpack
+    const double s_half = 0.5 * a.scale;
+    const float s_hi = __double2float_rn(s_half);
+    const float s_lo = __double2float_rn(s_half - (double)s_hi);
     // gather: candidates of bucket m1 (partner transform m1p) and, if distinct, of bucket m1p
     for (int b = 0; b < nb; ++b) {
         const int bucket = b ? m1p : m1;
@@ -403,7 +407,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_final_kernel(const __grid_con
             const C Za = Z[m2 * cols + b * Gt + c];
             const C Zb = Z[m2p * cols + pb * Gt + c];         // Z[M - m], conjugated in the unpack
             double2 even, odd;
-            A::unpack(Za, Zb, 0.5 * a.scale, even, odd);
+            A::unpack(Za, Zb, s_half, s_hi, s_lo, even, odd);
             const int g = 2 * (c0 + c);
             const int64_t k = a.bk[e];
             a.C[(int64_t)g * a.nJ + k] = even;
