@@ -50,12 +50,12 @@ FLOPS_PER_CG_ITER_PER_NODE = 21      # Jacobi-PCG: SpMV 9 + two dots 4 + three A
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
 # kernel, with a hash of the kernel source it was taken on; a changed source makes it null.
 PROFILE_TRAFFIC = {
-    "mixed": {"bytes": 263168 + 177223680, "files": ["k_sample2d_dst.cu", "k_pcg_common.cuh"],
-              "sha": "4b72ca9fa20f6d9c", "profile": "profiles/pcg2d_mixed_dst_c2_t3.md"},
-    "fp64": {"bytes": 7748608 + 169484288, "files": ["k_sample2d.cu", "k_pcg_common.cuh"],
-             "sha": "543258ce85e18805", "profile": "profiles/pcg2d_fp64_c2_t3.md"},
-    "fft": {"bytes": 221549312 + 159785728 + 747531008 + 557830144, "files": ["k_fft.cu"],
-            "sha": "7b4ea64a052c6718", "profile": "profiles/fft_c2_t3.md"},
+    "mixed": {"bytes": 177787136, "files": ["k_sample2d_dst.cu", "k_pcg_common.cuh", "k_theta.cuh"],
+              "sha": "4b08b753a3a23c5f", "profile": "profiles/pcg2d_mixed_dst_c2_t3.md"},
+    "fp64": {"bytes": 176823040, "files": ["k_sample2d.cu", "k_pcg_common.cuh", "k_theta.cuh"],
+             "sha": "d8ffe3f87fbb6272", "profile": "profiles/pcg2d_fp64_c2_t3.md"},
+    "fft": {"bytes": 1706983168, "files": ["k_fft.cu"],
+            "sha": "84b28114cbc6af38", "profile": "profiles/fft_c2_t3.md"},
 }
 
 
