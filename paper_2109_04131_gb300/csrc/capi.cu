@@ -620,7 +620,11 @@ usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params
         G = pr.n;
         E = pr.n + 1;
     } else if (pr.kind == USFFT_PDE_2D) {
-        if (pr.n < 1 || pr.n > 63) return fail(nullptr, USFFT_EINVAL, "2-D: n must lie in [1, 63] in this version");
+        if (pr.n < 1 || pr.n > 127) return fail(nullptr, USFFT_EINVAL, "2-D: n must lie in [1, 127]");
+        if (pr.n > 63 && pa.precision != USFFT_MIXED)
+            return fail(nullptr, USFFT_EINVAL, "2-D: n > 63 runs in the MIXED precision mode only");
+        if (pr.n > 63 && big_smem_bytes(pr.n, pr.d) > 232448)
+            return fail(nullptr, USFFT_EINVAL, "2-D: d too large for the shared-memory tables at n > 63");
         if (pa.precision == USFFT_MIXED_JACOBI && pr.n < 4) return fail(nullptr, USFFT_EINVAL, "2-D mixed: n >= 4");
         G = pr.n * pr.n;
         E = 2 * (pr.n + 1) * (pr.n + 1);

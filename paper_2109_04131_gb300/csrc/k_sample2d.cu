@@ -31,6 +31,7 @@ namespace usfft {
 size_t dst_smem_bytes(int n, int d);
 template <int NPT>
 cudaError_t launch_dst_npt(const Pcg2dArgs& a, int blocks, int threads, cudaStream_t s);
+cudaError_t launch_mixed_big(const Pcg2dArgs& a, int blocks, cudaStream_t s);
 template <int NPT>
 int dst_resident_blocks(int threads, int d, int n);
 
@@ -375,6 +376,15 @@ static int resident_blocks(int precision, int threads, int n) {
 
 // persistent grid: one wave of resident CTAs on every SM
 int sample_2d_default_blocks(int n, int precision) {
+    if (n > 63) {                       // large-mesh MIXED kernel: one 1024-thread CTA per SM
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 152;
+        }
+        return sms;
+    }
     const int G = n * n;
     const int npt = pick_npt(G, precision);
     const int threads = ((G + npt - 1) / npt + 31) / 32 * 32;
@@ -397,7 +407,7 @@ int sample_2d_default_blocks(int n, int precision) {
 size_t sample_2d_scratch_bytes(int n, int precision, int blocks) {
     if (precision == USFFT_FP64) return 0;
     const size_t W = (size_t)n + 2;
-    if (precision == USFFT_MIXED) return sizeof(double) * 3 * W * W * (size_t)blocks;
+    if (precision == USFFT_MIXED) return sizeof(double) * (n > 63 ? 9 : 3) * W * W * (size_t)blocks;
     return sizeof(double) * 2 * (size_t)n * (n + 1) * (size_t)blocks;
 }
 
@@ -423,7 +433,7 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
                              unsigned int* fail_count, unsigned long long* iters_sum, double* scratch,
                              size_t scratch_bytes, cudaStream_t s, int* launches) {
     if (count <= 0) return cudaSuccess;
-    if (n < 1 || n > 63) return cudaErrorInvalidValue;
+    if (n < 1 || n > 127 || (n > 63 && cg.precision != USFFT_MIXED)) return cudaErrorInvalidValue;
     Pcg2dArgs a;
     a.ns = ns;
     a.n = n;
@@ -452,6 +462,11 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
     if (cg.precision != USFFT_FP64 && scratch_bytes < sample_2d_scratch_bytes(n, cg.precision, blocks))
         return cudaErrorInvalidValue;
     cudaError_t e;
+    if (n > 63) {
+        e = launch_mixed_big(a, blocks, s);
+        if (launches) ++*launches;
+        return e;
+    }
     switch (npt) {
         case 1: e = launch_npt<1>(a, cg.precision, blocks, threads, s); break;
         case 2: e = launch_npt<2>(a, cg.precision, blocks, threads, s); break;

@@ -520,6 +520,367 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Large meshes (64 <= n <= 127): the same solver with the per-node vectors in the CTA's global
+// scratch slot (L2 / HBM) instead of shared memory and registers; shared memory holds only the
+// sine-transform operands (S, L, two transform buffers: 174 KB at P = 128), the separable-assembly
+// tables and the reduction buffers.  One CTA of 1024 threads per system; nodes are visited in
+// loops g = tid, tid + T, ... (column-major enumeration, halo h = (p+1) W + (q+1), transform
+// position p LD + q, as in the small kernel).  Scratch slot (in units of W^2): fp64 x, weights
+// (left, down), diagonal, residual (5); fp32 weights (left, down), scaling, p, r, z, q, d (4).
+// ---------------------------------------------------------------------------------------------
+struct BigLayout {
+    int W, LD, J1, JA;
+    size_t o_S, o_L, o_Ta, o_Tb, o_A, o_AF, o_Tr, o_md, o_sj, o_r64, o_r32, total;
+};
+
+__host__ __device__ inline BigLayout big_layout(int n, int d, int P) {
+    BigLayout L;
+    L.W = n + 2;
+    L.LD = P + 8;
+    size_t o = 0;
+    L.o_S = o;   o = align16(o + sizeof(__nv_bfloat16) * (size_t)P * L.LD);
+    L.o_L = o;   o = align16(o + sizeof(float) * (size_t)P * L.LD);
+    L.o_Ta = o;  o = align16(o + sizeof(__nv_bfloat16) * (size_t)P * L.LD);
+    L.o_Tb = o;  o = align16(o + sizeof(__nv_bfloat16) * (size_t)P * L.LD);
+    L.J1 = 1;
+    L.JA = 1;
+    for (int j = 1; j <= d; ++j) {
+        int j1, j2;
+        mode_pair(j, j1, j2);
+        if (j1 > L.J1) L.J1 = j1;
+        if (j1 > L.JA) L.JA = j1;
+        if (j2 > L.JA) L.JA = j2;
+    }
+    L.o_A = o;   o = align16(o + sizeof(double) * (size_t)L.JA * 2 * (n + 1));
+    L.o_AF = o;  o = align16(o + sizeof(float2) * (size_t)L.JA * 2 * (n + 1));
+    L.o_Tr = o;  o = align16(o + sizeof(float2) * (size_t)L.J1 * 2 * (n + 1));
+    L.o_md = o;  o = align16(o + sizeof(double) * (size_t)d + sizeof(int) * 2 * (size_t)d);
+    L.o_sj = o;  o = align16(o + sizeof(double) * (size_t)d);
+    L.o_r64 = o; o = align16(o + sizeof(double) * 36);
+    L.o_r32 = o; o = align16(o + sizeof(float) * 4 * 36);
+    L.total = o;
+    return L;
+}
+
+// block-wide sums of up to three fp32 partials (every thread receives them)
+__device__ __forceinline__ float3 block_sum3f(float v0, float v1, float v2, float* buf) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    if (lane == 0) {
+        buf[warp] = v0;
+        buf[36 + warp] = v1;
+        buf[72 + warp] = v2;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float a0 = lane < nw ? buf[lane] : 0.f, a1 = lane < nw ? buf[36 + lane] : 0.f;
+        float a2 = lane < nw ? buf[72 + lane] : 0.f;
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        a2 = warp_sum(a2);
+        if (lane == 0) {
+            buf[108] = a0;
+            buf[109] = a1;
+            buf[110] = a2;
+        }
+    }
+    __syncthreads();
+    const float3 r = make_float3(buf[108], buf[109], buf[110]);
+    __syncthreads();   // buf is reused by the next call
+    return r;
+}
+
+template <int P>
+__global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_constant__ Pcg2dArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = a.n, G = n * n, n1 = n + 1;
+    const BigLayout Lo = big_layout(n, a.ns.d, P);
+    const int W = Lo.W, LD = Lo.LD, WW = W * W;
+    bf16* S = reinterpret_cast<bf16*>(smraw + Lo.o_S);
+    float* Li = reinterpret_cast<float*>(smraw + Lo.o_L);
+    bf16* Ta = reinterpret_cast<bf16*>(smraw + Lo.o_Ta);
+    bf16* Tb = reinterpret_cast<bf16*>(smraw + Lo.o_Tb);
+    double* At = reinterpret_cast<double*>(smraw + Lo.o_A);
+    float2* AtF = reinterpret_cast<float2*>(smraw + Lo.o_AF);
+    float2* Tr = reinterpret_cast<float2*>(smraw + Lo.o_Tr);
+    double* amp = reinterpret_cast<double*>(smraw + Lo.o_md);
+    int* mj1 = reinterpret_cast<int*>(amp + a.ns.d);
+    int* mj2 = mj1 + a.ns.d;
+    double* sj = reinterpret_cast<double*>(smraw + Lo.o_sj);
+    double* red64 = reinterpret_cast<double*>(smraw + Lo.o_r64);
+    float* red32 = reinterpret_cast<float*>(smraw + Lo.o_r32);
+    const int J1 = Lo.J1, JA = Lo.JA;
+    const int T = blockDim.x, tid = threadIdx.x;
+    // the CTA's scratch slot
+    double* x64 = a.scratch + (size_t)blockIdx.x * 9 * WW;
+    double* w64l = x64 + WW;
+    double* w64d = w64l + WW;
+    double* d64 = w64d + WW;
+    double* r64 = d64 + WW;
+    float* wl = reinterpret_cast<float*>(r64 + WW);
+    float* wd = wl + WW;
+    float* scs = wd + WW;
+    float* ph = scs + WW;
+    float* rv = ph + WW;
+    float* zv = rv + WW;
+    float* qv = zv + WW;
+    float* dv = qv + WW;
+
+    const float c2 = 4.0f / ((float)n1 * (float)n1);
+    for (int e = tid; e < P * LD; e += T) {
+        const int j = e / LD, k = e % LD;
+        float sv = 0.f, lv = 0.f;
+        if (j < n && k < n) {
+            sv = sinpif((float)((j + 1) * (k + 1)) / (float)n1);
+            const float s1 = sinpif((float)(k + 1) / (2.0f * n1)), s2 = sinpif((float)(j + 1) / (2.0f * n1));
+            lv = c2 / (4.0f * s1 * s1 + 4.0f * s2 * s2);
+        }
+        S[e] = __float2bfloat16_rn(sv);
+        Li[e] = lv;
+        Ta[e] = __float2bfloat16_rn(0.f);
+        Tb[e] = __float2bfloat16_rn(0.f);
+    }
+    for (int e = tid; e < WW; e += T) {     // the halo ring stays zero (Dirichlet boundary)
+        wl[e] = 0.f;
+        wd[e] = 0.f;
+        ph[e] = 0.f;
+        w64l[e] = 0.0;
+        w64d[e] = 0.0;
+        x64[e] = 0.0;
+    }
+    {
+        const double hh = 1.0 / (double)n1;
+        for (int e = tid; e < JA * 2 * n1; e += T) {
+            const int jj = e / (2 * n1) + 1, o = (e / n1) % 2 + 1, Pp = e % n1;
+            At[e] = sinpi((double)jj * (((double)Pp + (double)o / 3.0) * hh));
+            AtF[e] = df_split(At[e]);
+        }
+        for (int j = tid; j < a.ns.d; j += T) {
+            int j1, j2;
+            mode_pair(j + 1, j1, j2);
+            mj1[j] = j1;
+            mj2[j] = j2;
+            amp[j] = a.coef_scale * pow((double)(j + 1), -a.coef_decay);
+        }
+    }
+    const double b = a.rhs;
+    const double rr0 = (double)G * b * b;
+    const double stop = a.tol * a.tol * rr0;
+    const float nstop = (float)(a.tol * sqrt(rr0));
+    const float tol_in = (float)a.tol_inner;
+    __syncthreads();
+
+    for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
+        const int64_t i = a.i0 + sys;
+        for (int j = tid; j < a.ns.d; j += T) sj[j] = node_theta(a.ns, j, i);
+        __syncthreads();
+        const bool logn = a.coef_model == USFFT_COEF_LOGNORMAL_SIN;
+        const int d = a.ns.d;
+        for (int e = tid; e < J1 * 2 * n1; e += T) {
+            const int j1 = e / (2 * n1) + 1, o = (e / n1) % 2, Q = e % n1;
+            double acc = 0.0;
+            for (int j = 0; j < d; ++j)
+                if (mj1[j] == j1) acc = fma(amp[j] * sj[j], At[((mj2[j] - 1) * 2 + o) * n1 + Q], acc);
+            Tr[e] = df_split(acc);
+        }
+        __syncthreads();
+        // weights: the lower-triangle coefficient of square (P, Q) is recomputed where needed
+        const float2 one = make_float2(1.f, 0.f);
+        for (int e = tid; e < n1 * n1; e += T) {
+            const int Pp = e % n1, Q = e / n1;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 0) * n1 + Pp], Tr[(j1 * 2 + 1) * n1 + Q]);
+            const float2 au = logn ? df_split(exp(df_to_double(acc))) : df_add(one, acc);
+            if (Q < n) {            // edge (Pp,Q+1)-(Pp+1,Q+1): left of node (Pp+1,Q+1); lower triangle of (Pp, Q+1)
+                float2 lo = make_float2(0.f, 0.f);
+                for (int j1 = 0; j1 < J1; ++j1) lo = df_fma(lo, AtF[(j1 * 2 + 1) * n1 + Pp], Tr[(j1 * 2 + 0) * n1 + Q + 1]);
+                lo = logn ? df_split(exp(df_to_double(lo))) : df_add(one, lo);
+                float2 w = df_add(lo, au);
+                w = make_float2(0.5f * w.x, 0.5f * w.y);
+                const int h = (Pp + 1) * W + Q + 1;
+                w64l[h] = df_to_double(w);
+                wl[h] = w.x;
+            }
+            if (Pp >= 1) {          // edge (Pp,Q)-(Pp,Q+1): below node (Pp,Q+1); lower triangle of (Pp-1, Q)
+                float2 lo = make_float2(0.f, 0.f);
+                for (int j1 = 0; j1 < J1; ++j1) lo = df_fma(lo, AtF[(j1 * 2 + 1) * n1 + Pp - 1], Tr[(j1 * 2 + 0) * n1 + Q]);
+                lo = logn ? df_split(exp(df_to_double(lo))) : df_add(one, lo);
+                float2 w = df_add(au, lo);
+                w = make_float2(0.5f * w.x, 0.5f * w.y);
+                const int h = Pp * W + Q + 1;
+                w64d[h] = df_to_double(w);
+                wd[h] = w.x;
+            }
+        }
+        __syncthreads();
+        for (int g = tid; g < G; g += T) {
+            const int h = (g / n + 1) * W + g % n + 1;
+            const double dg = (w64l[h] + w64l[h + W]) + (w64d[h] + w64d[h + 1]);
+            d64[h] = dg;
+            scs[h] = rsqrtf(0.25f * (float)dg);
+            x64[h] = 0.0;
+            r64[h] = b;
+        }
+        __syncthreads();
+
+        // ---- fp64 iterative refinement around fp32 flexible PCG ----
+        double rr64 = rr0, nr = sqrt(rr0);
+        int total = 0, outer = 0;
+        bool at_floor = false;     // the residual stagnated at its rounding floor (see below)
+        auto precond = [&]() {     // zv = D^-1/2 K_0^-1 D^-1/2 rv
+            for (int g = tid; g < G; g += T) {
+                const int pp = g / n, qq = g % n, h = (pp + 1) * W + qq + 1;
+                Ta[pp * LD + qq] = __float2bfloat16_rn(scs[h] * rv[h]);
+            }
+            __syncthreads();
+            gemm_bf16<P, false, false>(S, Ta, Tb, nullptr, LD);
+            __syncthreads();
+            gemm_bf16<P, true, true>(Tb, S, Ta, Li, LD);
+            __syncthreads();
+            gemm_bf16<P, false, false>(S, Ta, Tb, nullptr, LD);
+            __syncthreads();
+            gemm_bf16<P, true, false>(Tb, S, Ta, nullptr, LD);
+            __syncthreads();
+            for (int g = tid; g < G; g += T) {
+                const int pp = g / n, qq = g % n, h = (pp + 1) * W + qq + 1;
+                zv[h] = scs[h] * __bfloat162float(Ta[pp * LD + qq]);
+            }
+        };
+        while (rr64 > stop && outer < 16) {
+            const float inv = (float)(1.0 / nr);
+            float rl = 0.f;
+            for (int g = tid; g < G; g += T) {
+                const int h = (g / n + 1) * W + g % n + 1;
+                const float r = (float)r64[h] * inv;
+                rv[h] = r;
+                dv[h] = 0.f;
+                rl = fmaf(r, r, rl);
+            }
+            __syncthreads();
+            precond();
+            float rz_l = 0.f;
+            for (int g = tid; g < G; g += T) {
+                const int h = (g / n + 1) * W + g % n + 1;
+                ph[h] = zv[h];
+                rz_l = fmaf(rv[h], zv[h], rz_l);
+            }
+            float3 sums = block_sum3f(rz_l, rl, 0.f, red32);
+            float rz = sums.x, rr = sums.y;
+            const float gap = 0.3f * nstop / (float)nr;
+            const float tin = gap > tol_in ? gap : tol_in;
+            const float istop = tin * tin * rr;
+            int it = 0;
+            while (rr > istop && it < a.max_iters) {
+                float pq_l = 0.f;
+                for (int g = tid; g < G; g += T) {
+                    const int h = (g / n + 1) * W + g % n + 1;
+                    const float w0 = wl[h], w1 = wl[h + W], w2 = wd[h], w3 = wd[h + 1];
+                    float acc = w0 * ph[h - W];
+                    acc = fmaf(w1, ph[h + W], acc);
+                    acc = fmaf(w2, ph[h - 1], acc);
+                    acc = fmaf(w3, ph[h + 1], acc);
+                    const float q = fmaf((w0 + w1) + (w2 + w3), ph[h], -acc);
+                    qv[h] = q;
+                    pq_l = fmaf(ph[h], q, pq_l);
+                }
+                const float pq = block_sum3f(pq_l, 0.f, 0.f, red32).x;
+                const float alpha = rz / pq;
+                for (int g = tid; g < G; g += T) {
+                    const int h = (g / n + 1) * W + g % n + 1;
+                    dv[h] = fmaf(alpha, ph[h], dv[h]);
+                    rv[h] = fmaf(-alpha, qv[h], rv[h]);
+                }
+                __syncthreads();
+                precond();
+                float zr_l = 0.f, zq_l = 0.f, rn_l = 0.f;
+                for (int g = tid; g < G; g += T) {
+                    const int h = (g / n + 1) * W + g % n + 1;
+                    zr_l = fmaf(zv[h], rv[h], zr_l);
+                    zq_l = fmaf(zv[h], qv[h], zq_l);
+                    rn_l = fmaf(rv[h], rv[h], rn_l);
+                }
+                sums = block_sum3f(zr_l, zq_l, rn_l, red32);
+                // flexible beta: z_new . (r_new - r_old) / rz with r_old = r_new + alpha q
+                const float beta = -alpha * sums.y / rz;
+                rz = sums.x;
+                rr = sums.z;
+                for (int g = tid; g < G; g += T) {
+                    const int h = (g / n + 1) * W + g % n + 1;
+                    ph[h] = fmaf(beta, ph[h], zv[h]);
+                }
+                __syncthreads();
+                ++it;
+            }
+            total += it;
+            for (int g = tid; g < G; g += T) {
+                const int h = (g / n + 1) * W + g % n + 1;
+                x64[h] = fma(nr, (double)dv[h], x64[h]);
+            }
+            __syncthreads();
+            // residual in difference form, b - sum_e w_e (x_i - x_j): at these mesh widths the
+            // terms diag x_i and w x_j are ~1e4 times b and cancel, the differences do not
+            double rl64 = 0.0;
+            for (int g = tid; g < G; g += T) {
+                const int h = (g / n + 1) * W + g % n + 1;
+                const double xi = x64[h];
+                double acc = w64l[h] * (xi - x64[h - W]);
+                acc = fma(w64l[h + W], xi - x64[h + W], acc);
+                acc = fma(w64d[h], xi - x64[h - 1], acc);
+                acc = fma(w64d[h + 1], xi - x64[h + 1], acc);
+                const double r = b - acc;
+                r64[h] = r;
+                rl64 = fma(r, r, rl64);
+            }
+            const double rr_prev = rr64;
+            block_sum_sqrt(rl64, red64, rr64, nr);
+            ++outer;
+            // At these mesh widths the fp64 residual of the 5-point system has a rounding floor
+            // near 1e-13 relative (the granularity of x times the diagonal, ~1e4 b): an outer
+            // step that no longer halves the residual norm below 1e-11 relative has reached it.
+            if (rr64 > stop && rr64 > 0.25 * rr_prev && rr64 <= 1e-22 * rr0) {
+                at_floor = true;
+                break;
+            }
+        }
+        double* out = a.U + (size_t)sys * G;
+        for (int g = tid; g < G; g += T) out[g] = x64[((g % n) + 1) * W + (g / n) + 1];   // g = q n + p
+        if (tid == 0) {
+            if (a.iters_out) a.iters_out[sys] = total;
+            if (a.iters_sum) atomicAdd(a.iters_sum, (unsigned long long)total);
+            if (a.outer_sum) atomicAdd(a.outer_sum, (unsigned long long)outer);
+            if (rr64 > stop && !at_floor && a.fail_count) atomicAdd(a.fail_count, 1u);
+        }
+        __syncthreads();
+    }
+}
+
+size_t big_smem_bytes(int n, int d) { return big_layout(n, d, (n + 15) / 16 * 16).total; }
+static const size_t kMaxBigSmem = 232448;    // 227 KB of dynamic shared memory per CTA
+
+static void (*big_kernel_for(int n))(Pcg2dArgs) {
+    switch ((n + 15) / 16 * 16) {
+        case 64: return pcg2d_mixed_big_kernel<64>;
+        case 80: return pcg2d_mixed_big_kernel<80>;
+        case 96: return pcg2d_mixed_big_kernel<96>;
+        case 112: return pcg2d_mixed_big_kernel<112>;
+        case 128: return pcg2d_mixed_big_kernel<128>;
+        default: return nullptr;
+    }
+}
+
+cudaError_t launch_mixed_big(const Pcg2dArgs& a, int blocks, cudaStream_t s) {
+    void (*k)(Pcg2dArgs) = big_kernel_for(a.n);
+    const size_t smem = big_smem_bytes(a.n, a.ns.d);
+    if (!k || smem > kMaxBigSmem) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<blocks, 1024, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 size_t dst_smem_bytes(int n, int d) { return dst_layout(n, d).total; }
 
 // the kernel instance for (NPT, P = n rounded up to 16); nullptr for a pair no n produces

@@ -97,6 +97,8 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
                              unsigned int* fail_count, unsigned long long* iters_sum, double* scratch,
                              size_t scratch_bytes, cudaStream_t s, int* launches);
 size_t sample_2d_scratch_bytes(int n, int precision, int blocks);
+// shared memory of the large-mesh (n > 63) MIXED kernel; at most 232448 bytes can be launched
+size_t big_smem_bytes(int n, int d);
 int sample_2d_default_blocks(int n, int precision);
 
 // TRIGPOLY black box: U[i][g] = Re sum_s c_{g,s} exp(2 pi i h_{g,s} . y_i)
