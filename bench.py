@@ -505,6 +505,17 @@ def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind):
     stat_bytes = 16.0 * G * nI
     stat_gbs = stat_bytes / (ms_stat / 1e3) / 1e9
 
+    # the 128 x 128 mesh (16129 nodes, lognormal-type coefficient, d = 20): increments 1..3, mixed
+    w3 = W.c3(1)
+    p3 = binding.Plan(w3.problem, w3.params)
+    c3 = []
+    for _ in range(3):
+        info = p3.increment()
+        c3.append({"t": info["t"], "M": info["M"], "samples": info["samples"], "n_detected": info["n_detected"],
+                   "ms_device": info["ms_device"], "cg_iters_max": info["cg_iters_max"],
+                   "lattice_samples_per_s": info["samples"] / (info["ms_device"] / 1e3)})
+    p3.close()
+
     # random rank-1 lattices on the same workload (increments 1..d)
     prr = binding.Plan(w.problem, dataclasses.replace(W.with_precision(w, W.PRECISION_MIXED).params, rr_lattices=5,
                                                       rr_size_factor=2.0))
@@ -529,6 +540,9 @@ def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind):
                      "kernel": "evaluate_kernel (fp64 complex contraction, E formed on chip)"},
         "errors": {"n": n_test, "ms": ms_err, "err2_max": float(np.max(e2)), "errinf_max": float(np.max(ei)),
                    "err2_median": float(np.median(e2))},
+        "mesh_128x128": {"workload": "2-D P1 FE 127x127 interior (G=16129), lognormal-type coefficient, d=20, "
+                                     "Gamma=[-32,32]^20, s=1000, delta=1e-10 relative, r=2, mixed precision "
+                                     "(large-mesh sampler)", "increments": c3},
         "random_r1l": {"lattices": 5, "size_factor": 2.0, "precision": "mixed", "increments": rr,
                        "samples_total": int(sum(r["samples"] for r in rr)),
                        "ms_device_total": float(sum(r["ms_device"] for r in rr))},
