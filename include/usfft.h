@@ -305,6 +305,18 @@ usfft_status usfft_get_random_lattices(const usfft_plan_t* plan, int64_t* z, int
 /* Message of the last failure of this plan (plan == NULL: of the calling thread). */
 const char* usfft_last_error(const usfft_plan_t* plan);
 
+/* Device bytes the plan holds now (its buffers grow with the lattice sizes it meets). */
+size_t usfft_plan_bytes(const usfft_plan_t* plan);
+
+/* The batched form: one increment (usfft_increment) of each of `count` distinct plans at
+ * once.  The host work of the plans runs in up to max_threads threads (0: one per hardware
+ * thread) and their device work overlaps on the plans' streams, so the plans should have been
+ * created on distinct streams.  statuses[k] and infos[k] (infos may be NULL) receive plan k's
+ * result, which is the one the plan gives alone; the return value is the first non-OK status
+ * in plan order (USFFT_EINVAL for a NULL or repeated plan, nothing run). */
+usfft_status usfft_increment_many(usfft_plan_t* const* plans, int count, int max_threads,
+                                  usfft_increment_info* infos, usfft_status* statuses);
+
 /* Free every device buffer and the plan.  NULL is ignored. */
 void usfft_destroy(usfft_plan_t* plan);
 

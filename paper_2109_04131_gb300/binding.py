@@ -7,7 +7,7 @@ current PyTorch stream unless another stream is given.
 
 Module-level functions carry the C names (usfft_plan, usfft_increment, usfft_replay,
 usfft_rewind, usfft_resume, usfft_get_set, usfft_reconstruct, usfft_sample_points, usfft_evaluate,
-usfft_errors, usfft_statistics, usfft_get_lattice, usfft_get_candidates,
+usfft_errors, usfft_statistics, usfft_plan_bytes, usfft_increment_many, usfft_get_lattice, usfft_get_candidates,
 usfft_get_samples, usfft_get_coefficients, usfft_get_selection, usfft_last_error,
 usfft_destroy); ``Plan`` wraps them.
 """
@@ -83,6 +83,9 @@ SIGNATURES = {
     "usfft_get_coefficients": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "usfft_get_selection": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
     "usfft_last_error": (ctypes.c_char_p, [_P]),
+    "usfft_plan_bytes": (ctypes.c_size_t, [_P]),
+    "usfft_increment_many": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(UsfftIncrementInfo), ctypes.POINTER(ctypes.c_int)]),
     "usfft_destroy": (None, [_P]),
     "usfft_version": (ctypes.c_char_p, []),
     "usfft_search_lattice": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
@@ -236,6 +239,25 @@ def usfft_statistics(plan):
     return plan.statistics()
 
 
+def usfft_plan_bytes(plan):
+    return plan.bytes()
+
+
+def usfft_increment_many(plans, max_threads=0):
+    """One increment of every plan at once (the batched form): (infos, statuses), one entry per
+    plan; no exception for a failed plan, its status says so."""
+    lib = load_library()
+    n = len(plans)
+    handles = (_P * max(n, 1))(*[p.handle for p in plans])
+    infos = (UsfftIncrementInfo * max(n, 1))()
+    sts = (ctypes.c_int * max(n, 1))()
+    st = lib.usfft_increment_many(handles, n, int(max_threads), infos, sts)
+    if st == 1 and n and all(v == 0 for v in sts[:n]):
+        _check(st, None)                                   # rejected before running (NULL / repeated plan)
+    out = [{name: getattr(infos[k], name) for name, _ in UsfftIncrementInfo._fields_} for k in range(n)]
+    return out, [int(v) for v in sts[:n]]
+
+
 def usfft_get_lattice(plan):
     return plan.get_lattice()
 
@@ -346,6 +368,10 @@ class Plan:
 
     def _ck(self, st):
         _check(st, self.handle)
+
+    def bytes(self) -> int:
+        """Device bytes the plan holds now."""
+        return int(self._lib.usfft_plan_bytes(self.handle))
 
     def increment(self) -> dict:
         info = UsfftIncrementInfo()

@@ -1335,6 +1335,8 @@ double usfft_draw_uniform(uint64_t seed, const uint64_t* fields, int nfields) {
     return rng_uniform(seed, fields, nfields);
 }
 
+size_t usfft_plan_bytes(const usfft_plan_t* plan) { return plan ? plan->bytes : 0; }
+
 void usfft_destroy(usfft_plan_t* plan) {
     if (!plan) return;
     cudaStreamSynchronize(plan->stream);

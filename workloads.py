@@ -240,3 +240,44 @@ def with_map(w: "Workload", theta_map: int, alpha: float = -1.0, beta: float = 1
     """The same workload with another parameter map (Sec. 3.2)."""
     p = replace(w.problem, theta_map=theta_map, map_alpha=alpha, map_beta=beta, map_shift=shift)
     return replace(w, problem=p)
+
+
+def batch_instances(count: int = 64, seed: int = 42, N: int = 16):
+    """Independent instances shaped like the batching configuration: d ~ U{5..30}, meshes
+    n ~ U{31..127} per side (2-D), s ~ U{100..2000}, affine or lognormal-type coefficient with
+    probability 1/2 each; the mixed precision mode (the only one for n > 63).  Returns
+    [(Workload, increments)], three increments each."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 4]))
+    out = []
+    for k in range(count):
+        d = int(rng.integers(5, 31))
+        n = int(rng.integers(31, 128))
+        s = int(rng.integers(100, 2001))
+        logn = bool(rng.integers(0, 2))
+        prob = Problem(kind=PDE_2D, n=n, d=d, coef_model=COEF_LOGNORMAL_SIN if logn else COEF_AFFINE_SIN,
+                       coef_scale=0.5 if logn else 0.9 * 6.0 / math.pi ** 2)
+        par = Params(N=N, s=s, s_local=s, delta=1e-10, delta_is_relative=True, r=2, seed=seed * 1000 + k,
+                     precision=PRECISION_MIXED)
+        out.append((Workload(f"batch_{k}_n{n}_d{d}", prob, par), 3))
+    return out
+
+
+def serving_requests(count: int, rate: float = 200.0, seed: int = 7):
+    """A seeded Poisson stream shaped like the serving configuration: half 128x128-mesh
+    lognormal instances (d = 20, s = 1000, two increments), half 1-D instances with 255 nodes
+    (d ~ U{4..20}, all d increments).  Returns [(arrival_s, Workload, increments, reserve_bytes)]."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 5]))
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        if rng.random() < 0.5:
+            w = c3(seed * 10000 + k)
+            out.append((t, w, 2, 2 << 30))
+        else:
+            d = int(rng.integers(4, 21))
+            prob = Problem(kind=PDE_1D, n=255, d=d)
+            par = Params(N=16, s=50, s_local=50, delta=1e-12, delta_is_relative=True, r=1, seed=seed * 10000 + k,
+                         precision=PRECISION_MIXED)
+            out.append((t, Workload(f"serve_1d_{k}_d{d}", prob, par), d, 64 << 20))
+    return out
