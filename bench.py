@@ -457,7 +457,35 @@ def e2e_measure(plan, t, steps, barrier, world, dev):
                     "search, both detection iterations, host copies)"}
 
 
-def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind):
+def serving_measure(kind, count):
+    """Batched ("batch": `count` independent instances shaped like the batching configuration, all
+    present at the start, three increments each) or served ("serve": a seeded Poisson stream of
+    `count` requests at 200/s, half 128x128-mesh lognormal instances, half 1-D 255-node
+    instances, admitted within a 150 GB budget) against the same requests run one at a time."""
+    import torch
+    from paper_2109_04131_gb300 import binding, serving
+    if kind == "batch":
+        reqs = [serving.Request(k, 0.0, w, inc, 1 << 30) for k, (w, inc) in enumerate(W.batch_instances(count))]
+    else:
+        reqs = [serving.Request(k, t, w, inc, res) for k, (t, w, inc, res) in enumerate(W.serving_requests(count))]
+
+    def make_plan(r):
+        return binding.Plan(r.workload.problem, r.workload.params, stream=torch.cuda.Stream().cuda_stream)
+
+    srv = serving.Server(budget_bytes=150 << 30, make_plan=make_plan, increment_many=binding.usfft_increment_many)
+    rep = srv.run(reqs)
+    torch.cuda.synchronize()
+    alone = serving.run_one_at_a_time(reqs, lambda r: binding.Plan(r.workload.problem, r.workload.params))
+    rep.pop("instances")
+    alone.pop("results")
+    return {"requests": count, "served": rep, "one_at_a_time": alone,
+            "speedup_samples_per_s": rep["samples_per_s"] / alone["samples_per_s"] if alone["samples_per_s"] else None,
+            "precision": "mixed",
+            "note": "one-at-a-time runs the same requests in arrival order without overlap; the fp64 2-D path "
+                    "covers n <= 63 only, so both forms use the mixed precision mode"}
+
+
+def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind, n_batch=32, n_serve=200):
     """The rows past the detection increment, on the same workload: the remaining increments
     t0+1..d of the mixed plan (single reconstructing lattice per step), step 3 (usfft_reconstruct),
     the quantities of interest (usfft_statistics), FE solves at n_test random parameters and the
@@ -516,6 +544,10 @@ def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind):
                    "lattice_samples_per_s": info["samples"] / (info["ms_device"] / 1e3)})
     p3.close()
 
+    # batched and served forms (continuous batching through usfft_increment_many)
+    batching = serving_measure("batch", n_batch)
+    served = serving_measure("serve", n_serve)
+
     # random rank-1 lattices on the same workload (increments 1..d)
     prr = binding.Plan(w.problem, dataclasses.replace(W.with_precision(w, W.PRECISION_MIXED).params, rr_lattices=5,
                                                       rr_size_factor=2.0))
@@ -543,6 +575,8 @@ def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind):
         "mesh_128x128": {"workload": "2-D P1 FE 127x127 interior (G=16129), lognormal-type coefficient, d=20, "
                                      "Gamma=[-32,32]^20, s=1000, delta=1e-10 relative, r=2, mixed precision "
                                      "(large-mesh sampler)", "increments": c3},
+        "batching": batching,
+        "serving": served,
         "random_r1l": {"lattices": 5, "size_factor": 2.0, "precision": "mixed", "increments": rr,
                        "samples_total": int(sum(r["samples"] for r in rr)),
                        "ms_device_total": float(sum(r["ms_device"] for r in rr))},

@@ -181,7 +181,7 @@ cudaError_t launch_evaluate(const double* Y, int64_t n, int d, const ParamMap& p
     if (n <= 0 || G <= 0) return cudaSuccess;
     if (n > evaluate_max_points()) return cudaErrorInvalidValue;
     const size_t smem = eval_smem_bytes(d);
-    cudaError_t e = cudaFuncSetAttribute(evaluate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dyn_smem((const void*)evaluate_kernel, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((G + TG - 1) / TG), (unsigned)((n + TJ - 1) / TJ));
     evaluate_kernel<<<grid, NT, smem, s>>>(Y, n, d, pm, I, nI, C, G, V, Uchk, part_sum, part_max);

@@ -495,7 +495,7 @@ static cudaError_t launch_fft_impl(const FftPlan& p, int G, const double* U, con
         a.out_outer = 1;
         a.nst = factorize(a.L, a.radix);
         const size_t smem = pass_smem(a.L, a.Gt);
-        e = cudaFuncSetAttribute(fft_pass1_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_dyn_smem((const void*)fft_pass1_kernel<A>, smem);
         if (e != cudaSuccess) return e;
         const int ntile = (a.Gp + a.Gt - 1) / a.Gt;
         fft_pass1_kernel<A><<<(unsigned)((int64_t)a.nOuter * ntile), kFftThreads, smem, s>>>(a, W);
@@ -521,7 +521,7 @@ static cudaError_t launch_fft_impl(const FftPlan& p, int G, const double* U, con
     b.C = C;
     b.nst = factorize(b.L, b.radix);
     const size_t smem = pass_smem(b.L, (b.L1 > 2 ? 2 : 1) * b.Gt);
-    e = cudaFuncSetAttribute(fft_final_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_dyn_smem((const void*)fft_final_kernel<A>, smem);
     if (e != cudaSuccess) return e;
     const int ntile = (b.Gp + b.Gt - 1) / b.Gt;
     fft_final_kernel<A><<<(unsigned)((int64_t)b.nOuter * ntile), kFftThreads, smem, s>>>(b, W);

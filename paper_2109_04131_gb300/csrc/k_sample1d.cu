@@ -184,8 +184,7 @@ cudaError_t launch_sample_1d(const NodeSpec& ns, int n, int coef_model, double f
     if (warps < 1) warps = 1;
     size_t smem = per_warp * warps;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sample_1d_cr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = allow_dyn_smem((const void*)sample_1d_cr_kernel, smem);
         if (e != cudaSuccess) return e;
     }
     int64_t blocks = (count + warps - 1) / warps;

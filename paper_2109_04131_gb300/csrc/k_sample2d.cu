@@ -359,11 +359,11 @@ static int resident_blocks(int precision, int threads, int n) {
     int per_sm = 0;
     cudaError_t e;
     if (precision == USFFT_MIXED_JACOBI) {
-        e = cudaFuncSetAttribute(pcg2d_mixed_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_dyn_smem((const void*)pcg2d_mixed_kernel<NPT>, smem);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg2d_mixed_kernel<NPT>, threads, smem);
     } else {
-        e = cudaFuncSetAttribute(pcg2d_fp64_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_dyn_smem((const void*)pcg2d_fp64_kernel<NPT>, smem);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg2d_fp64_kernel<NPT>, threads, smem);
     }
@@ -417,11 +417,11 @@ static cudaError_t launch_npt(const Pcg2dArgs& a, int precision, int blocks, int
     const size_t smem = smem_bytes(a.n, a.ns.d);
     cudaError_t e;
     if (precision == USFFT_MIXED_JACOBI) {
-        e = cudaFuncSetAttribute(pcg2d_mixed_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_dyn_smem((const void*)pcg2d_mixed_kernel<NPT>, smem);
         if (e != cudaSuccess) return e;
         pcg2d_mixed_kernel<NPT><<<blocks, threads, smem, s>>>(a);
     } else {
-        e = cudaFuncSetAttribute(pcg2d_fp64_kernel<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_dyn_smem((const void*)pcg2d_fp64_kernel<NPT>, smem);
         if (e != cudaSuccess) return e;
         pcg2d_fp64_kernel<NPT><<<blocks, threads, smem, s>>>(a);
     }

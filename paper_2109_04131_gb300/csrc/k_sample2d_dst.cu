@@ -875,7 +875,7 @@ cudaError_t launch_mixed_big(const Pcg2dArgs& a, int blocks, cudaStream_t s) {
     void (*k)(Pcg2dArgs) = big_kernel_for(a.n);
     const size_t smem = big_smem_bytes(a.n, a.ns.d);
     if (!k || smem > kMaxBigSmem) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dyn_smem((const void*)k, smem);
     if (e != cudaSuccess) return e;
     k<<<blocks, 1024, smem, s>>>(a);
     return cudaGetLastError();
@@ -906,7 +906,7 @@ cudaError_t launch_dst_npt(const Pcg2dArgs& a, int blocks, int threads, cudaStre
     const size_t smem = dst_smem_bytes(a.n, a.ns.d);
     void (*k)(Pcg2dArgs) = dst_kernel_for<NPT>(a.n);
     if (!k) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dyn_smem((const void*)k, smem);
     if (e != cudaSuccess) return e;
     k<<<blocks, threads, smem, s>>>(a);
     return cudaGetLastError();
@@ -917,7 +917,7 @@ int dst_resident_blocks(int threads, int d, int n) {
     const size_t smem = dst_smem_bytes(n, d);
     int per_sm = 0;
     void (*k)(Pcg2dArgs) = dst_kernel_for<NPT>(n);
-    cudaError_t e = k ? cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+    cudaError_t e = k ? allow_dyn_smem((const void*)k, smem)
                       : cudaErrorInvalidValue;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
     if (e != cudaSuccess) {

@@ -156,7 +156,7 @@ cudaError_t launch_select_union(const double2* C, int G, int64_t nJ, double thet
     cudaError_t e;
     if (nJ <= kMaxSmemKeys) {
         const size_t smem = sizeof(unsigned long long) * (size_t)nJ;
-        e = cudaFuncSetAttribute(select_union_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_dyn_smem((const void*)select_union_kernel<true>, smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_union_kernel<true>, kSelThreads, smem);

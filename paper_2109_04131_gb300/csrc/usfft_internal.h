@@ -161,6 +161,10 @@ cudaError_t launch_statistics(const double2* C, int G, int64_t nI, int d, const 
                               const int64_t* offsets, double2* mean, double* var, double* gsi, cudaStream_t s,
                               int* launches);
 
+// Raises the kernel's dynamic shared-memory limit to at least `bytes` (never lowers it: plans
+// launch from several host threads at once); smem_attr.cpp.
+cudaError_t allow_dyn_smem(const void* func, size_t bytes);
+
 // Sets the message usfft_last_error(NULL) returns on the calling thread (capi.cu).
 void set_thread_error(const std::string& msg);
 

@@ -21,10 +21,16 @@ def B():
 
 
 def _instances():
+    # shapes that launch the same kernels with different shared-memory sizes at the same time
+    # (selection over different |J|, FFTs of different lengths, samplers of different meshes)
     return [W.with_precision(W.small_2d(n=15, d=4, seed=2, N=5, s=30), W.PRECISION_MIXED),
             W.with_precision(W.small_2d(n=31, d=3, seed=3, N=4, s=20), W.PRECISION_FP64),
             W.c1(2),
-            W.with_precision(W.small_2d(n=70, d=3, seed=4, N=3, s=10), W.PRECISION_MIXED)]
+            W.with_precision(W.small_2d(n=70, d=3, seed=4, N=3, s=10), W.PRECISION_MIXED),
+            W.with_precision(W.small_2d(n=40, d=4, seed=5, N=8, s=40), W.PRECISION_MIXED),
+            W.with_precision(W.small_2d(n=24, d=3, seed=6, N=12, s=60), W.PRECISION_MIXED),
+            W.c1(5),
+            W.with_precision(W.small_2d(n=9, d=5, seed=7, N=6, s=25), W.PRECISION_FP64)]
 
 
 def _plan(B, w):
