@@ -305,7 +305,8 @@ usfft_status usfft_get_random_lattices(const usfft_plan_t* plan, int64_t* z, int
 /* Message of the last failure of this plan (plan == NULL: of the calling thread). */
 const char* usfft_last_error(const usfft_plan_t* plan);
 
-/* Device bytes the plan holds now (its buffers grow with the lattice sizes it meets). */
+/* Device bytes the plan holds now (its buffers grow with the lattice sizes it meets).  The one
+ * call that may run while another thread works on the same plan (it reads one counter). */
 size_t usfft_plan_bytes(const usfft_plan_t* plan);
 
 /* The batched form: one increment (usfft_increment) of each of `count` distinct plans at

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -81,7 +82,7 @@ struct usfft_plan_s {
     std::vector<FftPlan> rr_fp;
     std::vector<size_t> rr_goff_at, rr_gk_at, rr_twid_at;
     Buf rr_goff, rr_gk, rr_gm2, rr_src, rr_twid, rr_C;
-    size_t bytes = 0;
+    std::atomic<size_t> bytes{0};   // read by usfft_plan_bytes from other threads
     int cg_blocks = 0;
     int launches = 0;
     int64_t cg_iters_total = 0;
@@ -135,7 +136,7 @@ usfft_status ensure(usfft_plan_t* plan, Buf& b, size_t bytes, const char* what) 
         if (after > plan->par.hbm_budget_bytes) {
             char msg[256];
             snprintf(msg, sizeof msg, "%s: %zu bytes would exceed the budget of %zu bytes (plan holds %zu)", what,
-                     bytes, plan->par.hbm_budget_bytes, plan->bytes);
+                     bytes, plan->par.hbm_budget_bytes, plan->bytes.load());
             return fail(plan, USFFT_ENOMEM, msg);
         }
     }
@@ -1335,7 +1336,7 @@ double usfft_draw_uniform(uint64_t seed, const uint64_t* fields, int nfields) {
     return rng_uniform(seed, fields, nfields);
 }
 
-size_t usfft_plan_bytes(const usfft_plan_t* plan) { return plan ? plan->bytes : 0; }
+size_t usfft_plan_bytes(const usfft_plan_t* plan) { return plan ? plan->bytes.load(std::memory_order_relaxed) : 0; }
 
 void usfft_destroy(usfft_plan_t* plan) {
     if (!plan) return;

@@ -124,6 +124,92 @@ class Server:
         }
 
 
+class AsyncServer:
+    """Continuous batching without a round barrier: every admitted instance runs its increments
+    back to back in a worker thread of its own (the library call releases the interpreter, so
+    the host planning of the instances runs in parallel and their device work overlaps on the
+    plans' streams); a finished instance frees its place and bytes for the next arrival at once.
+    Admission as in Server: arrival order, within the budget and at most max_active at a time."""
+
+    def __init__(self, budget_bytes: int, make_plan: Callable, max_active: int = 64,
+                 clock: Callable = time.perf_counter, collect: Optional[Callable] = None):
+        self.budget = int(budget_bytes)
+        self.make_plan = make_plan
+        self.max_active = max_active
+        self.clock = clock
+        self.collect = collect
+
+    def run(self, requests: List[Request]) -> dict:
+        import threading
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        lock = threading.Condition()
+        active: List[Instance] = []
+        done: List[Instance] = []
+        t0 = self.clock()
+        peak = {"active": 0, "bytes": 0}
+
+        def held():
+            return sum(max(int(i.plan.bytes()), i.req.reserve_bytes) for i in active)
+
+        def work(inst: Instance):
+            for _ in range(inst.req.increments):
+                t1 = self.clock()
+                try:
+                    info = inst.plan.increment()
+                    inst.samples += int(info["samples"])
+                except Exception as exc:          # the library's status, as an exception
+                    inst.status = getattr(exc, "status", -1)
+                    break
+                finally:
+                    inst.increment_latency.append(self.clock() - t1)
+                    inst.done_increments += 1
+            if inst.status == 0 and inst.req.reconstruct:
+                inst.plan.reconstruct()
+            inst.finished = self.clock() - t0
+            if self.collect is not None:
+                inst.result = self.collect(inst)
+            with lock:
+                peak["bytes"] = max(peak["bytes"], held())
+                inst.plan.close()
+                active.remove(inst)
+                done.append(inst)
+                lock.notify_all()
+
+        threads = []
+        with lock:
+            while pending or active:
+                now = self.clock() - t0
+                while (pending and pending[0].arrival <= now and len(active) < self.max_active
+                       and held() + pending[0].reserve_bytes <= self.budget):
+                    r = pending.pop(0)
+                    inst = Instance(r, self.make_plan(r), admitted=self.clock() - t0)
+                    active.append(inst)
+                    peak["active"] = max(peak["active"], len(active))
+                    th = threading.Thread(target=work, args=(inst,), daemon=True)
+                    threads.append(th)
+                    th.start()
+                if pending and not active and pending[0].reserve_bytes > self.budget:
+                    raise ValueError(f"request {pending[0].rid} reserves more than the whole budget")
+                wait = None
+                if pending and pending[0].arrival > now:
+                    wait = pending[0].arrival - now
+                if active or wait is not None:
+                    lock.wait(timeout=wait if wait is not None else 1.0)
+        for th in threads:
+            th.join()
+        wall = self.clock() - t0
+        inc_lat = [x for i in done for x in i.increment_latency]
+        inst_lat = [i.finished - i.req.arrival for i in done]
+        samples = sum(i.samples for i in done)
+        return {
+            "requests": len(done), "failed": sum(1 for i in done if i.status != 0), "rounds": None,
+            "wall_s": wall, "lattice_samples": samples, "samples_per_s": samples / wall if wall > 0 else None,
+            "increment_latency_ms": {"p50": 1e3 * percentile(inc_lat, 50), "p99": 1e3 * percentile(inc_lat, 99)},
+            "instance_latency_ms": {"p50": 1e3 * percentile(inst_lat, 50), "p99": 1e3 * percentile(inst_lat, 99)},
+            "peak_active": peak["active"], "peak_bytes": peak["bytes"], "instances": done,
+        }
+
+
 def run_one_at_a_time(requests: List[Request], make_plan: Callable, collect: Optional[Callable] = None,
                       clock: Callable = time.perf_counter) -> dict:
     """The requests in arrival order, each run alone to completion (no batching, no overlap)."""

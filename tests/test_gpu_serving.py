@@ -81,3 +81,24 @@ def test_served_results_equal_one_at_a_time(B):
         s2, c2 = alone["results"][inst.req.rid]
         assert np.array_equal(s1, s2) and np.array_equal(c1, c2)
     assert rep["lattice_samples"] == alone["lattice_samples"]
+
+
+def test_async_served_results_equal_one_at_a_time(B):
+    from paper_2109_04131_gb300 import serving
+    ws = _instances()
+    reqs = [serving.Request(k, 0.0005 * k, w, w.problem.d if k % 2 == 0 else 2, 256 << 20,
+                            reconstruct=(k % 2 == 0)) for k, w in enumerate(ws)]
+
+    def make_plan(r):
+        return _plan(B, r.workload)
+
+    def collect(inst):
+        return inst.plan.get_set(), inst.plan.get_coefficients()
+
+    rep = serving.AsyncServer(budget_bytes=8 << 30, make_plan=make_plan, max_active=5, collect=collect).run(reqs)
+    assert rep["requests"] == len(ws) and rep["failed"] == 0 and 2 <= rep["peak_active"] <= 5
+    alone = serving.run_one_at_a_time(reqs, make_plan, collect=collect)
+    for inst in rep["instances"]:
+        s1, c1 = inst.result
+        s2, c2 = alone["results"][inst.req.rid]
+        assert np.array_equal(s1, s2) and np.array_equal(c1, c2)

@@ -128,3 +128,28 @@ def test_workload_generators_are_seeded_and_shaped():
             assert w.problem.n == 255 and 4 <= w.problem.d <= 20 and inc == w.problem.d
     bi = W.batch_instances(64, seed=42)
     assert len(bi) == 64 and all(5 <= w.problem.d <= 30 and 31 <= w.problem.n <= 127 for w, _ in bi)
+
+
+def test_async_server_admission_and_completion():
+    import threading
+    import time as _t
+    log = []
+    lock = threading.Lock()
+
+    class P(FakePlan):
+        def increment(self):
+            _t.sleep(0.002 * (1 + self.req.rid % 3))
+            return super().increment()
+
+    def make_plan(r):
+        with lock:
+            log.append(("admit", r.rid))
+        return P(r, log, 0)
+
+    srv = serving.AsyncServer(budget_bytes=100, make_plan=make_plan, max_active=3)
+    reqs = [req(k, 0.001 * k, 2 + k % 3, 30) for k in range(10)]
+    rep = srv.run(reqs)
+    assert rep["requests"] == 10 and rep["failed"] == 0 and rep["peak_active"] <= 3
+    assert [e[1] for e in log if e[0] == "admit"] == list(range(10))
+    assert rep["lattice_samples"] == 10 * sum(2 + k % 3 for k in range(10))
+    assert all(len(i.increment_latency) == i.req.increments for i in rep["instances"])
