@@ -70,6 +70,8 @@ struct usfft_plan_s {
     FftPlan fp{};
     // device buffers
     Buf psi, U, C, bitmap, twid, goff, gk, gm2, fftscr, cgscr, iters, failc, scal, tpf, tpc, tpaux;
+    Buf fpos, fmk;            // single in-place FFT pass: digit-reversed positions, candidates' m_k
+    bool inplace = false;
     // step 3 result (usfft_reconstruct) and the buffers of point evaluation
     Buf Crec, Irec, Ypts, Upts, Vpts, epart, etot;
     int64_t nrec = -1;     // |I| of the stored reconstruction, -1: none
@@ -348,6 +350,19 @@ usfft_status prepare_step(usfft_plan_t* plan, int64_t M, const std::vector<int64
         bk[(size_t)e] = (int)k;
         bm2[(size_t)e] = (int)(m[(size_t)k] / L1);
     }
+    // the single in-place FFT pass when the lattice fits on chip
+    const std::vector<int> pos = fft_inplace_positions(M);
+    plan->inplace = !pos.empty();
+    std::vector<int> mk32;
+    if (plan->inplace) {
+        mk32.resize((size_t)std::max<int64_t>(nJ, 1));
+        for (int64_t k = 0; k < nJ; ++k) mk32[(size_t)k] = (int)m[(size_t)k];
+        if ((st = ensure(plan, plan->fpos, sizeof(int) * pos.size(), "fft positions")) != USFFT_OK) return st;
+        if ((st = ensure(plan, plan->fmk, sizeof(int) * mk32.size(), "candidate indices")) != USFFT_OK) return st;
+        CK(cudaMemcpyAsync(plan->fpos.p, pos.data(), sizeof(int) * pos.size(), cudaMemcpyHostToDevice, plan->stream));
+        CK(cudaMemcpyAsync(plan->fmk.p, mk32.data(), sizeof(int) * mk32.size(), cudaMemcpyHostToDevice, plan->stream));
+        plan->h2d += (int64_t)(sizeof(int) * (pos.size() + mk32.size()));
+    }
     if ((st = ensure(plan, plan->goff, sizeof(int) * off.size(), "gather offsets")) != USFFT_OK) return st;
     if ((st = ensure(plan, plan->gk, sizeof(int) * (size_t)std::max<int64_t>(nJ, 1), "gather k")) != USFFT_OK) return st;
     if ((st = ensure(plan, plan->gm2, sizeof(int) * (size_t)std::max<int64_t>(nJ, 1), "gather m2")) != USFFT_OK) return st;
@@ -514,6 +529,10 @@ usfft_status run_step_device(usfft_plan_t* plan, bool first_1d_sets_theta) {
     CK(cudaMemsetAsync(plan->bitmap.p, 0, sizeof(uint32_t) * (size_t)((nJ + 31) / 32), plan->stream));
     if (nJ == 0) return USFFT_OK;
     GatherPlan gp{(const int*)plan->goff.p, (const int*)plan->gk.p, (const int*)plan->gm2.p};
+    if (plan->inplace) {
+        gp.pos_of = (const int*)plan->fpos.p;
+        gp.mk = (const int*)plan->fmk.p;
+    }
     for (size_t it = 0; it < plan->specs.size(); ++it) {
         usfft_status st = run_sampler(plan, plan->specs[it]);
         if (st != USFFT_OK) return st;
@@ -1345,7 +1364,8 @@ void usfft_destroy(usfft_plan_t* plan) {
                    &plan->gk,    &plan->gm2,  &plan->fftscr, &plan->cgscr, &plan->iters, &plan->failc,
                    &plan->scal,  &plan->tpf,  &plan->tpc,  &plan->tpaux, &plan->Crec, &plan->Irec,
                    &plan->Ypts,  &plan->Upts, &plan->Vpts, &plan->epart, &plan->etot, &plan->rr_goff,
-                   &plan->rr_gk, &plan->rr_gm2, &plan->rr_src, &plan->rr_twid, &plan->rr_C};
+                   &plan->rr_gk, &plan->rr_gm2, &plan->rr_src, &plan->rr_twid, &plan->rr_C, &plan->fpos,
+                   &plan->fmk};
     for (Buf* b : bufs) buf_free(plan, *b);
     if (plan->pinned) cudaFreeHost(plan->pinned);
     if (plan->ev0) cudaEventDestroy(plan->ev0);

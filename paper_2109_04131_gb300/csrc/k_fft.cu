@@ -34,6 +34,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <vector>
+
 #include "usfft_internal.h"
 
 namespace usfft {
@@ -416,6 +418,161 @@ __global__ void __launch_bounds__(kFftThreads) fft_final_kernel(const __grid_con
     }
 }
 
+// ---- single pass, in place (lattices that fit on chip) ---------------------------------------
+// The whole length-M transform of CP packed column pairs in shared memory, in place: the samples
+// are loaded at their mixed-radix digit-reversed positions (pos_of[i], host-computed), then
+// decimation-in-time stages of radix R (8, 4, 2, 3 in registers, others by a direct DFT)
+// combine sub-transforms of length L into L R, leaving the spectrum in natural order; the
+// gather then reads Z[m_k] and Z[M - m_k] per candidate and writes C[g][k] with consecutive
+// threads on consecutive k (coalesced).  Twiddles W_M^e = T1[e mod B] T2[e div B] from two
+// small shared tables.  No intermediate array in HBM: the samples are read once and the
+// coefficients written once.
+static const int kInplaceThreads = 512;
+static const int kTwB = 128;
+
+template <class A>
+__device__ __forceinline__ typename A::C tw_pair(const typename A::C* T1, const typename A::C* T2, int64_t e) {
+    const int r = (int)(e % kTwB), q = (int)(e / kTwB);
+    if (q == 0) return T1[r];
+    if (r == 0) return T2[q];
+    return A::mul(T1[r], T2[q]);
+}
+
+// one radix-R decimation-in-time butterfly of the in-place pass (compile-time R: registers)
+template <class A, int R>
+__device__ __forceinline__ void inplace_butterfly(typename A::C* buf, int base, int L, int CP, int c, int j,
+                                                  int64_t estep, int M, const typename A::C* T1,
+                                                  const typename A::C* T2) {
+    typedef typename A::C C;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        v[r] = buf[(base + r * L) * CP + c];
+        if (r > 0 && j > 0) v[r] = A::mul(v[r], tw_pair<A>(T1, T2, (int64_t)j * r * estep));
+    }
+    if (R == 8) dft8<A>(v);
+    else if (R == 4) dft4<A>(v);
+    else if (R == 2) dft2<A>(v);
+    else if (R == 3) dft3<A>(v);
+    else {   // direct DFT of length R: out[k] = sum_r v[r] W_R^{rk}, W_R = W_M^(M/R)
+        C out[R];
+        const int64_t unit = M / R;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            C acc = v[0];
+#pragma unroll
+            for (int r = 1; r < R; ++r) acc = A::add(acc, A::mul(v[r], tw_pair<A>(T1, T2, (int64_t)((r * k) % R) * unit)));
+            out[k] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = out[k];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[(base + r * L) * CP + c] = v[r];
+}
+
+template <class A>
+__global__ void __launch_bounds__(kInplaceThreads) fft_inplace_kernel(const __grid_constant__ FftArgs a,
+                                                                        const typename A::C* W, const int* pos_of,
+                                                                        const int* mk, int CP) {
+    typedef typename A::C C;
+    extern __shared__ __align__(16) unsigned char fraw[];
+    const int M = (int)a.M;
+    const int nT2 = (M + kTwB - 1) / kTwB;
+    C* buf = reinterpret_cast<C*>(fraw);
+    C* T1 = buf + (size_t)M * CP;
+    C* T2 = T1 + kTwB;
+    const int c0 = blockIdx.x * CP;                        // first column pair of this CTA
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int r = tid; r < kTwB; r += T) T1[r] = r < M ? __ldg(W + r) : A::zero();
+    for (int q = tid; q < nT2; q += T) T2[q] = __ldg(W + (int64_t)q * kTwB);
+    // load at the digit-reversed positions
+    for (int idx = tid; idx < M * CP; idx += T) {
+        const int i = idx / CP, c = idx - i * CP, g = 2 * (c0 + c);
+        const double x = (c0 + c < a.Gp && g < a.G) ? __ldcs(a.Ur + (int64_t)i * a.G + g) : 0.0;
+        const double y = (c0 + c < a.Gp && g + 1 < a.G) ? __ldcs(a.Ur + (int64_t)i * a.G + g + 1) : 0.0;
+        buf[pos_of[i] * CP + c] = A::pair(x, y);
+    }
+    __syncthreads();
+    int L = 1;
+    for (int st = 0; st < a.nst; ++st) {
+        const int R = a.radix[st];
+        const int LR = L * R;
+        const int64_t estep = M / LR;                      // W_{LR}^1 = W_M^(M / LR)
+        const int nb = M / R;                               // butterflies per column pair
+        for (int item = tid; item < nb * CP; item += T) {
+            const int c = item % CP, bt = item / CP;
+            const int j = bt % L, base = (bt / L) * LR + j;
+            switch (R) {
+                case 8: inplace_butterfly<A, 8>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
+                case 4: inplace_butterfly<A, 4>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
+                case 2: inplace_butterfly<A, 2>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
+                case 3: inplace_butterfly<A, 3>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
+                case 5: inplace_butterfly<A, 5>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
+                default: inplace_butterfly<A, 7>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
+            }
+        }
+        __syncthreads();
+        L = LR;
+    }
+    // gather and unpack: C[g][k] for the candidates, consecutive threads on consecutive k
+    const double s_half = 0.5 * a.scale;
+    const float s_hi = __double2float_rn(s_half);
+    const float s_lo = __double2float_rn(s_half - (double)s_hi);
+    for (int idx = tid; idx < (int)a.nJ * CP; idx += T) {
+        const int c = idx / (int)a.nJ, k = idx - c * (int)a.nJ;
+        if (c0 + c >= a.Gp) continue;
+        const int m = mk[k];
+        const int mp = m == 0 ? 0 : M - m;
+        double2 even, odd;
+        A::unpack(buf[m * CP + c], buf[mp * CP + c], s_half, s_hi, s_lo, even, odd);
+        const int g = 2 * (c0 + c);
+        a.C[(int64_t)g * a.nJ + k] = even;
+        if (g + 1 < a.G) a.C[(int64_t)(g + 1) * a.nJ + k] = odd;
+    }
+}
+
+// one column pair per CTA (110 KB at M = 6912: two CTAs per SM) measured faster than two
+static int inplace_cp(int64_t M) {
+    const size_t tables = sizeof(double2) * (size_t)(kTwB + (M + kTwB - 1) / kTwB);
+    return sizeof(double2) * (size_t)M + tables <= 232448 ? 1 : 0;
+}
+
+static int factorize(int L, int* radix);
+
+// positions of the single in-place pass: input row i goes to pos_of[i] (mixed-radix digit
+// reversal for the stage radices); empty when M does not fit on chip
+std::vector<int> fft_inplace_positions(int64_t M) {
+    std::vector<int> pos;
+    if (M < 1 || inplace_cp(M) == 0) return pos;
+    int radix[32];
+    const int S = factorize((int)M, radix);
+    for (int st = 0; st < S; ++st)            // the butterflies exist for these radices only
+        if (radix[st] != 2 && radix[st] != 3 && radix[st] != 4 && radix[st] != 5 && radix[st] != 7 && radix[st] != 8)
+            return pos;
+    // position p holds input index perm[p]: the input splits by i mod R_last, recursively
+    std::vector<int> perm((size_t)M), tmp((size_t)M);
+    for (int64_t i = 0; i < M; ++i) perm[(size_t)i] = (int)i;
+    // build perm by repeatedly splitting blocks (outermost split uses the last radix)
+    int64_t blocks = 1, len = M;
+    for (int s = S - 1; s >= 0; --s) {
+        const int R = radix[s];
+        const int64_t sub = len / R;
+        for (int64_t b = 0; b < blocks; ++b) {
+            const int* src = perm.data() + b * len;
+            int* dst = tmp.data() + b * len;
+            for (int r = 0; r < R; ++r)
+                for (int64_t q = 0; q < sub; ++q) dst[r * sub + q] = src[r + q * R];
+        }
+        perm.swap(tmp);
+        blocks *= R;
+        len = sub;
+    }
+    pos.assign((size_t)M, 0);
+    for (int64_t p = 0; p < M; ++p) pos[(size_t)perm[(size_t)p]] = (int)p;
+    return pos;
+}
+
 FftPlan make_fft_plan(int64_t M) {
     FftPlan p;
     p.M = M;
@@ -471,7 +628,6 @@ static cudaError_t launch_fft_impl(const FftPlan& p, int G, const double* U, con
                                    const GatherPlan& gp, int64_t nJ, void* scratch, double2* C, cudaStream_t s,
                                    int* launches) {
     if (p.M <= 0 || nJ <= 0) return cudaSuccess;
-    if (p.L2 <= 0) return cudaErrorInvalidValue;
     FftArgs a;
     memset(&a, 0, sizeof(a));
     a.G = G;
@@ -480,6 +636,20 @@ static cudaError_t launch_fft_impl(const FftPlan& p, int G, const double* U, con
     a.nJ = nJ;
     a.scale = 1.0 / (double)p.M;
     cudaError_t e;
+    const int cp = (gp.pos_of && gp.mk) ? inplace_cp(p.M) : 0;
+    if (cp > 0) {
+        a.Ur = U;
+        a.C = C;
+        a.nst = factorize((int)p.M, a.radix);
+        const size_t smem = sizeof(typename A::C) * ((size_t)p.M * cp + kTwB + (p.M + kTwB - 1) / kTwB);
+        e = allow_dyn_smem((const void*)fft_inplace_kernel<A>, smem);
+        if (e != cudaSuccess) return e;
+        const int blocks = (a.Gp + cp - 1) / cp;
+        fft_inplace_kernel<A><<<blocks, kInplaceThreads, smem, s>>>(a, W, gp.pos_of, gp.mk, cp);
+        if (launches) ++*launches;
+        return cudaGetLastError();
+    }
+    if (p.L2 <= 0) return cudaErrorInvalidValue;
     const bool two = p.L1 > 1;
     if (two) {
         // pass 1: length L1 over i1 (rows i1 L2 + i2), outer index i2

@@ -112,7 +112,13 @@ struct GatherPlan {        // buckets of candidates by m mod L1 (CSR), entries (
     const int* offsets;    // [L1 + 1]
     const int* k;          // [nJ]
     const int* m2;         // [nJ]
+    // the single in-place pass (optional): input row i at position pos_of[i] ([M]); the
+    // candidates' DFT indices m_k ([nJ]); both NULL for the bucketed passes only
+    const int* pos_of = nullptr;
+    const int* mk = nullptr;
 };
+// pos_of of the single in-place pass for lattice size M (empty if M does not fit on chip)
+std::vector<int> fft_inplace_positions(int64_t M);
 FftPlan make_fft_plan(int64_t M);
 size_t fft_scratch_bytes(const FftPlan& p, int G);
 // W[j] = e^{-2 pi i j / M}: fp64 (double2) or double-float (float4 = re.hi, re.lo, im.hi, im.lo)
