@@ -33,10 +33,17 @@ __device__ __forceinline__ void set_bit(uint32_t* bitmap, int64_t k) {
 // when theta = 0).  With KEYS_IN_SMEM the keys of a node are computed once (three fp64
 // operations per candidate) into shared memory and every radix pass is integer work;
 // otherwise (more candidates than fit) they are recomputed from C in every pass.
+// The union of a CTA's nodes is collected in a shared-memory bitmap (sbits, when it fits) and
+// OR-ed into the global one once at the end: every node sets up to s~ bits, mostly the same
+// frequencies, and one global atomic per bit would contend on a few words of L2.
 template <bool KEYS_IN_SMEM>
 __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2* C, int G, int64_t nJ,
-                                                                     double theta2, int s_tilde, uint32_t* bitmap) {
+                                                                     double theta2, int s_tilde, uint32_t* bitmap,
+                                                                     bool local_bits) {
     extern __shared__ unsigned long long skeys[];
+    const int64_t nwords = (nJ + 31) / 32;
+    uint32_t* sbits = reinterpret_cast<uint32_t*>(skeys + (KEYS_IN_SMEM ? nJ : 0));
+    uint32_t* bits = local_bits ? sbits : bitmap;
     __shared__ unsigned int hist[256];
     __shared__ unsigned long long sh_prefix;
     __shared__ unsigned int sh_want;
@@ -44,6 +51,10 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
     __shared__ unsigned int sh_total;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = blockDim.x >> 5;
+    if (local_bits) {
+        for (int64_t w = tid; w < nwords; w += blockDim.x) sbits[w] = 0u;
+        __syncthreads();
+    }
 
     for (int g = blockIdx.x; g < G; g += gridDim.x) {
         const double2* row = C + (int64_t)g * nJ;
@@ -74,7 +85,7 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
         const unsigned int total = sh_total;
         if (total <= (unsigned int)s_tilde) {
             for (int64_t k = tid; k < nJ; k += blockDim.x)
-                if (key_of(k)) set_bit(bitmap, k);
+                if (key_of(k)) set_bit(bits, k);
             __syncthreads();
             continue;
         }
@@ -126,7 +137,7 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
         const unsigned long long tau = sh_prefix;
         const unsigned int take_eq = sh_want;        // how many keys == tau to take
         for (int64_t k = tid; k < nJ; k += blockDim.x)
-            if (key_of(k) > tau) set_bit(bitmap, k);
+            if (key_of(k) > tau) set_bit(bits, k);
         // keys equal to tau: the first take_eq in index order
         unsigned int taken = 0;
         for (int64_t base = 0; base < nJ && taken < take_eq; base += blockDim.x) {
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
             unsigned int before = taken;
             for (int w = 0; w < warp; ++w) before += warp_cnt[w];
             before += __popc(ball & ((1u << lane) - 1u));
-            if (eq && before < take_eq) set_bit(bitmap, k);
+            if (eq && before < take_eq) set_bit(bits, k);
             unsigned int chunk = 0;
             for (int w = 0; w < nw; ++w) chunk += warp_cnt[w];
             __syncthreads();
@@ -146,16 +157,22 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
         }
         __syncthreads();
     }
+    if (local_bits) {
+        __syncthreads();
+        for (int64_t w = tid; w < nwords; w += blockDim.x)
+            if (sbits[w]) atomicOr(bitmap + w, sbits[w]);
+    }
 }
 
-static const int64_t kMaxSmemKeys = 24576;   // 192 KB of keys per CTA
+static const int64_t kMaxSmemKeys = 24576;   // 192 KB of keys (+ 3 KB of bitmap) per CTA
 
 cudaError_t launch_select_union(const double2* C, int G, int64_t nJ, double theta, int s_tilde, uint32_t* bitmap,
                                 cudaStream_t s, int* launches) {
     if (G <= 0 || nJ <= 0) return cudaSuccess;
     cudaError_t e;
+    const size_t bits_bytes = sizeof(uint32_t) * (size_t)((nJ + 31) / 32);
     if (nJ <= kMaxSmemKeys) {
-        const size_t smem = sizeof(unsigned long long) * (size_t)nJ;
+        const size_t smem = sizeof(unsigned long long) * (size_t)nJ + bits_bytes;
         e = allow_dyn_smem((const void*)select_union_kernel<true>, smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
@@ -166,10 +183,16 @@ cudaError_t launch_select_union(const double2* C, int G, int64_t nJ, double thet
         }
         int blocks = 152 * per_sm;
         if (blocks > G) blocks = G;
-        select_union_kernel<true><<<blocks, kSelThreads, smem, s>>>(C, G, nJ, theta * theta, s_tilde, bitmap);
+        select_union_kernel<true><<<blocks, kSelThreads, smem, s>>>(C, G, nJ, theta * theta, s_tilde, bitmap, true);
     } else {
         int blocks = G < 152 * 8 ? G : 152 * 8;
-        select_union_kernel<false><<<blocks, kSelThreads, 0, s>>>(C, G, nJ, theta * theta, s_tilde, bitmap);
+        const bool local = bits_bytes <= 32768;          // 1M candidates
+        const size_t smem = local ? bits_bytes : 0;
+        if (local) {
+            e = allow_dyn_smem((const void*)select_union_kernel<false>, smem);
+            if (e != cudaSuccess) return e;
+        }
+        select_union_kernel<false><<<blocks, kSelThreads, smem, s>>>(C, G, nJ, theta * theta, s_tilde, bitmap, local);
     }
     if (launches) ++*launches;
     return cudaGetLastError();
