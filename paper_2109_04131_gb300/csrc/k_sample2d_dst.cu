@@ -446,11 +446,11 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                     if (nid[k] >= 0) {
                         const int h = nid[k] & 0xffff;
                         const float w0 = wl[h], w1 = wl[h + W], w2 = wd[h], w3 = wd[h + 1];
-                        float acc = w0 * ph[h - W];
-                        acc = fmaf(w1, ph[h + W], acc);
-                        acc = fmaf(w2, ph[h - 1], acc);
-                        acc = fmaf(w3, ph[h + 1], acc);
-                        q32[k] = fmaf((w0 + w1) + (w2 + w3), p32[k], -acc);
+                        const float pk = p32[k];
+                        float acc = w0 * (pk - ph[h - W]);
+                        acc = fmaf(w1, pk - ph[h + W], acc);
+                        acc = fmaf(w2, pk - ph[h - 1], acc);
+                        q32[k] = fmaf(w3, pk - ph[h + 1], acc);
                         pq_l = fmaf(p32[k], q32[k], pq_l);
                     }
                 }
