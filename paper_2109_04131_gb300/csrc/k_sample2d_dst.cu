@@ -33,7 +33,7 @@ namespace usfft {
 
 struct DstLayout {
     int n, W, P, LD, J1, JA;
-    size_t o_xh, o_S, o_L, o_Ta, o_Tb, o_wx, o_wy, o_ph, o_sc, o_sj, o_r64, o_r32, o_A, o_AF, o_Tr, o_md, total;
+    size_t o_xh, o_S, o_L, o_Ta, o_Tb, o_wq, o_ph, o_sc, o_sj, o_r64, o_r32, o_A, o_AF, o_Tr, o_md, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -50,8 +50,7 @@ __host__ __device__ inline DstLayout dst_layout(int n, int d) {
     L.o_L = o;   o = align16(o + sizeof(float) * (size_t)L.P * L.LD);
     L.o_Ta = o;  o = align16(o + sizeof(__nv_bfloat16) * (size_t)L.P * L.LD);
     L.o_Tb = o;  o = align16(o + sizeof(__nv_bfloat16) * (size_t)L.P * L.LD);
-    L.o_wx = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
-    L.o_wy = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
+    L.o_wq = o;  o = align16(o + sizeof(float4) * (size_t)L.W * L.W);   // a node's four edge weights
     L.o_ph = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
     L.o_sc = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);
     L.o_sj = o;  o = align16(o + sizeof(double) * (size_t)d);
@@ -102,40 +101,65 @@ __device__ __forceinline__ float2 df_fma(float2 acc, float2 a, float2 b) {   // 
 }
 __device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// four 8x8 BF16 matrices between shared memory and the mma fragment layout (one row address
+// per lane: lanes 8i..8i+7 give the rows of matrix i; the register i of a lane holds row
+// lane/4, columns 2(lane%4), 2(lane%4)+1 of matrix i).  .trans stores matrix i transposed.
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr)
+                 : "memory");
+}
+__device__ __forceinline__ void stsm_x4(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};\n"
+                 :
+                 : "r"(addr), "r"(r0), "r"(r1), "r"(r2), "r"(r3)
+                 : "memory");
+}
+__device__ __forceinline__ void stsm_x4_trans(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1,%2,%3,%4};\n"
+                 :
+                 : "r"(addr), "r"(r0), "r"(r1), "r"(r2), "r"(r3)
+                 : "memory");
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
 // C = A B on the tensor cores (P x P, row stride LD elements, P a multiple of 16), BF16
 // operands, fp32 accumulation.  A is stored row-major; B is stored TRANSPOSED
-// (Bt[n][k] = B[k][n]) so that both operand loads read 32-bit words at bank
-// (4 row + col) mod 32 (LD/2 = 4 mod 32 words: conflict-free).  C is written row-major
-// (TRANSPOSE_OUT = false) or transposed (true), as BF16; before rounding it is multiplied
-// elementwise by Lsc (fp32, symmetric, stride LD) if SCALE.  Fragment layouts of
-// mma.m16n8k16 (BF16): a0 (g, 2t..2t+1) a1 (g+8, 2t..) a2 (g, 2t+8..) a3 (g+8, 2t+8..);
-// b0 (k = 2t..2t+1, n = g) b1 (k = 2t+8.., n = g); c0 (g, 2t) c1 (g, 2t+1) c2 (g+8, 2t)
-// c3 (g+8, 2t+1); g = lane/4, t = lane%4.  Each warp takes 16x16 output tiles.
+// (Bt[n][k] = B[k][n]), so that the B fragment of mma.m16n8k16 (.col) has the same shape as
+// the A fragment and both come from one ldmatrix.x4 each per k-step.  Rows are LD = P + 8
+// elements apart (4 mod 32 words), so the eight 16-byte rows of each 8x8 matrix fall on
+// distinct banks.  C is written row-major (TRANSPOSE_OUT = false) or transposed (true) with
+// one stmatrix.x4 per 16x16 tile, as BF16; before rounding it is multiplied elementwise by
+// Lsc (fp32, stride LD) if SCALE.  Accumulator layout of mma.m16n8k16: c0 (g, 2t) c1 (g, 2t+1)
+// c2 (g+8, 2t) c3 (g+8, 2t+1), g = lane/4, t = lane%4.  Each warp takes 16x16 output tiles
+// (two n8 tiles sharing the A fragment).
 template <int P, bool TRANSPOSE_OUT, bool SCALE>
 __device__ __forceinline__ void gemm_bf16(const bf16* __restrict__ A, const bf16* __restrict__ Bt,
-                                          bf16* __restrict__ C, const float* __restrict__ Lsc, int LD) {
-    // warp tiles of 16 x 16 (two mma n-tiles sharing the A fragment): half the fragment bytes
-    // read from shared memory per output of 16 x 8 tiles, the bound of this small GEMM
+                                          bf16* __restrict__ C, const float* __restrict__ Lsc) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    constexpr int NT = P / 16, TILES = (P / 16) * NT;
+    constexpr int NT = P / 16, TILES = (P / 16) * NT, LD = P + 8;
+    // row addresses of this lane: A matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15) in the order of
+    // the A fragment registers a0..a3; Bt matrices (n 0-7: k 0-7 | 8-15), (n 8-15: k 0-7 | 8-15)
+    const uint32_t a_lane = smem_u32(A) + 2u * (uint32_t)((lane & 15) * LD + ((lane >> 4) << 3));
+    const uint32_t b_lane = smem_u32(Bt) + 2u * (uint32_t)(((lane & 7) + ((lane >> 4) << 3)) * LD + (((lane >> 3) & 1) << 3));
+    // stores: matrix i = lane / 8 is (rows 0-7 | 8-15 by bit 0 of i) x (cols 0-7 | 8-15 by bit 1)
+    const int st_r = (lane & 7) + (((lane >> 3) & 1) << 3), st_c = (lane >> 4) << 3;
     for (int tile = warp; tile < TILES; tile += nwarps) {
         const int m0 = (tile / NT) * 16, n0 = (tile % NT) * 16;
         float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-        const bf16* Ar0 = A + (m0 + g) * LD + 2 * t;
-        const bf16* Ar1 = Ar0 + 8 * LD;
-        const bf16* Br0 = Bt + (n0 + g) * LD + 2 * t;
-        const bf16* Br1 = Br0 + 8 * LD;
+        const uint32_t pa = a_lane + 2u * (uint32_t)(m0 * LD), pb = b_lane + 2u * (uint32_t)(n0 * LD);
 #pragma unroll
         for (int k0 = 0; k0 < P; k0 += 16) {
-            const uint32_t a0 = *reinterpret_cast<const uint32_t*>(Ar0 + k0);
-            const uint32_t a1 = *reinterpret_cast<const uint32_t*>(Ar1 + k0);
-            const uint32_t a2 = *reinterpret_cast<const uint32_t*>(Ar0 + k0 + 8);
-            const uint32_t a3 = *reinterpret_cast<const uint32_t*>(Ar1 + k0 + 8);
-            const uint32_t b00 = *reinterpret_cast<const uint32_t*>(Br0 + k0);
-            const uint32_t b01 = *reinterpret_cast<const uint32_t*>(Br0 + k0 + 8);
-            const uint32_t b10 = *reinterpret_cast<const uint32_t*>(Br1 + k0);
-            const uint32_t b11 = *reinterpret_cast<const uint32_t*>(Br1 + k0 + 8);
+            uint32_t a0, a1, a2, a3, b00, b01, b10, b11;
+            ldsm_x4(pa + 2u * k0, a0, a1, a2, a3);
+            ldsm_x4(pb + 2u * k0, b00, b01, b10, b11);
             asm volatile(
                 "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
@@ -147,26 +171,114 @@ __device__ __forceinline__ void gemm_bf16(const bf16* __restrict__ A, const bf16
                 : "+f"(c[1][0]), "+f"(c[1][1]), "+f"(c[1][2]), "+f"(c[1][3])
                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b10), "r"(b11));
         }
+        if (SCALE) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int row0 = m0 + g, row1 = m0 + g + 8, col0 = n0 + 8 * h + 2 * t, col1 = col0 + 1;
-            float c0 = c[h][0], c1 = c[h][1], c2 = c[h][2], c3 = c[h][3];
-            if (SCALE) {
-                c0 *= Lsc[row0 * LD + col0];
-                c1 *= Lsc[row0 * LD + col1];
-                c2 *= Lsc[row1 * LD + col0];
-                c3 *= Lsc[row1 * LD + col1];
-            }
-            if (TRANSPOSE_OUT) {
-                C[col0 * LD + row0] = __float2bfloat16_rn(c0);
-                C[col1 * LD + row0] = __float2bfloat16_rn(c1);
-                C[col0 * LD + row1] = __float2bfloat16_rn(c2);
-                C[col1 * LD + row1] = __float2bfloat16_rn(c3);
-            } else {
-                *reinterpret_cast<__nv_bfloat162*>(C + row0 * LD + col0) = __floats2bfloat162_rn(c0, c1);
-                *reinterpret_cast<__nv_bfloat162*>(C + row1 * LD + col0) = __floats2bfloat162_rn(c2, c3);
+            for (int h = 0; h < 2; ++h) {
+                const int col0 = n0 + 8 * h + 2 * t;
+                const float2 l0 = *reinterpret_cast<const float2*>(Lsc + (m0 + g) * LD + col0);
+                const float2 l1 = *reinterpret_cast<const float2*>(Lsc + (m0 + g + 8) * LD + col0);
+                c[h][0] *= l0.x;
+                c[h][1] *= l0.y;
+                c[h][2] *= l1.x;
+                c[h][3] *= l1.y;
             }
         }
+        const uint32_t r0 = pack_bf16x2(c[0][0], c[0][1]), r1 = pack_bf16x2(c[0][2], c[0][3]);
+        const uint32_t r2 = pack_bf16x2(c[1][0], c[1][1]), r3 = pack_bf16x2(c[1][2], c[1][3]);
+        if (TRANSPOSE_OUT)   // C^T: matrix (rows a, cols b) of C lands at rows b, cols a
+            stsm_x4_trans(smem_u32(C) + 2u * (uint32_t)((n0 + st_c + (lane & 7)) * LD + m0 + (st_r & 8)), r0, r1, r2, r3);
+        else
+            stsm_x4(smem_u32(C) + 2u * (uint32_t)((m0 + st_r) * LD + n0 + st_c), r0, r1, r2, r3);
+    }
+}
+
+// Two chained products on one 16-row strip per warp: C = ((A B1) B2) o Lsc (Lsc only if SCALE),
+// written transposed (Ct[n][m] = C[m][n]).  Warp w < P/16 owns rows 16w..16w+15; the other warps
+// have no work here.  The strip of A B1 stays in registers: its fp32 accumulators, rounded to
+// BF16 pairs, are exactly the A fragments of the second product (the accumulator of n8-tiles
+// 2k and 2k+1 is the A fragment of k-step k), so the intermediate never goes through shared
+// memory and needs no barrier.  B1 and B2 are given transposed (Bt[n][k] = B[k][n]).  Ct must
+// not be one of the operands (other warps still read them).  The rounding points are those of
+// two separate products through BF16 shared buffers, so the result is the same.
+template <int P, bool SCALE>
+__device__ __forceinline__ void gemm_pair_strip(const bf16* __restrict__ A, const bf16* __restrict__ Bt1,
+                                                const bf16* __restrict__ Bt2, bf16* __restrict__ Ct,
+                                                const float* __restrict__ Lsc) {
+    constexpr int NT = P / 16, LD = P + 8;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp >= NT) return;
+    const int g = lane >> 2, t = lane & 3, m0 = warp * 16;
+    const uint32_t a_lane = smem_u32(A) + 2u * (uint32_t)((m0 + (lane & 15)) * LD + ((lane >> 4) << 3));
+    const uint32_t b_off = 2u * (uint32_t)(((lane & 7) + ((lane >> 4) << 3)) * LD + (((lane >> 3) & 1) << 3));
+    const uint32_t b1_lane = smem_u32(Bt1) + b_off, b2_lane = smem_u32(Bt2) + b_off;
+    // first product: the whole strip (16 x P) in 2 NT accumulator tiles of 16 x 8
+    float c[2 * NT][4];
+#pragma unroll
+    for (int j = 0; j < 2 * NT; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < NT; ++kk) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(a_lane + 32u * kk, a0, a1, a2, a3);
+#pragma unroll
+        for (int np = 0; np < NT; ++np) {
+            uint32_t b00, b01, b10, b11;
+            ldsm_x4(b1_lane + 2u * (uint32_t)(16 * np * LD) + 32u * kk, b00, b01, b10, b11);
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                : "+f"(c[2 * np][0]), "+f"(c[2 * np][1]), "+f"(c[2 * np][2]), "+f"(c[2 * np][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b00), "r"(b01));
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                : "+f"(c[2 * np + 1][0]), "+f"(c[2 * np + 1][1]), "+f"(c[2 * np + 1][2]), "+f"(c[2 * np + 1][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b10), "r"(b11));
+        }
+    }
+    uint32_t af[NT][4];
+#pragma unroll
+    for (int kk = 0; kk < NT; ++kk) {
+        af[kk][0] = pack_bf16x2(c[2 * kk][0], c[2 * kk][1]);
+        af[kk][1] = pack_bf16x2(c[2 * kk][2], c[2 * kk][3]);
+        af[kk][2] = pack_bf16x2(c[2 * kk + 1][0], c[2 * kk + 1][1]);
+        af[kk][3] = pack_bf16x2(c[2 * kk + 1][2], c[2 * kk + 1][3]);
+    }
+    // second product, one 16 x 16 output tile at a time
+    const int st_c = (lane >> 4) << 3, st_rb = ((lane >> 3) & 1) << 3;
+#pragma unroll
+    for (int np = 0; np < NT; ++np) {
+        float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int kk = 0; kk < NT; ++kk) {
+            uint32_t b00, b01, b10, b11;
+            ldsm_x4(b2_lane + 2u * (uint32_t)(16 * np * LD) + 32u * kk, b00, b01, b10, b11);
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                : "+f"(d[0][0]), "+f"(d[0][1]), "+f"(d[0][2]), "+f"(d[0][3])
+                : "r"(af[kk][0]), "r"(af[kk][1]), "r"(af[kk][2]), "r"(af[kk][3]), "r"(b00), "r"(b01));
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                : "+f"(d[1][0]), "+f"(d[1][1]), "+f"(d[1][2]), "+f"(d[1][3])
+                : "r"(af[kk][0]), "r"(af[kk][1]), "r"(af[kk][2]), "r"(af[kk][3]), "r"(b10), "r"(b11));
+        }
+        const int n0 = 16 * np;
+        if (SCALE) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int col0 = n0 + 8 * h + 2 * t;
+                const float2 l0 = *reinterpret_cast<const float2*>(Lsc + (m0 + g) * LD + col0);
+                const float2 l1 = *reinterpret_cast<const float2*>(Lsc + (m0 + g + 8) * LD + col0);
+                d[h][0] *= l0.x;
+                d[h][1] *= l0.y;
+                d[h][2] *= l1.x;
+                d[h][3] *= l1.y;
+            }
+        }
+        stsm_x4_trans(smem_u32(Ct) + 2u * (uint32_t)((n0 + st_c + (lane & 7)) * LD + m0 + st_rb),
+                      pack_bf16x2(d[0][0], d[0][1]), pack_bf16x2(d[0][2], d[0][3]),
+                      pack_bf16x2(d[1][0], d[1][1]), pack_bf16x2(d[1][2], d[1][3]));
     }
 }
 
@@ -174,6 +286,7 @@ __device__ __forceinline__ void gemm_bf16(const bf16* __restrict__ A, const bf16
 // D = diag(K) / 4).  The transform grid X (rows q, columns p)
 // is kept transposed in Ta (Ta[p][q]), the layout the B operand wants; nid[k] >> 16 = p LD + q
 // of the node (nid[k] = -1: no node).  S is symmetric, so it serves as A and as transposed B.
+// Two strip-pair products: Tb = ((S X S) o L)^T, then Ta = (S Y S)^T = Z^T with Y = Tb^T.
 template <int NPT, int P>
 __device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[NPT], const int (&nid)[NPT],
                                               const float* sc, bf16* Ta, bf16* Tb, const bf16* S,
@@ -182,13 +295,9 @@ __device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[
     for (int k = 0; k < NPT; ++k)
         if (nid[k] >= 0) Ta[nid[k] >> 16] = __float2bfloat16_rn(sc[nid[k] & 0xffff] * r[k]);
     __syncthreads();
-    gemm_bf16<P, false, false>(S, Ta, Tb, nullptr, LD);     // Tb = S X
+    gemm_pair_strip<P, true>(S, Ta, S, Tb, Li);       // Tb = ((S X S) o L)^T
     __syncthreads();
-    gemm_bf16<P, true, true>(Tb, S, Ta, Li, LD);            // Ta = ((S X S) o L)^T
-    __syncthreads();
-    gemm_bf16<P, false, false>(S, Ta, Tb, nullptr, LD);     // Tb = S ((S X S) o L)
-    __syncthreads();
-    gemm_bf16<P, true, false>(Tb, S, Ta, nullptr, LD);      // Ta = Z^T
+    gemm_pair_strip<P, false>(S, Tb, S, Ta, nullptr);  // Ta = (S Y S)^T, Y = Tb^T
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
@@ -259,8 +368,9 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
     float* Li = reinterpret_cast<float*>(smraw + Lo.o_L);
     bf16* Ta = reinterpret_cast<bf16*>(smraw + Lo.o_Ta);
     bf16* Tb = reinterpret_cast<bf16*>(smraw + Lo.o_Tb);
-    float* wl = reinterpret_cast<float*>(smraw + Lo.o_wx);   // weight of the edge to the left of halo node h (x - h)
-    float* wd = reinterpret_cast<float*>(smraw + Lo.o_wy);   // weight of the edge below halo node h (y - h)
+    // fp32 weights of the four edges of halo node h: (left, right, below, above), i.e. to the
+    // neighbours h - W, h + W, h - 1, h + 1 (one 16-byte load per node in the SpMV)
+    float4* wq = reinterpret_cast<float4*>(smraw + Lo.o_wq);
     float* ph = reinterpret_cast<float*>(smraw + Lo.o_ph);
     float* scs = reinterpret_cast<float*>(smraw + Lo.o_sc);   // preconditioner scaling, halo layout
     double* sj = reinterpret_cast<double*>(smraw + Lo.o_sj);
@@ -309,8 +419,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
         Tb[e] = __float2bfloat16_rn(0.f);
     }
     for (int e = tid; e < W * W; e += T) {
-        wl[e] = 0.f;
-        wd[e] = 0.f;
+        wq[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         w64l[e] = 0.0;
         w64d[e] = 0.0;
         d64[e] = 0.0;
@@ -377,14 +486,16 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                 w = make_float2(0.5f * w.x, 0.5f * w.y);              // exact
                 const int h = (Pp + 1) * W + Q + 1;
                 w64l[h] = df_to_double(w);
-                wl[h] = w.x;
+                wq[h].x = w.x;          // left edge of h
+                wq[h - W].y = w.x;      // right edge of its left neighbour
             }
             if (Pp >= 1) {          // edge (Pp,Q)-(Pp,Q+1): below node (Pp,Q+1)
                 float2 w = df_add(au, low[Q * n1 + (Pp - 1)]);
                 w = make_float2(0.5f * w.x, 0.5f * w.y);
                 const int h = Pp * W + Q + 1;
                 w64d[h] = df_to_double(w);
-                wd[h] = w.x;
+                wq[h].z = w.x;          // lower edge of h
+                wq[h - 1].w = w.x;      // upper edge of the node below
             }
         }
         __syncthreads();
@@ -414,7 +525,9 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
         int total = 0, outer = 0;
         while (rr64 > stop && outer < 16) {
             const float inv = (float)(1.0 / nr);
-            float d32[NPT], r32[NPT], p32[NPT], z32[NPT], q32[NPT];
+            // p lives in ph (shared, halo layout) only: it is not held in registers across the
+            // preconditioner
+            float d32[NPT], r32[NPT], z32[NPT], q32[NPT];
             float rl = 0.f;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
@@ -426,9 +539,8 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
             float rz_l = 0.f;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
-                p32[k] = z32[k];
                 rz_l = fmaf(r32[k], z32[k], rz_l);
-                if (nid[k] >= 0) ph[nid[k] & 0xffff] = p32[k];
+                if (nid[k] >= 0) ph[nid[k] & 0xffff] = z32[k];
             }
             float rz, rr, unused;
             block_sum3(rz_l, 0.f, rl, 1.f, red32, rz, rr, unused);
@@ -439,19 +551,21 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
             const float istop = tin * tin * rr;
             int it = 0;
             while (rr > istop && it < a.max_iters) {
-                float pq_l = 0.f;
+                float pq_l = 0.f, p32[NPT];
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
                     q32[k] = 0.f;
+                    p32[k] = 0.f;
                     if (nid[k] >= 0) {
                         const int h = nid[k] & 0xffff;
-                        const float w0 = wl[h], w1 = wl[h + W], w2 = wd[h], w3 = wd[h + 1];
-                        const float pk = p32[k];
-                        float acc = w0 * (pk - ph[h - W]);
-                        acc = fmaf(w1, pk - ph[h + W], acc);
-                        acc = fmaf(w2, pk - ph[h - 1], acc);
-                        q32[k] = fmaf(w3, pk - ph[h + 1], acc);
-                        pq_l = fmaf(p32[k], q32[k], pq_l);
+                        const float4 w = wq[h];
+                        const float pk = ph[h];
+                        float acc = w.x * (pk - ph[h - W]);
+                        acc = fmaf(w.y, pk - ph[h + W], acc);
+                        acc = fmaf(w.z, pk - ph[h - 1], acc);
+                        q32[k] = fmaf(w.w, pk - ph[h + 1], acc);
+                        pq_l = fmaf(pk, q32[k], pq_l);
+                        p32[k] = pk;
                     }
                 }
                 float pq, alpha;
@@ -477,8 +591,10 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                 rz = rz_new;
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
-                    p32[k] = fmaf(beta, p32[k], z32[k]);
-                    if (nid[k] >= 0) ph[nid[k] & 0xffff] = p32[k];
+                    if (nid[k] >= 0) {
+                        const int h = nid[k] & 0xffff;
+                        ph[h] = fmaf(beta, ph[h], z32[k]);
+                    }
                 }
                 __syncthreads();
                 ++it;
@@ -736,13 +852,13 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 Ta[pp * LD + qq] = __float2bfloat16_rn(scs[h] * rv[h]);
             }
             __syncthreads();
-            gemm_bf16<P, false, false>(S, Ta, Tb, nullptr, LD);
+            gemm_bf16<P, false, false>(S, Ta, Tb, nullptr);
             __syncthreads();
-            gemm_bf16<P, true, true>(Tb, S, Ta, Li, LD);
+            gemm_bf16<P, true, true>(Tb, S, Ta, Li);
             __syncthreads();
-            gemm_bf16<P, false, false>(S, Ta, Tb, nullptr, LD);
+            gemm_bf16<P, false, false>(S, Ta, Tb, nullptr);
             __syncthreads();
-            gemm_bf16<P, true, false>(Tb, S, Ta, nullptr, LD);
+            gemm_bf16<P, true, false>(Tb, S, Ta, nullptr);
             __syncthreads();
             for (int g = tid; g < G; g += T) {
                 const int pp = g / n, qq = g % n, h = (pp + 1) * W + qq + 1;
