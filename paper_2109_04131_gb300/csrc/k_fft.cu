@@ -36,6 +36,7 @@
 
 #include <vector>
 
+#include "k_cvt.cuh"
 #include "usfft_internal.h"
 
 namespace usfft {
@@ -142,10 +143,7 @@ __device__ __forceinline__ float2 dfr_mul(float ahi, float alo, float bhi, float
 }
 struct DF {
     typedef float4 C;   // re.hi, re.lo, im.hi, im.lo
-    static __device__ __forceinline__ float2 split(double x) {
-        const float h = __double2float_rn(x);
-        return make_float2(h, __double2float_rn(x - (double)h));
-    }
+    static __device__ __forceinline__ float2 split(double x) { return d2df(x); }
     static __device__ __forceinline__ C zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
     static __device__ __forceinline__ C pair(double x, double y) {
         const float2 a = split(x), b = split(y);
@@ -182,8 +180,8 @@ struct DF {
         const float2 orr = dfr_mul(os.x, os.y, sh, sl);
         const float2 od = dfr_add(B.x, B.y, -A.x, -A.y);
         const float2 oi = dfr_mul(od.x, od.y, sh, sl);
-        even = make_double2((double)er.x + (double)er.y, (double)ei.x + (double)ei.y);
-        odd = make_double2((double)orr.x + (double)orr.y, (double)oi.x + (double)oi.y);
+        even = make_double2(df2d(er.x, er.y), df2d(ei.x, ei.y));
+        odd = make_double2(df2d(orr.x, orr.y), df2d(oi.x, oi.y));
     }
 };
 

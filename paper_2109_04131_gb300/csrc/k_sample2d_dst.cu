@@ -26,6 +26,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "k_cvt.cuh"
 #include "k_pcg_common.cuh"
 #include "usfft_internal.h"
 
@@ -81,10 +82,7 @@ typedef __nv_bfloat16 bf16;
 // here with fmaf): the coefficient assembly runs on the FP32 pipe at a precision far below
 // the 1e-10 bar instead of on the 64x slower FP64 pipe.  Every operation is explicitly
 // rounded (__fadd_rn, __fmul_rn) so that no contraction changes the transformations.
-__device__ __forceinline__ float2 df_split(double x) {
-    const float h = __double2float_rn(x);
-    return make_float2(h, __double2float_rn(x - (double)h));
-}
+__device__ __forceinline__ float2 df_split(double x) { return d2df(x); }
 __device__ __forceinline__ float2 df_add(float2 a, float2 b) {          // a + b
     const float s = __fadd_rn(a.x, b.x);
     const float bb = __fadd_rn(s, -a.x);
@@ -99,7 +97,7 @@ __device__ __forceinline__ float2 df_fma(float2 acc, float2 a, float2 b) {   // 
     pe = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, pe));
     return df_add(acc, make_float2(p, pe));
 }
-__device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ double df_to_double(float2 a) { return df2d(a.x, a.y); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -507,7 +505,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                 const int h = nid[k] & 0xffff;
                 const double dg = (w64l[h] + w64l[h + W]) + (w64d[h] + w64d[h + 1]);
                 d64[h] = dg;
-                scs[h] = rsqrtf(0.25f * (float)dg);
+                scs[h] = rsqrtf(0.25f * d2f_round(dg));
             }
         }
         __syncthreads();
@@ -532,7 +530,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
                 d32[k] = 0.f;
-                r32[k] = (float)r64[k] * inv;
+                r32[k] = d2f_round(r64[k]) * inv;
                 rl = fmaf(r32[k], r32[k], rl);
             }
             apply_precond<NPT, P>(r32, z32, nid, scs, Ta, Tb, S, Li, LD);
@@ -603,7 +601,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
             // x += ||r|| d in fp64, then the fp64 residual with the fp64 weights
 #pragma unroll
             for (int k = 0; k < NPT; ++k)
-                if (nid[k] >= 0) xh[nid[k] & 0xffff] = fma(nr, (double)d32[k], xh[nid[k] & 0xffff]);
+                if (nid[k] >= 0) xh[nid[k] & 0xffff] = fma(nr, f2d_exact(d32[k]), xh[nid[k] & 0xffff]);
             __syncthreads();
             double rl64 = 0.0;
 #pragma unroll
@@ -836,7 +834,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             const int h = (g / n + 1) * W + g % n + 1;
             const double dg = (w64l[h] + w64l[h + W]) + (w64d[h] + w64d[h + 1]);
             d64[h] = dg;
-            scs[h] = rsqrtf(0.25f * (float)dg);
+            scs[h] = rsqrtf(0.25f * d2f_round(dg));
             x64[h] = 0.0;
             r64[h] = b;
         }
@@ -870,7 +868,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             float rl = 0.f;
             for (int g = tid; g < G; g += T) {
                 const int h = (g / n + 1) * W + g % n + 1;
-                const float r = (float)r64[h] * inv;
+                const float r = d2f_round(r64[h]) * inv;
                 rv[h] = r;
                 dv[h] = 0.f;
                 rl = fmaf(r, r, rl);
@@ -933,7 +931,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             total += it;
             for (int g = tid; g < G; g += T) {
                 const int h = (g / n + 1) * W + g % n + 1;
-                x64[h] = fma(nr, (double)dv[h], x64[h]);
+                x64[h] = fma(nr, f2d_exact(dv[h]), x64[h]);
             }
             __syncthreads();
             // residual in difference form, b - sum_e w_e (x_i - x_j): at these mesh widths the
