@@ -334,8 +334,16 @@ __device__ __forceinline__ void block_sum3(float v0, float v1, float v2, float d
     ratio = buf[34];
 }
 
-// block-wide fp64 sum; thread 0 also takes its square root (both broadcast)
-__device__ __forceinline__ void block_sum_sqrt(double v, double* buf, double& sum, double& root) {
+// Block-wide sum of squares w (partials v, of r / prev) and what every thread needs from it,
+// formed once by thread 0: ||r||^2 = w prev^2, ||r|| = sqrt(w) prev, 1/||r|| and ||r|| as floats,
+// and ||r||^2 > stop.  No thread repeats the fp64 division, conversions and comparison (on this
+// GPU the FP64 pipe, which also issues the conversions, runs at 1/64 of the FP32 rate).
+struct Norm2 {
+    double sq, root;
+    float inv, rootf;
+    int above;
+};
+__device__ __forceinline__ Norm2 block_norm2(double v, double* buf, double prev, double stop) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     v = warp_sum(v);
     if (lane == 0) buf[warp] = v;
@@ -344,13 +352,24 @@ __device__ __forceinline__ void block_sum_sqrt(double v, double* buf, double& su
         double w = lane < nw ? buf[lane] : 0.0;
         w = warp_sum(w);
         if (lane == 0) {
-            buf[32] = w;
-            buf[33] = sqrt(w);
+            const double sq = w * prev * prev, root = sqrt(w) * prev;
+            buf[32] = sq;
+            buf[33] = root;
+            float* f = reinterpret_cast<float*>(buf + 34);
+            f[0] = (float)(1.0 / root);
+            f[1] = (float)root;
+            reinterpret_cast<int*>(buf + 35)[0] = sq > stop;
         }
     }
     __syncthreads();
-    sum = buf[32];
-    root = buf[33];
+    Norm2 o;
+    o.sq = buf[32];
+    o.root = buf[33];
+    const float* f = reinterpret_cast<const float*>(buf + 34);
+    o.inv = f[0];
+    o.rootf = f[1];
+    o.above = reinterpret_cast<const int*>(buf + 35)[0];
+    return o;
 }
 
 // P = the transform size, n rounded up to a multiple of 16 (a compile-time constant, so the
@@ -445,6 +464,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
     const double nr0 = sqrt(rr0);
     const float nstop = (float)(a.tol * nr0);        // sqrt(stop)
     const float tol_in = (float)a.tol_inner;
+    const float inv0 = (float)(1.0 / nr0), nrf0 = (float)nr0;
     __syncthreads();
 
     for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
@@ -520,9 +540,10 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
 #pragma unroll
         for (int k = 0; k < NPT; ++k) r64[k] = (nid[k] >= 0) ? b : 0.0;
         double rr64 = rr0, nr = nr0;
+        float inv = inv0, nrf = nrf0;
+        int more = rr0 > stop;
         int total = 0, outer = 0;
-        while (rr64 > stop && outer < 16) {
-            const float inv = (float)(1.0 / nr);
+        while (more && outer < 16) {
             // p lives in ph (shared, halo layout) only: it is not held in registers across the
             // preconditioner
             float d32[NPT], r32[NPT], z32[NPT], q32[NPT];
@@ -544,7 +565,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
             block_sum3(rz_l, 0.f, rl, 1.f, red32, rz, rr, unused);
             // inner target: tol_inner, or less when this step only has to close the remaining
             // gap to the outer tolerance (0.3 x the reduction still missing)
-            const float gap = 0.3f * nstop / (float)nr;
+            const float gap = 0.3f * nstop / nrf;
             const float tin = gap > tol_in ? gap : tol_in;
             const float istop = tin * tin * rr;
             int it = 0;
@@ -603,7 +624,10 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
             for (int k = 0; k < NPT; ++k)
                 if (nid[k] >= 0) xh[nid[k] & 0xffff] = fma(nr, f2d_exact(d32[k]), xh[nid[k] & 0xffff]);
             __syncthreads();
-            double rl64 = 0.0;
+            // ||r||^2 in fp32 from r / ||r_prev|| (about 1e-5 and below: far inside the fp32 range);
+            // the norm only sets the stop and the scale of the next correction, and x and r use
+            // the same value of it
+            float rs_l = 0.f;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
                 r64[k] = 0.0;
@@ -616,10 +640,16 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                     acc = fma(w2, xh[h - 1], acc);
                     acc = fma(w3, xh[h + 1], acc);
                     r64[k] = b - fma(__ldcg(d64 + h), xh[h], -acc);
-                    rl64 = fma(r64[k], r64[k], rl64);
+                    const float rs = d2f_round(r64[k]) * inv;
+                    rs_l = fmaf(rs, rs, rs_l);
                 }
             }
-            block_sum_sqrt(rl64, red64, rr64, nr);
+            const Norm2 nm = block_norm2((double)rs_l, red64, nr, stop);
+            rr64 = nm.sq;
+            nr = nm.root;
+            inv = nm.inv;
+            nrf = nm.rootf;
+            more = nm.above;
             ++outer;
         }
         double* out = a.U + (size_t)sys * G;
@@ -842,6 +872,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
 
         // ---- fp64 iterative refinement around fp32 flexible PCG ----
         double rr64 = rr0, nr = sqrt(rr0);
+        float inv = (float)(1.0 / nr), nrf = (float)nr;
         int total = 0, outer = 0;
         bool at_floor = false;     // the residual stagnated at its rounding floor (see below)
         auto precond = [&]() {     // zv = D^-1/2 K_0^-1 D^-1/2 rv
@@ -864,7 +895,6 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             }
         };
         while (rr64 > stop && outer < 16) {
-            const float inv = (float)(1.0 / nr);
             float rl = 0.f;
             for (int g = tid; g < G; g += T) {
                 const int h = (g / n + 1) * W + g % n + 1;
@@ -883,7 +913,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             }
             float3 sums = block_sum3f(rz_l, rl, 0.f, red32);
             float rz = sums.x, rr = sums.y;
-            const float gap = 0.3f * nstop / (float)nr;
+            const float gap = 0.3f * nstop / nrf;
             const float tin = gap > tol_in ? gap : tol_in;
             const float istop = tin * tin * rr;
             int it = 0;
@@ -949,7 +979,13 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 rl64 = fma(r, r, rl64);
             }
             const double rr_prev = rr64;
-            block_sum_sqrt(rl64, red64, rr64, nr);
+            {
+                const Norm2 nm = block_norm2(rl64, red64, 1.0, stop);
+                rr64 = nm.sq;
+                nr = nm.root;
+                inv = nm.inv;
+                nrf = nm.rootf;
+            }
             ++outer;
             // At these mesh widths the fp64 residual of the 5-point system has a rounding floor
             // near 1e-13 relative (the granularity of x times the diagonal, ~1e4 b): an outer
