@@ -302,36 +302,48 @@ __device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[
         z[k] = (nid[k] >= 0) ? sc[nid[k] & 0xffff] * __bfloat162float(Ta[nid[k] >> 16]) : 0.f;
 }
 
-// three block sums in one pass; thread 0 also forms ratio = (s0 - s1) / den
-__device__ __forceinline__ void block_sum3(float v0, float v1, float v2, float den, float* buf, float& s0,
-                                           float& s2, float& ratio) {
+// Eight block-wide fp32 sums in one reduction (every thread receives all eight).  Within a
+// warp the eight values are reduced and spread at once (xor 16: four values each way, xor 8:
+// two, xor 4: one, then xor 2 and 1): lane l ends with value (l >> 2) & 7; lanes l % 4 == 0
+// write it.  Warp 0 then adds the per-warp partials (at most 16 warps).
+// buf holds 136 floats.
+__device__ __forceinline__ void block_sum8(float (&v)[8], float* buf) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
-    v2 = warp_sum(v2);
-    if (lane == 0) {
-        buf[warp] = v0;
-        buf[36 + warp] = v1;
-        buf[72 + warp] = v2;
+    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+    float u4[4], u2[2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float keep = b16 ? v[4 + j] : v[j], give = b16 ? v[j] : v[4 + j];
+        u4[j] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
     }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float keep = b8 ? u4[2 + j] : u4[j], give = b8 ? u4[j] : u4[2 + j];
+        u2[j] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+    float u = (b4 ? u2[1] : u2[0]) + __shfl_xor_sync(0xffffffffu, b4 ? u2[0] : u2[1], 4);
+    u += __shfl_xor_sync(0xffffffffu, u, 2);
+    u += __shfl_xor_sync(0xffffffffu, u, 1);
+    // value index held by this lane: 4 (bit 16) + 2 (bit 8) + 1 (bit 4)
+    const int idx = (b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0);
+    if ((lane & 3) == 0) buf[idx * 16 + warp] = u;
     __syncthreads();
     if (warp == 0) {
-        float a = lane < nw ? buf[lane] : 0.f;
-        float b = lane < nw ? buf[36 + lane] : 0.f;
-        float c = lane < nw ? buf[72 + lane] : 0.f;
-        a = warp_sum(a);
-        b = warp_sum(b);
-        c = warp_sum(c);
-        if (lane == 0) {
-            buf[32] = a;
-            buf[33] = c;
-            buf[34] = (a - b) / den;
+        // lane l adds warps (l & 15) of values 2j + (l >> 4), j = 0..3
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int vi = 2 * j + (lane >> 4), w = lane & 15;
+            float x = w < nw ? buf[vi * 16 + w] : 0.f;
+            x += __shfl_xor_sync(0xffffffffu, x, 8);
+            x += __shfl_xor_sync(0xffffffffu, x, 4);
+            x += __shfl_xor_sync(0xffffffffu, x, 2);
+            x += __shfl_xor_sync(0xffffffffu, x, 1);
+            if ((lane & 15) == 0) buf[128 + vi] = x;
         }
     }
     __syncthreads();
-    s0 = buf[32];
-    s2 = buf[33];
-    ratio = buf[34];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = buf[128 + j];
 }
 
 // Block-wide sum of squares w (partials v, of r / prev) and what every thread needs from it,
@@ -544,79 +556,80 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
         int more = rr0 > stop;
         int total = 0, outer = 0;
         while (more && outer < 16) {
-            // p lives in ph (shared, halo layout) only: it is not held in registers across the
-            // preconditioner
-            float d32[NPT], r32[NPT], z32[NPT], q32[NPT];
-            float rl = 0.f;
+            // Flexible PCG in the single-reduction form of Chronopoulos and Gear on K d = r / ||r||:
+            // each iteration applies the preconditioner, z = M r, and the operator to z, w = K z
+            // (ph holds z in the halo layout), and forms every inner product it needs in one block
+            // reduction: gamma = r.z, delta = z.w, zeta = z.q, rho = r.r, nu = r.w, mu = r.q,
+            // omega = w.w, phi = w.q (q = K p of the previous direction).  Then
+            //   beta = -alpha_prev zeta / gamma_prev      (Polak-Ribiere: z.(r - r_prev) / gamma_prev)
+            //   p.q  = delta + 2 beta zeta + beta^2 (p.q)_prev   (q_new = w + beta q, K symmetric)
+            //   alpha = gamma / p.q,  p = z + beta p,  q = w + beta q,  d += alpha p,  r -= alpha q
+            //   ||r_new||^2 = rho - 2 alpha (nu + beta mu) + alpha^2 q_new.q_new
+            // The stop test uses that recurrence, re-anchored every iteration on the exact rho.
+            float d32[NPT], r32[NPT], p32[NPT], q32[NPT];
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
                 d32[k] = 0.f;
+                p32[k] = 0.f;
+                q32[k] = 0.f;
                 r32[k] = d2f_round(r64[k]) * inv;
-                rl = fmaf(r32[k], r32[k], rl);
             }
-            apply_precond<NPT, P>(r32, z32, nid, scs, Ta, Tb, S, Li, LD);
-            float rz_l = 0.f;
-#pragma unroll
-            for (int k = 0; k < NPT; ++k) {
-                rz_l = fmaf(r32[k], z32[k], rz_l);
-                if (nid[k] >= 0) ph[nid[k] & 0xffff] = z32[k];
-            }
-            float rz, rr, unused;
-            block_sum3(rz_l, 0.f, rl, 1.f, red32, rz, rr, unused);
             // inner target: tol_inner, or less when this step only has to close the remaining
             // gap to the outer tolerance (0.3 x the reduction still missing)
             const float gap = 0.3f * nstop / nrf;
             const float tin = gap > tol_in ? gap : tol_in;
-            const float istop = tin * tin * rr;
+            float alpha = 0.f, gamma_prev = 1.f, pq_prev = 0.f, qq = 0.f, istop = 0.f;
             int it = 0;
-            while (rr > istop && it < a.max_iters) {
-                float pq_l = 0.f, p32[NPT];
+            while (it < a.max_iters) {
+                float z32[NPT];
+                apply_precond<NPT, P>(r32, z32, nid, scs, Ta, Tb, S, Li, LD);
+#pragma unroll
+                for (int k = 0; k < NPT; ++k)
+                    if (nid[k] >= 0) ph[nid[k] & 0xffff] = z32[k];
+                __syncthreads();
+                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float w32[NPT];
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
-                    q32[k] = 0.f;
-                    p32[k] = 0.f;
+                    w32[k] = 0.f;
                     if (nid[k] >= 0) {
                         const int h = nid[k] & 0xffff;
                         const float4 w = wq[h];
-                        const float pk = ph[h];
-                        float acc = w.x * (pk - ph[h - W]);
-                        acc = fmaf(w.y, pk - ph[h + W], acc);
-                        acc = fmaf(w.z, pk - ph[h - 1], acc);
-                        q32[k] = fmaf(w.w, pk - ph[h + 1], acc);
-                        pq_l = fmaf(pk, q32[k], pq_l);
-                        p32[k] = pk;
+                        const float zk = z32[k];
+                        float acc = w.x * (zk - ph[h - W]);
+                        acc = fmaf(w.y, zk - ph[h + W], acc);
+                        acc = fmaf(w.z, zk - ph[h - 1], acc);
+                        w32[k] = fmaf(w.w, zk - ph[h + 1], acc);
                     }
+                    const float rk = r32[k], zk = z32[k], wk = w32[k], qk = q32[k];
+                    v[0] = fmaf(rk, zk, v[0]);
+                    v[1] = fmaf(zk, wk, v[1]);
+                    v[2] = fmaf(zk, qk, v[2]);
+                    v[3] = fmaf(rk, rk, v[3]);
+                    v[4] = fmaf(rk, wk, v[4]);
+                    v[5] = fmaf(rk, qk, v[5]);
+                    v[6] = fmaf(wk, wk, v[6]);
+                    v[7] = fmaf(wk, qk, v[7]);
                 }
-                float pq, alpha;
-                block_sum_ratio<float, NUM_OVER_SUM>(pq_l, rz, red32 + 108, pq, alpha);
-                float rold[NPT];
-                float rn_l = 0.f;
+                block_sum8(v, red32);
+                if (it == 0) istop = tin * tin * v[3];
+                const float beta = it == 0 ? 0.f : -alpha * v[2] / gamma_prev;
+                const float pq = v[1] + beta * (2.f * v[2] + beta * pq_prev);
+                alpha = v[0] / pq;
+                const float qq_new = v[6] + beta * (2.f * v[7] + beta * qq);
+                const float rr = v[3] - 2.f * alpha * (v[4] + beta * v[5]) + alpha * alpha * qq_new;
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
+                    p32[k] = fmaf(beta, p32[k], z32[k]);
+                    q32[k] = fmaf(beta, q32[k], w32[k]);
                     d32[k] = fmaf(alpha, p32[k], d32[k]);
-                    rold[k] = r32[k];
                     r32[k] = fmaf(-alpha, q32[k], r32[k]);
-                    rn_l = fmaf(r32[k], r32[k], rn_l);
                 }
-                apply_precond<NPT, P>(r32, z32, nid, scs, Ta, Tb, S, Li, LD);
-                float zr_l = 0.f, zro_l = 0.f;
-#pragma unroll
-                for (int k = 0; k < NPT; ++k) {
-                    zr_l = fmaf(z32[k], r32[k], zr_l);
-                    zro_l = fmaf(z32[k], rold[k], zro_l);
-                }
-                float rz_new, beta;
-                block_sum3(zr_l, zro_l, rn_l, rz, red32, rz_new, rr, beta);   // flexible beta
-                rz = rz_new;
-#pragma unroll
-                for (int k = 0; k < NPT; ++k) {
-                    if (nid[k] >= 0) {
-                        const int h = nid[k] & 0xffff;
-                        ph[h] = fmaf(beta, ph[h], z32[k]);
-                    }
-                }
-                __syncthreads();
+                gamma_prev = v[0];
+                pq_prev = pq;
+                qq = qq_new;
                 ++it;
+                if (rr <= istop) break;
             }
             total += it;
             // x += ||r|| d in fp64, then the fp64 residual with the fp64 weights
