@@ -24,6 +24,15 @@ __device__ __forceinline__ double mag2_rn(double2 c) {
     return __dadd_rn(__dmul_rn(c.x, c.x), __dmul_rn(c.y, c.y));
 }
 
+// key of a magnitude: 1 + its bit pattern if m2 >= theta^2, else 0.  The comparison is done
+// on the bit patterns (non-negative doubles order like their bits; the bound at the pattern
+// of +inf keeps a nan out, as the fp64 comparison would), on the integer pipe: on this GPU
+// the fp64 comparison issues at the FP64 pipe's rate (1/64 of FP32).
+__device__ __forceinline__ unsigned long long key_bits(double m2, unsigned long long tbits) {
+    const unsigned long long mb = (unsigned long long)__double_as_longlong(m2);
+    return (mb >= tbits && mb <= 0x7ff0000000000000ull) ? mb + 1ull : 0ull;
+}
+
 __device__ __forceinline__ void set_bit(uint32_t* bitmap, int64_t k) {
     atomicOr(bitmap + (k >> 5), 1u << (k & 31));
 }
@@ -56,18 +65,19 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
         __syncthreads();
     }
 
+    const unsigned long long tbits = theta2 > 0.0 ? (unsigned long long)__double_as_longlong(theta2) : 0ull;
     for (int g = blockIdx.x; g < G; g += gridDim.x) {
         const double2* row = C + (int64_t)g * nJ;
         auto key_of = [&](int64_t k) -> unsigned long long {
             if (KEYS_IN_SMEM) return skeys[k];
             const double m2 = mag2_rn(row[k]);
-            return m2 >= theta2 ? (unsigned long long)__double_as_longlong(m2) + 1ull : 0ull;
+            return key_bits(m2, tbits);
         };
         // pass 0: keys and the count of candidates above the threshold
         unsigned int cnt = 0;
         for (int64_t k = tid; k < nJ; k += blockDim.x) {
             const double m2 = mag2_rn(row[k]);
-            const unsigned long long key = m2 >= theta2 ? (unsigned long long)__double_as_longlong(m2) + 1ull : 0ull;
+            const unsigned long long key = key_bits(m2, tbits);
             if (KEYS_IN_SMEM) skeys[k] = key;
             cnt += key ? 1u : 0u;
         }
