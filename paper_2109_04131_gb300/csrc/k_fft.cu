@@ -425,6 +425,8 @@ __global__ void __launch_bounds__(kFftThreads) fft_final_kernel(const __grid_con
 // threads on consecutive k (coalesced).  Twiddles W_M^e = T1[e mod B] T2[e div B] from two
 // small shared tables.  No intermediate array in HBM: the samples are read once and the
 // coefficients written once.
+// Launch bound: two CTAs per SM (64 registers a thread; the radix-8 double-float butterfly
+// spills a few values to L1), which measured 15% faster than one CTA at 106 registers.
 static const int kInplaceThreads = 512;
 static const int kTwB = 128;
 
@@ -470,7 +472,7 @@ __device__ __forceinline__ void inplace_butterfly(typename A::C* buf, int base, 
 }
 
 template <class A>
-__global__ void __launch_bounds__(kInplaceThreads) fft_inplace_kernel(const __grid_constant__ FftArgs a,
+__global__ void __launch_bounds__(kInplaceThreads, 2) fft_inplace_kernel(const __grid_constant__ FftArgs a,
                                                                         const typename A::C* W, const int* pos_of,
                                                                         const int* mk, int CP) {
     typedef typename A::C C;
@@ -530,7 +532,9 @@ __global__ void __launch_bounds__(kInplaceThreads) fft_inplace_kernel(const __gr
     }
 }
 
-// one column pair per CTA (110 KB at M = 6912: two CTAs per SM) measured faster than two
+// one column pair per CTA (110 KB at M = 6912: two CTAs per SM, which the kernel's launch
+// bound of two 512-thread CTAs, 64 registers a thread, also lets the register file hold) measured
+// faster than two; the second resident CTA hides the shared-memory latency of the stages
 static int inplace_cp(int64_t M) {
     const size_t tables = sizeof(double2) * (size_t)(kTwB + (M + kTwB - 1) / kTwB);
     return sizeof(double2) * (size_t)M + tables <= 232448 ? 1 : 0;
