@@ -1,6 +1,6 @@
 // Conversions between binary32 and binary64 built from the IEEE-754 bit fields (binary32:
 // sign, 8 exponent bits biased by 127, 23 fraction bits; binary64: sign, 11 exponent bits
-// biased by 1023, 52 fraction bits), on the integer pipe.  On this GPU the F2F conversion
+// biased by 1023, 52 fraction bits), on the integer pipe.  On this GPU the conversion
 // instructions issue at the FP64 pipe's rate (1/64 of FP32), so a phase that converts once or
 // twice per node is bound by them; these run at more than twice that rate and leave the FP64
 // pipe to the fp64 arithmetic.  Branch-free (selects only), so that no fallback conversion
