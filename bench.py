@@ -437,7 +437,7 @@ def run_ours(args, rank, world):
 
 
 def e2e_measure(plan, t, steps, barrier, world, dev):
-    times, samples, h2d, d2h = [], [], [], []
+    times, samples, h2d, d2h, dev_ms, host_ms = [], [], [], [], [], []
     plan.rewind(t - 1)
     plan.increment()                              # warm
     barrier()
@@ -449,11 +449,14 @@ def e2e_measure(plan, t, steps, barrier, world, dev):
         samples.append(info["samples"])
         h2d.append(info["h2d_bytes"])
         d2h.append(info["d2h_bytes"])
+        dev_ms.append(info["ms_device"])
+        host_ms.append(info["ms_host_plan"])
     tot = max_over_ranks(sum(times), world, dev)
     return {"value": whole_job_rate(world, sum(samples), 1e3 * tot), "unit": UNIT, "h2d_bytes_per_step": int(np.mean(h2d)),
             "d2h_bytes_per_step": int(np.mean(d2h)), "steps": steps,
             "ms_per_step": 1e3 * tot / steps,
             "latency_ms": {"p50": 1e3 * percentile(times, 50), "p99": 1e3 * percentile(times, 99)},
+            "ms_device_per_step": float(np.mean(dev_ms)), "ms_host_plan_per_step": float(np.mean(host_ms)),
             "call": "usfft_rewind(t-1) + usfft_increment (1-D detections of dimension t, J_t, lattice "
                     "search, both detection iterations, host copies)"}
 

@@ -19,6 +19,11 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "usfft_internal.h"
@@ -121,16 +126,22 @@ void candidate_set(const int8_t* I_prev, int64_t n_prev, int t_prev, const std::
 }
 
 // Injectivity of k -> k.z mod M on J with an M-bit bitmap; early exit on the first collision.
+// The residue is formed with a floating-point quotient estimate: |k.z| < 2^45 (|k_j| <= 127,
+// z_j < 2^31, t <= 64) is exact in a double, the estimate floor(k.z / M) is off by at most one,
+// and one correction each way gives the exact residue (an integer division per candidate is
+// the slowest step of the check otherwise).
 static bool injective(const int8_t* J, int64_t n, int t, const int64_t* z, int64_t M,
                       std::vector<uint64_t>& bits) {
     const size_t words = (size_t)((M + 63) / 64);
     if (bits.size() < words) bits.resize(words);
     std::fill(bits.begin(), bits.begin() + words, 0ULL);
+    const double inv = 1.0 / (double)M;
     for (int64_t a = 0; a < n; ++a) {
         int64_t acc = 0;
         for (int j = 0; j < t; ++j) acc += (int64_t)J[a * t + j] * z[j];
-        int64_t m = acc % M;
+        int64_t m = acc - (int64_t)floor((double)acc * inv) * M;
         if (m < 0) m += M;
+        if (m >= M) m -= M;
         uint64_t bit = 1ULL << (m & 63);
         uint64_t& w = bits[(size_t)(m >> 6)];
         if (w & bit) return false;
@@ -138,6 +149,108 @@ static bool injective(const int8_t* J, int64_t n, int t, const int64_t* z, int64
     }
     return true;
 }
+
+// true if two rows of J (n rows of t entries) are equal: rows folded into 64-bit keys (exact
+// for t <= 8, a hash otherwise, with equal keys compared in full), sorted
+static bool has_repeated_row(const int8_t* J, int64_t n, int t) {
+    std::vector<std::pair<uint64_t, int64_t>> key((size_t)n);
+    for (int64_t a = 0; a < n; ++a) {
+        uint64_t k = 0;
+        if (t <= 8) {
+            for (int j = 0; j < t; ++j) k = (k << 8) | (uint8_t)J[a * t + j];
+        } else {
+            for (int j = 0; j < t; ++j) {
+                k ^= (uint64_t)(uint8_t)J[a * t + j] + kGoldenGamma + (k << 6) + (k >> 2);
+            }
+        }
+        key[(size_t)a] = {k, a};
+    }
+    std::sort(key.begin(), key.end());
+    for (size_t a = 1; a < key.size(); ++a) {
+        if (key[a].first != key[a - 1].first) continue;
+        if (t <= 8) return true;
+        // equal hashes: compare against every earlier row with the same key
+        for (size_t b = a; b-- > 0 && key[b].first == key[a].first;)
+            if (std::equal(J + key[b].second * t, J + (key[b].second + 1) * t, J + key[a].second * t)) return true;
+    }
+    return false;
+}
+
+// the generating vector of trial tr at size m
+static void draw_z(int t, int64_t m, int tr, uint64_t seed, uint64_t phase, int64_t* z) {
+    z[0] = 1;
+    for (int j = 2; j <= t; ++j) {
+        if (m > 1) {
+            uint64_t f[5] = {phase, (uint64_t)t, (uint64_t)m, (uint64_t)tr, (uint64_t)j};
+            z[j - 1] = rng_uniform_int(1, m - 1, seed, f, 5);
+        } else {
+            z[j - 1] = 0;
+        }
+    }
+}
+
+// A small persistent pool of host threads for the lattice search (thread creation costs more
+// than a search step).  One job at a time: a search that finds the pool busy (another plan is
+// searching concurrently) runs alone, so many instances planned at once never oversubscribe
+// the host.  The workers are detached and live as long as the process.
+class SearchPool {
+  public:
+    static SearchPool& get() {
+        static SearchPool* pool = new SearchPool();   // never destroyed (detached workers)
+        return *pool;
+    }
+    int workers() const { return (int)nworkers_; }
+    // runs f(0..count-1) on the workers and the caller; false (nothing run) if the pool is busy
+    bool try_run(int count, const std::function<void(int)>& f) {
+        std::unique_lock<std::mutex> job(job_mu_, std::try_to_lock);
+        if (!job.owns_lock() || nworkers_ == 0) return false;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            fn_ = &f;
+            count_ = count;
+            next_.store(0);
+            active_ = nworkers_;
+            ++gen_;
+        }
+        cv_.notify_all();
+        for (int i; (i = next_.fetch_add(1)) < count;) f(i);
+        std::unique_lock<std::mutex> lk(mu_);
+        done_.wait(lk, [&] { return active_ == 0; });
+        fn_ = nullptr;
+        return true;
+    }
+
+  private:
+    SearchPool() {
+        const unsigned hc = std::thread::hardware_concurrency();
+        nworkers_ = hc > 1 ? std::min(hc, 16u) - 1 : 0;
+        for (unsigned w = 0; w < nworkers_; ++w) std::thread([this] { loop(); }).detach();
+    }
+    void loop() {
+        uint64_t seen = 0;
+        for (;;) {
+            const std::function<void(int)>* f;
+            int count;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return gen_ != seen; });
+                seen = gen_;
+                f = fn_;
+                count = count_;
+            }
+            for (int i; (i = next_.fetch_add(1)) < count;) (*f)(i);
+            std::lock_guard<std::mutex> lk(mu_);
+            if (--active_ == 0) done_.notify_one();
+        }
+    }
+    std::mutex job_mu_, mu_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int)>* fn_ = nullptr;
+    int count_ = 0;
+    std::atomic<int> next_{0};
+    unsigned nworkers_ = 0, active_ = 0;
+    uint64_t gen_ = 0;
+};
 
 bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials, int max_sizes,
                     std::vector<int64_t>& z, int64_t& M, uint64_t phase) {
@@ -147,38 +260,49 @@ bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials
         return true;
     }
     // a repeated candidate can never be separated: fail at once
-    {
-        std::vector<int8_t> rows(J, J + n * t);
-        std::vector<int64_t> idx((size_t)n);
-        for (int64_t a = 0; a < n; ++a) idx[(size_t)a] = a;
-        std::sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) {
-            return std::lexicographical_compare(rows.begin() + x * t, rows.begin() + (x + 1) * t,
-                                                rows.begin() + y * t, rows.begin() + (y + 1) * t);
-        });
-        for (int64_t a = 1; a < n; ++a)
-            if (std::equal(rows.begin() + idx[(size_t)a - 1] * t, rows.begin() + (idx[(size_t)a - 1] + 1) * t,
-                           rows.begin() + idx[(size_t)a] * t))
-                return false;
-    }
+    if (has_repeated_row(J, n, t)) return false;
+    // The sizes in order; the result is the first size with a successful trial and its first
+    // such trial.  For large candidate sets the next few sizes are examined at once in borrowed
+    // host threads (each size's trials in order in one thread) and the smallest size index with
+    // a success is kept: the same (z, M) as the sequential scan, in less wall time.
+    // Large sets: the (size, trial) pairs of the next sizes, in order, are shared out among the
+    // pool's threads; each pair past the best success found so far is skipped, and the smallest
+    // successful pair is kept -- the same (z, M) as the sequential scan.
+    SearchPool& pool = SearchPool::get();
+    const int batch = n >= 1024 ? 16 : 1;
     std::vector<uint64_t> bits;
     int64_t m = next_admissible(n);
-    for (int size = 0; size < max_sizes && m <= kMaxLatticeSize; ++size) {
-        for (int tr = 0; tr < trials; ++tr) {
-            z[0] = 1;
-            for (int j = 2; j <= t; ++j) {
-                if (m > 1) {
-                    uint64_t f[5] = {phase, (uint64_t)t, (uint64_t)m, (uint64_t)tr, (uint64_t)j};
-                    z[(size_t)(j - 1)] = rng_uniform_int(1, m - 1, seed, f, 5);
-                } else {
-                    z[(size_t)(j - 1)] = 0;
+    int size = 0;
+    while (size < max_sizes && m <= kMaxLatticeSize) {
+        std::vector<int64_t> ms;
+        for (int b = 0; b < batch && size + b < max_sizes && m <= kMaxLatticeSize; ++b) {
+            ms.push_back(m);
+            m = next_admissible((105 * m + 99) / 100);
+        }
+        const int items = (int)ms.size() * trials;
+        std::atomic<int> best{items};
+        const std::function<void(int)> job = [&](int i) {
+            if (i >= best.load()) return;
+            thread_local std::vector<uint64_t> tbits;
+            std::vector<int64_t> zz((size_t)t);
+            const int64_t mi = ms[(size_t)(i / trials)];
+            draw_z(t, mi, i % trials, seed, phase, zz.data());
+            if (injective(J, n, t, zz.data(), mi, tbits)) {
+                int cur = best.load();
+                while (i < cur && !best.compare_exchange_weak(cur, i)) {
                 }
             }
-            if (injective(J, n, t, z.data(), m, bits)) {
-                M = m;
-                return true;
-            }
+        };
+        if (batch == 1 || !pool.try_run(items, job)) {
+            for (int i = 0; i < items && best.load() == items; ++i) job(i);   // alone, in order
         }
-        m = next_admissible((105 * m + 99) / 100);
+        if (best.load() < items) {
+            const int i = best.load();
+            M = ms[(size_t)(i / trials)];
+            draw_z(t, M, i % trials, seed, phase, z.data());
+            return true;
+        }
+        size += (int)ms.size();
     }
     return false;
 }

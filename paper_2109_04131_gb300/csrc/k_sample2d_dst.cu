@@ -305,8 +305,8 @@ __device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[
 // Eight block-wide fp32 sums in one reduction (every thread receives all eight).  Within a
 // warp the eight values are reduced and spread at once (xor 16: four values each way, xor 8:
 // two, xor 4: one, then xor 2 and 1): lane l ends with value (l >> 2) & 7; lanes l % 4 == 0
-// write it.  Warp 0 then adds the per-warp partials (at most 16 warps).
-// buf holds 136 floats.
+// write it.  Then every warp adds the per-warp partials (at most 16 warps).  buf holds 128
+// floats; the caller's next use of it comes after a barrier.
 __device__ __forceinline__ void block_sum8(float (&v)[8], float* buf) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
@@ -328,22 +328,22 @@ __device__ __forceinline__ void block_sum8(float (&v)[8], float* buf) {
     const int idx = (b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0);
     if ((lane & 3) == 0) buf[idx * 16 + warp] = u;
     __syncthreads();
-    if (warp == 0) {
-        // lane l adds warps (l & 15) of values 2j + (l >> 4), j = 0..3
+    // every warp adds the per-warp partials itself (the same operations in the same order, so
+    // every thread gets the same sums) instead of waiting at a second barrier for warp 0:
+    // lane l adds warps (l & 15) of values 2j + (l >> 4), then takes the partner half's value
+    const bool odd = lane & 16;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int vi = 2 * j + (lane >> 4), w = lane & 15;
-            float x = w < nw ? buf[vi * 16 + w] : 0.f;
-            x += __shfl_xor_sync(0xffffffffu, x, 8);
-            x += __shfl_xor_sync(0xffffffffu, x, 4);
-            x += __shfl_xor_sync(0xffffffffu, x, 2);
-            x += __shfl_xor_sync(0xffffffffu, x, 1);
-            if ((lane & 15) == 0) buf[128 + vi] = x;
-        }
+    for (int j = 0; j < 4; ++j) {
+        const int vi = 2 * j + (odd ? 1 : 0), w = lane & 15;
+        float x = w < nw ? buf[vi * 16 + w] : 0.f;
+        x += __shfl_xor_sync(0xffffffffu, x, 8);
+        x += __shfl_xor_sync(0xffffffffu, x, 4);
+        x += __shfl_xor_sync(0xffffffffu, x, 2);
+        x += __shfl_xor_sync(0xffffffffu, x, 1);
+        const float y = __shfl_xor_sync(0xffffffffu, x, 16);
+        v[2 * j] = odd ? y : x;
+        v[2 * j + 1] = odd ? x : y;
     }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = buf[128 + j];
 }
 
 // Block-wide sum of squares w (partials v, of r / prev) and what every thread needs from it,
