@@ -407,7 +407,7 @@ int sample_2d_default_blocks(int n, int precision) {
 size_t sample_2d_scratch_bytes(int n, int precision, int blocks) {
     if (precision == USFFT_FP64) return 0;
     const size_t W = (size_t)n + 2;
-    if (precision == USFFT_MIXED) return sizeof(double) * (n > 63 ? 9 : 3) * W * W * (size_t)blocks;
+    if (precision == USFFT_MIXED) return sizeof(double) * (n > 63 ? 10 : 3) * W * W * (size_t)blocks;
     return sizeof(double) * 2 * (size_t)n * (n + 1) * (size_t)blocks;
 }
 

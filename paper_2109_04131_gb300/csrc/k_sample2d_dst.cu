@@ -305,8 +305,9 @@ __device__ __forceinline__ void apply_precond(const float (&r)[NPT], float (&z)[
 // Eight block-wide fp32 sums in one reduction (every thread receives all eight).  Within a
 // warp the eight values are reduced and spread at once (xor 16: four values each way, xor 8:
 // two, xor 4: one, then xor 2 and 1): lane l ends with value (l >> 2) & 7; lanes l % 4 == 0
-// write it.  Then every warp adds the per-warp partials (at most 16 warps).  buf holds 128
-// floats; the caller's next use of it comes after a barrier.
+// write it.  Then every warp adds the per-warp partials (at most MAXW = 16 or 32 warps).  buf
+// holds 8 MAXW floats; the caller's next use of it comes after a barrier.
+template <int MAXW = 16>
 __device__ __forceinline__ void block_sum8(float (&v)[8], float* buf) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
@@ -326,8 +327,16 @@ __device__ __forceinline__ void block_sum8(float (&v)[8], float* buf) {
     u += __shfl_xor_sync(0xffffffffu, u, 1);
     // value index held by this lane: 4 (bit 16) + 2 (bit 8) + 1 (bit 4)
     const int idx = (b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0);
-    if ((lane & 3) == 0) buf[idx * 16 + warp] = u;
+    if ((lane & 3) == 0) buf[idx * MAXW + warp] = u;
     __syncthreads();
+    if (MAXW == 32) {      // up to 32 warps: every warp adds all 32 partials of each value
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float x = lane < nw ? buf[j * 32 + lane] : 0.f;
+            v[j] = warp_sum(x);
+        }
+        return;
+    }
     // every warp adds the per-warp partials itself (the same operations in the same order, so
     // every thread gets the same sums) instead of waiting at a second barrier for warp 0:
     // lane l adds warps (l & 15) of values 2j + (l >> 4), then takes the partner half's value
@@ -684,7 +693,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
 // tables and the reduction buffers.  One CTA of 1024 threads per system; nodes are visited in
 // loops g = tid, tid + T, ... (column-major enumeration, halo h = (p+1) W + (q+1), transform
 // position p LD + q, as in the small kernel).  Scratch slot (in units of W^2): fp64 x, weights
-// (left, down), diagonal, residual (5); fp32 weights (left, down), scaling, p, r, z, q, d (4).
+// (left, down), diagonal, residual (5); fp32 weights (left, down), scaling, p, r, z, q, d, w (5).
 // ---------------------------------------------------------------------------------------------
 struct BigLayout {
     int W, LD, J1, JA;
@@ -715,39 +724,9 @@ __host__ __device__ inline BigLayout big_layout(int n, int d, int P) {
     L.o_md = o;  o = align16(o + sizeof(double) * (size_t)d + sizeof(int) * 2 * (size_t)d);
     L.o_sj = o;  o = align16(o + sizeof(double) * (size_t)d);
     L.o_r64 = o; o = align16(o + sizeof(double) * 36);
-    L.o_r32 = o; o = align16(o + sizeof(float) * 4 * 36);
+    L.o_r32 = o; o = align16(o + sizeof(float) * 8 * 36);
     L.total = o;
     return L;
-}
-
-// block-wide sums of up to three fp32 partials (every thread receives them)
-__device__ __forceinline__ float3 block_sum3f(float v0, float v1, float v2, float* buf) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
-    v2 = warp_sum(v2);
-    if (lane == 0) {
-        buf[warp] = v0;
-        buf[36 + warp] = v1;
-        buf[72 + warp] = v2;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        float a0 = lane < nw ? buf[lane] : 0.f, a1 = lane < nw ? buf[36 + lane] : 0.f;
-        float a2 = lane < nw ? buf[72 + lane] : 0.f;
-        a0 = warp_sum(a0);
-        a1 = warp_sum(a1);
-        a2 = warp_sum(a2);
-        if (lane == 0) {
-            buf[108] = a0;
-            buf[109] = a1;
-            buf[110] = a2;
-        }
-    }
-    __syncthreads();
-    const float3 r = make_float3(buf[108], buf[109], buf[110]);
-    __syncthreads();   // buf is reused by the next call
-    return r;
 }
 
 template <int P>
@@ -772,7 +751,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
     const int J1 = Lo.J1, JA = Lo.JA;
     const int T = blockDim.x, tid = threadIdx.x;
     // the CTA's scratch slot
-    double* x64 = a.scratch + (size_t)blockIdx.x * 9 * WW;
+    double* x64 = a.scratch + (size_t)blockIdx.x * 10 * WW;
     double* w64l = x64 + WW;
     double* w64d = w64l + WW;
     double* d64 = w64d + WW;
@@ -785,6 +764,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
     float* zv = rv + WW;
     float* qv = zv + WW;
     float* dv = qv + WW;
+    float* wv = dv + WW;
 
     const float c2 = 4.0f / ((float)n1 * (float)n1);
     for (int e = tid; e < P * LD; e += T) {
@@ -804,6 +784,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
         wl[e] = 0.f;
         wd[e] = 0.f;
         ph[e] = 0.f;
+        zv[e] = 0.f;
         w64l[e] = 0.0;
         w64d[e] = 0.0;
         x64[e] = 0.0;
@@ -908,68 +889,64 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             }
         };
         while (rr64 > stop && outer < 16) {
-            float rl = 0.f;
+            // single-reduction flexible PCG (the small-mesh kernel's inner solve; p in ph, w = K z in wv)
             for (int g = tid; g < G; g += T) {
                 const int h = (g / n + 1) * W + g % n + 1;
-                const float r = d2f_round(r64[h]) * inv;
-                rv[h] = r;
+                rv[h] = d2f_round(r64[h]) * inv;
                 dv[h] = 0.f;
-                rl = fmaf(r, r, rl);
+                ph[h] = 0.f;
+                qv[h] = 0.f;
             }
             __syncthreads();
-            precond();
-            float rz_l = 0.f;
-            for (int g = tid; g < G; g += T) {
-                const int h = (g / n + 1) * W + g % n + 1;
-                ph[h] = zv[h];
-                rz_l = fmaf(rv[h], zv[h], rz_l);
-            }
-            float3 sums = block_sum3f(rz_l, rl, 0.f, red32);
-            float rz = sums.x, rr = sums.y;
             const float gap = 0.3f * nstop / nrf;
             const float tin = gap > tol_in ? gap : tol_in;
-            const float istop = tin * tin * rr;
+            float alpha = 0.f, gamma_prev = 1.f, pq_prev = 0.f, qq = 0.f, istop = 0.f;
             int it = 0;
-            while (rr > istop && it < a.max_iters) {
-                float pq_l = 0.f;
+            while (it < a.max_iters) {
+                precond();
+                __syncthreads();
+                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 for (int g = tid; g < G; g += T) {
                     const int h = (g / n + 1) * W + g % n + 1;
                     const float w0 = wl[h], w1 = wl[h + W], w2 = wd[h], w3 = wd[h + 1];
-                    float acc = w0 * ph[h - W];
-                    acc = fmaf(w1, ph[h + W], acc);
-                    acc = fmaf(w2, ph[h - 1], acc);
-                    acc = fmaf(w3, ph[h + 1], acc);
-                    const float q = fmaf((w0 + w1) + (w2 + w3), ph[h], -acc);
+                    const float zk = zv[h];
+                    float acc = w0 * zv[h - W];
+                    acc = fmaf(w1, zv[h + W], acc);
+                    acc = fmaf(w2, zv[h - 1], acc);
+                    acc = fmaf(w3, zv[h + 1], acc);
+                    const float wk = fmaf((w0 + w1) + (w2 + w3), zk, -acc);
+                    wv[h] = wk;
+                    const float rk = rv[h], qk = qv[h];
+                    v[0] = fmaf(rk, zk, v[0]);
+                    v[1] = fmaf(zk, wk, v[1]);
+                    v[2] = fmaf(zk, qk, v[2]);
+                    v[3] = fmaf(rk, rk, v[3]);
+                    v[4] = fmaf(rk, wk, v[4]);
+                    v[5] = fmaf(rk, qk, v[5]);
+                    v[6] = fmaf(wk, wk, v[6]);
+                    v[7] = fmaf(wk, qk, v[7]);
+                }
+                block_sum8<32>(v, red32);
+                if (it == 0) istop = tin * tin * v[3];
+                const float beta = it == 0 ? 0.f : -alpha * v[2] / gamma_prev;
+                const float pq = v[1] + beta * (2.f * v[2] + beta * pq_prev);
+                alpha = v[0] / pq;
+                const float qq_new = v[6] + beta * (2.f * v[7] + beta * qq);
+                const float rr = v[3] - 2.f * alpha * (v[4] + beta * v[5]) + alpha * alpha * qq_new;
+                for (int g = tid; g < G; g += T) {
+                    const int h = (g / n + 1) * W + g % n + 1;
+                    const float p = fmaf(beta, ph[h], zv[h]);
+                    const float q = fmaf(beta, qv[h], wv[h]);
+                    ph[h] = p;
                     qv[h] = q;
-                    pq_l = fmaf(ph[h], q, pq_l);
+                    dv[h] = fmaf(alpha, p, dv[h]);
+                    rv[h] = fmaf(-alpha, q, rv[h]);
                 }
-                const float pq = block_sum3f(pq_l, 0.f, 0.f, red32).x;
-                const float alpha = rz / pq;
-                for (int g = tid; g < G; g += T) {
-                    const int h = (g / n + 1) * W + g % n + 1;
-                    dv[h] = fmaf(alpha, ph[h], dv[h]);
-                    rv[h] = fmaf(-alpha, qv[h], rv[h]);
-                }
-                __syncthreads();
-                precond();
-                float zr_l = 0.f, zq_l = 0.f, rn_l = 0.f;
-                for (int g = tid; g < G; g += T) {
-                    const int h = (g / n + 1) * W + g % n + 1;
-                    zr_l = fmaf(zv[h], rv[h], zr_l);
-                    zq_l = fmaf(zv[h], qv[h], zq_l);
-                    rn_l = fmaf(rv[h], rv[h], rn_l);
-                }
-                sums = block_sum3f(zr_l, zq_l, rn_l, red32);
-                // flexible beta: z_new . (r_new - r_old) / rz with r_old = r_new + alpha q
-                const float beta = -alpha * sums.y / rz;
-                rz = sums.x;
-                rr = sums.z;
-                for (int g = tid; g < G; g += T) {
-                    const int h = (g / n + 1) * W + g % n + 1;
-                    ph[h] = fmaf(beta, ph[h], zv[h]);
-                }
-                __syncthreads();
+                gamma_prev = v[0];
+                pq_prev = pq;
+                qq = qq_new;
                 ++it;
+                if (rr <= istop) break;
             }
             total += it;
             for (int g = tid; g < G; g += T) {
