@@ -98,6 +98,20 @@ def test_lattice_search_is_bit_exact_with_the_oracle(binding, seed):
         assert M1 == M0 and np.array_equal(z1, z0)
 
 
+@pytest.mark.parametrize("seed,t,n_prev,span", [(5, 3, 400, 10), (11, 3, 700, 12), (3, 4, 300, 5)])
+def test_lattice_search_parallel_path_is_bit_exact_with_the_oracle(binding, seed, t, n_prev, span):
+    # candidate sets of a few thousand rows (the size of the coupled steps of the 2-D workload):
+    # the library shares the (size, trial) pairs out over host threads and must still return the
+    # first success of the sequential scan, as the oracle's loop does
+    r = np.random.default_rng(seed)
+    prev = np.unique(r.integers(-span, span + 1, size=(n_prev, t - 1)), axis=0)
+    J = lattice.candidate_set(prev, np.arange(-6, 7), N=32)
+    assert len(J) >= 1024
+    z0, M0 = lattice.search(J, t, seed)
+    z1, M1 = binding.usfft_search_lattice(J, t, seed)
+    assert M1 == M0 and np.array_equal(z1, z0)
+
+
 def test_lattice_search_on_the_c1_increments(binding):
     # the candidate sets the oracle builds for the 1-D workload (increments 2..4)
     from oracle.usfft import OracleRun
