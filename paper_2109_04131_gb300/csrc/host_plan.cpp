@@ -17,6 +17,7 @@
 // detection (random_lattices) follow their own rule, stated at its declaration.
 #include <math.h>
 #include <stdint.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <atomic>
@@ -192,7 +193,8 @@ static void draw_z(int t, int64_t m, int tr, uint64_t seed, uint64_t phase, int6
 // A small persistent pool of host threads for the lattice search (thread creation costs more
 // than a search step).  One job at a time: a search that finds the pool busy (another plan is
 // searching concurrently) runs alone, so many instances planned at once never oversubscribe
-// the host.  The workers are detached and live as long as the process.
+// the host.  The workers are detached and live as long as the process; a process forked from
+// it has no workers, so the pool serves only the process that created it.
 class SearchPool {
   public:
     static SearchPool& get() {
@@ -202,8 +204,9 @@ class SearchPool {
     int workers() const { return (int)nworkers_; }
     // runs f(0..count-1) on the workers and the caller; false (nothing run) if the pool is busy
     bool try_run(int count, const std::function<void(int)>& f) {
+        if (nworkers_ == 0 || getpid() != owner_) return false;
         std::unique_lock<std::mutex> job(job_mu_, std::try_to_lock);
-        if (!job.owns_lock() || nworkers_ == 0) return false;
+        if (!job.owns_lock()) return false;
         {
             std::lock_guard<std::mutex> lk(mu_);
             fn_ = &f;
@@ -221,7 +224,7 @@ class SearchPool {
     }
 
   private:
-    SearchPool() {
+    SearchPool() : owner_(getpid()) {
         const unsigned hc = std::thread::hardware_concurrency();
         nworkers_ = hc > 1 ? std::min(hc, 16u) - 1 : 0;
         for (unsigned w = 0; w < nworkers_; ++w) std::thread([this] { loop(); }).detach();
@@ -243,6 +246,7 @@ class SearchPool {
             if (--active_ == 0) done_.notify_one();
         }
     }
+    const pid_t owner_;
     std::mutex job_mu_, mu_;
     std::condition_variable cv_, done_;
     const std::function<void(int)>* fn_ = nullptr;
