@@ -68,7 +68,7 @@ def test_budget_order_and_continuous_batching():
     assert rep["requests"] == 4 and rep["failed"] == 0
     rounds = [e for e in log if e[0] == "round"]
     assert all(e[2] <= 100 for e in rounds)                        # never above the budget
-    # round 1 runs 0 and 1; request 2 (50) waits for 1 to leave, then joins 0's batch
+    # the first scheduling round runs 0 and 1; request 2 (50) waits for 1 to leave, then joins 0's batch
     assert rounds[0][1] == (0, 1)
     assert rounds[1][1] == (0, 2)
     admits = [e for e in log if e[0] == "admit"]
