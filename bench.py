@@ -627,11 +627,12 @@ def alu_probe():
 
 
 def profile_case(args):
-    """A short, fixed run for ncu: increments 1..K of the 2-D workload in one precision."""
+    """A short, fixed run for ncu: increments 1..K of the 2-D workload (63x63 mesh, either precision)
+    or of the 127x127 lognormal-type workload (mixed precision, large-mesh sampler)."""
     import torch
     from paper_2109_04131_gb300 import binding
     prec = W.PRECISION_MIXED if args.precision == "mixed" else W.PRECISION_FP64
-    w = W.with_precision(W.c2(1), prec)
+    w = W.with_precision(W.c3(1) if args.profile_workload == "mesh127" else W.c2(1), prec)
     plan = binding.Plan(w.problem, w.params)
     for _ in range(args.profile_increments):
         info = plan.increment()
@@ -657,6 +658,8 @@ def main():
     ap.add_argument("--profile-increments", type=int, default=0,
                     help="profiling mode: only run this many increments of the 2-D workload (no timing)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--profile-workload", choices=["mesh63", "mesh127"], default="mesh63",
+                    help="profiling mode: the 63x63 2-D workload or the 127x127 lognormal-type one")
     ap.add_argument("--alu-probe", action="store_true",
                     help="build and run the FP64/FP32 FMA throughput probe (paper_2109_04131_gb300/probe)")
     args = ap.parse_args()
