@@ -83,9 +83,10 @@ typedef enum {
 /* precision of the sampler */
 #define USFFT_FP64 0          /* fp64 everywhere; 2-D solves by Jacobi-preconditioned CG */
 #define USFFT_MIXED 1         /* 2-D: fp64-residual iterative refinement around fp32 flexible CG
-                                 preconditioned by the constant-coefficient operator (2-D sine
-                                 transform as BF16 tensor-core GEMMs); 1-D: fp64; FFT, gather and
-                                 selection stay fp64 */
+                                 (one block reduction per iteration) preconditioned by the
+                                 constant-coefficient operator (2-D sine transform as BF16
+                                 tensor-core GEMMs); 1-D: fp64; the lattice FFT in double-float
+                                 (pairs of fp32), its gathered output and the selection in fp64 */
 #define USFFT_MIXED_JACOBI 2  /* 2-D: the same refinement around fp32 Jacobi-CG (for comparison) */
 
 typedef struct {
