@@ -112,6 +112,23 @@ def test_lattice_search_parallel_path_is_bit_exact_with_the_oracle(binding, seed
     assert M1 == M0 and np.array_equal(z1, z0)
 
 
+def test_lattice_search_concurrent_callers_get_the_sequential_result(binding):
+    # served instances plan in parallel host threads: searches that find the thread pool busy run
+    # alone, and every caller must still get the (z, M) of the sequential scan
+    from concurrent.futures import ThreadPoolExecutor
+    r = np.random.default_rng(21)
+    sets = []
+    for k in range(6):
+        prev = np.unique(r.integers(-8 - k, 9 + k, size=(300 + 60 * k, 2)), axis=0)
+        sets.append(lattice.candidate_set(prev, np.arange(-6, 7), N=32))
+    want = [binding.usfft_search_lattice(J, 3, 5) for J in sets]
+    with ThreadPoolExecutor(max_workers=6) as ex:
+        for _ in range(3):
+            got = list(ex.map(lambda J: binding.usfft_search_lattice(J, 3, 5), sets))
+            for (z0, M0), (z1, M1) in zip(want, got):
+                assert M1 == M0 and np.array_equal(z1, z0)
+
+
 def test_lattice_search_on_the_c1_increments(binding):
     # the candidate sets the oracle builds for the 1-D workload (increments 2..4)
     from oracle.usfft import OracleRun
