@@ -190,34 +190,85 @@ def oracle_shape(w, t):
     return run, J, z, M
 
 
+def _oracle_rows(job):
+    """Worker of the oracle pool: the oracle's FE samples of some lattice nodes (unchanged oracle
+    code); job None only starts the worker."""
+    if job is None:
+        return None
+    prob, nodes, rows = job
+    from oracle import fe
+    from oracle.usfft import sample_rows
+    return sample_rows(prob, nodes, rows, fe.make_mesh(prob.kind, prob.n))
+
+
+_ORACLE_POOL = None
+
+
+def oracle_pool():
+    """Processes for the oracle's independent FE solves, one per host core (spawn: the parent holds
+    a CUDA context), BLAS single-threaded in each; started and warmed before any timing.  None if
+    the workers cannot start (the solves then run in this process)."""
+    global _ORACLE_POOL
+    if _ORACLE_POOL is None:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            pool = ProcessPoolExecutor(max_workers=os.cpu_count() or 1, mp_context=mp.get_context("spawn"))
+            list(pool.map(_oracle_rows, [None] * (os.cpu_count() or 1), timeout=300))   # workers up
+            _ORACLE_POOL = pool
+        except Exception:                              # a broken pool raises instead of hanging
+            _ORACLE_POOL = False
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+    return _ORACLE_POOL or None
+
+
 def oracle_sample_time(w, t, J, z, M, rows):
-    """Seconds for the oracle's sampler and DFT on `rows` lattice nodes of iteration 1."""
-    from oracle import dft, fe, lattice, rng
-    from oracle.usfft import NodeSet, sample_rows
+    """Seconds for the oracle's sampler (the rows' FE solves shared out over one process per host
+    core) and its DFT (numpy, BLAS threads on all cores) on `rows` lattice nodes of iteration 1;
+    and the processes the solves used."""
+    from oracle import dft, lattice, rng
+    from oracle.usfft import NodeSet
     d = w.problem.d
     tails = {j - 1: rng.uniform(w.params.seed, rng.PHASE_TAIL, t, 1, j) for j in range(t + 1, d + 1)}
     nodes = NodeSet(d, list(range(t)), z, M, tails)
-    mesh = fe.make_mesh(w.problem.kind, w.problem.n)
     m = lattice.lattice_indices(J, z, M)
+    pool = oracle_pool()
+    procs = (os.cpu_count() or 1) if pool else 1
+    parts = [c for c in np.array_split(np.asarray(rows), procs) if len(c)]
+    if pool:
+        list(pool.map(_oracle_rows, [(w.problem, nodes, c[:1]) for c in parts]))    # warm (meshes)
     t0 = time.perf_counter()
-    U = sample_rows(w.problem, nodes, rows, mesh)
+    if pool:
+        U = np.concatenate(list(pool.map(_oracle_rows, [(w.problem, nodes, c) for c in parts])))
+    else:
+        U = np.concatenate([_oracle_rows((w.problem, nodes, c)) for c in parts])
     t1 = time.perf_counter()
     dft.partial_coefficients(U, np.asarray(rows), m, M)
     t2 = time.perf_counter()
-    return t2 - t0, t1 - t0, t2 - t1
+    return t2 - t0, t1 - t0, t2 - t1, procs
 
 
-def cpu_baseline(w, t, rows_n=96):
+def cpu_baseline(w, t, rows_n=None):
     t0 = time.perf_counter()
     run, J, z, M = oracle_shape(w, t)
     setup = time.perf_counter() - t0
+    if rows_n is None:
+        rows_n = 24 * (os.cpu_count() or 1)
     rows = np.linspace(0, M - 1, rows_n).astype(np.int64)
-    tot, ts, td = oracle_sample_time(w, t, J, z, M, rows)
-    return {"value": rows_n / tot, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    tot, ts, td, procs = oracle_sample_time(w, t, J, z, M, rows)
+    return {"value": rows_n / tot, "unit": UNIT, "cores": os.cpu_count() if procs > 1 else 1, "kind": "oracle",
             "sample": f"{rows_n} of the M={M} lattice nodes of increment t={t}, iteration 1 (|J|={len(J)}): "
-                      f"banded-Cholesky FE solves ({ts:.2f} s, one thread) + naive DFT of those rows at all "
-                      f"|J| indices ({td:.2f} s, numpy BLAS on all cores); oracle setup (increments 1..{t - 1}) "
-                      f"untimed ({setup:.1f} s)",
+                      f"banded-Cholesky FE solves ({ts:.2f} s, {procs} processes) + naive DFT of those rows "
+                      f"at all |J| indices ({td:.2f} s, numpy BLAS on all cores); oracle setup (increments "
+                      f"1..{t - 1}) and process start untimed ({setup:.1f} s)",
             "seconds": tot}
 
 
@@ -233,7 +284,7 @@ def run_reference(args, rank, world):
     times = []
     for k in range(args.warmup + args.steps):
         rows = np.sort(rng_.choice(M, size=rows_n, replace=False))
-        tot, _, _ = oracle_sample_time(w, t, J, z, M, rows)
+        tot, _, _, procs = oracle_sample_time(w, t, J, z, M, rows)
         if k >= args.warmup:
             times.append(tot)
     per = [rows_n / x for x in times]
@@ -243,9 +294,10 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(w, t) | {"M": int(M), "n_candidates": int(len(J))},
             "latency_ms": {"p50": 1e3 * percentile(times, 50), "p99": 1e3 * percentile(times, 99)},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count() if procs > 1 else 1,
+                             "kind": "oracle",
                              "sample": f"each step: {rows_n} random lattice nodes of increment t={t} "
-                                       f"(M={M}, |J|={len(J)}): FE solves + naive DFT rows"},
+                                       f"(M={M}, |J|={len(J)}): FE solves ({procs} processes) + naive DFT rows"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
