@@ -240,17 +240,25 @@ def oracle_sample_time(w, t, J, z, M, rows):
     tails = {j - 1: rng.uniform(w.params.seed, rng.PHASE_TAIL, t, 1, j) for j in range(t + 1, d + 1)}
     nodes = NodeSet(d, list(range(t)), z, M, tails)
     m = lattice.lattice_indices(J, z, M)
+    global _ORACLE_POOL
     pool = oracle_pool()
-    procs = (os.cpu_count() or 1) if pool else 1
-    parts = [c for c in np.array_split(np.asarray(rows), procs) if len(c)]
+    U = None
     if pool:
-        list(pool.map(_oracle_rows, [(w.problem, nodes, c[:1]) for c in parts]))    # warm (meshes)
-    t0 = time.perf_counter()
-    if pool:
-        U = np.concatenate(list(pool.map(_oracle_rows, [(w.problem, nodes, c) for c in parts])))
-    else:
-        U = np.concatenate([_oracle_rows((w.problem, nodes, c)) for c in parts])
-    t1 = time.perf_counter()
+        procs = os.cpu_count() or 1
+        parts = [c for c in np.array_split(np.asarray(rows), procs) if len(c)]
+        try:
+            list(pool.map(_oracle_rows, [(w.problem, nodes, c[:1]) for c in parts], timeout=600))   # warm
+            t0 = time.perf_counter()
+            U = np.concatenate(list(pool.map(_oracle_rows, [(w.problem, nodes, c) for c in parts], timeout=600)))
+            t1 = time.perf_counter()
+        except Exception:                              # a worker died: the solves run in this process
+            _ORACLE_POOL = False
+            U = None
+    if U is None:
+        procs = 1
+        t0 = time.perf_counter()
+        U = _oracle_rows((w.problem, nodes, np.asarray(rows)))
+        t1 = time.perf_counter()
     dft.partial_coefficients(U, np.asarray(rows), m, M)
     t2 = time.perf_counter()
     return t2 - t0, t1 - t0, t2 - t1, procs
