@@ -17,10 +17,11 @@
 // and leaves its variation, so a handful of iterations reduce the residual by 1e-5
 // (Jacobi-PCG needs hundreds).  The four n x n matrix products run on
 // the tensor cores (mma.sync m16n8k16, BF16 operands in shared memory, fp32
-// accumulation); the rounded preconditioner is slightly non-symmetric, which the
-// flexible (Polak-Ribiere) beta tolerates -- only the convergence rate depends on it, the
-// solution accuracy comes from the fp64 refinement.  One CTA owns one system at a time
-// (persistent grid).
+// accumulation), as two chained pairs per application; the rounded preconditioner is slightly
+// non-symmetric, which the flexible (Polak-Ribiere) beta tolerates -- only the convergence rate
+// depends on it, the solution accuracy comes from the fp64 refinement.  The inner CG takes the
+// single-reduction form (all inner products of an iteration in one block reduction).  One CTA
+// owns one system at a time (persistent grid).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
