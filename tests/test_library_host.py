@@ -129,6 +129,21 @@ def test_lattice_search_concurrent_callers_get_the_sequential_result(binding):
                 assert M1 == M0 and np.array_equal(z1, z0)
 
 
+@pytest.mark.parametrize("t", [10, 12])
+def test_lattice_search_long_rows_and_repeated_rows(binding, t):
+    # rows of more than 8 coordinates take the hashed repeated-row check: a planted duplicate is
+    # still found (EINVAL), and distinct rows give the oracle's (z, M)
+    r = np.random.default_rng(t)
+    prev = np.unique(r.integers(-2, 3, size=(60, t - 1)), axis=0)
+    J = lattice.candidate_set(prev, np.arange(-2, 3), N=8)
+    z0, M0 = lattice.search(J, t, 3)
+    z1, M1 = binding.usfft_search_lattice(J, t, 3)
+    assert M1 == M0 and np.array_equal(z1, z0)
+    Jd = np.concatenate([J, J[len(J) // 2:len(J) // 2 + 1]])
+    with pytest.raises(binding.UsfftError):
+        binding.usfft_search_lattice(Jd, t, 3)
+
+
 def test_lattice_search_on_the_c1_increments(binding):
     # the candidate sets the oracle builds for the 1-D workload (increments 2..4)
     from oracle.usfft import OracleRun
