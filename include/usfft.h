@@ -340,7 +340,10 @@ usfft_status usfft_random_lattices(int t, int i, int64_t n_prev, int64_t n_t, in
  * z = (1, z_2, ..., z_t), z_j uniform in [1, M-1] from the counter-based draws keyed by
  * (seed, 3, t, M, trial, j); the first z with k -> k.z mod M injective on J is returned
  * (Appendix A: a reconstructing lattice makes the single-lattice DFT exact on J).
- * z receives t entries.  USFFT_ELATTICE if none is found within max_sizes sizes. */
+ * z receives t entries.  USFFT_ELATTICE if none is found within max_sizes sizes.
+ * Host only, thread-safe.  For n >= 1024 the (size, trial) pairs of the next sizes are shared out
+ * over a small pool of host threads of the calling process (one search at a time; a concurrent
+ * search runs in its own thread); the result is that of the sequential scan. */
 usfft_status usfft_search_lattice(const int8_t* J, int64_t n, int t, uint64_t seed, int trials,
                                   int max_sizes, int64_t* z, int64_t* M);
 
