@@ -287,7 +287,7 @@ def run_reference(args, rank, world):
     w = W.c2(1)
     t = args.t
     _, J, z, M = oracle_shape(w, t)
-    rows_n = args.ref_rows
+    rows_n = args.ref_rows or 24 * (os.cpu_count() or 1)
     rng_ = np.random.default_rng(0)
     times = []
     for k in range(args.warmup + args.steps):
@@ -300,7 +300,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(w, t) | {"M": int(M), "n_candidates": int(len(J))},
+            "data": "synthetic", "config": workload_config(w, t, {"M": M, "n_candidates": len(J)}),
             "latency_ms": {"p50": 1e3 * percentile(times, 50), "p99": 1e3 * percentile(times, 99)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count() if procs > 1 else 1,
                              "kind": "oracle",
@@ -428,28 +428,41 @@ def run_ours(args, rank, world):
                 "peak_note": f"fp64 peak from unit counts at {SM_MAX_MHZ:.0f} MHz (2 DFMA/clk/SM)"}
 
     def mixed_roofline(res):
-        # MIXED path: fp64 work (assembly 2 d E per solve, refinement residual + update 17 G per step)
-        # is the binding roof at peak; fp32 CG (21 G per inner iteration) and the BF16 sine
-        # transforms (4 x 2 P^3 per preconditioner application, one per inner iteration) are
-        # listed beside it.
+        # MIXED sampler.  Work it issues per solve (counted from the kernel's code):
+        #   FP64 pipe: per refinement step x += ||r|| d (1 DFMA) and r = b - K x with the fp64
+        #     weights (1 DMUL, 3 DFMA, 1 DFMA, 1 DADD): 12 flops per node; once per solve the fp64
+        #     edge weights (2 DADD from the double-float pairs) and diagonal (3 DADD): 5 flops per
+        #     node.  The coefficient assembly runs in double-float on the FP32 pipe, not here.
+        #   FP32 pipe: per inner iteration the preconditioner scaling (2), the SpMV in difference
+        #     form (4 sub + 1 mul + 3 fma = 11), eight inner products (16), four updates (8): 37
+        #     flops per node.
+        #   Tensor pipe (BF16): per inner iteration four P x P x P products, 4 * 2 P^3 flops.
+        # The roof reported is the FP64 pipe's (the busiest pipe in the ncu capture); the others and
+        # the HBM view (the samples written) are listed beside it.
         st = res["stages"]
         n = max(1, st["launches"]["sample"])
         solves = res["samples_per_step"] * args.steps
         inner, outer = st["cg_iters_total"], st["refine_steps_total"]
-        f64 = (2.0 * d_ * E_ * solves + 17.0 * G * outer) / n
-        f32 = FLOPS_PER_CG_ITER_PER_NODE * G * inner / n
-        ftc = 4 * 2.0 * P_ ** 3 * inner / n                    # BF16 tensor flops of the sine transforms
+        f64 = (12.0 * G * outer + 5.0 * G * solves) / n
+        f32 = 37.0 * G * inner / n
+        ftc = 4 * 2.0 * P_ ** 3 * inner / n
         dur = st["ms"]["sample"] / n / 1e3
         ach = f64 / dur / 1e12
+        out_bytes = 8.0 * G * solves / n
         return {"bound": "alu", "achieved": ach, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / PEAK_FP64_TFLOPS, "traffic": profiled_traffic("mixed"),
-                "kernel": f"pcg2d_mixed_dst_kernel (assembly + refinement + fp32 PCG + BF16 DST, {n} launches timed)",
+                "kernel": f"pcg2d_mixed_dst_kernel (fp64 refinement + fp32 flexible PCG + BF16 DST, {n} launches timed)",
                 "flops_per_launch": f64, "ms_per_launch": dur * 1e3,
+                "work_per_solve": {"fp64_flops": "12 G per refinement step + 5 G", "fp32_flops": "37 G per inner iteration",
+                                   "bf16_tensor_flops": f"4 * 2 * {P_}^3 per inner iteration"},
                 "units": {"fp64": {"tflops": ach, "frac": ach / PEAK_FP64_TFLOPS},
                           "fp32": {"tflops": f32 / dur / 1e12, "frac": f32 / dur / 1e12 / PEAK_FP32_TFLOPS},
-                          "tensor_bf16": {"tflops": ftc / dur / 1e12, "frac": ftc / dur / 1e12 / peak_bf16}},
+                          "tensor_bf16": {"tflops": ftc / dur / 1e12, "frac": ftc / dur / 1e12 / peak_bf16},
+                          "hbm": {"gbs": out_bytes / dur / 1e9, "frac": out_bytes / dur / 1e9 / peaks["hbm_gbs"],
+                                  "bytes_per_launch": out_bytes}},
                 "inner_iters_per_solve": inner / max(1, solves), "refine_steps_per_solve": outer / max(1, solves),
-                "peak_note": f"fp64 peak from unit counts at {SM_MAX_MHZ:.0f} MHz; bf16 peak measured (cuBLAS)"}
+                "peak_note": f"fp64 and fp32 peaks from unit counts at {SM_MAX_MHZ:.0f} MHz; bf16 and hbm {peak_kind} "
+                             f"(MEASURED_PEAKS.json burst figures)"}
 
     def fft_roofline(res):
         st = res["stages"]
@@ -674,18 +687,6 @@ def sampled_accuracy(w, t, plans, rows=4):
     return out
 
 
-def alu_probe():
-    """Measured FMA throughput of the GPU (the ALU peaks of the roofline are derived from the
-    unit counts; this checks them on the device)."""
-    src = os.path.join(ROOT, "paper_2109_04131_gb300", "probe", "alu_probe.cu")
-    exe = os.path.join(ROOT, "paper_2109_04131_gb300", "_build", "alu_probe")
-    os.makedirs(os.path.dirname(exe), exist_ok=True)
-    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
-    subprocess.run([nvcc if os.path.exists(nvcc) else "nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
-                    "-o", exe, src], check=True)
-    print(subprocess.run([exe], capture_output=True, text=True, check=True).stdout.strip(), flush=True)
-
-
 def profile_case(args):
     """A short, fixed run for ncu: increments 1..K of the 2-D workload (63x63 mesh, either precision)
     or of the 127x127 lognormal-type workload (mixed precision, large-mesh sampler)."""
@@ -709,7 +710,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--t", type=int, default=3, help="coupled increment timed as one step")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--ref-rows", type=int, default=24)
+    ap.add_argument("--ref-rows", type=int, default=0,
+                    help="lattice nodes per reference step (0: 24 per host core, the cpu_baseline sample)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-next-rows", action="store_true",
@@ -720,12 +722,7 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--profile-workload", choices=["mesh63", "mesh127"], default="mesh63",
                     help="profiling mode: the 63x63 2-D workload or the 127x127 lognormal-type one")
-    ap.add_argument("--alu-probe", action="store_true",
-                    help="build and run the FP64/FP32 FMA throughput probe (paper_2109_04131_gb300/probe)")
     args = ap.parse_args()
-    if args.alu_probe:
-        alu_probe()
-        return
     if args.profile_increments:
         profile_case(args)
         return

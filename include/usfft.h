@@ -42,7 +42,7 @@ typedef enum {
     USFFT_OK = 0,
     USFFT_EINVAL = 1,     /* invalid argument or problem (e.g. a_min <= 0, sizes out of range) */
     USFFT_ENOMEM = 2,     /* allocation failed or the hbm_budget_bytes would be exceeded */
-    USFFT_ELATTICE = 3,   /* no reconstructing lattice within max_lattice_trials x 400 sizes */
+    USFFT_ELATTICE = 3,   /* no reconstructing lattice within max_lattice_trials x max_lattice_sizes */
     USFFT_ENOCONV = 4,    /* a CG solve hit max_cg_iters before its tolerance */
     USFFT_ETIMEOUT = 5,   /* the device did not finish before the host-side deadline */
     USFFT_ECUDA = 6,      /* a CUDA runtime call failed (message holds the CUDA error string) */
@@ -91,7 +91,8 @@ typedef enum {
 
 typedef struct {
     int kind;                 /* USFFT_PDE_1D | USFFT_PDE_2D | USFFT_TRIGPOLY */
-    int n;                    /* PDE: interior nodes per side, 1 <= n <= 1023 (1-D), n <= 63 (2-D) */
+    int n;                    /* PDE: interior nodes per side, 1 <= n <= 1023 (1-D); 2-D: 1 <= n <= 127
+                                 with USFFT_MIXED, 1 <= n <= 63 with USFFT_FP64 and USFFT_MIXED_JACOBI */
     int d;                    /* stochastic dimension, 1 <= d <= 64 */
     int coef_model;           /* USFFT_COEF_* (PDE kinds) */
     double coef_scale;        /* c  */
@@ -150,6 +151,7 @@ typedef struct {
      *   (proof of Theorem 1.1, Appendix B).  Step 3 always uses one reconstructing lattice. */
     int rr_lattices;
     double rr_size_factor;    /* 0 = 2.0 */
+    int max_lattice_sizes;    /* lattice sizes the reconstructing-lattice search tries; 0 = 400 */
 } usfft_params;
 
 typedef struct {
@@ -293,6 +295,20 @@ usfft_status usfft_get_coefficients(const usfft_plan_t* plan, double* C /* host 
 usfft_status usfft_get_selection(const usfft_plan_t* plan, uint32_t* bitmap /* host, ceil(|J|/32) */,
                                  int64_t* n);
 
+/* Per-iteration inspection of the last detection step (Algorithm 1, steps 2b-2e, repeated over
+ * the r~ detection iterations; single reconstructing lattice only).  usfft_set_keep_iterations
+ * (plan, 1) makes every later detection step copy, after each iteration i, its samples U [M][G],
+ * coefficients C [G][|J|] and the union bitmap of iterations 1..i into plan-owned device buffers
+ * (r~ copies of each; counted in usfft_plan_bytes); on = 0 frees them.  Off by default (the
+ * copies cost device time and memory).  usfft_get_iteration: *count (may be NULL) receives the
+ * number of kept iterations of the last detection step (0 after a random-lattice step or with
+ * keeping off); if any of U, C, bitmap (host, sized as for usfft_get_samples,
+ * usfft_get_coefficients and usfft_get_selection) is non-NULL, iteration i (1 <= i <= count,
+ * else USFFT_EINVAL) is copied there.  Synchronises the plan's stream. */
+usfft_status usfft_set_keep_iterations(usfft_plan_t* plan, int on);
+usfft_status usfft_get_iteration(const usfft_plan_t* plan, int i, double* U, double* C, uint32_t* bitmap,
+                                 int32_t* count);
+
 /* The random rank-1 lattices of the last coupled step when params.rr_lattices > 0: *count
  * receives r~ * L (0 after a single-lattice step or a 1-D step), *t the number of lattice
  * coordinates; z (may be NULL) receives [count][t] generating vectors and M (may be NULL)
@@ -372,14 +388,18 @@ double usfft_draw_uniform(uint64_t seed, const uint64_t* fields, int nfields);
  * usfft_params.  If unconverged is non-NULL the call synchronises `stream` and stores how many
  * solves missed tol; with NULL it returns after enqueueing the work on `stream`.
  *
- * Scratch: one fixed 16 MiB device array in the library (the mode table and one slot of fp64
- * edge weights per resident CTA), held by every GPU that loads the library until the process
- * exits.  Requests that would need more are rejected with USFFT_EINVAL and a message in
- * usfft_last_error(NULL).  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make it before any stream capture.  All
- * calls share the array and it keeps the last call's contents: calls whose work overlaps on
- * the GPU (other streams, or other host threads) race and corrupt each other's results;
- * serialise them. */
+ * Scratch: one fixed 16 MiB device array in the library (a counter of unconverged solves and
+ * one slot of fp64 edge weights and diagonal per resident CTA; the sampler assembles the
+ * coefficient in separable form and needs no mode table).  Requests that would need more are
+ * rejected with USFFT_EINVAL and a message in usfft_last_error(NULL).  CUDA loads modules lazily
+ * by default, so a device first holds the array when the first call on it sets it up, and keeps
+ * it until the process exits: a caller that reserves nearly all of HBM for its own pool should
+ * make its first call on each device (count = 0 is enough: the set-up runs before that early
+ * return) before reserving the pool.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make it before any stream capture.
+ * All calls share the array and it keeps the last call's contents (the counter is cleared by
+ * every call): calls whose work overlaps on the GPU (other streams, or other host threads) race
+ * and corrupt each other's results; serialise them. */
 usfft_status usfft_sample_2d_static(const usfft_problem* problem, const int64_t* z, const double* tails,
                                     int64_t M, int64_t i0, int64_t count, double tol, int max_iters,
                                     double* U, void* stream, uint32_t* unconverged);

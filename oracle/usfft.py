@@ -171,7 +171,7 @@ class OracleRun:
         J = lattice.candidate_set(self.I_prefix, np.array(self.I1d[t], dtype=np.int64), p.N)
         if getattr(p, "rr_lattices", 0) > 0:
             return self._coupled_random(t, J, r_t, s_t)
-        z, M = lattice.search(J, t, p.seed, p.max_lattice_trials)
+        z, M = lattice.search(J, t, p.seed, p.max_lattice_trials, getattr(p, "max_lattice_sizes", 400))
         self.J, self.z, self.M = J, z, M
         found = set()
         if len(J) > 0:
@@ -243,7 +243,8 @@ class OracleRun:
         assert self.t == self.prob.d
         I = self.I_prefix
         d = self.prob.d
-        z, M = lattice.search(I, d, self.p.seed, self.p.max_lattice_trials, phase=rng.PHASE_RECON)
+        z, M = lattice.search(I, d, self.p.seed, self.p.max_lattice_trials, getattr(self.p, "max_lattice_sizes", 400),
+                              phase=rng.PHASE_RECON)
         if len(I) == 0:
             return I, z, M, np.zeros((0, 0), dtype=np.complex128)
         m = lattice.lattice_indices(I, z, M)

@@ -8,7 +8,8 @@ current PyTorch stream unless another stream is given.
 Module-level functions carry the C names (usfft_plan, usfft_increment, usfft_replay,
 usfft_rewind, usfft_resume, usfft_get_set, usfft_reconstruct, usfft_sample_points, usfft_evaluate,
 usfft_errors, usfft_statistics, usfft_plan_bytes, usfft_increment_many, usfft_get_lattice, usfft_get_candidates,
-usfft_get_samples, usfft_get_coefficients, usfft_get_selection, usfft_last_error,
+usfft_get_samples, usfft_get_coefficients, usfft_get_selection, usfft_set_keep_iterations,
+usfft_get_iteration, usfft_last_error,
 usfft_destroy); ``Plan`` wraps them.
 """
 from __future__ import annotations
@@ -42,7 +43,8 @@ class UsfftParams(ctypes.Structure):
                 ("precision", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
                 ("max_cg_iters", ctypes.c_int), ("max_lattice_trials", ctypes.c_int), ("cg_tol", ctypes.c_double),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
-                ("rr_lattices", ctypes.c_int), ("rr_size_factor", ctypes.c_double)]
+                ("rr_lattices", ctypes.c_int), ("rr_size_factor", ctypes.c_double),
+                ("max_lattice_sizes", ctypes.c_int)]
 
 
 class UsfftIncrementInfo(ctypes.Structure):
@@ -82,6 +84,8 @@ SIGNATURES = {
     "usfft_get_samples": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "usfft_get_coefficients": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "usfft_get_selection": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "usfft_set_keep_iterations": (ctypes.c_int, [_P, ctypes.c_int]),
+    "usfft_get_iteration": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "usfft_last_error": (ctypes.c_char_p, [_P]),
     "usfft_plan_bytes": (ctypes.c_size_t, [_P]),
     "usfft_increment_many": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
@@ -188,6 +192,7 @@ def make_params(par, alloc=None, free=None) -> UsfftParams:
     q.cg_tol = par.cg_tol
     q.rr_lattices = getattr(par, "rr_lattices", 0)
     q.rr_size_factor = getattr(par, "rr_size_factor", 0.0)
+    q.max_lattice_sizes = getattr(par, "max_lattice_sizes", 0)
     q.alloc = alloc if alloc is not None else ALLOC_FN()
     q.free = free if free is not None else FREE_FN()
     q.alloc_ctx = None
@@ -276,6 +281,14 @@ def usfft_get_coefficients(plan):
 
 def usfft_get_selection(plan):
     return plan.get_selection()
+
+
+def usfft_set_keep_iterations(plan, on=True):
+    return plan.set_keep_iterations(on)
+
+
+def usfft_get_iteration(plan, i):
+    return plan.get_iteration(i)
 
 
 def usfft_last_error(plan=None):
@@ -513,6 +526,31 @@ class Plan:
         self._ck(self._lib.usfft_get_selection(self.handle, words.ctypes.data, ctypes.byref(n)))
         bits = np.unpackbits(words.view(np.uint8), bitorder="little")[: n.value]
         return bits.astype(bool)
+
+    def set_keep_iterations(self, on: bool) -> None:
+        self._ck(self._lib.usfft_set_keep_iterations(self.handle, int(bool(on))))
+
+    def kept_iterations(self) -> int:
+        cnt = ctypes.c_int32(0)
+        self._ck(self._lib.usfft_get_iteration(self.handle, 0, None, None, None, ctypes.byref(cnt)))
+        return cnt.value
+
+    def get_iteration(self, i: int):
+        """(U [M][G], C [G][|J|] complex, union bitmap of iterations 1..i as bool [|J|]) of
+        detection iteration i (1-based) of the last step (keeping must be on)."""
+        M = ctypes.c_int64(0)
+        G = ctypes.c_int64(0)
+        n = ctypes.c_int64(0)
+        self._ck(self._lib.usfft_get_samples(self.handle, None, ctypes.byref(M), ctypes.byref(G)))
+        self._ck(self._lib.usfft_get_coefficients(self.handle, None, ctypes.byref(G), ctypes.byref(n)))
+        U = np.zeros((M.value, G.value), dtype=np.float64)
+        C = np.zeros((G.value, n.value, 2), dtype=np.float64)
+        words = np.zeros(max(1, (n.value + 31) // 32), dtype=np.uint32)
+        cnt = ctypes.c_int32(0)
+        self._ck(self._lib.usfft_get_iteration(self.handle, int(i), U.ctypes.data, C.ctypes.data, words.ctypes.data,
+                                               ctypes.byref(cnt)))
+        bits = np.unpackbits(words.view(np.uint8), bitorder="little")[: n.value].astype(bool)
+        return U, C[..., 0] + 1j * C[..., 1], bits
 
     def close(self):
         if self.handle:

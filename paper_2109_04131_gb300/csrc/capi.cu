@@ -91,6 +91,11 @@ struct usfft_plan_s {
     int cg_iters_max = 0;
     int64_t h2d = 0, d2h = 0;
     bool replay_valid = false;
+    // per-iteration copies of the last single-lattice detection step (usfft_set_keep_iterations):
+    // samples, coefficients and the union bitmap after iteration i (cumulative over 1..i)
+    bool keep_iters = false;
+    int kept = 0;
+    std::vector<Buf> kU, kC, kB;
     // stage timing (usfft_set_timing): event pairs per stage launch
     bool timing = false;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
@@ -523,7 +528,28 @@ usfft_status run_rr_device(usfft_plan_t* plan) {
 }
 
 // device part of a detection step: r~ iterations of sample -> FFT+gather -> select/union
+// copies of iteration it's samples, coefficients and union bitmap (inspection only)
+usfft_status keep_iteration(usfft_plan_t* plan, size_t it) {
+    const size_t ub = sizeof(double) * (size_t)plan->M * plan->G, cb = sizeof(double2) * (size_t)plan->nJ * plan->G;
+    const size_t bb = sizeof(uint32_t) * (size_t)((plan->nJ + 31) / 32);
+    if (plan->kU.size() <= it) {
+        plan->kU.resize(it + 1);
+        plan->kC.resize(it + 1);
+        plan->kB.resize(it + 1);
+    }
+    usfft_status st;
+    if ((st = ensure(plan, plan->kU[it], ub, "kept samples")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->kC[it], cb, "kept coefficients")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->kB[it], bb, "kept bitmap")) != USFFT_OK) return st;
+    CK(cudaMemcpyAsync(plan->kU[it].p, plan->U.p, ub, cudaMemcpyDeviceToDevice, plan->stream));
+    CK(cudaMemcpyAsync(plan->kC[it].p, plan->C.p, cb, cudaMemcpyDeviceToDevice, plan->stream));
+    CK(cudaMemcpyAsync(plan->kB[it].p, plan->bitmap.p, bb, cudaMemcpyDeviceToDevice, plan->stream));
+    plan->kept = (int)it + 1;
+    return USFFT_OK;
+}
+
 usfft_status run_step_device(usfft_plan_t* plan, bool first_1d_sets_theta) {
+    plan->kept = 0;
     if (plan->rr_active) return run_rr_device(plan);
     const int64_t nJ = plan->nJ;
     CK(cudaMemsetAsync(plan->bitmap.p, 0, sizeof(uint32_t) * (size_t)((nJ + 31) / 32), plan->stream));
@@ -557,6 +583,10 @@ usfft_status run_step_device(usfft_plan_t* plan, bool first_1d_sets_theta) {
             StageTimer timer(plan, USFFT_STAGE_SELECT);
             CK(launch_select_union((const double2*)plan->C.p, plan->G, nJ, plan->theta, plan->s_tilde,
                                    (uint32_t*)plan->bitmap.p, plan->stream, &plan->launches));
+        }
+        if (plan->keep_iters) {
+            usfft_status st2 = keep_iteration(plan, it);
+            if (st2 != USFFT_OK) return st2;
         }
     }
     return USFFT_OK;
@@ -684,6 +714,7 @@ usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params
     plan->par = pa;
     if (plan->par.max_cg_iters <= 0) plan->par.max_cg_iters = 4000;
     if (plan->par.max_lattice_trials <= 0) plan->par.max_lattice_trials = 64;
+    if (plan->par.max_lattice_sizes <= 0) plan->par.max_lattice_sizes = 400;
     if (!(plan->par.cg_tol > 0.0)) plan->par.cg_tol = 1e-13;
     plan->stream = (cudaStream_t)stream;
     plan->G = G;
@@ -826,7 +857,7 @@ usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
         } else {
             std::vector<int64_t> z;
             int64_t M = 0;
-            if (!lattice_search(J.data(), nJ, t, plan->par.seed, plan->par.max_lattice_trials, 400, z, M))
+            if (!lattice_search(J.data(), nJ, t, plan->par.seed, plan->par.max_lattice_trials, plan->par.max_lattice_sizes, z, M))
                 return fail(plan, USFFT_ELATTICE, "no reconstructing rank-1 lattice found");
             std::vector<int64_t> m((size_t)nJ);
             for (int64_t a = 0; a < nJ; ++a) {
@@ -1060,6 +1091,42 @@ usfft_status usfft_get_selection(const usfft_plan_t* plan_c, uint32_t* bitmap, i
     return USFFT_OK;
 }
 
+usfft_status usfft_set_keep_iterations(usfft_plan_t* plan, int on) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    plan->keep_iters = on != 0;
+    if (!plan->keep_iters) {
+        usfft_status st = wait_stream(plan);
+        if (st != USFFT_OK) return st;
+        for (std::vector<Buf>* v : {&plan->kU, &plan->kC, &plan->kB})
+            for (Buf& b : *v) buf_free(plan, b);
+        plan->kU.clear();
+        plan->kC.clear();
+        plan->kB.clear();
+        plan->kept = 0;
+    }
+    return USFFT_OK;
+}
+
+usfft_status usfft_get_iteration(const usfft_plan_t* plan_c, int i, double* U, double* C, uint32_t* bitmap,
+                                 int32_t* count) {
+    usfft_plan_t* plan = const_cast<usfft_plan_t*>(plan_c);
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (count) *count = plan->kept;
+    if (!U && !C && !bitmap) return USFFT_OK;
+    if (i < 1 || i > plan->kept) return fail(plan, USFFT_EINVAL, "usfft_get_iteration: no such kept iteration");
+    const size_t it = (size_t)(i - 1);
+    if (U && plan->M > 0)
+        CK(cudaMemcpyAsync(U, plan->kU[it].p, sizeof(double) * (size_t)plan->M * plan->G, cudaMemcpyDeviceToHost,
+                           plan->stream));
+    if (C && plan->nJ > 0)
+        CK(cudaMemcpyAsync(C, plan->kC[it].p, sizeof(double2) * (size_t)plan->nJ * plan->G, cudaMemcpyDeviceToHost,
+                           plan->stream));
+    if (bitmap && plan->nJ > 0)
+        CK(cudaMemcpyAsync(bitmap, plan->kB[it].p, sizeof(uint32_t) * (size_t)((plan->nJ + 31) / 32),
+                           cudaMemcpyDeviceToHost, plan->stream));
+    return wait_stream(plan);
+}
+
 usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, double* coefs, int coefs_on_device) {
     if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
     if (plan->t != plan->d) return fail(plan, USFFT_ESTATE, "usfft_reconstruct needs all d increments done");
@@ -1076,7 +1143,7 @@ usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, do
     // one reconstructing rank-1 lattice for I (Algorithm 1, step 3; single-lattice reading)
     std::vector<int64_t> z;
     int64_t M = 0;
-    if (!lattice_search(plan->Ipre.data(), nI, d, plan->par.seed, plan->par.max_lattice_trials, 400, z, M,
+    if (!lattice_search(plan->Ipre.data(), nI, d, plan->par.seed, plan->par.max_lattice_trials, plan->par.max_lattice_sizes, z, M,
                         PHASE_RECON))
         return fail(plan, USFFT_ELATTICE, "no reconstructing rank-1 lattice for the detected set");
     std::vector<int64_t> m((size_t)nI);
@@ -1367,6 +1434,8 @@ void usfft_destroy(usfft_plan_t* plan) {
                    &plan->rr_gk, &plan->rr_gm2, &plan->rr_src, &plan->rr_twid, &plan->rr_C, &plan->fpos,
                    &plan->fmk};
     for (Buf* b : bufs) buf_free(plan, *b);
+    for (std::vector<Buf>* v : {&plan->kU, &plan->kC, &plan->kB})
+        for (Buf& b : *v) buf_free(plan, b);
     if (plan->pinned) cudaFreeHost(plan->pinned);
     if (plan->ev0) cudaEventDestroy(plan->ev0);
     if (plan->ev1) cudaEventDestroy(plan->ev1);

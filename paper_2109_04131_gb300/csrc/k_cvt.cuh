@@ -23,13 +23,15 @@ __device__ __forceinline__ double f2d_exact(float f) {
 
 // double -> float rounded to nearest, ties away from zero (round to nearest even differs on
 // exact ties only); magnitudes below the smallest normal float give a signed zero, above the
-// largest finite one inf; nan stays nan.  The rounding carry runs into the exponent field.
+// largest finite one inf; inf stays inf and nan stays nan.  The rounding carry runs into the exponent field.
 __device__ __forceinline__ float d2f_round(double x) {
     const uint32_t uh = (uint32_t)__double2hiint(x), ul = (uint32_t)__double2loint(x);
     const uint32_t e = (uh >> 20) & 0x7ffu;
     uint32_t v = ((((uh << 3) | (ul >> 29)) - (896u << 23)) + ((ul >> 28) & 1u)) & 0x7fffffffu;
     v = e < 897u ? 0u : v;
-    v = e > 1150u ? (e == 2047u ? 0x7fc00000u : 0x7f800000u) : v;
+    // exponent field 2047: a nan (non-zero fraction) stays a quiet nan, +-inf stays inf
+    const uint32_t special = ((uh & 0xfffffu) | ul) ? 0x7fc00000u : 0x7f800000u;
+    v = e > 1150u ? (e == 2047u ? special : 0x7f800000u) : v;
     return __uint_as_float(v | (uh & 0x80000000u));
 }
 

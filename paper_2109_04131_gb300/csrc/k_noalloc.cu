@@ -5,10 +5,15 @@
 // cudaMalloc / cudaFree or an allocating library routine -- e.g. a plug-in running inside a
 // framework that has already reserved (almost) all of HBM for its own pool, or a
 // latency-critical loop that must never enter the allocator.  Such a caller passes its own
-// input description and output buffer; the scratch the sampler needs (the mode table
-// c j^-mu psi_j(centroid_e) and one slot of fp64 edge weights per resident CTA) lives in
-// g_static_scratch below, which every GPU that loads this library holds until the process
-// exits.
+// input description and output buffer; the scratch the sampler needs (a counter of unconverged
+// solves and one slot of fp64 edge weights and diagonal per resident CTA) lives in g_static_scratch below.
+//
+// When the array is backed by device memory: CUDA loads a module lazily by default (CUDA 12.2
+// and later), so the driver places g_static_scratch on a device when this file's module is
+// first used there -- the set-up of the first call on that device -- not when the library is
+// loaded.  From then on the device holds it until the process exits.  A caller that reserves
+// nearly all of HBM for its own pool should therefore make its first call on each device (a
+// call with count = 0 is enough) before it reserves the pool.
 //
 // Set-up: the first call on a device (with that device current) looks up the device
 // address of g_static_scratch with cudaGetSymbolAddress -- the host-side symbol is only a
@@ -51,9 +56,11 @@ usfft_status scratch_address(void** out) {
     if (!g_scratch_addr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p)
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();   // do not leave the error for the next launch check of any entry point
             return static_fail(USFFT_ECUDA, std::string("cudaGetSymbolAddress(g_static_scratch): ") +
                                                 cudaGetErrorString(e));
+        }
         g_scratch_addr[dev] = p;
     }
     *out = g_scratch_addr[dev];
@@ -90,33 +97,32 @@ extern "C" usfft_status usfft_sample_2d_static(const usfft_problem* problem, con
         ns.z[j] = z[j] < 0 ? -1 : z[j];
         ns.tail[j] = tails[j];
     }
+    // scratch layout: [counters, 256 bytes][per-CTA slots of fp64 edge weights and diagonal].
+    // The mixed sampler assembles the coefficient in separable form from c and mu directly, so
+    // it needs no mode table.
+    const int n = pr.n;
+    const size_t cnt_bytes = 256;
+    const size_t slot_bytes = sample_2d_scratch_bytes(n, USFFT_MIXED, 1);
+    if (cnt_bytes + slot_bytes > kStaticScratchBytes)
+        return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: the problem needs more than the 16 MiB static scratch");
+    int blocks = sample_2d_default_blocks(n, USFFT_MIXED);
+    const int fit = (int)((kStaticScratchBytes - cnt_bytes) / slot_bytes);
+    if (blocks > fit) blocks = fit;
+
+    // the per-device set-up comes before the count == 0 return, so that an empty call can
+    // serve as the set-up call
+    void* base = nullptr;
+    usfft_status st = scratch_address(&base);
+    if (st != USFFT_OK) return st;
     if (count == 0) {
         if (unconverged) *unconverged = 0;
         return USFFT_OK;
     }
-
-    // scratch layout: [mode table d*E doubles][2 counters][per-CTA weight slots]
-    const int n = pr.n;
-    const size_t E = 2 * (size_t)(n + 1) * (n + 1);
-    const size_t psi_bytes = (sizeof(double) * E * pr.d + 255) & ~(size_t)255;
-    const size_t cnt_bytes = 256;
-    const size_t slot_bytes = sample_2d_scratch_bytes(n, USFFT_MIXED, 1);
-    if (psi_bytes + cnt_bytes + slot_bytes > kStaticScratchBytes)
-        return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: the problem needs more than the 16 MiB static scratch");
-    int blocks = sample_2d_default_blocks(n, USFFT_MIXED);
-    const int fit = (int)((kStaticScratchBytes - psi_bytes - cnt_bytes) / slot_bytes);
-    if (blocks > fit) blocks = fit;
-
-    void* base = nullptr;
-    usfft_status st = scratch_address(&base);
-    if (st != USFFT_OK) return st;
-    double* psi = reinterpret_cast<double*>(base);
-    unsigned int* fails = reinterpret_cast<unsigned int*>(static_cast<unsigned char*>(base) + psi_bytes);
-    double* slots = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + psi_bytes + cnt_bytes);
+    unsigned int* fails = reinterpret_cast<unsigned int*>(base);
+    double* slots = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + cnt_bytes);
     cudaStream_t s = (cudaStream_t)stream;
 
-    cudaError_t e = launch_psi_table(USFFT_PDE_2D, n, pr.d, pr.coef_scale, pr.coef_decay, psi, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(fails, 0, sizeof(unsigned int), s);   // counters start at zero
+    cudaError_t e = cudaMemsetAsync(fails, 0, sizeof(unsigned int), s);   // the counter starts at zero
     if (e == cudaSuccess) {
         CgConfig cg;
         cg.precision = USFFT_MIXED;
@@ -125,7 +131,7 @@ extern "C" usfft_status usfft_sample_2d_static(const usfft_problem* problem, con
         cg.blocks = blocks;
         cg.coef_scale = pr.coef_scale;
         cg.coef_decay = pr.coef_decay;
-        e = launch_sample_2d(ns, n, pr.coef_model, pr.f_const, psi, cg, i0, count, U, nullptr, fails, nullptr, slots,
+        e = launch_sample_2d(ns, n, pr.coef_model, pr.f_const, nullptr, cg, i0, count, U, nullptr, fails, nullptr, slots,
                              slot_bytes * (size_t)blocks, s, nullptr);
     }
     if (e != cudaSuccess) return static_fail(USFFT_ECUDA, std::string("usfft_sample_2d_static: ") + cudaGetErrorString(e));

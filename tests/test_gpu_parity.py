@@ -223,6 +223,56 @@ def test_host_injected_failures(B):
     p.close()
 
 
+def test_lattice_search_exhaustion_is_elattice(B):
+    # full grid [-4,4]^2 (81 candidates at t = 2): with one size (M = 81) and one trial, the draw
+    # of seed 3 is not reconstructing on either side (the oracle's search raises as well); the
+    # plan reports USFFT_ELATTICE and stays usable
+    from oracle import lattice
+    prob = W.trigpoly_grid(G=2, d=2, K=4, seed=3)
+    J = lattice.candidate_set(np.arange(-4, 5)[:, None], np.arange(-4, 5), N=4)
+    with pytest.raises(RuntimeError):
+        lattice.search(J, 2, 3, trials=1, max_sizes=1)
+    params = W.Params(N=4, s=200, s_local=200, delta=1e-9, delta_is_relative=False, r=1, seed=3,
+                      max_lattice_trials=1, max_lattice_sizes=1)
+    plan = B.Plan(prob, params)
+    plan.increment()
+    assert len(plan.get_set()) == 9
+    with pytest.raises(B.UsfftError) as e:
+        plan.increment()
+    assert e.value.status == 3
+    plan.close()
+    # the same increment with the default search succeeds
+    plan = B.Plan(prob, dataclasses.replace(params, max_lattice_trials=64, max_lattice_sizes=400))
+    plan.increment()
+    plan.increment()
+    assert len(plan.get_set()) == 81
+    plan.close()
+
+
+def test_host_deadline_is_etimeout_and_the_increment_can_be_retried(B, monkeypatch):
+    # a host deadline of 1 ns around the first wait of a normal increment (2-D 63x63 mesh, fp64:
+    # the first wait follows about a millisecond of FE solves, so the device is still busy): the
+    # call returns USFFT_ETIMEOUT while the work finishes on the GPU; after a synchronize the same
+    # plan runs the increment again and gives the result of a fresh plan
+    import torch
+    w = W.with_precision(W.c2(1), W.PRECISION_FP64)
+    plan = B.Plan(w.problem, w.params)
+    monkeypatch.setenv("USFFT_TIMEOUT_S", "1e-9")
+    with pytest.raises(B.UsfftError) as e:
+        plan.increment()
+    assert e.value.status == 5
+    monkeypatch.delenv("USFFT_TIMEOUT_S")
+    torch.cuda.synchronize()
+    info = plan.increment()
+    assert info["t"] == 1
+    fresh = B.Plan(w.problem, w.params)
+    fresh.increment()
+    assert np.array_equal(plan.get_set(), fresh.get_set())
+    assert np.array_equal(plan.get_coefficients(), fresh.get_coefficients())
+    fresh.close()
+    plan.close()
+
+
 def test_increment_after_last_is_a_state_error(B):
     prob = W.trigpoly(G=2, d=2, N=3, seed=1, base_terms=2, node_terms=1, kmax=2, mag_lo=1e-2)
     params = W.Params(N=3, s=10, s_local=10, delta=1e-9, delta_is_relative=False, r=1, seed=1)

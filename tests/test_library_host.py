@@ -57,7 +57,7 @@ int main(void) {
   P(usfft_problem, tp_freqs) P(usfft_problem, tp_coefs) P(usfft_problem, coef_scale)
   P(usfft_problem, theta_map) P(usfft_problem, map_shift)
   P(usfft_params, seed) P(usfft_params, hbm_budget_bytes) P(usfft_params, cg_tol) P(usfft_params, alloc_ctx)
-  P(usfft_params, rr_lattices) P(usfft_params, rr_size_factor)
+  P(usfft_params, rr_lattices) P(usfft_params, rr_size_factor) P(usfft_params, max_lattice_sizes)
   P(usfft_increment_info, M) P(usfft_increment_info, kernel_launches) P(usfft_increment_info, ms_host_plan)
   P(usfft_increment_info, d2h_bytes)
   return 0;
@@ -178,3 +178,16 @@ def test_random_lattice_rule_is_bit_exact_with_the_oracle(binding, t, i, n_prev,
     assert all(math.gcd(int(v), int(m)) == 1 for row, m in zip(z, M) for v in row)
     with pytest.raises(binding.UsfftError):
         binding.usfft_random_lattices(t, i, n_prev, n_t, s_t, 32, factor, seed)
+
+
+def test_lattice_search_exhaustion(binding):
+    # one size and one trial: the oracle's search and the library's both give up (ELATTICE)
+    J = lattice.candidate_set(np.arange(-4, 5)[:, None], np.arange(-4, 5), N=4)
+    with pytest.raises(RuntimeError):
+        lattice.search(J, 2, 3, trials=1, max_sizes=1)
+    with pytest.raises(binding.UsfftError) as e:
+        binding.usfft_search_lattice(J, 2, 3, trials=1, max_sizes=1)
+    assert e.value.status == 3
+    z0, M0 = lattice.search(J, 2, 2, trials=1, max_sizes=1)
+    z1, M1 = binding.usfft_search_lattice(J, 2, 2, trials=1, max_sizes=1)
+    assert M0 == M1 == 81 and np.array_equal(z0, z1)

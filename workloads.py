@@ -83,6 +83,7 @@ class Params:
     rr_lattices: int = 0               # 0: one reconstructing lattice per coupled step; odd L >= 1:
                                        # L random rank-1 lattices (Algorithm A), median estimate
     rr_size_factor: float = 2.0        # random lattice size >= factor * max(|I^(1..t-1)|, |I^(t)|, s~)
+    max_lattice_sizes: int = 400       # sizes the reconstructing-lattice search tries
 
 
 @dataclass
