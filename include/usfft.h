@@ -88,11 +88,16 @@ typedef enum {
                                  tensor-core GEMMs); 1-D: fp64; the lattice FFT in double-float
                                  (pairs of fp32), its gathered output and the selection in fp64 */
 #define USFFT_MIXED_JACOBI 2  /* 2-D: the same refinement around fp32 Jacobi-CG (for comparison) */
+#define USFFT_FP64_DST 3      /* fp64 everywhere; 2-D solves by fp64 CG preconditioned by the same
+                                 constant-coefficient operator as USFFT_MIXED, applied exactly (the
+                                 sine transforms as fp64 matrix products): against USFFT_MIXED it
+                                 differs in the arithmetic precision only; 1-D and TRIGPOLY as FP64 */
 
 typedef struct {
     int kind;                 /* USFFT_PDE_1D | USFFT_PDE_2D | USFFT_TRIGPOLY */
     int n;                    /* PDE: interior nodes per side, 1 <= n <= 1023 (1-D); 2-D: 1 <= n <= 127
-                                 with USFFT_MIXED, 1 <= n <= 63 with USFFT_FP64 and USFFT_MIXED_JACOBI */
+                                 with USFFT_MIXED and USFFT_FP64_DST, 1 <= n <= 63 with USFFT_FP64 and
+                                 USFFT_MIXED_JACOBI */
     int d;                    /* stochastic dimension, 1 <= d <= 64 */
     int coef_model;           /* USFFT_COEF_* (PDE kinds) */
     double coef_scale;        /* c  */
@@ -130,7 +135,7 @@ typedef struct {
     int delta_is_relative;    /* relative: A = max_g |c~_{g,0}| of the 1-D detection t=1, i=1 */
     int r;                    /* detection iterations r (r~ = 1 at t = d) */
     uint64_t seed;            /* key of the counter-based SplitMix64 draws (tails, lattices) */
-    int precision;            /* USFFT_FP64 | USFFT_MIXED */
+    int precision;            /* USFFT_FP64 | USFFT_MIXED | USFFT_MIXED_JACOBI | USFFT_FP64_DST */
     size_t hbm_budget_bytes;  /* 0 = unlimited; otherwise ENOMEM beyond this many plan bytes */
     int max_cg_iters;         /* per CG solve (inner solve in MIXED); 0 = 4000 */
     int max_lattice_trials;   /* generating vectors tried per lattice size; 0 = 64 */

@@ -658,7 +658,8 @@ usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params
     if (pa.N < 1 || pa.N > 127) return fail(nullptr, USFFT_EINVAL, "N must lie in [1, 127] (int8 frequencies)");
     if (pa.r < 1 || pa.s < 0 || pa.s_local < 0) return fail(nullptr, USFFT_EINVAL, "r >= 1, s >= 0, s_local >= 0");
     if (!(pa.delta >= 0.0)) return fail(nullptr, USFFT_EINVAL, "delta must be >= 0");
-    if (pa.precision != USFFT_FP64 && pa.precision != USFFT_MIXED && pa.precision != USFFT_MIXED_JACOBI)
+    if (pa.precision != USFFT_FP64 && pa.precision != USFFT_MIXED && pa.precision != USFFT_MIXED_JACOBI &&
+        pa.precision != USFFT_FP64_DST)
         return fail(nullptr, USFFT_EINVAL, "precision");
     if (pa.rr_lattices < 0 || pa.rr_lattices > 31 || (pa.rr_lattices > 0 && pa.rr_lattices % 2 == 0))
         return fail(nullptr, USFFT_EINVAL, "rr_lattices must be 0 or odd in [1, 31]");
@@ -671,9 +672,9 @@ usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params
         E = pr.n + 1;
     } else if (pr.kind == USFFT_PDE_2D) {
         if (pr.n < 1 || pr.n > 127) return fail(nullptr, USFFT_EINVAL, "2-D: n must lie in [1, 127]");
-        if (pr.n > 63 && pa.precision != USFFT_MIXED)
-            return fail(nullptr, USFFT_EINVAL, "2-D: n > 63 runs in the MIXED precision mode only");
-        if (pr.n > 63 && big_smem_bytes(pr.n, pr.d) > 232448)
+        if (pr.n > 63 && pa.precision != USFFT_MIXED && pa.precision != USFFT_FP64_DST)
+            return fail(nullptr, USFFT_EINVAL, "2-D: n > 63 runs in the MIXED and FP64_DST precision modes only");
+        if (pr.n > 63 && pa.precision == USFFT_MIXED && big_smem_bytes(pr.n, pr.d) > 232448)
             return fail(nullptr, USFFT_EINVAL, "2-D: d too large for the shared-memory tables at n > 63");
         if (pa.precision == USFFT_MIXED_JACOBI && pr.n < 4) return fail(nullptr, USFFT_EINVAL, "2-D mixed: n >= 4");
         G = pr.n * pr.n;

@@ -34,6 +34,10 @@ cudaError_t launch_dst_npt(const Pcg2dArgs& a, int blocks, int threads, cudaStre
 cudaError_t launch_mixed_big(const Pcg2dArgs& a, int blocks, cudaStream_t s);
 template <int NPT>
 int dst_resident_blocks(int threads, int d, int n);
+// fp64 sampler with the same preconditioner (k_sample2d_dst64.cu)
+size_t fp64_dst_slot_bytes(int n, int d);
+int fp64_dst_default_blocks(int n, int d);
+cudaError_t launch_fp64_dst(const Pcg2dArgs& a, int blocks, cudaStream_t s);
 
 // Shared-memory layout (doubles): ph[(n+2)^2] | wx[n(n+1)] | wy[(n+1)n] | sj[d] | red[2*34]
 // wx[qq(n+1)+P]: edge (P,qq+1)-(P+1,qq+1) (global node coords), P = 0..n
@@ -376,6 +380,7 @@ static int resident_blocks(int precision, int threads, int n) {
 
 // persistent grid: one wave of resident CTAs on every SM
 int sample_2d_default_blocks(int n, int precision) {
+    if (precision == USFFT_FP64_DST) return fp64_dst_default_blocks(n, USFFT_MAX_D);
     if (n > 63) {                       // large-mesh MIXED kernel: one 1024-thread CTA per SM
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -406,6 +411,7 @@ int sample_2d_default_blocks(int n, int precision) {
 
 size_t sample_2d_scratch_bytes(int n, int precision, int blocks) {
     if (precision == USFFT_FP64) return 0;
+    if (precision == USFFT_FP64_DST) return fp64_dst_slot_bytes(n, USFFT_MAX_D) * (size_t)blocks;
     const size_t W = (size_t)n + 2;
     if (precision == USFFT_MIXED) return sizeof(double) * (n > 63 ? 10 : 3) * W * W * (size_t)blocks;
     return sizeof(double) * 2 * (size_t)n * (n + 1) * (size_t)blocks;
@@ -433,7 +439,8 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
                              unsigned int* fail_count, unsigned long long* iters_sum, double* scratch,
                              size_t scratch_bytes, cudaStream_t s, int* launches) {
     if (count <= 0) return cudaSuccess;
-    if (n < 1 || n > 127 || (n > 63 && cg.precision != USFFT_MIXED)) return cudaErrorInvalidValue;
+    if (n < 1 || n > 127 || (n > 63 && cg.precision != USFFT_MIXED && cg.precision != USFFT_FP64_DST))
+        return cudaErrorInvalidValue;
     Pcg2dArgs a;
     a.ns = ns;
     a.n = n;
@@ -462,6 +469,11 @@ cudaError_t launch_sample_2d(const NodeSpec& ns, int n, int coef_model, double f
     if (cg.precision != USFFT_FP64 && scratch_bytes < sample_2d_scratch_bytes(n, cg.precision, blocks))
         return cudaErrorInvalidValue;
     cudaError_t e;
+    if (cg.precision == USFFT_FP64_DST) {
+        e = launch_fp64_dst(a, blocks, s);
+        if (launches) ++*launches;
+        return e;
+    }
     if (n > 63) {
         e = launch_mixed_big(a, blocks, s);
         if (launches) ++*launches;

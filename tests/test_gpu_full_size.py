@@ -110,7 +110,7 @@ def check_coupled_step(B, plan, run, w, t, rows_per_iter=5, dft_nodes=None, ctx=
     return info, J, got
 
 
-@pytest.mark.parametrize("precision", [W.PRECISION_MIXED, W.PRECISION_FP64])
+@pytest.mark.parametrize("precision", [W.PRECISION_MIXED, W.PRECISION_FP64, W.PRECISION_FP64_DST])
 def test_c2_timed_step_t3_full_size(B, c2_state_t2, precision):
     w, run0 = c2_state_t2
     w = W.with_precision(w, precision)
@@ -140,15 +140,17 @@ def test_c2_two_pass_step_t4(B, c2_state_t2):
     plan.close()
 
 
-def test_c3_coupled_step_t3(B):
+@pytest.mark.parametrize("precision", [W.PRECISION_MIXED, W.PRECISION_FP64_DST])
+def test_c3_coupled_step_t3(B, precision):
     # the 128x128 mesh (G = 16129), lognormal-type coefficient, d = 20, r = 2: increments 1 and 2 on
-    # the GPU, then step 3 from that state against the oracle
-    w = W.c3(1)
+    # the GPU, then step 3 from that state against the oracle (the large-mesh mixed sampler and the
+    # fp64 sampler with the same preconditioner)
+    w = W.with_precision(W.c3(1), precision)
     plan = B.Plan(w.problem, w.params)
     plan.increment()
     info2 = plan.increment()
     run = OracleRun(w.problem, w.params)
     run.resume(2, plan.get_set(), info2["theta"])      # theta: fixed by the plan's first 1-D detection
     run.t = 3
-    check_coupled_step(B, plan, run, w, 3, rows_per_iter=3, ctx="c3 t=3")
+    check_coupled_step(B, plan, run, w, 3, rows_per_iter=3, ctx=f"c3 t=3 precision {precision}")
     plan.close()

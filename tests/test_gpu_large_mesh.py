@@ -83,7 +83,12 @@ def test_large_mesh_boundary_sizes(B, n):
     U = plan.sample_points(Y)
     Uo = ev.sample_points(w.problem, Y, run.mesh)
     assert np.max(np.abs(U - Uo)) <= TOL * np.max(np.abs(Uo))
-    # the fp64 and Jacobi modes stay limited to n <= 63
+    # the fp64 mode with the same preconditioner serves these sizes too
+    p64 = B.Plan(w.problem, dataclasses.replace(w.params, precision=W.PRECISION_FP64_DST))
+    U64 = p64.sample_points(Y)
+    assert np.max(np.abs(U64 - Uo)) <= TOL * np.max(np.abs(Uo))
+    p64.close()
+    # the Jacobi modes stay limited to n <= 63
     with pytest.raises(B.UsfftError):
         B.Plan(w.problem, dataclasses.replace(w.params, precision=W.PRECISION_FP64))
     plan.close()

@@ -143,7 +143,8 @@ def test_trigpoly_two_pass_fft(B):
     plan.close()
 
 
-@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED, W.PRECISION_MIXED_JACOBI])
+@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED, W.PRECISION_MIXED_JACOBI,
+                                       W.PRECISION_FP64_DST])
 def test_small_2d_matches_oracle(B, precision):
     w = W.with_precision(W.small_2d(n=15, d=4, seed=2, N=6, s=30), precision)
     plan = B.Plan(w.problem, w.params)
@@ -156,8 +157,11 @@ def test_small_2d_matches_oracle(B, precision):
 
 def test_2d_ragged_mesh_sizes(B):
     # n = 9 (81 nodes: one partial warp) and n = 33 (1089 nodes: two nodes per thread, ragged;
-    # DST tiles padded from 33 to 48), both precisions
-    for n, prec in ((9, W.PRECISION_FP64), (33, W.PRECISION_FP64), (9, W.PRECISION_MIXED), (33, W.PRECISION_MIXED)):
+    # DST tiles padded from 33 to 48), both precisions; the fp64 sine-transform mode also at
+    # n = 1 and 2 (a single transform tile, odd and even sizes)
+    for n, prec in ((9, W.PRECISION_FP64), (33, W.PRECISION_FP64), (9, W.PRECISION_MIXED), (33, W.PRECISION_MIXED),
+                    (1, W.PRECISION_FP64_DST), (2, W.PRECISION_FP64_DST), (9, W.PRECISION_FP64_DST),
+                    (33, W.PRECISION_FP64_DST)):
         w = W.with_precision(W.small_2d(n=n, d=3, seed=5, N=4, s=20), prec)
         plan = B.Plan(w.problem, w.params)
         run = OracleRun(w.problem, w.params, keep=True)

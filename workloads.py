@@ -34,6 +34,7 @@ MAP_NORMAL = 2          # Theta_j = y_j standard normal, tau_1 o tau_{2,Delta} p
 PRECISION_FP64 = 0
 PRECISION_MIXED = 1
 PRECISION_MIXED_JACOBI = 2
+PRECISION_FP64_DST = 3
 
 
 @dataclass
