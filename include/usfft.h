@@ -46,7 +46,8 @@ typedef enum {
     USFFT_ENOCONV = 4,    /* a CG solve hit max_cg_iters before its tolerance */
     USFFT_ETIMEOUT = 5,   /* the device did not finish before the host-side deadline */
     USFFT_ECUDA = 6,      /* a CUDA runtime call failed (message holds the CUDA error string) */
-    USFFT_ESTATE = 7      /* call not valid in the plan's state (e.g. increment after t = d) */
+    USFFT_ESTATE = 7,     /* call not valid in the plan's state (e.g. increment after t = d) */
+    USFFT_ECOMM = 8       /* the collective hook of the sharded form reported a failure */
 } usfft_status;
 
 /* problem kinds */
@@ -339,6 +340,49 @@ size_t usfft_plan_bytes(const usfft_plan_t* plan);
  * in plan order (USFFT_EINVAL for a NULL or repeated plan, nothing run). */
 usfft_status usfft_increment_many(usfft_plan_t* const* plans, int count, int max_threads,
                                   usfft_increment_info* infos, usfft_status* statuses);
+
+/* ---- Sharded form: one instance over several GPUs (one process or thread per rank) ----
+ *
+ * The coupled step of increment t splits by lattice residue: with P ranks the lattice size M is
+ * taken from the sizes that are also multiples of P (the rule of usfft_search_lattice_multiple),
+ * rank p solves the FE problem at the nodes i = p + P i2 (i2 < M / P) only, runs the length-M/P
+ * lattice FFT over them, reads it at k.z mod (M/P) and multiplies by e^{-2 pi i p (k.z mod M) / M}
+ * / P: the sum of these partial coefficients over the ranks is the DFT of Algorithm 1, step 2d.
+ * The exchange is an all-reduce through the caller's hook (below): a sum of the G x |J_t| complex
+ * coefficients per detection iteration, then each rank selects the <= s~ largest >= theta at its
+ * block of mesh nodes (g in [G p / P, G (p+1) / P)) and the union is a maximum-reduce of one byte
+ * per candidate.  The 1-D detections (2N + 1 nodes) run in full on every rank.  Every rank ends
+ * with the same detected set, which equals the unsharded result for the same lattice (the sums
+ * are ordered differently, so coefficients agree to rounding).
+ *
+ * Hook: allreduce(buf, count, dtype, op, stream, ctx) must replace the `count` elements at the
+ * device pointer buf by their sum (op USFFT_RED_SUM) or maximum (USFFT_RED_MAX) over all ranks,
+ * ordered after the work already issued on `stream` (the plan's stream) and before the work issued
+ * on it later; dtype USFFT_RED_F64 (double) or USFFT_RED_U8 (uint8_t).  It returns 0 on success;
+ * anything else ends the call with USFFT_ECOMM.  Every rank must make the same sequence of calls.
+ * The Python module paper_2109_04131_gb300/sharded.py provides one over torch.distributed (NCCL). */
+#define USFFT_RED_SUM 0
+#define USFFT_RED_MAX 1
+#define USFFT_RED_F64 0
+#define USFFT_RED_U8 1
+typedef int (*usfft_allreduce_fn)(void* buf, size_t count, int dtype, int op, void* stream, void* ctx);
+
+/* Increment t of the plan as rank `rank` of `nranks` (1 <= nranks <= 64, all prime factors <= 7;
+ * nranks = 1 is usfft_increment).  Each rank holds its own plan of the same problem and
+ * parameters (single-lattice detection: rr_lattices = 0).  info->samples counts this rank's
+ * solves; info->M is the full lattice size.  Afterwards usfft_get_lattice and
+ * usfft_get_candidates describe the full lattice, usfft_get_samples returns this rank's M / P
+ * sample rows (node i = p + P row), usfft_get_coefficients the summed coefficients.
+ * usfft_replay of a sharded step repeats its exchange through the same hook (every rank must
+ * replay; hook and ctx must still be valid). */
+usfft_status usfft_increment_sharded(usfft_plan_t* plan, int rank, int nranks, usfft_allreduce_fn allreduce,
+                                     void* ctx, usfft_increment_info* info);
+
+/* The lattice rule of usfft_search_lattice restricted to sizes that are multiples of `divisor`
+ * (1 <= divisor <= 64, prime factors <= 7; 1 gives usfft_search_lattice): the sharded form's rule.
+ * Host only. */
+usfft_status usfft_search_lattice_multiple(const int8_t* J, int64_t n, int t, uint64_t seed, int trials,
+                                           int max_sizes, int64_t divisor, int64_t* z, int64_t* M);
 
 /* Free every device buffer and the plan.  NULL is ignored. */
 void usfft_destroy(usfft_plan_t* plan);

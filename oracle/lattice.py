@@ -22,7 +22,10 @@ reading used here (the same on both sides, so (z, M) are bit-exact):
   [1, M-1] (j = 2..t) from key(seed, PHASE_LATTICE, t, M, tr, j); the first z that
   is injective on J is accepted;
 - the search gives up on a repeated candidate, after 400 sizes, or beyond
-  M = 4096^2 (a limit of the library's FFT, adopted here so both sides agree).
+  M = 4096^2 (a limit of the library's FFT, adopted here so both sides agree);
+- for the sharded form over P ranks (the lattice nodes split by residue i mod P, which
+  needs P | M) the admissible sizes are the 7-smooth multiples of P; P = 1 is the rule
+  above.
 
 Pins (tests/test_oracle_lattice.py): on tiny sets, the injectivity test agrees with
 the definition through the lattice Fourier matrix (its columns for J are orthonormal
@@ -77,14 +80,25 @@ def is_reconstructing(J: np.ndarray, z: np.ndarray, M: int) -> bool:
     return len(np.unique(m)) == len(m)
 
 
-def search(J: np.ndarray, t: int, seed: int, trials: int = 64, max_sizes: int = 400, phase: int = rng.PHASE_LATTICE):
+def next_admissible_multiple(x: int, divisor: int) -> int:
+    """Smallest admissible size >= x that is a multiple of divisor (itself 7-smooth)."""
+    k = max(1, -(-max(x, 1) // divisor))
+    while not is_smooth7(k * divisor):
+        k += 1
+    return k * divisor
+
+
+def search(J: np.ndarray, t: int, seed: int, trials: int = 64, max_sizes: int = 400, phase: int = rng.PHASE_LATTICE,
+           divisor: int = 1):
     """(z, M) of the first reconstructing lattice under the rule in the module header; the
-    draws are keyed by `phase` (PHASE_LATTICE in the coupled steps, PHASE_RECON in step 3)."""
+    draws are keyed by `phase` (PHASE_LATTICE in the coupled steps, PHASE_RECON in step 3).
+    With divisor P > 1 only sizes that are multiples of P are admissible (the strided split of
+    the lattice nodes over P ranks needs P | M); P = 1 is the plain rule."""
     if len(J) == 0:
         return np.zeros(t, dtype=np.int64), 0
     if len(np.unique(J, axis=0)) < len(J):
         raise RuntimeError("repeated candidate: no lattice can separate it")
-    M = next_admissible(len(J))
+    M = next_admissible_multiple(len(J), divisor)
     for _ in range(max_sizes):
         if M > MAX_LATTICE_SIZE:
             break
@@ -94,7 +108,7 @@ def search(J: np.ndarray, t: int, seed: int, trials: int = 64, max_sizes: int = 
                 z[j - 1] = rng.uniform_int(1, M - 1, seed, phase, t, M, tr, j) if M > 1 else 0
             if is_reconstructing(J, z, M):
                 return z, M
-        M = next_admissible((105 * M + 99) // 100)
+        M = next_admissible_multiple((105 * M + 99) // 100, divisor)
     raise RuntimeError("no reconstructing lattice found")
 
 

@@ -121,10 +121,11 @@ class Record:
 
 
 class OracleRun:
-    def __init__(self, prob, params, keep=False):
+    def __init__(self, prob, params, keep=False, lattice_divisor=1):
         self.prob = prob
         self.p = params
         self.keep = keep
+        self.divisor = lattice_divisor      # > 1: lattice sizes of the sharded form over that many ranks
         self.t = 0
         self.theta = None if params.delta_is_relative else params.delta
         self.A = None
@@ -171,7 +172,8 @@ class OracleRun:
         J = lattice.candidate_set(self.I_prefix, np.array(self.I1d[t], dtype=np.int64), p.N)
         if getattr(p, "rr_lattices", 0) > 0:
             return self._coupled_random(t, J, r_t, s_t)
-        z, M = lattice.search(J, t, p.seed, p.max_lattice_trials, getattr(p, "max_lattice_sizes", 400))
+        z, M = lattice.search(J, t, p.seed, p.max_lattice_trials, getattr(p, "max_lattice_sizes", 400),
+                              divisor=self.divisor)
         self.J, self.z, self.M = J, z, M
         found = set()
         if len(J) > 0:

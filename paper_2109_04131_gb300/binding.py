@@ -22,10 +22,16 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libusfft.so")
 
-STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ELATTICE", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ECUDA", 7: "ESTATE"}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ELATTICE", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ECUDA", 7: "ESTATE",
+          8: "ECOMM"}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+# usfft_allreduce_fn(buf, count, dtype, op, stream, ctx) -> int
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_void_p, ctypes.c_void_p)
+RED_SUM, RED_MAX = 0, 1
+RED_F64, RED_U8 = 0, 1
 
 
 class UsfftProblem(ctypes.Structure):
@@ -90,6 +96,10 @@ SIGNATURES = {
     "usfft_plan_bytes": (ctypes.c_size_t, [_P]),
     "usfft_increment_many": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(UsfftIncrementInfo), ctypes.POINTER(ctypes.c_int)]),
+    "usfft_increment_sharded": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ALLREDUCE_FN, _P,
+                                               ctypes.POINTER(UsfftIncrementInfo)]),
+    "usfft_search_lattice_multiple": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                                     ctypes.c_int, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_int64)]),
     "usfft_destroy": (None, [_P]),
     "usfft_version": (ctypes.c_char_p, []),
     "usfft_search_lattice": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
@@ -311,6 +321,27 @@ def usfft_search_lattice(J, t, seed, trials=64, max_sizes=400):
                                   z.ctypes.data, ctypes.byref(M))
     _check(st, None)
     return z, M.value
+
+
+def usfft_search_lattice_multiple(J, t, seed, divisor, trials=64, max_sizes=400):
+    """Host-only lattice rule of the sharded form: (z, M) with M a multiple of divisor."""
+    lib = load_library()
+    Jc = np.ascontiguousarray(J, dtype=np.int8).reshape(-1, t) if len(J) else np.zeros((0, t), np.int8)
+    z = np.zeros(t, dtype=np.int64)
+    M = ctypes.c_int64(0)
+    st = lib.usfft_search_lattice_multiple(Jc.ctypes.data if len(Jc) else None, len(Jc), t, seed, trials, max_sizes,
+                                           int(divisor), z.ctypes.data, ctypes.byref(M))
+    _check(st, None)
+    return z, M.value
+
+
+def usfft_increment_sharded(plan, rank, nranks, allreduce_fn):
+    """One increment of `plan` as rank `rank` of `nranks` through the collective hook allreduce_fn
+    (an ALLREDUCE_FN); the info dict of the increment."""
+    info = UsfftIncrementInfo()
+    plan._ck(plan._lib.usfft_increment_sharded(plan.handle, int(rank), int(nranks), allreduce_fn, None,
+                                               ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in UsfftIncrementInfo._fields_}
 
 
 def usfft_random_lattices(t, i, n_prev, n_t, s_t, L, factor, seed):

@@ -21,6 +21,14 @@
 
 using namespace usfft;
 
+namespace usfft {
+// k_shard.cu
+cudaError_t launch_shard_twist(double2* C, int G, int64_t nJ, const int* mk, int64_t p, int64_t M, double scale,
+                               cudaStream_t s, int* launches);
+cudaError_t launch_bits_to_bytes(const uint32_t* bits, int64_t n, uint8_t* bytes, cudaStream_t s, int* launches);
+cudaError_t launch_bytes_to_bits(const uint8_t* bytes, int64_t n, uint32_t* bits, cudaStream_t s, int* launches);
+}  // namespace usfft
+
 namespace {
 
 struct Buf {
@@ -95,6 +103,14 @@ struct usfft_plan_s {
     // samples, coefficients and the union bitmap after iteration i (cumulative over 1..i)
     bool keep_iters = false;
     int kept = 0;
+    // sharded form (usfft_increment_sharded): this rank's share of the last coupled step
+    bool step_sharded = false;                // the last detection step ran sharded
+    int shard_rank = 0, shard_n = 1;
+    usfft_allreduce_fn shard_fn = nullptr;
+    void* shard_ctx = nullptr;
+    int64_t shard_M = 0;                      // full lattice size (plan->M is the rank's M / P)
+    std::vector<int64_t> shard_m;             // full DFT indices k.z mod M (plan->m: mod M / P)
+    Buf smk, sflags;                          // the full indices (int32) and the union flags (bytes)
     std::vector<Buf> kU, kC, kB;
     // stage timing (usfft_set_timing): event pairs per stage launch
     bool timing = false;
@@ -301,9 +317,10 @@ usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns, double* out = n
     const int kind = plan->prob.kind;
     double* U = out ? out : (double*)plan->U.p;
     StageTimer timer(plan, USFFT_STAGE_SAMPLE);
+    const int64_t count = node_count(ns);
     if (kind == USFFT_PDE_1D) {
         CK(launch_sample_1d(ns, plan->prob.n, plan->prob.coef_model, plan->prob.f_const, (const double*)plan->psi.p,
-                            0, ns.M, U, plan->stream, &plan->launches));
+                            0, count, U, plan->stream, &plan->launches));
     } else if (kind == USFFT_PDE_2D) {
         CgConfig cg;
         cg.precision = plan->par.precision;
@@ -313,7 +330,7 @@ usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns, double* out = n
         cg.coef_scale = plan->prob.coef_scale;
         cg.coef_decay = plan->prob.coef_decay;
         CK(launch_sample_2d(ns, plan->prob.n, plan->prob.coef_model, plan->prob.f_const, (const double*)plan->psi.p, cg,
-                            0, ns.M, U, (int*)plan->iters.p, (unsigned int*)plan->failc.p,
+                            0, count, U, (int*)plan->iters.p, (unsigned int*)plan->failc.p,
                             (unsigned long long*)((char*)plan->failc.p + 8), (double*)plan->cgscr.p,
                             plan->cgscr.bytes, plan->stream, &plan->launches));
     } else {
@@ -325,10 +342,12 @@ usfft_status run_sampler(usfft_plan_t* plan, const NodeSpec& ns, double* out = n
 }
 
 // buffers and gather plan for a detection step with nJ candidates at indices m, lattice size M
-usfft_status prepare_step(usfft_plan_t* plan, int64_t M, const std::vector<int64_t>& m) {
+usfft_status prepare_step(usfft_plan_t* plan, int64_t M, const std::vector<int64_t>& m, bool check_poles = true) {
     const int64_t nJ = (int64_t)m.size();
     usfft_status st;
-    if (plan->prob.kind != USFFT_TRIGPOLY && plan->prob.theta_map == USFFT_MAP_NORMAL &&
+    plan->step_sharded = false;
+    plan->shard_M = 0;
+    if (check_poles && plan->prob.kind != USFFT_TRIGPOLY && plan->prob.theta_map == USFFT_MAP_NORMAL &&
         lattice_hits_pole(M, plan->prob.map_shift)) {
         char msg[200];
         snprintf(msg, sizeof msg, "a node of the lattice of size %lld lies on a pole of the lognormal map "
@@ -548,9 +567,70 @@ usfft_status keep_iteration(usfft_plan_t* plan, size_t it) {
     return USFFT_OK;
 }
 
+// the caller's all-reduce of the sharded form
+usfft_status shard_allreduce(usfft_plan_t* plan, void* buf, size_t count, int dtype, int op) {
+    if (count == 0) return USFFT_OK;
+    const int rc = plan->shard_fn(buf, count, dtype, op, (void*)plan->stream, plan->shard_ctx);
+    if (rc != 0) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "the collective hook failed (%d) on an all-reduce of %zu elements", rc, count);
+        return fail(plan, USFFT_ECOMM, msg);
+    }
+    return USFFT_OK;
+}
+
+// device part of a sharded coupled step on this rank: r~ iterations of (its M/P solves, its
+// length-M/P FFT + gather, the twist, sum over ranks, selection at its node block, union of
+// the flags over ranks)
+usfft_status run_sharded_device(usfft_plan_t* plan) {
+    const int64_t nJ = plan->nJ;
+    const int G = plan->G, P = plan->shard_n, p = plan->shard_rank;
+    CK(cudaMemsetAsync(plan->bitmap.p, 0, sizeof(uint32_t) * (size_t)((nJ + 31) / 32), plan->stream));
+    if (nJ == 0) return USFFT_OK;
+    GatherPlan gp{(const int*)plan->goff.p, (const int*)plan->gk.p, (const int*)plan->gm2.p};
+    if (plan->inplace) {
+        gp.pos_of = (const int*)plan->fpos.p;
+        gp.mk = (const int*)plan->fmk.p;
+    }
+    const int g0 = (int)((int64_t)G * p / P), g1 = (int)((int64_t)G * (p + 1) / P);
+    for (size_t it = 0; it < plan->specs.size(); ++it) {
+        usfft_status st = run_sampler(plan, plan->specs[it]);
+        if (st != USFFT_OK) return st;
+        {
+            StageTimer timer(plan, USFFT_STAGE_FFT);
+            CK(launch_fft_gather(plan->fp, G, (const double*)plan->U.p, plan->twid.p, fft_df(plan), gp, nJ,
+                                 plan->fftscr.p, (double2*)plan->C.p, plan->stream, &plan->launches));
+            CK(launch_shard_twist((double2*)plan->C.p, G, nJ, (const int*)plan->smk.p, p, plan->shard_M,
+                                  1.0 / (double)P, plan->stream, &plan->launches));
+        }
+        if ((st = shard_allreduce(plan, plan->C.p, 2 * (size_t)G * nJ, USFFT_RED_F64, USFFT_RED_SUM)) != USFFT_OK)
+            return st;
+        if (plan->s_tilde > 0) {
+            StageTimer timer(plan, USFFT_STAGE_SELECT);
+            if (g1 > g0)
+                CK(launch_select_union((const double2*)plan->C.p + (size_t)g0 * nJ, g1 - g0, nJ, plan->theta,
+                                       plan->s_tilde, (uint32_t*)plan->bitmap.p, plan->stream, &plan->launches));
+            CK(launch_bits_to_bytes((const uint32_t*)plan->bitmap.p, nJ, (uint8_t*)plan->sflags.p, plan->stream,
+                                    &plan->launches));
+        }
+        if (plan->s_tilde > 0) {
+            if ((st = shard_allreduce(plan, plan->sflags.p, (size_t)nJ, USFFT_RED_U8, USFFT_RED_MAX)) != USFFT_OK)
+                return st;
+            CK(launch_bytes_to_bits((const uint8_t*)plan->sflags.p, nJ, (uint32_t*)plan->bitmap.p, plan->stream,
+                                    &plan->launches));
+        }
+        if (plan->keep_iters) {
+            usfft_status st2 = keep_iteration(plan, it);
+            if (st2 != USFFT_OK) return st2;
+        }
+    }
+    return USFFT_OK;
+}
+
 usfft_status run_step_device(usfft_plan_t* plan, bool first_1d_sets_theta) {
     plan->kept = 0;
     if (plan->rr_active) return run_rr_device(plan);
+    if (plan->step_sharded) return run_sharded_device(plan);
     const int64_t nJ = plan->nJ;
     CK(cudaMemsetAsync(plan->bitmap.p, 0, sizeof(uint32_t) * (size_t)((nJ + 31) / 32), plan->stream));
     if (nJ == 0) return USFFT_OK;
@@ -782,12 +862,23 @@ usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params
     return USFFT_OK;
 }
 
-usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
-    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+}  // extern "C"
+
+namespace {
+
+struct ShardCtx {
+    int rank = 0, nranks = 1;
+    usfft_allreduce_fn fn = nullptr;
+    void* ctx = nullptr;
+};
+
+// usfft_increment (sh.nranks == 1) and usfft_increment_sharded
+usfft_status increment_impl(usfft_plan_t* plan, usfft_increment_info* info, const ShardCtx& sh) {
     if (plan->t >= plan->d) return fail(plan, USFFT_ESTATE, "all d increments are done");
     const int t = plan->t + 1;
     const int N = plan->N, K = plan->K;
     plan->rr_active = false;
+    plan->step_sharded = false;
     plan->launches = 0;
     plan->cg_iters_total = 0;
     plan->cg_iters_max = 0;
@@ -858,7 +949,8 @@ usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
         } else {
             std::vector<int64_t> z;
             int64_t M = 0;
-            if (!lattice_search(J.data(), nJ, t, plan->par.seed, plan->par.max_lattice_trials, plan->par.max_lattice_sizes, z, M))
+            if (!lattice_search(J.data(), nJ, t, plan->par.seed, plan->par.max_lattice_trials, plan->par.max_lattice_sizes,
+                                z, M, PHASE_LATTICE, sh.nranks))
                 return fail(plan, USFFT_ELATTICE, "no reconstructing rank-1 lattice found");
             std::vector<int64_t> m((size_t)nJ);
             for (int64_t a = 0; a < nJ; ++a) {
@@ -872,14 +964,48 @@ usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
             plan->z = z;
             plan->last_coupled = true;
             plan->last_t = t;
-            if (nJ > 0) {
+            if (nJ > 0 && sh.nranks > 1) {
+                // this rank's share: nodes p + P i2, a length-M/P FFT read at m mod M/P
+                const int64_t P = sh.nranks, L = M / P;
+                if (plan->prob.kind != USFFT_TRIGPOLY && plan->prob.theta_map == USFFT_MAP_NORMAL &&
+                    lattice_hits_pole(M, plan->prob.map_shift))
+                    return fail(plan, USFFT_EINVAL, "a node of the lattice lies on a pole of the lognormal map");
+                std::vector<int64_t> mr((size_t)nJ);
+                std::vector<int> m32((size_t)nJ);
+                for (int64_t a = 0; a < nJ; ++a) {
+                    mr[(size_t)a] = m[(size_t)a] % L;
+                    m32[(size_t)a] = (int)m[(size_t)a];
+                }
+                if ((st = prepare_step(plan, L, mr, false)) != USFFT_OK) return st;
+                if ((st = ensure(plan, plan->smk, sizeof(int) * (size_t)nJ, "full lattice indices")) != USFFT_OK) return st;
+                if ((st = ensure(plan, plan->sflags, (size_t)nJ, "union flags")) != USFFT_OK) return st;
+                CK(cudaMemcpyAsync(plan->smk.p, m32.data(), sizeof(int) * (size_t)nJ, cudaMemcpyHostToDevice,
+                                   plan->stream));
+                plan->h2d += (int64_t)(sizeof(int) * (size_t)nJ);
+                CK(cudaStreamSynchronize(plan->stream));   // m32 outlives the copy
+                plan->step_sharded = true;
+                plan->shard_rank = sh.rank;
+                plan->shard_n = sh.nranks;
+                plan->shard_fn = sh.fn;
+                plan->shard_ctx = sh.ctx;
+                plan->shard_M = M;
+                plan->shard_m = m;
+            } else if (nJ > 0) {
                 if ((st = prepare_step(plan, M, m)) != USFFT_OK) return st;
             } else {
                 plan->M = 0;
                 plan->m.clear();
                 plan->nJ = 0;
             }
-            for (int i = 1; i <= rt && nJ > 0; ++i) plan->specs.push_back(spec_coupled(plan, t, i));
+            for (int i = 1; i <= rt && nJ > 0; ++i) {
+                NodeSpec ns = spec_coupled(plan, t, i);
+                if (plan->step_sharded) {
+                    ns.M = plan->shard_M;
+                    ns.first = sh.rank;
+                    ns.stride = sh.nranks;
+                }
+                plan->specs.push_back(ns);
+            }
         }
         if ((st = run_step_device(plan, false)) != USFFT_OK) return st;
         if ((st = read_cg_stats(plan, plan->M)) != USFFT_OK) return st;
@@ -894,7 +1020,7 @@ usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
             }
         plan->Ipre.swap(I);
         plan->nIpre = nI;
-        for (const NodeSpec& ns : plan->specs) samples += ns.M;
+        for (const NodeSpec& ns : plan->specs) samples += node_count(ns);
     }
     CK(cudaEventRecord(plan->ev1, plan->stream));
     if ((st = wait_stream(plan)) != USFFT_OK) return st;
@@ -904,7 +1030,7 @@ usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
     if (info) {
         memset(info, 0, sizeof *info);
         info->t = t;
-        info->M = plan->last_coupled ? plan->M : 0;
+        info->M = plan->last_coupled ? (plan->step_sharded ? plan->shard_M : plan->M) : 0;
         info->n_candidates = plan->last_coupled ? plan->nJ : K;
         info->n_detected = plan->nIpre;
         info->n_1d = (int64_t)plan->I1d[(size_t)t].size();
@@ -920,6 +1046,48 @@ usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
         info->h2d_bytes = plan->h2d;
         info->d2h_bytes = plan->d2h;
     }
+    return USFFT_OK;
+}
+
+// P is a valid rank count of the sharded form: 1 <= P <= 64 and 7-smooth (so that 7-smooth
+// lattice sizes that are multiples of P exist)
+bool valid_rank_count(int64_t P) { return P >= 1 && P <= 64 && is_smooth7(P); }
+
+}  // namespace
+
+extern "C" {
+
+usfft_status usfft_increment(usfft_plan_t* plan, usfft_increment_info* info) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    return increment_impl(plan, info, ShardCtx());
+}
+
+usfft_status usfft_increment_sharded(usfft_plan_t* plan, int rank, int nranks, usfft_allreduce_fn allreduce,
+                                     void* ctx, usfft_increment_info* info) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (!valid_rank_count(nranks) || rank < 0 || rank >= nranks)
+        return fail(plan, USFFT_EINVAL, "usfft_increment_sharded: need 0 <= rank < nranks <= 64, nranks 7-smooth");
+    if (nranks > 1 && !allreduce) return fail(plan, USFFT_EINVAL, "usfft_increment_sharded: allreduce hook is NULL");
+    if (nranks > 1 && plan->par.rr_lattices > 0)
+        return fail(plan, USFFT_EINVAL, "usfft_increment_sharded: single reconstructing lattices only (rr_lattices = 0)");
+    ShardCtx sh;
+    sh.rank = rank;
+    sh.nranks = nranks;
+    sh.fn = allreduce;
+    sh.ctx = ctx;
+    return increment_impl(plan, info, sh);
+}
+
+usfft_status usfft_search_lattice_multiple(const int8_t* J, int64_t n, int t, uint64_t seed, int trials, int max_sizes,
+                                           int64_t divisor, int64_t* z, int64_t* M) {
+    if (t < 1 || n < 0 || (n > 0 && !J) || !z || !M || trials < 1 || max_sizes < 1 || !valid_rank_count(divisor))
+        return fail(nullptr, USFFT_EINVAL, "usfft_search_lattice_multiple: invalid argument");
+    std::vector<int64_t> zz;
+    int64_t mm = 0;
+    if (!lattice_search(J, n, t, seed, trials, max_sizes, zz, mm, PHASE_LATTICE, divisor))
+        return fail(nullptr, USFFT_ELATTICE, "no reconstructing rank-1 lattice found");
+    for (int j = 0; j < t; ++j) z[j] = zz[(size_t)j];
+    *M = mm;
     return USFFT_OK;
 }
 
@@ -1027,7 +1195,7 @@ usfft_status usfft_get_lattice(const usfft_plan_t* plan, int64_t* z, int64_t* M,
     if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
     const int tt = plan->last_coupled ? plan->last_t : 1;
     if (t) *t = tt;
-    if (M) *M = plan->last_coupled ? plan->M : plan->K;
+    if (M) *M = plan->last_coupled ? (plan->step_sharded ? plan->shard_M : plan->M) : plan->K;
     if (z) for (int j = 0; j < tt; ++j) z[j] = plan->last_coupled ? plan->z[(size_t)j] : 1;
     return USFFT_OK;
 }
@@ -1036,7 +1204,8 @@ usfft_status usfft_get_candidates(const usfft_plan_t* plan, int8_t* J, int64_t* 
     if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
     if (n) *n = plan->nJ;
     if (J) memcpy(J, plan->J.data(), plan->J.size());
-    if (m) for (int64_t k = 0; k < plan->nJ; ++k) m[k] = plan->m[(size_t)k];
+    const std::vector<int64_t>& mm = plan->step_sharded ? plan->shard_m : plan->m;
+    if (m) for (int64_t k = 0; k < plan->nJ; ++k) m[k] = mm[(size_t)k];
     return USFFT_OK;
 }
 
@@ -1437,6 +1606,8 @@ void usfft_destroy(usfft_plan_t* plan) {
     for (Buf* b : bufs) buf_free(plan, *b);
     for (std::vector<Buf>* v : {&plan->kU, &plan->kC, &plan->kB})
         for (Buf& b : *v) buf_free(plan, b);
+    buf_free(plan, plan->smk);
+    buf_free(plan, plan->sflags);
     if (plan->pinned) cudaFreeHost(plan->pinned);
     if (plan->ev0) cudaEventDestroy(plan->ev0);
     if (plan->ev1) cudaEventDestroy(plan->ev1);

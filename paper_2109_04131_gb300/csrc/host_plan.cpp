@@ -7,6 +7,8 @@
 //   - admissible sizes are 7-smooth (radix 2/3/5/7 FFT passes);
 //   - the first size is the smallest admissible M >= |J|, the next one the smallest
 //     admissible M' >= ceil(1.05 M) = floor((105 M + 99) / 100);
+//   - for the sharded form over P ranks (strided lattice partition) admissible sizes are
+//     also multiples of P (P = 1: every 7-smooth size);
 //   - at each size trials tr = 0..T-1 set z_1 = 1 and draw z_j in [1, M-1], j = 2..t,
 //     from key(seed, PHASE_LATTICE, t, M, tr, j); the first z for which
 //     k -> k.z mod M is injective on J is taken;
@@ -69,6 +71,13 @@ int64_t next_admissible(int64_t x) {
     int64_t m = x < 1 ? 1 : x;
     while (!is_smooth7(m)) ++m;
     return m;
+}
+
+int64_t next_admissible_multiple(int64_t x, int64_t divisor) {
+    if (divisor <= 1) return next_admissible(x);
+    int64_t k = ((x < 1 ? 1 : x) + divisor - 1) / divisor;
+    while (!is_smooth7(k * divisor)) ++k;
+    return k * divisor;
 }
 
 static int64_t gcd64(int64_t a, int64_t b) {
@@ -257,7 +266,7 @@ class SearchPool {
 };
 
 bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials, int max_sizes,
-                    std::vector<int64_t>& z, int64_t& M, uint64_t phase) {
+                    std::vector<int64_t>& z, int64_t& M, uint64_t phase, int64_t divisor) {
     z.assign((size_t)t, 0);
     if (n == 0) {
         M = 0;
@@ -275,13 +284,13 @@ bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials
     SearchPool& pool = SearchPool::get();
     const int batch = n >= 1024 ? 16 : 1;
     std::vector<uint64_t> bits;
-    int64_t m = next_admissible(n);
+    int64_t m = next_admissible_multiple(n, divisor);
     int size = 0;
     while (size < max_sizes && m <= kMaxLatticeSize) {
         std::vector<int64_t> ms;
         for (int b = 0; b < batch && size + b < max_sizes && m <= kMaxLatticeSize; ++b) {
             ms.push_back(m);
-            m = next_admissible((105 * m + 99) / 100);
+            m = next_admissible_multiple((105 * m + 99) / 100, divisor);
         }
         const int items = (int)ms.size() * trials;
         std::atomic<int> best{items};

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) sample_1d_cr_kernel(const __grid_constant
     double* sj = ae + (n + 1);
 
     for (int64_t sys = (int64_t)blockIdx.x * warps + warp; sys < a.count; sys += (int64_t)gridDim.x * warps) {
-        const int64_t i = a.i0 + sys;
+        const int64_t i = lattice_node(a.ns, a.i0 + sys);
         for (int j = lane; j < d; j += 32) sj[j] = node_theta(a.ns, j, i);
         __syncwarp();
         // element coefficients (fused assembly; never stored in HBM)

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(1024) pcg2d_fp64_kernel(const __grid_constant_
     const int T = blockDim.x, tid = threadIdx.x;
 
     for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
-        const int64_t i = a.i0 + sys;
+        const int64_t i = lattice_node(a.ns, a.i0 + sys);
         assemble_scaled(a, i, ph, wx, wy, sj);
         // D^-1/2 is parked in the output row until the solution is scaled back
         double* out = a.U + (size_t)sys * G;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_kernel(const __grid_constant
     double* w64y = w64x + n * n1;
 
     for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
-        const int64_t i = a.i0 + sys;
+        const int64_t i = lattice_node(a.ns, a.i0 + sys);
         assemble_scaled(a, i, ph, wx, wy, sj);
         double* out = a.U + (size_t)sys * G;     // holds D^-1/2 until the end
         double x[NPT], bt[NPT];

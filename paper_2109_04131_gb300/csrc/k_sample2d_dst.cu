@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
     __syncthreads();
 
     for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
-        const int64_t i = a.i0 + sys;
+        const int64_t i = lattice_node(a.ns, a.i0 + sys);
         // ---- assembly: fp64 weights to the CTA's scratch slot, fp32 copies to shared memory ----
         for (int j = tid; j < a.ns.d; j += T) sj[j] = node_theta(a.ns, j, i);
         __syncthreads();
@@ -813,7 +813,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
     __syncthreads();
 
     for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
-        const int64_t i = a.i0 + sys;
+        const int64_t i = lattice_node(a.ns, a.i0 + sys);
         for (int j = tid; j < a.ns.d; j += T) sj[j] = node_theta(a.ns, j, i);
         __syncthreads();
         const bool logn = a.coef_model == USFFT_COEF_LOGNORMAL_SIN;

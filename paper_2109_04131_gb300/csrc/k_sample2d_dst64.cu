@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(TPT == 1 ? 256 : 512) pcg2d_fp64_dst_kernel(co
     __syncthreads();
 
     for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
-        const int64_t i = a.i0 + sys;
+        const int64_t i = lattice_node(a.ns, a.i0 + sys);
         // ---- assembly (fp64, separable form of psi_j = sin(j1 pi x1) sin(j2 pi x2)) ----
         for (int j = tid; j < d; j += T) sj[j] = node_theta(a.ns, j, i);
         __syncthreads();

@@ -20,6 +20,11 @@ __device__ __forceinline__ double theta_of_torus(int map, double a, double b, do
     return M_SQRT2 * erfinv(2.0 * v);
 }
 
+// the lattice node index of the k-th node of a node set
+__host__ __device__ __forceinline__ int64_t lattice_node(const NodeSpec& ns, int64_t k) {
+    return ns.stride > 1 ? ns.first + ns.stride * k : ns.first + k;
+}
+
 // Theta_j of node i of a node set: explicit point, lattice coordinate (exact integer
 // reduction n = i z_j mod M, Eq. (3.4)) or fixed tail
 __device__ __forceinline__ double node_theta(const NodeSpec& ns, int j, int64_t i) {

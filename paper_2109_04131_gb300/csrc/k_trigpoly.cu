@@ -38,12 +38,13 @@ __global__ void trigpoly_setup_kernel(const __grid_constant__ NodeSpec ns, int G
     }
 }
 
-__global__ void trigpoly_sample_kernel(int64_t M, int G, int nterms, const double* coefs, const double* aux,
-                                       double* U) {
-    const int64_t total = M * G;
+// rows k < count: lattice node i = first + stride k (stride >= 1) of the lattice of size M
+__global__ void trigpoly_sample_kernel(int64_t M, int64_t count, int64_t first, int64_t stride, int G, int nterms,
+                                       const double* coefs, const double* aux, double* U) {
+    const int64_t total = count * G;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / G;
+        const int64_t i = first + stride * (idx / G);
         const int g = (int)(idx % G);
         double acc = 0.0;
         for (int s = 0; s < nterms; ++s) {
@@ -110,10 +111,13 @@ cudaError_t launch_sample_trigpoly(const NodeSpec& ns, int G, int nterms, const 
     int64_t tot = (int64_t)G * nterms;
     int b1 = (int)((tot + 255) / 256);
     trigpoly_setup_kernel<<<b1 > 0 ? b1 : 1, 256, 0, s>>>(ns, G, nterms, freqs, aux);
-    int64_t tot2 = ns.M * G;
+    const int64_t count = node_count(ns);
+    int64_t tot2 = count * G;
     int64_t b2 = (tot2 + 255) / 256;
     if (b2 > 152 * 64) b2 = 152 * 64;
-    trigpoly_sample_kernel<<<(unsigned)b2, 256, 0, s>>>(ns.M, G, nterms, coefs, aux, U);
+    if (b2 < 1) b2 = 1;
+    trigpoly_sample_kernel<<<(unsigned)b2, 256, 0, s>>>(ns.M, count, ns.first, ns.stride > 1 ? ns.stride : 1, G, nterms,
+                                                        coefs, aux, U);
     if (launches) *launches += 2;
     return cudaGetLastError();
 }

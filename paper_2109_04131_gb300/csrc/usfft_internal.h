@@ -25,12 +25,15 @@ int64_t rng_uniform_int(int64_t lo, int64_t hi, uint64_t seed, const uint64_t* f
 
 bool is_smooth7(int64_t m);
 int64_t next_admissible(int64_t x);
+// smallest 7-smooth multiple of divisor that is >= x (divisor itself 7-smooth)
+int64_t next_admissible_multiple(int64_t x, int64_t divisor);
 
 // Reconstructing rank-1 lattice search: J is [n][t] int8 row-major.  Returns false if
 // none is found within max_sizes sizes; z receives t entries.  `phase` keys the draws
 // (PHASE_LATTICE for the coupled steps, PHASE_RECON for step 3).
+// divisor: admissible sizes are multiples of it (the sharded form over that many ranks).
 bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials, int max_sizes,
-                    std::vector<int64_t>& z, int64_t& M, uint64_t phase = PHASE_LATTICE);
+                    std::vector<int64_t>& z, int64_t& M, uint64_t phase = PHASE_LATTICE, int64_t divisor = 1);
 
 // The L random rank-1 lattices of detection iteration i of the coupled step t (random R1L
 // approach in the role of Algorithm A): M_1 = smallest admissible size >= ceil(factor *
@@ -56,7 +59,15 @@ struct NodeSpec {          // M sampling nodes: lattice coordinates and fixed ta
                                  // parameters of the model's domain; z and tail unused)
     int map;                     // USFFT_MAP_*: Theta_j of a torus coordinate (Sec. 3.2)
     double map_alpha, map_beta, map_shift;
+    // the k-th node of the set is lattice node first + max(stride, 1) k (a rank's strided part of
+    // the lattice in the sharded form; first = stride = 0: node k is lattice node k)
+    int64_t first, stride;
 };
+
+// number of nodes of a lattice node set (M, or the rank's strided share of it)
+inline int64_t node_count(const NodeSpec& ns) {
+    return ns.stride > 1 ? (ns.M - ns.first + ns.stride - 1) / ns.stride : ns.M;
+}
 
 // Theta_j and the inverse map on the device (k_theta.cuh) take these fields of a problem.
 struct ParamMap {
