@@ -336,59 +336,28 @@ def run_ours(args, rank, world):
 
     w = W.c2(1 + rank)
     t = args.t
-    # setup: increments 1..t-1 in fp64; both precisions then run increment t from that state
+    # setup: increments 1..t-1 in fp64; every precision then runs increment t from that state
     p64 = binding.Plan(w.problem, W.with_precision(w, W.PRECISION_FP64).params)
     for _ in range(t - 1):
         p64.increment()
     I_prev = p64.get_set()
     info64 = p64.increment()
-    pmx = binding.Plan(w.problem, W.with_precision(w, W.PRECISION_MIXED).params)
-    pmx.resume(t - 1, I_prev, info64["theta"])
-    info_mx = pmx.increment()
-    plans = {"mixed": pmx, "fp64": p64}
-    infos = {"mixed": info_mx, "fp64": info64}
+    plans = {"fp64_jacobi": p64}
+    infos = {"fp64_jacobi": info64}
+    for name, prec in (("mixed", W.PRECISION_MIXED), ("fp64", W.PRECISION_FP64_DST)):
+        pl = binding.Plan(w.problem, W.with_precision(w, prec).params)
+        pl.resume(t - 1, I_prev, info64["theta"])
+        infos[name] = pl.increment()
+        plans[name] = pl
 
-    # accuracy of both precisions against the oracle on sampled lattice nodes
+    # accuracy of every precision against the oracle on sampled lattice nodes
     accuracy = sampled_accuracy(w, t, plans, rows=4) if rank == 0 and not args.skip_accuracy else None
 
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     results = {}
-    for name in ("mixed", "fp64"):
-        plan = plans[name]
-        info = infos[name]
-        samples_per_step = int(info["M"]) * (w.params.r if t < w.problem.d else 1)
-        for _ in range(args.warmup):
-            plan.replay(sync=True)
-        plan.set_timing(True)
-        launches = 0
-        evs = []
-        barrier()
-        torch.cuda.synchronize()
-        clocks = ClockSampler(uuid) if rank == 0 else None
-        if clocks:
-            clocks.start()
-            time.sleep(0.3)
-        t_wall0 = time.perf_counter()
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            launches += plan.replay(sync=False)
-            e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t_wall0
-        barrier()
-        if clocks:
-            clocks.stop()
-        step_ms = [a.elapsed_time(b) for a, b in evs]
-        stages = plan.stage_times()
-        plan.set_timing(False)
-        tot_ms = max_over_ranks(sum(step_ms), world, dev)
-        results[name] = {"samples_per_step": samples_per_step, "step_ms": step_ms, "tot_ms": tot_ms,
-                         "wall_s": wall, "launches": launches, "stages": stages,
-                         "clocks": clocks.summary() if clocks else None, "info": info}
+    for name in (("mixed",) if args.skip_fp64 else ("mixed", "fp64", "fp64_jacobi")):
+        results[name] = time_replays(plans[name], infos[name], w, t, args.steps, args.warmup, flush, stream, barrier,
+                                     world, dev, uuid if rank == 0 else None)
 
     # end to end through the public call (rewind + usfft_increment), mixed precision
     e2e = e2e_measure(plans["mixed"], t, args.e2e_steps, barrier, world, dev)
@@ -396,7 +365,7 @@ def run_ours(args, rank, world):
     next_rows = None
     if rank == 0 and not args.skip_next_rows:
         pk, pkind = measured_peaks()
-        next_rows = next_rows_measure(w, plans["mixed"], t, args.n_test, pk, pkind)
+        next_rows = next_rows_measure(w, plans["mixed"], t, args.n_test, pk, pkind, steps=args.steps)
 
     if rank != 0:
         for p in plans.values():
@@ -404,16 +373,35 @@ def run_ours(args, rank, world):
         return
     peaks, peak_kind = measured_peaks()
     G = w.problem.G
-    mx, f64 = results["mixed"], results["fp64"]
+    if args.skip_fp64:                       # profiling runs: the mixed leg stands in for the others
+        results["fp64"] = results["fp64_jacobi"] = results["mixed"]
+    mx, f64, fjac = results["mixed"], results["fp64"], results["fp64_jacobi"]
     value = whole_job_rate(world, mx["samples_per_step"] * args.steps, mx["tot_ms"])
     value64 = whole_job_rate(world, f64["samples_per_step"] * args.steps, f64["tot_ms"])
+    value_jac = whole_job_rate(world, fjac["samples_per_step"] * args.steps, fjac["tot_ms"])
 
     d_, E_ = w.problem.d, 2 * (w.problem.n + 1) ** 2
     P_ = (w.problem.n + 15) // 16 * 16
     peak_bf16 = peaks.get("bf16_tflops", 1921.8)
 
+    def dst64_roofline(res, n_mesh, label):
+        # fp64 sampler with the sine-transform preconditioner: the transforms' fused multiply-adds
+        # dominate (dst64_flops_per_solve); FP64-pipe bound
+        st = res["stages"]
+        n = max(1, st["launches"]["sample"])
+        solves = res["samples_per_step"] * args.steps
+        iters = st["cg_iters_total"] / max(1, solves)
+        flops = dst64_flops_per_solve(n_mesh, iters) * solves / n
+        dur = st["ms"]["sample"] / n / 1e3
+        ach = flops / dur / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / PEAK_FP64_TFLOPS, "traffic": None,
+                "kernel": f"pcg2d_fp64_dst_kernel ({label}, {n} launches timed)",
+                "flops_per_launch": flops, "ms_per_launch": dur * 1e3, "cg_iters_per_solve": iters,
+                "peak_note": f"fp64 peak from unit counts at {SM_MAX_MHZ:.0f} MHz (2 DFMA/clk/SM)"}
+
     def fp64_roofline(res):
-        # FP64 path: 21 G flops per Jacobi-PCG iteration + 2 d E flops of coefficient assembly per solve
+        # FP64 Jacobi path: 21 G flops per Jacobi-PCG iteration + 2 d E flops of coefficient assembly per solve
         st = res["stages"]
         n = max(1, st["launches"]["sample"])
         solves = res["samples_per_step"] * args.steps
@@ -488,9 +476,17 @@ def run_ours(args, rank, world):
         "fe_node_samples_per_s": value * G,
         "latency_ms": {"p50": percentile(mx["step_ms"], 50), "p99": percentile(mx["step_ms"], 99)},
         "fp64": {"value": value64, "unit": UNIT, "dtype": "f64", "ms_per_step": f64["tot_ms"] / args.steps,
+                 "solver": "fp64 CG with the same sine-transform preconditioner as the mixed mode, applied in fp64 "
+                           "(USFFT_FP64_DST): the two differ in arithmetic precision only",
                  "latency_ms": {"p50": percentile(f64["step_ms"], 50), "p99": percentile(f64["step_ms"], 99)},
-                 "roofline": fp64_roofline(f64), "clocks": f64["clocks"]},
+                 "roofline": dst64_roofline(f64, w.problem.n, "63x63"), "clocks": f64["clocks"],
+                 "stage_ms_per_step": {k: v / args.steps for k, v in f64["stages"]["ms"].items()}},
+        "fp64_jacobi": {"value": value_jac, "unit": UNIT, "dtype": "f64", "ms_per_step": fjac["tot_ms"] / args.steps,
+                        "solver": "fp64 Jacobi-preconditioned CG (USFFT_FP64)",
+                        "latency_ms": {"p50": percentile(fjac["step_ms"], 50), "p99": percentile(fjac["step_ms"], 99)},
+                        "roofline": fp64_roofline(fjac), "clocks": fjac["clocks"]},
         "speedup_mixed_vs_fp64": value / value64,
+        "speedup_mixed_vs_fp64_jacobi": value / value_jac,
         "accuracy": accuracy,
         "roofline": roof,
         "roofline_fft": fft_roofline(mx),
@@ -502,11 +498,61 @@ def run_ours(args, rank, world):
         "e2e": e2e,
         "next_rows": next_rows,
     }
+    if args.skip_fp64:
+        for k in ("fp64", "fp64_jacobi", "speedup_mixed_vs_fp64", "speedup_mixed_vs_fp64_jacobi"):
+            line[k] = None
     if not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(w, t)
     print(json.dumps(line), flush=True)
     for p in plans.values():
         p.close()
+
+
+def time_replays(plan, info, w, t, steps, warmup, flush, stream, barrier, world, dev, clock_uuid):
+    """CUDA-event time of `steps` replays of the plan's last increment (all its detection
+    iterations), an L2 flush between steps, clocks sampled during the timed region."""
+    import torch
+    samples_per_step = int(info["M"]) * (w.params.r if t < w.problem.d else 1)
+    for _ in range(warmup):
+        plan.replay(sync=True)
+    plan.set_timing(True)
+    launches = 0
+    evs = []
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(clock_uuid) if clock_uuid is not None else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    t_wall0 = time.perf_counter()
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        launches += plan.replay(sync=False)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    barrier()
+    if clocks:
+        clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    stages = plan.stage_times()
+    plan.set_timing(False)
+    tot_ms = max_over_ranks(sum(step_ms), world, dev)
+    return {"samples_per_step": samples_per_step, "step_ms": step_ms, "tot_ms": tot_ms, "wall_s": wall,
+            "launches": launches, "stages": stages, "clocks": clocks.summary() if clocks else None, "info": info}
+
+
+def dst64_flops_per_solve(n, iters):
+    """fp64 flops of one solve of the fp64 sampler with the sine-transform preconditioner: per
+    preconditioner application (iters + 1 of them) four 1-D transforms of n^2 ceil(n/2) fused
+    multiply-adds; per CG iteration the SpMV (9 G), two inner products and the residual norm (6 G),
+    three updates (6 G) and the scalings (3 G)."""
+    G = n * n
+    return (iters + 1) * 4 * 2.0 * G * ((n + 1) // 2) + iters * 24.0 * G
 
 
 def e2e_measure(plan, t, steps, barrier, world, dev):
@@ -557,17 +603,67 @@ def serving_measure(kind, count):
                             increment_many=binding.usfft_increment_many).run(reqs)
     torch.cuda.synchronize()
     alone = serving.run_one_at_a_time(reqs, lambda r: binding.Plan(r.workload.problem, r.workload.params))
+    torch.cuda.synchronize()
+    alone64 = serving.run_one_at_a_time(
+        reqs, lambda r: binding.Plan(r.workload.problem, W.with_precision(r.workload, W.PRECISION_FP64_DST).params))
     rep.pop("instances")
     rounds.pop("instances")
     alone.pop("results")
+    alone64.pop("results")
     return {"requests": count, "served": rep, "served_in_rounds": rounds, "one_at_a_time": alone,
+            "one_at_a_time_fp64": alone64,
             "speedup_samples_per_s": rep["samples_per_s"] / alone["samples_per_s"] if alone["samples_per_s"] else None,
+            "speedup_vs_fp64_one_at_a_time": rep["samples_per_s"] / alone64["samples_per_s"]
+            if alone64["samples_per_s"] else None,
             "precision": "mixed",
-            "note": "one-at-a-time runs the same requests in arrival order without overlap; the fp64 2-D path "
-                    "covers n <= 63 only, so both forms use the mixed precision mode"}
+            "note": "one-at-a-time runs the same requests in arrival order without overlap, in the mixed mode "
+                    "and in fp64 with the same preconditioner (USFFT_FP64_DST; plain fp64 for the 1-D requests); "
+                    "every mode meets the 1e-10 bar"}
 
 
-def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind, n_batch=32, n_serve=200):
+def precision_mesh127(steps, warmup, t=3):
+    """Mixed vs fp64 (same preconditioner) on the 128x128-mesh lognormal workload at step t."""
+    import torch
+    from paper_2109_04131_gb300 import binding
+    w3 = W.c3(1)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream(dev)
+    base = binding.Plan(w3.problem, W.with_precision(w3, W.PRECISION_MIXED).params)
+    for _ in range(t - 1):
+        info = base.increment()
+    I_prev, theta = base.get_set(), info["theta"]
+    base.close()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    plans, res = {}, {}
+    for name, prec in (("mixed", W.PRECISION_MIXED), ("fp64", W.PRECISION_FP64_DST)):
+        pl = binding.Plan(w3.problem, W.with_precision(w3, prec).params)
+        pl.resume(t - 1, I_prev, theta)
+        inf = pl.increment()
+        plans[name] = pl
+        res[name] = time_replays(pl, inf, w3, t, steps, warmup, flush, stream, lambda: None, 1, dev, None)
+    acc = sampled_accuracy(w3, t, plans, rows=2)
+    out = {"workload": "2-D P1 FE 127x127 interior (G=16129), lognormal-type coefficient, d=20, Gamma=[-32,32]^20, "
+                       f"s=1000, delta=1e-10 relative, r=2; coupled increment t={t}",
+           "M": int(res["mixed"]["info"]["M"]), "n_candidates": int(res["mixed"]["info"]["n_candidates"]),
+           "accuracy": acc}
+    for name, r in res.items():
+        st = r["stages"]
+        solves = r["samples_per_step"] * steps
+        leg = {"value": r["samples_per_step"] * steps / (r["tot_ms"] / 1e3), "unit": UNIT,
+               "ms_per_step": r["tot_ms"] / steps,
+               "stage_ms_per_step": {k: v / steps for k, v in st["ms"].items()},
+               "cg_iters_per_solve": st["cg_iters_total"] / max(1, solves)}
+        if name == "fp64":
+            flops = dst64_flops_per_solve(w3.problem.n, leg["cg_iters_per_solve"]) * solves
+            ach = flops / (st["ms"]["sample"] / 1e3) / 1e12
+            leg["sampler_fp64"] = {"achieved_tflops": ach, "frac_of_fp64_peak": ach / PEAK_FP64_TFLOPS}
+        out[name] = leg
+        plans[name].close()
+    out["speedup_mixed_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind, n_batch=32, n_serve=200, steps=10):
     """The rows past the detection increment, on the same workload: the remaining increments
     t0+1..d of the mixed plan (single reconstructing lattice per step), step 3 (usfft_reconstruct),
     the quantities of interest (usfft_statistics), FE solves at n_test random parameters and the
@@ -615,16 +711,10 @@ def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind, n_batch=32, n_serve=
     stat_bytes = 16.0 * G * nI
     stat_gbs = stat_bytes / (ms_stat / 1e3) / 1e9
 
-    # the 128 x 128 mesh (16129 nodes, lognormal-type coefficient, d = 20): increments 1..3, mixed
-    w3 = W.c3(1)
-    p3 = binding.Plan(w3.problem, w3.params)
-    c3 = []
-    for _ in range(3):
-        info = p3.increment()
-        c3.append({"t": info["t"], "M": info["M"], "samples": info["samples"], "n_detected": info["n_detected"],
-                   "ms_device": info["ms_device"], "cg_iters_max": info["cg_iters_max"],
-                   "lattice_samples_per_s": info["samples"] / (info["ms_device"] / 1e3)})
-    p3.close()
+    # the precision configuration: 128 x 128 mesh (16129 nodes, lognormal-type coefficient, d = 20),
+    # coupled step t = 3 in the mixed mode and in fp64 with the same preconditioner, both from the
+    # state after increments 1-2, timed like the headline and checked against the oracle
+    c3 = precision_mesh127(steps=min(steps, 10), warmup=3)
 
     # batched and served forms (continuous batching through usfft_increment_many)
     batching = serving_measure("batch", n_batch)
@@ -654,9 +744,7 @@ def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind, n_batch=32, n_serve=
                      "kernel": "evaluate_kernel (fp64 complex contraction, E formed on chip)"},
         "errors": {"n": n_test, "ms": ms_err, "err2_max": float(np.max(e2)), "errinf_max": float(np.max(ei)),
                    "err2_median": float(np.median(e2))},
-        "mesh_128x128": {"workload": "2-D P1 FE 127x127 interior (G=16129), lognormal-type coefficient, d=20, "
-                                     "Gamma=[-32,32]^20, s=1000, delta=1e-10 relative, r=2, mixed precision "
-                                     "(large-mesh sampler)", "increments": c3},
+        "precision_mesh127": c3,
         "batching": batching,
         "serving": served,
         "random_r1l": {"lattices": 5, "size_factor": 2.0, "precision": "mixed", "increments": rr,
@@ -692,7 +780,7 @@ def profile_case(args):
     or of the 127x127 lognormal-type workload (mixed precision, large-mesh sampler)."""
     import torch
     from paper_2109_04131_gb300 import binding
-    prec = W.PRECISION_MIXED if args.precision == "mixed" else W.PRECISION_FP64
+    prec = {"mixed": W.PRECISION_MIXED, "fp64": W.PRECISION_FP64, "fp64_dst": W.PRECISION_FP64_DST}[args.precision]
     w = W.with_precision(W.c3(1) if args.profile_workload == "mesh127" else W.c2(1), prec)
     plan = binding.Plan(w.problem, w.params)
     for _ in range(args.profile_increments):
@@ -719,7 +807,9 @@ def main():
     ap.add_argument("--n-test", type=int, default=4096, help="test points of the error evaluation")
     ap.add_argument("--profile-increments", type=int, default=0,
                     help="profiling mode: only run this many increments of the 2-D workload (no timing)")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "fp64_dst"], default="mixed")
+    ap.add_argument("--skip-fp64", action="store_true",
+                    help="time the mixed path only (profiling runs of the headline step)")
     ap.add_argument("--profile-workload", choices=["mesh63", "mesh127"], default="mesh63",
                     help="profiling mode: the 63x63 2-D workload or the 127x127 lognormal-type one")
     args = ap.parse_args()

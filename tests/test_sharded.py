@@ -189,7 +189,9 @@ class ThreadAllreduce:
         return call
 
 
-def _run_ranks(B, w, P, increments):
+def _run_ranks(B, w, P, increments, states=None):
+    """Run `increments` sharded increments on P plans in P threads.  states (optional): for each
+    increment the state (t, I^(1..t), theta) every rank resumes from before it (t = 0: none)."""
     import torch
     plans = [B.Plan(w.problem, w.params, stream=torch.cuda.Stream().cuda_stream) for _ in range(P)]
     red = ThreadAllreduce(P, B)
@@ -199,6 +201,8 @@ def _run_ranks(B, w, P, increments):
     def worker(rank):
         try:
             for k in range(increments):
+                if states is not None and states[k][0] > 0:
+                    plans[rank].resume(*states[k])
                 info = B.usfft_increment_sharded(plans[rank], rank, P, red.fns[rank])
                 results[rank][k] = (info, plans[rank].get_set(), plans[rank].get_lattice(),
                                     plans[rank].get_candidates(), plans[rank].get_coefficients())
@@ -248,29 +252,37 @@ def test_sharded_increments_match_the_oracle(binding, P):
     for w in (W.with_precision(W.small_2d(n=15, d=4, seed=2, N=6, s=30), W.PRECISION_MIXED),
               W.with_precision(W.small_2d(n=15, d=4, seed=5, N=6, s=30, r=2), W.PRECISION_FP64)):
         incs = 3
-        plans, res, red = _run_ranks(binding, w, P, incs)
+        # the oracle first; every sharded increment then starts from the oracle's state before it
         run = OracleRun(w.problem, w.params, keep=True, lattice_divisor=P)
+        states, wants, firsts, lasts, Js = [], [], [], [], []
         for k in range(incs):
-            first = len(run.records)
-            want = run.increment()
+            states.append((run.t, np.array(run.I_prefix), run.theta))
+            firsts.append(len(run.records))
+            wants.append(run.increment().copy())
+            lasts.append(run.records[-1])
+            Js.append(None if run.J is None else np.array(run.J))
+        plans, res, red = _run_ranks(binding, w, P, incs, states)
+        for k in range(incs):
+            first, want = firsts[k], wants[k]
             # every rank holds the same set, lattice and coefficients
             for rank in range(1, P):
                 assert np.array_equal(res[rank][k][1], res[0][k][1])
                 assert np.array_equal(res[rank][k][4], res[0][k][4])
             info, got, (z, M), (J, m), C = res[0][k]
-            last = run.records[-1]
+            last = lasts[k]
+            recs_k = run.records[first:firsts[k + 1]] if k + 1 < incs else run.records[first:]
             assert M == last.M and np.array_equal(z, last.z)
             if last.coupled:
                 assert M % P == 0 and info["M"] == M
-                assert np.array_equal(J, run.J) and np.array_equal(m, last.m)
+                assert np.array_equal(J, Js[k]) and np.array_equal(m, last.m)
                 assert _node_rel(C, last.C) < TOL
                 assert sum(res[r][k][0]["samples"] for r in range(P)) == \
-                    sum(rec.M for rec in run.records[first:] if rec.coupled) + P * run.p.r * (2 * run.p.N + 1)
+                    sum(rec.M for rec in recs_k if rec.coupled) + P * run.p.r * (2 * run.p.N + 1)
             if not np.array_equal(got, want):
-                recs = [rr for rr in run.records[first:] if rr.coupled]
+                recs = [rr for rr in recs_k if rr.coupled]
                 amb = near_ties(recs, run.theta, lambda rr: run.p.s_local if rr.t < w.problem.d else run.p.s)
                 diff = {tuple(x) for x in got.tolist()} ^ {tuple(x) for x in want.tolist()}
-                assert diff <= {tuple(int(v) for v in run.J[a]) for a in amb}
+                assert diff <= {tuple(int(v) for v in Js[k][a]) for a in amb}
         # a replay of the last sharded step repeats its exchange and its result
         C_last = plans[0].get_coefficients()
         calls = red.calls
