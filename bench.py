@@ -50,8 +50,10 @@ FLOPS_PER_CG_ITER_PER_NODE = 21      # Jacobi-PCG: SpMV 9 + two dots 4 + three A
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
 # kernel, with a hash of the kernel source it was taken on; a changed source makes it null.
 PROFILE_TRAFFIC = {
-    "mixed": {"bytes": 178577920, "files": ["k_sample2d_dst.cu", "k_pcg_common.cuh", "k_theta.cuh", "k_cvt.cuh"],
-              "sha": "542ee5599298501f", "profile": "profiles/pcg2d_mixed_dst_c2_t3.md"},
+    "mixed": {"bytes": 178343168, "files": ["k_sample2d_dst.cu", "k_pcg_common.cuh", "k_theta.cuh", "k_cvt.cuh"],
+              "sha": "bf11d21f4a1a3650", "profile": "profiles/pcg2d_mixed_dst_c2_t3.md"},
+    "fp64_dst": {"bytes": 3496581064, "files": ["k_sample2d_dst64.cu", "k_pcg_common.cuh", "k_theta.cuh"],
+                 "sha": "34d37d1241cb3db6", "profile": "profiles/pcg2d_fp64_dst_c2_t3.md"},
     "fp64": {"bytes": 174643200, "files": ["k_sample2d.cu", "k_pcg_common.cuh", "k_theta.cuh"],
              "sha": "4432e9a0bf66a956", "profile": "profiles/pcg2d_fp64_c2_t3.md"},
     "fft": {"bytes": 546580224, "files": ["k_fft.cu", "k_cvt.cuh"],
@@ -395,7 +397,7 @@ def run_ours(args, rank, world):
         dur = st["ms"]["sample"] / n / 1e3
         ach = flops / dur / 1e12
         return {"bound": "alu", "achieved": ach, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / PEAK_FP64_TFLOPS, "traffic": None,
+                "frac": ach / PEAK_FP64_TFLOPS, "traffic": profiled_traffic("fp64_dst") if n_mesh == 63 else None,
                 "kernel": f"pcg2d_fp64_dst_kernel ({label}, {n} launches timed)",
                 "flops_per_launch": flops, "ms_per_launch": dur * 1e3, "cg_iters_per_solve": iters,
                 "peak_note": f"fp64 peak from unit counts at {SM_MAX_MHZ:.0f} MHz (2 DFMA/clk/SM)"}
