@@ -623,6 +623,40 @@ def serving_measure(kind, count):
                     "every mode meets the 1e-10 bar"}
 
 
+def config_1d(seeds=10):
+    """The 1-D configuration (31 interior nodes, d = 4, N = 16, s = 50, delta = 1e-12 relative, r = 1):
+    every increment of full runs (seeds 1..seeds) through usfft_increment, per-increment device time and
+    wall latency, fp64 (the 1-D solves are fp64 cyclic reduction in every mode; the modes differ in the
+    lattice FFT) and mixed."""
+    import torch
+    from paper_2109_04131_gb300 import binding
+    out = {"workload": "1-D P1 FE on (0,1), 31 interior nodes, affine periodic coefficient, d=4, Gamma=[-16,16]^4, "
+                       "s=50, delta=1e-12 relative, r=1; full runs t=1..4"}
+    for name, prec in (("fp64", W.PRECISION_FP64), ("mixed", W.PRECISION_MIXED)):
+        lat, dev_ms, samples = [], [], 0
+        for sd in range(1, seeds + 1):
+            w = W.with_precision(W.c1(sd), prec)
+            plan = binding.Plan(w.problem, w.params)
+            if sd == 1:                              # warm the kernels
+                for _ in range(w.problem.d):
+                    plan.increment()
+                plan.close()
+                plan = binding.Plan(w.problem, w.params)
+            torch.cuda.synchronize()
+            for _ in range(w.problem.d):
+                t0 = time.perf_counter()
+                info = plan.increment()
+                lat.append(1e3 * (time.perf_counter() - t0))
+                dev_ms.append(info["ms_device"])
+                samples += info["samples"]
+            plan.close()
+        out[name] = {"lattice_samples": samples, "value": samples / (sum(lat) / 1e3), "unit": UNIT,
+                     "device_samples_per_s": samples / (sum(dev_ms) / 1e3),
+                     "increment_latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99)},
+                     "increment_device_ms": {"p50": percentile(dev_ms, 50), "p99": percentile(dev_ms, 99)}}
+    return out
+
+
 def precision_mesh127(steps, warmup, t=3):
     """Mixed vs fp64 (same preconditioner) on the 128x128-mesh lognormal workload at step t."""
     import torch
@@ -717,6 +751,7 @@ def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind, n_batch=32, n_serve=
     # coupled step t = 3 in the mixed mode and in fp64 with the same preconditioner, both from the
     # state after increments 1-2, timed like the headline and checked against the oracle
     c3 = precision_mesh127(steps=min(steps, 10), warmup=3)
+    c1 = config_1d()
 
     # batched and served forms (continuous batching through usfft_increment_many)
     batching = serving_measure("batch", n_batch)
@@ -747,6 +782,7 @@ def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind, n_batch=32, n_serve=
         "errors": {"n": n_test, "ms": ms_err, "err2_max": float(np.max(e2)), "errinf_max": float(np.max(ei)),
                    "err2_median": float(np.median(e2))},
         "precision_mesh127": c3,
+        "config_1d": c1,
         "batching": batching,
         "serving": served,
         "random_r1l": {"lattices": 5, "size_factor": 2.0, "precision": "mixed", "increments": rr,
