@@ -413,7 +413,8 @@ size_t sample_2d_scratch_bytes(int n, int precision, int blocks) {
     if (precision == USFFT_FP64) return 0;
     if (precision == USFFT_FP64_DST) return fp64_dst_slot_bytes(n, USFFT_MAX_D) * (size_t)blocks;
     const size_t W = (size_t)n + 2;
-    if (precision == USFFT_MIXED) return sizeof(double) * (n > 63 ? 10 : 3) * W * W * (size_t)blocks;
+    if (precision == USFFT_MIXED)
+        return sizeof(double) * (n > 63 ? 7 * W * W + 22 * ((size_t)n + 1) : 3 * W * W) * (size_t)blocks;
     return sizeof(double) * 2 * (size_t)n * (n + 1) * (size_t)blocks;
 }
 

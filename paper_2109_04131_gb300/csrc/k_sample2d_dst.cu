@@ -140,7 +140,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // (two n8 tiles sharing the A fragment).
 template <int P, bool TRANSPOSE_OUT, bool SCALE>
 __device__ __forceinline__ void gemm_bf16(const bf16* __restrict__ A, const bf16* __restrict__ Bt,
-                                          bf16* __restrict__ C, const float* __restrict__ Lsc) {
+                                          bf16* __restrict__ C, const float* __restrict__ mu, int n, float c2) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     constexpr int NT = P / 16, TILES = (P / 16) * NT, LD = P + 8;
@@ -170,16 +170,17 @@ __device__ __forceinline__ void gemm_bf16(const bf16* __restrict__ A, const bf16
                 : "+f"(c[1][0]), "+f"(c[1][1]), "+f"(c[1][2]), "+f"(c[1][3])
                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b10), "r"(b11));
         }
-        if (SCALE) {
+        if (SCALE) {    // the scaled inverse eigenvalues c^2 / (mu_row + mu_col), zero in the padding
+            const int ra = m0 + g, rb = m0 + g + 8;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int col0 = n0 + 8 * h + 2 * t;
-                const float2 l0 = *reinterpret_cast<const float2*>(Lsc + (m0 + g) * LD + col0);
-                const float2 l1 = *reinterpret_cast<const float2*>(Lsc + (m0 + g + 8) * LD + col0);
-                c[h][0] *= l0.x;
-                c[h][1] *= l0.y;
-                c[h][2] *= l1.x;
-                c[h][3] *= l1.y;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int col = col0 + e;
+                    c[h][e] = (ra < n && col < n) ? c[h][e] * (c2 / (mu[ra] + mu[col])) : 0.f;
+                    c[h][2 + e] = (rb < n && col < n) ? c[h][2 + e] * (c2 / (mu[rb] + mu[col])) : 0.f;
+                }
             }
         }
         const uint32_t r0 = pack_bf16x2(c[0][0], c[0][1]), r1 = pack_bf16x2(c[0][2], c[0][3]);
@@ -698,7 +699,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
 // ---------------------------------------------------------------------------------------------
 struct BigLayout {
     int W, LD, J1, JA;
-    size_t o_S, o_L, o_Ta, o_Tb, o_A, o_AF, o_Tr, o_md, o_sj, o_r64, o_r32, total;
+    size_t o_S, o_mu, o_zs, o_Ta, o_Tb, o_A, o_AF, o_Tr, o_md, o_sj, o_r64, o_r32, total;
 };
 
 __host__ __device__ inline BigLayout big_layout(int n, int d, int P) {
@@ -707,7 +708,8 @@ __host__ __device__ inline BigLayout big_layout(int n, int d, int P) {
     L.LD = P + 8;
     size_t o = 0;
     L.o_S = o;   o = align16(o + sizeof(__nv_bfloat16) * (size_t)P * L.LD);
-    L.o_L = o;   o = align16(o + sizeof(float) * (size_t)P * L.LD);
+    L.o_mu = o;  o = align16(o + sizeof(float) * (size_t)P);                       // mu_k of K_0
+    L.o_zs = o;  o = align16(o + sizeof(float) * (size_t)L.W * L.W);               // z, halo layout
     L.o_Ta = o;  o = align16(o + sizeof(__nv_bfloat16) * (size_t)P * L.LD);
     L.o_Tb = o;  o = align16(o + sizeof(__nv_bfloat16) * (size_t)P * L.LD);
     L.J1 = 1;
@@ -719,7 +721,7 @@ __host__ __device__ inline BigLayout big_layout(int n, int d, int P) {
         if (j1 > L.JA) L.JA = j1;
         if (j2 > L.JA) L.JA = j2;
     }
-    L.o_A = o;   o = align16(o + sizeof(double) * (size_t)L.JA * 2 * (n + 1));
+    L.o_A = 0;   // the fp64 mode table lives in the scratch slot (read once per solve)
     L.o_AF = o;  o = align16(o + sizeof(float2) * (size_t)L.JA * 2 * (n + 1));
     L.o_Tr = o;  o = align16(o + sizeof(float2) * (size_t)L.J1 * 2 * (n + 1));
     L.o_md = o;  o = align16(o + sizeof(double) * (size_t)d + sizeof(int) * 2 * (size_t)d);
@@ -730,6 +732,13 @@ __host__ __device__ inline BigLayout big_layout(int n, int d, int P) {
     return L;
 }
 
+// doubles of one CTA's scratch slot of the large-mesh kernel: 7 W^2 (vectors and weights) and the
+// fp64 mode table At for up to 11 first-mode indices (d <= 64) by 2 (n + 1)
+__host__ __device__ inline size_t big_slot_doubles(int n) {
+    const size_t W = (size_t)n + 2;
+    return 7 * W * W + 22 * ((size_t)n + 1);
+}
+
 template <int P>
 __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_constant__ Pcg2dArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -737,10 +746,10 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
     const BigLayout Lo = big_layout(n, a.ns.d, P);
     const int W = Lo.W, LD = Lo.LD, WW = W * W;
     bf16* S = reinterpret_cast<bf16*>(smraw + Lo.o_S);
-    float* Li = reinterpret_cast<float*>(smraw + Lo.o_L);
+    float* mu = reinterpret_cast<float*>(smraw + Lo.o_mu);
+    float* zv = reinterpret_cast<float*>(smraw + Lo.o_zs);      // z in shared memory (the SpMV reads its neighbours)
     bf16* Ta = reinterpret_cast<bf16*>(smraw + Lo.o_Ta);
     bf16* Tb = reinterpret_cast<bf16*>(smraw + Lo.o_Tb);
-    double* At = reinterpret_cast<double*>(smraw + Lo.o_A);
     float2* AtF = reinterpret_cast<float2*>(smraw + Lo.o_AF);
     float2* Tr = reinterpret_cast<float2*>(smraw + Lo.o_Tr);
     double* amp = reinterpret_cast<double*>(smraw + Lo.o_md);
@@ -751,35 +760,33 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
     float* red32 = reinterpret_cast<float*>(smraw + Lo.o_r32);
     const int J1 = Lo.J1, JA = Lo.JA;
     const int T = blockDim.x, tid = threadIdx.x;
-    // the CTA's scratch slot
-    double* x64 = a.scratch + (size_t)blockIdx.x * 10 * WW;
+    // the CTA's scratch slot: fp64 x and edge weights, fp32 weights, scaling, p, r, q, d, w (7 W^2
+    // doubles), then the fp64 mode table At
+    double* x64 = a.scratch + (size_t)blockIdx.x * big_slot_doubles(n);
+    double* At = x64 + 7 * (size_t)WW;
     double* w64l = x64 + WW;
     double* w64d = w64l + WW;
-    double* d64 = w64d + WW;
-    double* r64 = d64 + WW;
-    float* wl = reinterpret_cast<float*>(r64 + WW);
+    float* wl = reinterpret_cast<float*>(w64d + WW);
     float* wd = wl + WW;
     float* scs = wd + WW;
     float* ph = scs + WW;
     float* rv = ph + WW;
-    float* zv = rv + WW;
-    float* qv = zv + WW;
+    float* qv = rv + WW;
     float* dv = qv + WW;
     float* wv = dv + WW;
 
     const float c2 = 4.0f / ((float)n1 * (float)n1);
     for (int e = tid; e < P * LD; e += T) {
         const int j = e / LD, k = e % LD;
-        float sv = 0.f, lv = 0.f;
-        if (j < n && k < n) {
-            sv = sinpif((float)((j + 1) * (k + 1)) / (float)n1);
-            const float s1 = sinpif((float)(k + 1) / (2.0f * n1)), s2 = sinpif((float)(j + 1) / (2.0f * n1));
-            lv = c2 / (4.0f * s1 * s1 + 4.0f * s2 * s2);
-        }
+        float sv = 0.f;
+        if (j < n && k < n) sv = sinpif((float)((j + 1) * (k + 1)) / (float)n1);
         S[e] = __float2bfloat16_rn(sv);
-        Li[e] = lv;
         Ta[e] = __float2bfloat16_rn(0.f);
         Tb[e] = __float2bfloat16_rn(0.f);
+    }
+    for (int k = tid; k < P; k += T) {     // eigenvalues of K_0's 1-D factor, mu_k = 4 sin^2(pi (k+1) / (2(n+1)))
+        const float s1 = sinpif((float)(k + 1) / (2.0f * n1));
+        mu[k] = 4.0f * s1 * s1;
     }
     for (int e = tid; e < WW; e += T) {     // the halo ring stays zero (Dirichlet boundary)
         wl[e] = 0.f;
@@ -858,10 +865,9 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
         for (int g = tid; g < G; g += T) {
             const int h = (g / n + 1) * W + g % n + 1;
             const double dg = (w64l[h] + w64l[h + W]) + (w64d[h] + w64d[h + 1]);
-            d64[h] = dg;
             scs[h] = rsqrtf(0.25f * d2f_round(dg));
             x64[h] = 0.0;
-            r64[h] = b;
+            rv[h] = d2f_round(b);        // r = b, kept as fp32 (the inner solve starts from fp32(r) / ||r||)
         }
         __syncthreads();
 
@@ -876,13 +882,13 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 Ta[pp * LD + qq] = __float2bfloat16_rn(scs[h] * rv[h]);
             }
             __syncthreads();
-            gemm_bf16<P, false, false>(S, Ta, Tb, nullptr);
+            gemm_bf16<P, false, false>(S, Ta, Tb, nullptr, n, c2);
             __syncthreads();
-            gemm_bf16<P, true, true>(Tb, S, Ta, Li);
+            gemm_bf16<P, true, true>(Tb, S, Ta, mu, n, c2);
             __syncthreads();
-            gemm_bf16<P, false, false>(S, Ta, Tb, nullptr);
+            gemm_bf16<P, false, false>(S, Ta, Tb, nullptr, n, c2);
             __syncthreads();
-            gemm_bf16<P, true, false>(Tb, S, Ta, nullptr);
+            gemm_bf16<P, true, false>(Tb, S, Ta, nullptr, n, c2);
             __syncthreads();
             for (int g = tid; g < G; g += T) {
                 const int pp = g / n, qq = g % n, h = (pp + 1) * W + qq + 1;
@@ -893,7 +899,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             // single-reduction flexible PCG (the small-mesh kernel's inner solve; p in ph, w = K z in wv)
             for (int g = tid; g < G; g += T) {
                 const int h = (g / n + 1) * W + g % n + 1;
-                rv[h] = d2f_round(r64[h]) * inv;
+                rv[h] = rv[h] * inv;       // fp32(r) / ||r||
                 dv[h] = 0.f;
                 ph[h] = 0.f;
                 qv[h] = 0.f;
@@ -966,7 +972,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 acc = fma(w64d[h], xi - x64[h - 1], acc);
                 acc = fma(w64d[h + 1], xi - x64[h + 1], acc);
                 const double r = b - acc;
-                r64[h] = r;
+                rv[h] = d2f_round(r);
                 rl64 = fma(r, r, rl64);
             }
             const double rr_prev = rr64;
