@@ -582,6 +582,31 @@ def e2e_measure(plan, t, steps, barrier, world, dev):
                     "search, both detection iterations, host copies)"}
 
 
+def autotune_shapes(reqs, precisions):
+    """usfft_autotune on the first request of every (precision, mesh-size bucket) shape, after its
+    increments (untimed); the process-wide table then serves every later plan of that shape.  Returns
+    the table, the reports and the seconds spent."""
+    from paper_2109_04131_gb300 import binding
+    t0 = time.perf_counter()
+    seen, reports = set(), []
+    for r in reqs:
+        if r.workload.problem.kind != W.PDE_2D:
+            continue
+        for prec in precisions:
+            key = (prec, (r.workload.problem.n + 15) // 16)
+            if key in seen:
+                continue
+            seen.add(key)
+            wl = W.with_precision(r.workload, prec)
+            plan = binding.Plan(wl.problem, wl.params)
+            for _ in range(r.increments):
+                plan.increment()
+            rep = plan.autotune(reps=2 if prec == W.PRECISION_MIXED else 1)
+            reports.append({"precision": prec, "n": wl.problem.n, **rep})
+            plan.close()
+    return {"table": binding.usfft_tune_export(), "shapes": reports, "seconds": time.perf_counter() - t0}
+
+
 def serving_measure(kind, count):
     """Batched ("batch": `count` independent instances shaped like the batching configuration, all
     present at the start, three increments each) or served ("serve": a seeded Poisson stream of
@@ -596,6 +621,9 @@ def serving_measure(kind, count):
 
     def make_plan(r):
         return binding.Plan(r.workload.problem, r.workload.params, stream=torch.cuda.Stream().cuda_stream)
+
+    # launch parameters tuned per shape for both modes compared below (bit-identical results)
+    tuned = autotune_shapes(reqs, (W.PRECISION_MIXED, W.PRECISION_FP64_DST))
 
     # continuous batching without a round barrier (one worker thread per admitted instance)
     rep = serving.AsyncServer(budget_bytes=150 << 30, make_plan=make_plan, max_active=64).run(reqs)
@@ -612,7 +640,7 @@ def serving_measure(kind, count):
     rounds.pop("instances")
     alone.pop("results")
     alone64.pop("results")
-    return {"requests": count, "served": rep, "served_in_rounds": rounds, "one_at_a_time": alone,
+    return {"requests": count, "autotune": tuned, "served": rep, "served_in_rounds": rounds, "one_at_a_time": alone,
             "one_at_a_time_fp64": alone64,
             "speedup_samples_per_s": rep["samples_per_s"] / alone["samples_per_s"] if alone["samples_per_s"] else None,
             "speedup_vs_fp64_one_at_a_time": rep["samples_per_s"] / alone64["samples_per_s"]

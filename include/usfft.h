@@ -384,6 +384,33 @@ usfft_status usfft_increment_sharded(usfft_plan_t* plan, int rank, int nranks, u
 usfft_status usfft_search_lattice_multiple(const int8_t* J, int64_t n, int t, uint64_t seed, int trials,
                                            int max_sizes, int64_t divisor, int64_t* z, int64_t* M);
 
+/* ---- Autotuning of launch parameters ----
+ *
+ * usfft_autotune times `reps` replays (usfft_replay) of the plan's last step (0: 3) for each
+ * candidate of the launch parameters that leave every result bit-identical, keeps the fastest in a
+ * process-wide table and applies it to the plan:
+ *   - the persistent grid of the 2-D sampler (the resident CTAs, twice and four times that), keyed
+ *     by precision and mesh-size bucket (n + 15) / 16; plans created later start from it;
+ *   - the column-pair tile of each pass of the two-pass lattice FFT (1 .. 32 within shared memory),
+ *     keyed by the pass's sub-transform length, used by every later launch of that length.
+ * The plan needs a completed increment (USFFT_ESTATE otherwise); its detected set and state are
+ * unchanged (the replays recompute the last step's result).  out (may be NULL) receives the times
+ * per replay before and after and the chosen values (0 where a parameter did not apply).
+ * The table as text ("<knob> <key> <value> <ms per replay>" per line, knob 1 = sampler grid,
+ * 2 = FFT tile): usfft_tune_export (text may be NULL to query *length; capacity >= length + 1),
+ * usfft_tune_import (adds or replaces the entries of the text; NULL clears the table; USFFT_EINVAL
+ * and no change if a line does not parse).  The table is shared by all plans of the process and
+ * guarded for concurrent use. */
+typedef struct {
+    double ms_before, ms_after;   /* ms per replay of the last step */
+    int32_t sampler_blocks;       /* chosen persistent grid of the 2-D sampler (0: not tuned) */
+    int32_t fft_pass1_tile;       /* chosen tiles of the two-pass FFT (0: not tuned) */
+    int32_t fft_final_tile;
+} usfft_tune_report;
+usfft_status usfft_autotune(usfft_plan_t* plan, int reps, usfft_tune_report* out);
+usfft_status usfft_tune_export(char* text, size_t capacity, size_t* length);
+usfft_status usfft_tune_import(const char* text);
+
 /* Free every device buffer and the plan.  NULL is ignored. */
 void usfft_destroy(usfft_plan_t* plan);
 

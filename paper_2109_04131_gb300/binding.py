@@ -66,6 +66,11 @@ class UsfftStageTimes(ctypes.Structure):
                 ("refine_steps_total", ctypes.c_int64)]
 
 
+class UsfftTuneReport(ctypes.Structure):
+    _fields_ = [("ms_before", ctypes.c_double), ("ms_after", ctypes.c_double), ("sampler_blocks", ctypes.c_int32),
+                ("fft_pass1_tile", ctypes.c_int32), ("fft_final_tile", ctypes.c_int32)]
+
+
 # exported symbols and their signatures (restype, argtypes)
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -100,6 +105,9 @@ SIGNATURES = {
                                                ctypes.POINTER(UsfftIncrementInfo)]),
     "usfft_search_lattice_multiple": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                                      ctypes.c_int, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "usfft_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(UsfftTuneReport)]),
+    "usfft_tune_export": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "usfft_tune_import": (ctypes.c_int, [ctypes.c_char_p]),
     "usfft_destroy": (None, [_P]),
     "usfft_version": (ctypes.c_char_p, []),
     "usfft_search_lattice": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
@@ -344,6 +352,26 @@ def usfft_increment_sharded(plan, rank, nranks, allreduce_fn):
     return {name: getattr(info, name) for name, _ in UsfftIncrementInfo._fields_}
 
 
+def usfft_autotune(plan, reps=3):
+    return plan.autotune(reps)
+
+
+def usfft_tune_export() -> str:
+    """The process-wide table of tuned launch parameters as text."""
+    lib = load_library()
+    n = ctypes.c_size_t(0)
+    _check(lib.usfft_tune_export(None, 0, ctypes.byref(n)), None)
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(lib.usfft_tune_export(buf, n.value + 1, ctypes.byref(n)), None)
+    return buf.value.decode()
+
+
+def usfft_tune_import(text):
+    """Add the entries of `text` to the table (None clears it)."""
+    lib = load_library()
+    _check(lib.usfft_tune_import(None if text is None else text.encode()), None)
+
+
 def usfft_random_lattices(t, i, n_prev, n_t, s_t, L, factor, seed):
     """Host-only random rank-1 lattice rule of the library: (z [L][t], M [L])."""
     lib = load_library()
@@ -557,6 +585,12 @@ class Plan:
         self._ck(self._lib.usfft_get_selection(self.handle, words.ctypes.data, ctypes.byref(n)))
         bits = np.unpackbits(words.view(np.uint8), bitorder="little")[: n.value]
         return bits.astype(bool)
+
+    def autotune(self, reps: int = 3) -> dict:
+        """Tune the launch parameters on replays of the last step (usfft_autotune)."""
+        rep = UsfftTuneReport()
+        self._ck(self._lib.usfft_autotune(self.handle, int(reps), ctypes.byref(rep)))
+        return {name: getattr(rep, name) for name, _ in UsfftTuneReport._fields_}
 
     def set_keep_iterations(self, on: bool) -> None:
         self._ck(self._lib.usfft_set_keep_iterations(self.handle, int(bool(on))))

@@ -851,7 +851,8 @@ usfft_status usfft_plan(const usfft_problem* problem, const usfft_params* params
             return bail(USFFT_ECUDA);
         }
         if (pr.kind == USFFT_PDE_2D) {
-            plan->cg_blocks = sample_2d_default_blocks(pr.n, pa.precision);
+            plan->cg_blocks = tune_get(TUNE_SAMPLER_BLOCKS, tune_key_sampler(pa.precision, pr.n),
+                                       sample_2d_default_blocks(pr.n, pa.precision));
             size_t sb = sample_2d_scratch_bytes(pr.n, pa.precision, plan->cg_blocks);
             if ((st = ensure(plan, plan->cgscr, sb, "cg scratch")) != USFFT_OK) return bail(st);
         }
@@ -1088,6 +1089,107 @@ usfft_status usfft_search_lattice_multiple(const int8_t* J, int64_t n, int t, ui
         return fail(nullptr, USFFT_ELATTICE, "no reconstructing rank-1 lattice found");
     for (int j = 0; j < t; ++j) z[j] = zz[(size_t)j];
     *M = mm;
+    return USFFT_OK;
+}
+
+// ms per replay of the plan's last step: one untimed replay, then `reps` between two events
+static usfft_status time_replays(usfft_plan_t* plan, int reps, double* ms) {
+    usfft_status st = run_step_device(plan, false);
+    if (st != USFFT_OK) return st;
+    CK(cudaEventRecord(plan->ev0, plan->stream));
+    for (int k = 0; k < reps; ++k)
+        if ((st = run_step_device(plan, false)) != USFFT_OK) return st;
+    CK(cudaEventRecord(plan->ev1, plan->stream));
+    if ((st = wait_stream(plan)) != USFFT_OK) return st;
+    float e = 0.f;
+    CK(cudaEventElapsedTime(&e, plan->ev0, plan->ev1));
+    *ms = (double)e / reps;
+    return USFFT_OK;
+}
+
+usfft_status usfft_autotune(usfft_plan_t* plan, int reps, usfft_tune_report* out) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (plan->t < 1 || !plan->replay_valid) return fail(plan, USFFT_ESTATE, "usfft_autotune needs a completed increment");
+    if (reps < 1) reps = 3;
+    const int saved_launches = plan->launches;
+    const bool saved_keep = plan->keep_iters, saved_timing = plan->timing;
+    plan->keep_iters = false;
+    plan->timing = false;
+    usfft_tune_report rep;
+    memset(&rep, 0, sizeof rep);
+    usfft_status st = time_replays(plan, reps, &rep.ms_before);
+    double best_ms = rep.ms_before;
+    // 1. persistent grid of the 2-D sampler: one, two or four CTAs per SM's worth of resident CTAs
+    if (st == USFFT_OK && plan->prob.kind == USFFT_PDE_2D && plan->par.precision != USFFT_FP64) {
+        const int def = sample_2d_default_blocks(plan->prob.n, plan->par.precision);
+        const int cur = plan->cg_blocks;
+        int best = cur;
+        for (int mult : {1, 2, 4}) {
+            const int cand = def * mult;
+            if (cand == cur) continue;
+            if ((st = ensure(plan, plan->cgscr, sample_2d_scratch_bytes(plan->prob.n, plan->par.precision, cand),
+                             "cg scratch")) != USFFT_OK)
+                break;
+            plan->cg_blocks = cand;
+            double ms = 0.0;
+            if ((st = time_replays(plan, reps, &ms)) != USFFT_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+            }
+        }
+        plan->cg_blocks = best;
+        if (st == USFFT_OK) tune_set(TUNE_SAMPLER_BLOCKS, tune_key_sampler(plan->par.precision, plan->prob.n), best, best_ms);
+        rep.sampler_blocks = best;
+    }
+    // 2. column-pair tile of each pass of the two-pass lattice FFT (when the last step used it)
+    if (st == USFFT_OK && !plan->rr_active && !plan->inplace && plan->nJ > 0 && plan->fp.L2 > 0) {
+        const int Gp = (plan->G + 1) / 2;
+        const bool two = plan->fp.L1 > 1;
+        for (int pass = two ? 0 : 1; pass < 2 && st == USFFT_OK; ++pass) {
+            const bool fin = pass == 1;
+            const int L = fin ? plan->fp.L2 : plan->fp.L1;
+            const int nb = fin ? (two && plan->fp.L1 > 2 ? 2 : 1) : 1;
+            const int64_t key = tune_key_fft(L, fin);
+            int best = tune_get(TUNE_FFT_TILE, key, fft_default_tile(L, Gp, nb));
+            for (int cand : {1, 2, 4, 8, 16, 32}) {
+                if (cand > Gp || !fft_tile_fits(L, cand, nb) || cand == best) continue;
+                tune_set(TUNE_FFT_TILE, key, cand, 0.0);
+                double ms = 0.0;
+                if ((st = time_replays(plan, reps, &ms)) != USFFT_OK) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = cand;
+                }
+            }
+            tune_set(TUNE_FFT_TILE, key, best, best_ms);
+            if (fin) rep.fft_final_tile = best; else rep.fft_pass1_tile = best;
+        }
+    }
+    if (st == USFFT_OK) st = time_replays(plan, reps, &rep.ms_after);
+    plan->keep_iters = saved_keep;
+    plan->timing = saved_timing;
+    plan->launches = saved_launches;
+    if (out) *out = rep;
+    return st;
+}
+
+usfft_status usfft_tune_export(char* text, size_t capacity, size_t* length) {
+    const std::string t = tune_dump();
+    if (length) *length = t.size();
+    if (!text) return USFFT_OK;
+    if (capacity < t.size() + 1) return fail(nullptr, USFFT_EINVAL, "usfft_tune_export: buffer too small");
+    memcpy(text, t.c_str(), t.size() + 1);
+    return USFFT_OK;
+}
+
+usfft_status usfft_tune_import(const char* text) {
+    if (!text) {
+        tune_clear();
+        return USFFT_OK;
+    }
+    std::string err;
+    if (!tune_parse(text, err)) return fail(nullptr, USFFT_EINVAL, err);
     return USFFT_OK;
 }
 

@@ -625,6 +625,18 @@ static size_t pass_smem(int L, int cols) {
     return s;
 }
 
+int fft_default_tile(int L, int Gp, int nb) { return pick_gt(L, Gp, nb); }
+bool fft_tile_fits(int L, int Gt, int nb) { return Gt >= 1 && pass_smem(L, nb * Gt) <= 232448; }
+
+// the tuned tile of a pass (usfft_autotune), else the default; clamped to the columns and the
+// shared memory
+static int pass_tile(int L, int Gp, int nb, bool final_pass) {
+    const int def = pick_gt(L, Gp, nb);
+    int gt = tune_get(TUNE_FFT_TILE, tune_key_fft(L, final_pass), def);
+    if (gt > Gp) gt = Gp;
+    return fft_tile_fits(L, gt, nb) ? gt : def;
+}
+
 template <class A>
 static cudaError_t launch_fft_impl(const FftPlan& p, int G, const double* U, const typename A::C* W,
                                    const GatherPlan& gp, int64_t nJ, void* scratch, double2* C, cudaStream_t s,
@@ -656,7 +668,7 @@ static cudaError_t launch_fft_impl(const FftPlan& p, int G, const double* U, con
     if (two) {
         // pass 1: length L1 over i1 (rows i1 L2 + i2), outer index i2
         a.L = p.L1;
-        a.Gt = pick_gt(a.L, a.Gp, 1);
+        a.Gt = pass_tile(a.L, a.Gp, 1, false);
         a.nOuter = p.L2;
         a.wstride = p.M / a.L;
         a.Ur = U;
@@ -679,7 +691,7 @@ static cudaError_t launch_fft_impl(const FftPlan& p, int G, const double* U, con
     FftArgs b = a;
     b.L = p.L2;
     b.L1 = two ? p.L1 : 1;
-    b.Gt = pick_gt(b.L, b.Gp, b.L1 > 2 ? 2 : 1);
+    b.Gt = pass_tile(b.L, b.Gp, b.L1 > 2 ? 2 : 1, true);
     b.nOuter = b.L1 / 2 + 1;
     b.wstride = p.M / b.L;
     b.Ur = two ? nullptr : U;

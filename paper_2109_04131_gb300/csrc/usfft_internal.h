@@ -178,6 +178,22 @@ cudaError_t launch_statistics(const double2* C, int G, int64_t nI, int d, const 
                               const int64_t* offsets, double2* mean, double* var, double* gsi, cudaStream_t s,
                               int* launches);
 
+// Tuned launch parameters (tune.cpp; filled by usfft_autotune): tune_get returns the stored value
+// or `fallback`.  Knobs that leave results bit-identical only.
+enum TuneKnob { TUNE_SAMPLER_BLOCKS = 1, TUNE_FFT_TILE = 2 };
+int tune_get(int knob, int64_t key, int fallback);
+void tune_set(int knob, int64_t key, int value, double ms);
+void tune_erase(int knob, int64_t key);
+std::string tune_dump();
+bool tune_parse(const char* text, std::string& err);
+void tune_clear();
+// keys of the knobs
+inline int64_t tune_key_sampler(int precision, int n) { return (int64_t)precision * 64 + (n + 15) / 16; }
+inline int64_t tune_key_fft(int L, bool final_pass) { return 2 * (int64_t)L + (final_pass ? 1 : 0); }
+// the two-pass FFT's default column-pair tile, and whether a tile fits its shared memory
+int fft_default_tile(int L, int Gp, int nb);
+bool fft_tile_fits(int L, int Gt, int nb);
+
 // Raises the kernel's dynamic shared-memory limit to at least `bytes` (never lowers it: plans
 // launch from several host threads at once); smem_attr.cpp.
 cudaError_t allow_dyn_smem(const void* func, size_t bytes);

@@ -277,6 +277,41 @@ def test_host_deadline_is_etimeout_and_the_increment_can_be_retried(B, monkeypat
     plan.close()
 
 
+def test_autotune_keeps_results_bit_identical(B):
+    # the tuned parameters (sampler grid, two-pass FFT tiles) change no result: the replayed step
+    # after tuning gives the same coefficients and selection bit for bit, and a later plan of the
+    # same shape starts from the tuned grid
+    B.usfft_tune_import(None)
+    w = W.with_precision(W.small_2d(n=15, d=4, seed=3, N=6, s=30), W.PRECISION_MIXED)
+    plan = B.Plan(w.problem, w.params)
+    with pytest.raises(B.UsfftError) as e:
+        plan.autotune()
+    assert e.value.status == 7                    # needs a completed increment
+    for _ in range(3):
+        plan.increment()
+    C, sel, S = plan.get_coefficients(), plan.get_selection(), plan.get_set()
+    rep = plan.autotune(reps=2)
+    assert rep["sampler_blocks"] > 0 and rep["ms_before"] > 0 and rep["ms_after"] > 0
+    assert "1 " in B.usfft_tune_export()
+    plan.replay(sync=True)
+    assert np.array_equal(plan.get_coefficients(), C) and np.array_equal(plan.get_selection(), sel)
+    assert np.array_equal(plan.get_set(), S)
+    plan.close()
+    # the two-pass FFT (|J| = 81^2 > 4096): tiles tuned, result unchanged
+    prob = W.trigpoly_grid(G=3, d=2, K=40, seed=5)
+    params = W.Params(N=45, s=20000, s_local=20000, delta=1e-9, delta_is_relative=False, r=1, seed=3)
+    plan = B.Plan(prob, params)
+    plan.increment()
+    plan.increment()
+    C = plan.get_coefficients()
+    rep = plan.autotune(reps=2)
+    assert rep["fft_final_tile"] > 0
+    plan.replay(sync=True)
+    assert np.array_equal(plan.get_coefficients(), C)
+    plan.close()
+    B.usfft_tune_import(None)
+
+
 def test_increment_after_last_is_a_state_error(B):
     prob = W.trigpoly(G=2, d=2, N=3, seed=1, base_terms=2, node_terms=1, kmax=2, mag_lo=1e-2)
     params = W.Params(N=3, s=10, s_local=10, delta=1e-9, delta_is_relative=False, r=1, seed=1)

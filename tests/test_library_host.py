@@ -191,3 +191,22 @@ def test_lattice_search_exhaustion(binding):
     z0, M0 = lattice.search(J, 2, 2, trials=1, max_sizes=1)
     z1, M1 = binding.usfft_search_lattice(J, 2, 2, trials=1, max_sizes=1)
     assert M0 == M1 == 81 and np.array_equal(z0, z1)
+
+
+def test_tune_table_import_export(binding):
+    # the process-wide table of tuned launch parameters (host only): text round trip, a malformed
+    # line leaves the table unchanged, None clears it
+    binding.usfft_tune_import(None)
+    assert binding.usfft_tune_export() == ""
+    binding.usfft_tune_import("1 68 304 1.5\n2 8193 4 0.25\n")
+    rows = sorted(tuple(line.split()[:3]) for line in binding.usfft_tune_export().strip().split("\n"))
+    assert rows == [("1", "68", "304"), ("2", "8193", "4")]
+    for bad in ("1 68\n", "3 1 1 1\n", "1 68 0 1\n", "1 68 304 1.5 extra\n"):
+        with pytest.raises(binding.UsfftError) as e:
+            binding.usfft_tune_import(bad)
+        assert e.value.status == 1
+    assert len(binding.usfft_tune_export().strip().split("\n")) == 2
+    binding.usfft_tune_import("1 68 152 1.0\n")          # replaces the entry
+    assert "1 68 152" in binding.usfft_tune_export()
+    binding.usfft_tune_import(None)
+    assert binding.usfft_tune_export() == ""
