@@ -56,8 +56,10 @@ PROFILE_TRAFFIC = {
                  "sha": "34d37d1241cb3db6", "profile": "profiles/pcg2d_fp64_dst_c2_t3.md"},
     "fp64": {"bytes": 174643200, "files": ["k_sample2d.cu", "k_pcg_common.cuh", "k_theta.cuh"],
              "sha": "4432e9a0bf66a956", "profile": "profiles/pcg2d_fp64_c2_t3.md"},
-    "fft": {"bytes": 546580224, "files": ["k_fft.cu", "k_cvt.cuh"],
-            "sha": "cc730b2a5f636e57", "profile": "profiles/fft_c2_t3.md"},
+    "fft": {"bytes": 547250176, "files": ["k_fft.cu", "k_cvt.cuh"],
+            "sha": "53e4a6d795acf610", "profile": "profiles/fft_c2_t3.md"},
+    "big": {"bytes": 6153799000, "files": ["k_sample2d_dst.cu", "k_pcg_common.cuh", "k_theta.cuh", "k_cvt.cuh"],
+            "sha": "e529b6bac93a64ac", "profile": "profiles/pcg2d_mixed_big_mesh127_t3.md"},
 }
 
 

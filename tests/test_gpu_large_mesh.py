@@ -92,3 +92,19 @@ def test_large_mesh_boundary_sizes(B, n):
     with pytest.raises(B.UsfftError):
         B.Plan(w.problem, dataclasses.replace(w.params, precision=W.PRECISION_FP64))
     plan.close()
+
+
+@pytest.mark.parametrize("precision", [W.PRECISION_MIXED, W.PRECISION_FP64_DST])
+def test_largest_mesh_and_dimension(B, precision):
+    # n = 127 with d = 64 (the largest mesh with the largest stochastic dimension; the mixed kernel's
+    # shared-memory tables are then at their largest): FE samples at explicit points against the
+    # oracle's banded solves
+    prob = W.Problem(kind=W.PDE_2D, n=127, d=64)
+    params = W.Params(N=3, s=10, s_local=10, delta=1e-8, delta_is_relative=True, r=1, seed=2, precision=precision)
+    plan = B.Plan(prob, params)
+    run = OracleRun(prob, params)
+    Y = W.test_points(2, 64, seed=9)
+    U = plan.sample_points(Y)
+    Uo = ev.sample_points(prob, Y, run.mesh)
+    assert np.max(np.abs(U - Uo)) <= TOL * np.max(np.abs(Uo))
+    plan.close()

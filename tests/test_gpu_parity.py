@@ -58,13 +58,39 @@ def near_ties(records, theta, s_tilde_of, rel=2e-10):
 
 
 def compare_increment(plan, run, ctx, exact=True):
-    """Run increment t = run.t + 1 on both sides from the oracle's state and compare."""
+    """Run increment t = run.t + 1 on both sides from the oracle's state and compare: lattice,
+    candidates, every detection iteration's samples, coefficients and cumulative union, and the
+    detected set."""
     if run.t > 0:
         plan.resume(run.t, run.I_prefix, run.theta)
     first = len(run.records)
     want = run.increment()
+    plan.set_keep_iterations(True)
     info = plan.increment()
     got = plan.get_set()
+    # every detection iteration of the last detection step (the coupled step, or the 1-D detection
+    # at t = 1): samples and coefficients within TOL, the union of iterations 1..i against the
+    # oracle's (exact, or up to near-ties)
+    coupled = [r for r in run.records[first:] if r.coupled]
+    recs = run.records[first:] if run.t == 1 else coupled      # none: an empty candidate set
+    kept = plan.kept_iterations()
+    if recs and recs[-1].U is not None and not isinstance(recs[-1].M, list):
+        assert kept == len(recs), f"{ctx}: kept {kept} iterations, oracle ran {len(recs)}"
+        union = set()
+        for i, rec in enumerate(recs, start=1):
+            U, C, bits = plan.get_iteration(i)
+            assert np.max(np.abs(U - rec.U)) <= TOL * np.max(np.abs(rec.U)), f"{ctx}: iteration {i} samples"
+            assert node_rel(C, rec.C) < TOL, f"{ctx}: iteration {i} coefficients"
+            for sg in rec.selected:
+                union.update(int(k) for k in sg)
+            want_bits = np.zeros(len(bits), dtype=bool)
+            want_bits[sorted(union)] = True
+            if not np.array_equal(bits, want_bits):
+                assert not exact, f"{ctx}: iteration {i} union differs"
+                d = run.prob.d
+                amb = near_ties(recs[:i], run.theta, lambda r: run.p.s_local if (r.t < d or not r.coupled) else run.p.s)
+                assert set(np.nonzero(bits != want_bits)[0].tolist()) <= amb, f"{ctx}: iteration {i} union"
+    plan.set_keep_iterations(False)
     assert info["t"] == run.t
     if not (got.shape == want.shape and np.array_equal(got, want)):
         assert not exact, f"{ctx}: detected sets differ at t={run.t}"
@@ -130,8 +156,10 @@ def test_trigpoly_exact_recovery(B, G, seed):
     plan.close()
 
 
-def test_trigpoly_two_pass_fft(B):
-    # full-grid support [-40,40]^2: |J| = 81^2 = 6561 > 4096 needs the two-pass FFT
+def test_trigpoly_full_grid_radix3_lattice(B):
+    # full-grid support [-40,40]^2: |J| = 81^2 = 6561 candidates on the lattice of size 3^8 (the
+    # in-place FFT with radix-3 stages only); the two-pass FFT is exercised by
+    # test_largest_search_domain_two_pass_exact_recovery and the full-size step t = 4
     prob = W.trigpoly_grid(G=3, d=2, K=40, seed=5)
     params = W.Params(N=45, s=20000, s_local=20000, delta=1e-9, delta_is_relative=False, r=1, seed=3)
     plan = B.Plan(prob, params)
@@ -152,6 +180,30 @@ def test_small_2d_matches_oracle(B, precision):
     for t in range(1, 4):
         info = compare_increment(plan, run, f"2-D n=15 precision={precision}", exact=False)
         assert info["cg_iters_max"] > 0
+    plan.close()
+
+
+def test_largest_search_domain_two_pass_exact_recovery(B):
+    # the largest search domain (N = 127, int8 frequencies): a polynomial supported on the full grid
+    # [-127, 127]^2 has |J| = 255^2 = 65025 candidates at t = 2, far beyond the in-place FFT (two
+    # passes with L1, L2 in the hundreds); its coefficients are recovered exactly (Theorem 1.1)
+    prob = W.trigpoly_grid(G=2, d=2, K=127, seed=11)
+    params = W.Params(N=127, s=70000, s_local=70000, delta=1e-9, delta_is_relative=False, r=1, seed=4)
+    plan = B.Plan(prob, params)
+    plan.increment()
+    info = plan.increment()
+    assert info["n_candidates"] == 255 * 255 and info["M"] >= 255 * 255
+    z, M = plan.get_lattice()
+    J, m = plan.get_candidates()
+    from oracle import lattice
+    zo, Mo = lattice.search(J, 2, params.seed)
+    assert M == Mo and np.array_equal(z, zo)
+    C = plan.get_coefficients()
+    for g in range(prob.G):
+        truth = {tuple(int(v) for v in f): c for f, c in zip(prob.tp_freqs[g], prob.tp_coefs[g]) if c != 0}
+        want = np.array([truth[tuple(int(v) for v in k)] for k in J])
+        assert np.max(np.abs(C[g] - want)) < 1e-13
+    assert len(plan.get_set()) == 255 * 255
     plan.close()
 
 
@@ -297,9 +349,10 @@ def test_autotune_keeps_results_bit_identical(B):
     assert np.array_equal(plan.get_coefficients(), C) and np.array_equal(plan.get_selection(), sel)
     assert np.array_equal(plan.get_set(), S)
     plan.close()
-    # the two-pass FFT (|J| = 81^2 > 4096): tiles tuned, result unchanged
-    prob = W.trigpoly_grid(G=3, d=2, K=40, seed=5)
-    params = W.Params(N=45, s=20000, s_local=20000, delta=1e-9, delta_is_relative=False, r=1, seed=3)
+    # the two-pass FFT (the full grid [-127, 127]^2: M = 69120, beyond the in-place pass): tiles
+    # tuned, result unchanged
+    prob = W.trigpoly_grid(G=1, d=2, K=127, seed=5)
+    params = W.Params(N=127, s=70000, s_local=70000, delta=1e-9, delta_is_relative=False, r=1, seed=4)
     plan = B.Plan(prob, params)
     plan.increment()
     plan.increment()
