@@ -430,9 +430,10 @@ __global__ void __launch_bounds__(kFftThreads) fft_final_kernel(const __grid_con
 static const int kInplaceThreads = 512;
 static const int kTwB = 128;
 
+// e < M < 2^31: 32-bit exponent arithmetic (kTwB is a power of two)
 template <class A>
-__device__ __forceinline__ typename A::C tw_pair(const typename A::C* T1, const typename A::C* T2, int64_t e) {
-    const int r = (int)(e % kTwB), q = (int)(e / kTwB);
+__device__ __forceinline__ typename A::C tw_pair(const typename A::C* T1, const typename A::C* T2, unsigned e) {
+    const unsigned r = e & (kTwB - 1), q = e / kTwB;
     if (q == 0) return T1[r];
     if (r == 0) return T2[q];
     return A::mul(T1[r], T2[q]);
@@ -440,15 +441,14 @@ __device__ __forceinline__ typename A::C tw_pair(const typename A::C* T1, const 
 
 // one radix-R decimation-in-time butterfly of the in-place pass (compile-time R: registers)
 template <class A, int R>
-__device__ __forceinline__ void inplace_butterfly(typename A::C* buf, int base, int L, int CP, int c, int j,
-                                                  int64_t estep, int M, const typename A::C* T1,
-                                                  const typename A::C* T2) {
+__device__ __forceinline__ void inplace_butterfly(typename A::C* buf, int base, int L, int j, unsigned estep, int M,
+                                                  const typename A::C* T1, const typename A::C* T2) {
     typedef typename A::C C;
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        v[r] = buf[(base + r * L) * CP + c];
-        if (r > 0 && j > 0) v[r] = A::mul(v[r], tw_pair<A>(T1, T2, (int64_t)j * r * estep));
+        v[r] = buf[base + r * L];
+        if (r > 0 && j > 0) v[r] = A::mul(v[r], tw_pair<A>(T1, T2, (unsigned)j * (unsigned)r * estep));
     }
     if (R == 8) dft8<A>(v);
     else if (R == 4) dft4<A>(v);
@@ -456,60 +456,64 @@ __device__ __forceinline__ void inplace_butterfly(typename A::C* buf, int base, 
     else if (R == 3) dft3<A>(v);
     else {   // direct DFT of length R: out[k] = sum_r v[r] W_R^{rk}, W_R = W_M^(M/R)
         C out[R];
-        const int64_t unit = M / R;
+        const unsigned unit = (unsigned)(M / R);
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             C acc = v[0];
 #pragma unroll
-            for (int r = 1; r < R; ++r) acc = A::add(acc, A::mul(v[r], tw_pair<A>(T1, T2, (int64_t)((r * k) % R) * unit)));
+            for (int r = 1; r < R; ++r) acc = A::add(acc, A::mul(v[r], tw_pair<A>(T1, T2, (unsigned)((r * k) % R) * unit)));
             out[k] = acc;
         }
 #pragma unroll
         for (int k = 0; k < R; ++k) v[k] = out[k];
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[(base + r * L) * CP + c] = v[r];
+    for (int r = 0; r < R; ++r) buf[base + r * L] = v[r];
 }
 
+// One column pair per CTA.  Per butterfly the group index q = bt / L comes from a multiply-high by
+// the stage's reciprocal ceil(2^32 / L): exact while bt L < 2^32 (bt < M / R, L <= M <= 14528), and a
+// few integer instructions instead of a division by a value known only at run time.
 template <class A>
 __global__ void __launch_bounds__(kInplaceThreads, 2) fft_inplace_kernel(const __grid_constant__ FftArgs a,
                                                                         const typename A::C* W, const int* pos_of,
-                                                                        const int* mk, int CP) {
+                                                                        const int* mk) {
     typedef typename A::C C;
     extern __shared__ __align__(16) unsigned char fraw[];
     const int M = (int)a.M;
     const int nT2 = (M + kTwB - 1) / kTwB;
     C* buf = reinterpret_cast<C*>(fraw);
-    C* T1 = buf + (size_t)M * CP;
+    C* T1 = buf + M;
     C* T2 = T1 + kTwB;
-    const int c0 = blockIdx.x * CP;                        // first column pair of this CTA
+    const int cp = blockIdx.x;                             // the column pair of this CTA
     const int tid = threadIdx.x, T = blockDim.x;
     for (int r = tid; r < kTwB; r += T) T1[r] = r < M ? __ldg(W + r) : A::zero();
     for (int q = tid; q < nT2; q += T) T2[q] = __ldg(W + (int64_t)q * kTwB);
     // load at the digit-reversed positions
-    for (int idx = tid; idx < M * CP; idx += T) {
-        const int i = idx / CP, c = idx - i * CP, g = 2 * (c0 + c);
-        const double x = (c0 + c < a.Gp && g < a.G) ? __ldcs(a.Ur + (int64_t)i * a.G + g) : 0.0;
-        const double y = (c0 + c < a.Gp && g + 1 < a.G) ? __ldcs(a.Ur + (int64_t)i * a.G + g + 1) : 0.0;
-        buf[pos_of[i] * CP + c] = A::pair(x, y);
+    const int g = 2 * cp;
+    const bool hx = g < a.G, hy = g + 1 < a.G;
+    for (int i = tid; i < M; i += T) {
+        const double* u = a.Ur + (int64_t)i * a.G + g;
+        buf[pos_of[i]] = A::pair(hx ? __ldcs(u) : 0.0, hy ? __ldcs(u + 1) : 0.0);
     }
     __syncthreads();
     int L = 1;
     for (int st = 0; st < a.nst; ++st) {
         const int R = a.radix[st];
         const int LR = L * R;
-        const int64_t estep = M / LR;                      // W_{LR}^1 = W_M^(M / LR)
-        const int nb = M / R;                               // butterflies per column pair
-        for (int item = tid; item < nb * CP; item += T) {
-            const int c = item % CP, bt = item / CP;
-            const int j = bt % L, base = (bt / L) * LR + j;
+        const unsigned estep = (unsigned)(M / LR);         // W_{LR}^1 = W_M^(M / LR)
+        const int nb = M / R;                               // butterflies of the column pair
+        const unsigned mulL = L > 1 ? (unsigned)((0x100000000ull + (unsigned)L - 1) / (unsigned)L) : 0u;
+        for (int bt = tid; bt < nb; bt += T) {
+            const int q = L > 1 ? (int)__umulhi((unsigned)bt, mulL) : bt;
+            const int j = bt - q * L, base = q * LR + j;
             switch (R) {
-                case 8: inplace_butterfly<A, 8>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
-                case 4: inplace_butterfly<A, 4>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
-                case 2: inplace_butterfly<A, 2>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
-                case 3: inplace_butterfly<A, 3>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
-                case 5: inplace_butterfly<A, 5>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
-                default: inplace_butterfly<A, 7>(buf, base, L, CP, c, j, estep, M, T1, T2); break;
+                case 8: inplace_butterfly<A, 8>(buf, base, L, j, estep, M, T1, T2); break;
+                case 4: inplace_butterfly<A, 4>(buf, base, L, j, estep, M, T1, T2); break;
+                case 2: inplace_butterfly<A, 2>(buf, base, L, j, estep, M, T1, T2); break;
+                case 3: inplace_butterfly<A, 3>(buf, base, L, j, estep, M, T1, T2); break;
+                case 5: inplace_butterfly<A, 5>(buf, base, L, j, estep, M, T1, T2); break;
+                default: inplace_butterfly<A, 7>(buf, base, L, j, estep, M, T1, T2); break;
             }
         }
         __syncthreads();
@@ -519,16 +523,15 @@ __global__ void __launch_bounds__(kInplaceThreads, 2) fft_inplace_kernel(const _
     const double s_half = 0.5 * a.scale;
     const float s_hi = __double2float_rn(s_half);
     const float s_lo = __double2float_rn(s_half - (double)s_hi);
-    for (int idx = tid; idx < (int)a.nJ * CP; idx += T) {
-        const int c = idx / (int)a.nJ, k = idx - c * (int)a.nJ;
-        if (c0 + c >= a.Gp) continue;
+    const int nJ = (int)a.nJ;
+    double2* Ce = a.C + (int64_t)g * a.nJ;
+    for (int k = tid; k < nJ; k += T) {
         const int m = mk[k];
         const int mp = m == 0 ? 0 : M - m;
         double2 even, odd;
-        A::unpack(buf[m * CP + c], buf[mp * CP + c], s_half, s_hi, s_lo, even, odd);
-        const int g = 2 * (c0 + c);
-        a.C[(int64_t)g * a.nJ + k] = even;
-        if (g + 1 < a.G) a.C[(int64_t)(g + 1) * a.nJ + k] = odd;
+        A::unpack(buf[m], buf[mp], s_half, s_hi, s_lo, even, odd);
+        Ce[k] = even;
+        if (hy) Ce[a.nJ + k] = odd;
     }
 }
 
@@ -655,11 +658,10 @@ static cudaError_t launch_fft_impl(const FftPlan& p, int G, const double* U, con
         a.Ur = U;
         a.C = C;
         a.nst = factorize((int)p.M, a.radix);
-        const size_t smem = sizeof(typename A::C) * ((size_t)p.M * cp + kTwB + (p.M + kTwB - 1) / kTwB);
+        const size_t smem = sizeof(typename A::C) * ((size_t)p.M + kTwB + (p.M + kTwB - 1) / kTwB);
         e = allow_dyn_smem((const void*)fft_inplace_kernel<A>, smem);
         if (e != cudaSuccess) return e;
-        const int blocks = (a.Gp + cp - 1) / cp;
-        fft_inplace_kernel<A><<<blocks, kInplaceThreads, smem, s>>>(a, W, gp.pos_of, gp.mk, cp);
+        fft_inplace_kernel<A><<<a.Gp, kInplaceThreads, smem, s>>>(a, W, gp.pos_of, gp.mk);
         if (launches) ++*launches;
         return cudaGetLastError();
     }
