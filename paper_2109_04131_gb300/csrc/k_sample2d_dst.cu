@@ -760,6 +760,9 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
     float* red32 = reinterpret_cast<float*>(smraw + Lo.o_r32);
     const int J1 = Lo.J1, JA = Lo.JA;
     const int T = blockDim.x, tid = threadIdx.x;
+    // node g = q n + r: q = g / n from a multiply-high by ceil(2^32 / n), exact for g n < 2^32
+    // (g < n^2, n <= 127); a division by the run-time n costs tens of integer instructions
+    const unsigned mul_n = (unsigned)((0x100000000ull + (unsigned)n - 1) / (unsigned)n);
     // the CTA's scratch slot: fp64 x and edge weights, fp32 weights, scaling, p, r, q, d, w (7 W^2
     // doubles), then the fp64 mode table At
     double* x64 = a.scratch + (size_t)blockIdx.x * big_slot_doubles(n);
@@ -863,7 +866,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
         }
         __syncthreads();
         for (int g = tid; g < G; g += T) {
-            const int h = (g / n + 1) * W + g % n + 1;
+            const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
             const double dg = (w64l[h] + w64l[h + W]) + (w64d[h] + w64d[h + 1]);
             scs[h] = rsqrtf(0.25f * d2f_round(dg));
             x64[h] = 0.0;
@@ -878,7 +881,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
         bool at_floor = false;     // the residual stagnated at its rounding floor (see below)
         auto precond = [&]() {     // zv = D^-1/2 K_0^-1 D^-1/2 rv
             for (int g = tid; g < G; g += T) {
-                const int pp = g / n, qq = g % n, h = (pp + 1) * W + qq + 1;
+                const int pp = (int)__umulhi((unsigned)g, mul_n), qq = g - pp * n, h = (pp + 1) * W + qq + 1;
                 Ta[pp * LD + qq] = __float2bfloat16_rn(scs[h] * rv[h]);
             }
             __syncthreads();
@@ -891,14 +894,14 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             gemm_bf16<P, true, false>(Tb, S, Ta, nullptr, n, c2);
             __syncthreads();
             for (int g = tid; g < G; g += T) {
-                const int pp = g / n, qq = g % n, h = (pp + 1) * W + qq + 1;
+                const int pp = (int)__umulhi((unsigned)g, mul_n), qq = g - pp * n, h = (pp + 1) * W + qq + 1;
                 zv[h] = scs[h] * __bfloat162float(Ta[pp * LD + qq]);
             }
         };
         while (rr64 > stop && outer < 16) {
             // single-reduction flexible PCG (the small-mesh kernel's inner solve; p in ph, w = K z in wv)
             for (int g = tid; g < G; g += T) {
-                const int h = (g / n + 1) * W + g % n + 1;
+                const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
                 rv[h] = rv[h] * inv;       // fp32(r) / ||r||
                 dv[h] = 0.f;
                 ph[h] = 0.f;
@@ -914,7 +917,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 __syncthreads();
                 float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 for (int g = tid; g < G; g += T) {
-                    const int h = (g / n + 1) * W + g % n + 1;
+                    const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
                     const float w0 = wl[h], w1 = wl[h + W], w2 = wd[h], w3 = wd[h + 1];
                     const float zk = zv[h];
                     float acc = w0 * zv[h - W];
@@ -941,7 +944,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 const float qq_new = v[6] + beta * (2.f * v[7] + beta * qq);
                 const float rr = v[3] - 2.f * alpha * (v[4] + beta * v[5]) + alpha * alpha * qq_new;
                 for (int g = tid; g < G; g += T) {
-                    const int h = (g / n + 1) * W + g % n + 1;
+                    const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
                     const float p = fmaf(beta, ph[h], zv[h]);
                     const float q = fmaf(beta, qv[h], wv[h]);
                     ph[h] = p;
@@ -957,7 +960,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             }
             total += it;
             for (int g = tid; g < G; g += T) {
-                const int h = (g / n + 1) * W + g % n + 1;
+                const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
                 x64[h] = fma(nr, f2d_exact(dv[h]), x64[h]);
             }
             __syncthreads();
@@ -965,7 +968,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             // terms diag x_i and w x_j are ~1e4 times b and cancel, the differences do not
             double rl64 = 0.0;
             for (int g = tid; g < G; g += T) {
-                const int h = (g / n + 1) * W + g % n + 1;
+                const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
                 const double xi = x64[h];
                 double acc = w64l[h] * (xi - x64[h - W]);
                 acc = fma(w64l[h + W], xi - x64[h + W], acc);
@@ -993,7 +996,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             }
         }
         double* out = a.U + (size_t)sys * G;
-        for (int g = tid; g < G; g += T) out[g] = x64[((g % n) + 1) * W + (g / n) + 1];   // g = q n + p
+        for (int g = tid; g < G; g += T) out[g] = x64[(g - (int)__umulhi((unsigned)g, mul_n) * n + 1) * W + (int)__umulhi((unsigned)g, mul_n) + 1];   // g = q n + p
         if (tid == 0) {
             if (a.iters_out) a.iters_out[sys] = total;
             if (a.iters_sum) atomicAdd(a.iters_sum, (unsigned long long)total);
