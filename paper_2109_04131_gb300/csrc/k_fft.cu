@@ -104,6 +104,7 @@ struct FftArgs {
 // ---- complex arithmetic: fp64 -----------------------------------------------------------
 struct F64 {
     typedef double2 C;
+    static constexpr bool kFastDiv = false;   // index division by a multiply-high (measured slower here)
     static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
     static __device__ __forceinline__ C pair(double x, double y) { return make_double2(x, y); }
     static __device__ __forceinline__ C add(C a, C b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -143,6 +144,7 @@ __device__ __forceinline__ float2 dfr_mul(float ahi, float alo, float bhi, float
 }
 struct DF {
     typedef float4 C;   // re.hi, re.lo, im.hi, im.lo
+    static constexpr bool kFastDiv = true;    // index division by a multiply-high (measured faster here)
     static __device__ __forceinline__ float2 split(double x) { return d2df(x); }
     static __device__ __forceinline__ C zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
     static __device__ __forceinline__ C pair(double x, double y) {
@@ -240,15 +242,32 @@ __device__ __forceinline__ CT twid(const CT* tw, const CT* W, int e, int64_t wst
     return tw ? tw[e] : __ldg(W + (int64_t)e * wstride);
 }
 
+// q = x / d from a multiply-high by ceil(2^32 / d): exact whenever x d < 2^32, which every index of the
+// two-pass tiles satisfies (x < L cols <= 2^18, d <= 4096); a division by a value known only at run
+// time would cost tens of integer instructions per butterfly
+// (FAST; the fp64 instantiations keep the plain division, which measured faster there)
+template <bool FAST>
+struct Recip {
+    unsigned m;
+    int d;
+    __device__ __forceinline__ explicit Recip(int dd)
+        : m(FAST && dd > 1 ? (unsigned)((0x100000000ull + (unsigned)dd - 1) / (unsigned)dd) : 0u), d(dd) {}
+    __device__ __forceinline__ int div(int x) const {
+        if (!FAST) return x / d;
+        return d > 1 ? (int)__umulhi((unsigned)x, m) : x;
+    }
+};
+
 // one Stockham stage over `cols` columns (column c of the tile at buf[l * cols + c])
 template <class A, int R>
 __device__ __forceinline__ void stage_reg(const typename A::C* src, typename A::C* dst, const typename A::C* tw,
                                           const typename A::C* W, int L, int cols, int Ns, int64_t wstride) {
     const int nb = L / R;
     const int tw_unit = L / (Ns * R);
+    const Recip<A::kFastDiv> rc(cols), rn(Ns);
     for (int item = threadIdx.x; item < nb * cols; item += blockDim.x) {
-        const int c = item % cols, j = item / cols;
-        const int jm = j % Ns;
+        const int j = rc.div(item), c = item - j * cols;
+        const int jq = rn.div(j), jm = j - jq * Ns;
         typename A::C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -259,7 +278,7 @@ __device__ __forceinline__ void stage_reg(const typename A::C* src, typename A::
         if (R == 3) dft3<A>(v);
         if (R == 4) dft4<A>(v);
         if (R == 8) dft8<A>(v);
-        const int base = (j / Ns) * Ns * R + jm;
+        const int base = jq * Ns * R + jm;
 #pragma unroll
         for (int r = 0; r < R; ++r) dst[(base + r * Ns) * cols + c] = v[r];
     }
@@ -273,18 +292,18 @@ __device__ __forceinline__ void stage_generic(const typename A::C* src, typename
     const int nb = L / R;
     const int tw_unit = L / (Ns * R);
     const int unit = L / R;                                   // W_R^1 = W_L^(L/R)
+    const Recip<A::kFastDiv> rc(cols), rr(R), rn(Ns);
     for (int item = threadIdx.x; item < L * cols; item += blockDim.x) {
-        const int c = item % cols;
-        const int rest = item / cols;
-        const int k = rest % R, j = rest / R;
-        const int jm = j % Ns;
+        const int rest = rc.div(item), c = item - rest * cols;
+        const int j = rr.div(rest), k = rest - j * R;
+        const int jq = rn.div(j), jm = j - jq * Ns;
         typename A::C acc = A::zero();
         for (int r = 0; r < R; ++r) {
             const typename A::C v = src[(j + r * nb) * cols + c];
             const int e = (jm * r * tw_unit + ((r * k) % R) * unit) % L;
             acc = A::add(acc, A::mul(v, twid(tw, W, e, wstride)));
         }
-        dst[((j / Ns) * Ns * R + jm + k * Ns) * cols + c] = acc;
+        dst[(jq * Ns * R + jm + k * Ns) * cols + c] = acc;
     }
 }
 
@@ -333,8 +352,9 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass1_kernel(const __grid_con
         stage_twiddles(tw, W, L, a.wstride);
         for (int m = threadIdx.x; m < L; m += blockDim.x) ot[m] = __ldg(W + ((int64_t)o * m) % a.M);
     }
+    const Recip<A::kFastDiv> rg(Gt);
     for (int idx = threadIdx.x; idx < L * Gt; idx += blockDim.x) {
-        const int l = idx / Gt, c = idx % Gt, g = 2 * (c0 + c);
+        const int l = rg.div(idx), c = idx - l * Gt, g = 2 * (c0 + c);
         const int64_t row = (int64_t)o * a.in_outer + (int64_t)l * a.in_step;
         const double x = g < a.G ? __ldcs(a.Ur + row * a.G + g) : 0.0;
         const double y = g + 1 < a.G ? __ldcs(a.Ur + row * a.G + g + 1) : 0.0;
@@ -344,7 +364,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass1_kernel(const __grid_con
     const C* res = fft_tile<A>(b0, b1, tw, W, a, Gt);
     C* Yo = reinterpret_cast<C*>(a.Yo);
     for (int idx = threadIdx.x; idx < L * Gt; idx += blockDim.x) {
-        const int m = idx / Gt, c = idx % Gt;
+        const int m = rg.div(idx), c = idx - m * Gt;
         if (c0 + c >= a.Gp) continue;
         C v = res[idx];
         if (m) v = A::mul(v, ot ? ot[m] : __ldg(W + ((int64_t)o * m) % a.M));
@@ -372,9 +392,10 @@ __global__ void __launch_bounds__(kFftThreads) fft_final_kernel(const __grid_con
     C* tw = (L <= kTwSmem) ? b1 + (size_t)L * cols : nullptr;
     if (tw) stage_twiddles(tw, W, L, a.wstride);
     const C* Yc = reinterpret_cast<const C*>(a.Yc);
+    const Recip<A::kFastDiv> rcol(cols), rg(Gt);
     for (int idx = threadIdx.x; idx < L * cols; idx += blockDim.x) {
-        const int l = idx / cols, cc = idx % cols;
-        const int b = cc / Gt, c = cc % Gt;
+        const int l = rcol.div(idx), cc = idx - l * cols;
+        const int b = rg.div(cc), c = cc - b * Gt;
         const int bucket = b ? m1p : m1;
         const int64_t row = (int64_t)bucket * a.in_outer + (int64_t)l * a.in_step;
         C v = A::zero();
@@ -472,8 +493,8 @@ __device__ __forceinline__ void inplace_butterfly(typename A::C* buf, int base, 
 }
 
 // One column pair per CTA.  Per butterfly the group index q = bt / L comes from a multiply-high by
-// the stage's reciprocal ceil(2^32 / L): exact while bt L < 2^32 (bt < M / R, L <= M <= 14528), and a
-// few integer instructions instead of a division by a value known only at run time.
+// the stage's reciprocal ceil(2^32 / L) in the double-float instantiation (Recip: exact while
+// bt L < 2^32, bt < M / R, L <= M <= 14528).
 template <class A>
 __global__ void __launch_bounds__(kInplaceThreads, 2) fft_inplace_kernel(const __grid_constant__ FftArgs a,
                                                                         const typename A::C* W, const int* pos_of,
@@ -503,9 +524,9 @@ __global__ void __launch_bounds__(kInplaceThreads, 2) fft_inplace_kernel(const _
         const int LR = L * R;
         const unsigned estep = (unsigned)(M / LR);         // W_{LR}^1 = W_M^(M / LR)
         const int nb = M / R;                               // butterflies of the column pair
-        const unsigned mulL = L > 1 ? (unsigned)((0x100000000ull + (unsigned)L - 1) / (unsigned)L) : 0u;
+        const Recip<A::kFastDiv> rl(L);
         for (int bt = tid; bt < nb; bt += T) {
-            const int q = L > 1 ? (int)__umulhi((unsigned)bt, mulL) : bt;
+            const int q = rl.div(bt);
             const int j = bt - q * L, base = q * LR + j;
             switch (R) {
                 case 8: inplace_butterfly<A, 8>(buf, base, L, j, estep, M, T1, T2); break;
