@@ -485,6 +485,8 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
     const double rr0 = (double)G * b * b;
     const double stop = a.tol * a.tol * rr0;
     const double nr0 = sqrt(rr0);
+    // square e = Q (n+1) + P: Q from a multiply-high by ceil(2^32 / (n+1)), exact for e (n+1) < 2^32
+    const unsigned mul_n1 = (unsigned)((0x100000000ull + (unsigned)n1 - 1) / (unsigned)n1);
     const float nstop = (float)(a.tol * nr0);        // sqrt(stop)
     const float tol_in = (float)a.tol_inner;
     const float inv0 = (float)(1.0 / nr0), nrf0 = (float)nr0;
@@ -511,14 +513,14 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
         const float2 one = make_float2(1.f, 0.f);
         float2* low = reinterpret_cast<float2*>(xh);   // lower-triangle coefficients (temporary)
         for (int e = tid; e < sq; e += T) {
-            const int Pp = e % n1, Q = e / n1;
+            const int Q = (int)__umulhi((unsigned)e, mul_n1), Pp = e - Q * n1;
             float2 acc = make_float2(0.f, 0.f);
             for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 1) * n1 + Pp], Tr[(j1 * 2 + 0) * n1 + Q]);
             low[e] = logn ? df_split(exp(df_to_double(acc))) : df_add(one, acc);
         }
         __syncthreads();
         for (int e = tid; e < sq; e += T) {
-            const int Pp = e % n1, Q = e / n1;
+            const int Q = (int)__umulhi((unsigned)e, mul_n1), Pp = e - Q * n1;
             float2 acc = make_float2(0.f, 0.f);
             for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 0) * n1 + Pp], Tr[(j1 * 2 + 1) * n1 + Q]);
             const float2 au = logn ? df_split(exp(df_to_double(acc))) : df_add(one, acc);
@@ -763,6 +765,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
     // node g = q n + r: q = g / n from a multiply-high by ceil(2^32 / n), exact for g n < 2^32
     // (g < n^2, n <= 127); a division by the run-time n costs tens of integer instructions
     const unsigned mul_n = (unsigned)((0x100000000ull + (unsigned)n - 1) / (unsigned)n);
+    const unsigned mul_n1 = (unsigned)((0x100000000ull + (unsigned)n1 - 1) / (unsigned)n1);
     // the CTA's scratch slot: fp64 x and edge weights, fp32 weights, scaling, p, r, q, d, w (7 W^2
     // doubles), then the fp64 mode table At
     double* x64 = a.scratch + (size_t)blockIdx.x * big_slot_doubles(n);
@@ -839,7 +842,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
         // weights: the lower-triangle coefficient of square (P, Q) is recomputed where needed
         const float2 one = make_float2(1.f, 0.f);
         for (int e = tid; e < n1 * n1; e += T) {
-            const int Pp = e % n1, Q = e / n1;
+            const int Q = (int)__umulhi((unsigned)e, mul_n1), Pp = e - Q * n1;
             float2 acc = make_float2(0.f, 0.f);
             for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 0) * n1 + Pp], Tr[(j1 * 2 + 1) * n1 + Q]);
             const float2 au = logn ? df_split(exp(df_to_double(acc))) : df_add(one, acc);
