@@ -115,6 +115,7 @@ struct F64 {
     static __device__ __forceinline__ C mul_mi(C a) { return make_double2(a.y, -a.x); }   // * (-i)
     static __device__ __forceinline__ C mul_k(C a, double k) { return make_double2(a.x * k, a.y * k); }
     static __device__ __forceinline__ C half(C a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
+    static __device__ __forceinline__ C norm(C a) { return a; }
     // (A + conj B) s and (A - conj B) s / i, the unpacked transforms of the two real columns
     static __device__ __forceinline__ void unpack(C A, C B, double s, float, float, double2& even, double2& odd) {
         even = make_double2((A.x + B.x) * s, (A.y - B.y) * s);
@@ -142,6 +143,20 @@ __device__ __forceinline__ float2 dfr_mul(float ahi, float alo, float bhi, float
     e = __fmaf_rn(ahi, blo, __fmaf_rn(alo, bhi, e));
     return df_norm(p, e);
 }
+// Unnormalised forms for the transform's inner arithmetic: the high parts' sum or product is
+// still split exactly (TwoSum, fma), but the low word is left as it falls instead of being
+// folded into a canonical pair after every operation; the value hi + lo carries the same
+// information, and each stage renormalises once per value as it stores (DF::norm), so the low
+// word never grows by more than the few operations of one butterfly.
+__device__ __forceinline__ float2 dfl_add(float hi, float lo, float bhi, float blo) {
+    const float2 se = df_two_sum(hi, bhi);
+    return make_float2(se.x, __fadd_rn(se.y, __fadd_rn(lo, blo)));
+}
+__device__ __forceinline__ float2 dfl_mul(float ahi, float alo, float bhi, float blo) {
+    const float p = __fmul_rn(ahi, bhi);
+    const float e = __fmaf_rn(ahi, bhi, -p);
+    return make_float2(p, __fmaf_rn(ahi, blo, __fmaf_rn(alo, bhi, e)));
+}
 struct DF {
     typedef float4 C;   // re.hi, re.lo, im.hi, im.lo
     static constexpr bool kFastDiv = true;    // index division by a multiply-high (measured faster here)
@@ -152,23 +167,27 @@ struct DF {
         return make_float4(a.x, a.y, b.x, b.y);
     }
     static __device__ __forceinline__ C add(C a, C b) {
-        const float2 r = dfr_add(a.x, a.y, b.x, b.y), i = dfr_add(a.z, a.w, b.z, b.w);
+        const float2 r = dfl_add(a.x, a.y, b.x, b.y), i = dfl_add(a.z, a.w, b.z, b.w);
         return make_float4(r.x, r.y, i.x, i.y);
     }
     static __device__ __forceinline__ C sub(C a, C b) {
-        const float2 r = dfr_add(a.x, a.y, -b.x, -b.y), i = dfr_add(a.z, a.w, -b.z, -b.w);
+        const float2 r = dfl_add(a.x, a.y, -b.x, -b.y), i = dfl_add(a.z, a.w, -b.z, -b.w);
         return make_float4(r.x, r.y, i.x, i.y);
     }
     static __device__ __forceinline__ C mul(C a, C b) {
-        const float2 rr = dfr_mul(a.x, a.y, b.x, b.y), ii = dfr_mul(a.z, a.w, b.z, b.w);
-        const float2 ri = dfr_mul(a.x, a.y, b.z, b.w), ir = dfr_mul(a.z, a.w, b.x, b.y);
-        const float2 r = dfr_add(rr.x, rr.y, -ii.x, -ii.y), i = dfr_add(ri.x, ri.y, ir.x, ir.y);
+        const float2 rr = dfl_mul(a.x, a.y, b.x, b.y), ii = dfl_mul(a.z, a.w, b.z, b.w);
+        const float2 ri = dfl_mul(a.x, a.y, b.z, b.w), ir = dfl_mul(a.z, a.w, b.x, b.y);
+        const float2 r = dfl_add(rr.x, rr.y, -ii.x, -ii.y), i = dfl_add(ri.x, ri.y, ir.x, ir.y);
+        return make_float4(r.x, r.y, i.x, i.y);
+    }
+    static __device__ __forceinline__ C norm(C a) {
+        const float2 r = df_norm(a.x, a.y), i = df_norm(a.z, a.w);
         return make_float4(r.x, r.y, i.x, i.y);
     }
     static __device__ __forceinline__ C mul_mi(C a) { return make_float4(a.z, a.w, -a.x, -a.y); }
     static __device__ __forceinline__ C mul_k(C a, double k) {
         const float kh = (float)k, kl = (float)(k - (double)kh);   // folded at compile time for literals
-        const float2 r = dfr_mul(a.x, a.y, kh, kl), i = dfr_mul(a.z, a.w, kh, kl);
+        const float2 r = dfl_mul(a.x, a.y, kh, kl), i = dfl_mul(a.z, a.w, kh, kl);
         return make_float4(r.x, r.y, i.x, i.y);
     }
     static __device__ __forceinline__ C half(C a) { return make_float4(0.5f * a.x, 0.5f * a.y, 0.5f * a.z, 0.5f * a.w); }
@@ -280,7 +299,7 @@ __device__ __forceinline__ void stage_reg(const typename A::C* src, typename A::
         if (R == 8) dft8<A>(v);
         const int base = jq * Ns * R + jm;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[(base + r * Ns) * cols + c] = v[r];
+        for (int r = 0; r < R; ++r) dst[(base + r * Ns) * cols + c] = A::norm(v[r]);
     }
 }
 
@@ -303,7 +322,7 @@ __device__ __forceinline__ void stage_generic(const typename A::C* src, typename
             const int e = (jm * r * tw_unit + ((r * k) % R) * unit) % L;
             acc = A::add(acc, A::mul(v, twid(tw, W, e, wstride)));
         }
-        dst[(jq * Ns * R + jm + k * Ns) * cols + c] = acc;
+        dst[(jq * Ns * R + jm + k * Ns) * cols + c] = A::norm(acc);
     }
 }
 
@@ -368,7 +387,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass1_kernel(const __grid_con
         if (c0 + c >= a.Gp) continue;
         C v = res[idx];
         if (m) v = A::mul(v, ot ? ot[m] : __ldg(W + ((int64_t)o * m) % a.M));
-        Yo[((int64_t)m * a.out_m + (int64_t)o * a.out_outer) * a.Gp + c0 + c] = v;
+        Yo[((int64_t)m * a.out_m + (int64_t)o * a.out_outer) * a.Gp + c0 + c] = A::norm(v);
     }
 }
 
@@ -489,7 +508,7 @@ __device__ __forceinline__ void inplace_butterfly(typename A::C* buf, int base, 
         for (int k = 0; k < R; ++k) v[k] = out[k];
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[base + r * L] = v[r];
+    for (int r = 0; r < R; ++r) buf[base + r * L] = A::norm(v[r]);
 }
 
 // One column pair per CTA.  Per butterfly the group index q = bt / L comes from a multiply-high by
