@@ -421,13 +421,17 @@ def run_ours(args, rank, world):
 
     def mixed_roofline(res):
         # MIXED sampler.  Work it issues per solve (counted from the kernel's code):
-        #   FP64 pipe: per refinement step x += ||r|| d (1 DFMA) and r = b - K x with the fp64
-        #     weights (1 DMUL, 3 DFMA, 1 DFMA, 1 DADD): 12 flops per node; once per solve the fp64
-        #     edge weights (2 DADD from the double-float pairs) and diagonal (3 DADD): 5 flops per
-        #     node.  The coefficient assembly runs in double-float on the FP32 pipe, not here.
+        #   FP64 pipe: first refinement step x += ||r|| d (1 DFMA), r = b - K x with the fp64
+        #     weights (1 DMUL, 3 DFMA, 1 DFMA, 1 DADD) and its double-float split (1 DADD): 13 flops
+        #     per node; every later step only the x update (2 flops; r is updated in double-float);
+        #     once per solve the fp64 edge weights (2 DADD from the double-float pairs) and
+        #     diagonal (3 DADD): 5 flops per node.  The coefficient assembly runs in double-float on
+        #     the FP32 pipe, not here.
         #   FP32 pipe: per inner iteration the preconditioner scaling (2), the SpMV in difference
         #     form (4 sub + 1 mul + 3 fma = 11), eight inner products (16), four updates (8): 37
-        #     flops per node.
+        #     flops per node; per refinement step after the first the double-float update
+        #     r -= ||r|| K d (K d 57, the product 7, the renormalised sum 11, the norm term 3): 78;
+        #     once per solve the double-float diagonal (3 sums): 33.
         #   Tensor pipe (BF16): per inner iteration four P x P x P products, 4 * 2 P^3 flops.
         # The roof reported is the FP64 pipe's (the busiest pipe in the ncu capture); the others and
         # the HBM view (the samples written) are listed beside it.
@@ -435,17 +439,18 @@ def run_ours(args, rank, world):
         n = max(1, st["launches"]["sample"])
         solves = res["samples_per_step"] * args.steps
         inner, outer = st["cg_iters_total"], st["refine_steps_total"]
-        f64 = (12.0 * G * outer + 5.0 * G * solves) / n
-        f32 = 37.0 * G * inner / n
+        f64 = (18.0 * G * solves + 2.0 * G * (outer - solves)) / n
+        f32 = (37.0 * G * inner + 78.0 * G * (outer - solves) + 33.0 * G * solves) / n
         ftc = 4 * 2.0 * P_ ** 3 * inner / n
         dur = st["ms"]["sample"] / n / 1e3
         ach = f64 / dur / 1e12
         out_bytes = 8.0 * G * solves / n
         return {"bound": "alu", "achieved": ach, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / PEAK_FP64_TFLOPS, "traffic": profiled_traffic("mixed"),
-                "kernel": f"pcg2d_mixed_dst_kernel (fp64 refinement + fp32 flexible PCG + BF16 DST, {n} launches timed)",
+                "kernel": f"pcg2d_mixed_dst_kernel (fp64 and double-float refinement + fp32 flexible PCG + BF16 DST, {n} launches timed)",
                 "flops_per_launch": f64, "ms_per_launch": dur * 1e3,
-                "work_per_solve": {"fp64_flops": "12 G per refinement step + 5 G", "fp32_flops": "37 G per inner iteration",
+                "work_per_solve": {"fp64_flops": "18 G + 2 G per refinement step after the first",
+                                   "fp32_flops": "37 G per inner iteration + 78 G per refinement step after the first + 33 G",
                                    "bf16_tensor_flops": f"4 * 2 * {P_}^3 per inner iteration"},
                 "units": {"fp64": {"tflops": ach, "frac": ach / PEAK_FP64_TFLOPS},
                           "fp32": {"tflops": f32 / dur / 1e12, "frac": f32 / dur / 1e12 / PEAK_FP32_TFLOPS},

@@ -464,8 +464,8 @@ double usfft_draw_uniform(uint64_t seed, const uint64_t* fields, int nfields);
  * usfft_params.  If unconverged is non-NULL the call synchronises `stream` and stores how many
  * solves missed tol; with NULL it returns after enqueueing the work on `stream`.
  *
- * Scratch: one fixed 16 MiB device array in the library (a counter of unconverged solves and
- * one slot of fp64 edge weights and diagonal per resident CTA; the sampler assembles the
+ * Scratch: one fixed 40 MiB device array in the library (a counter of unconverged solves and
+ * one slot of edge weights, diagonal and residual per resident CTA; the sampler assembles the
  * coefficient in separable form and needs no mode table).  Requests that would need more are
  * rejected with USFFT_EINVAL and a message in usfft_last_error(NULL).  CUDA loads modules lazily
  * by default, so a device first holds the array when the first call on it sets it up, and keeps

@@ -6,7 +6,7 @@
 // framework that has already reserved (almost) all of HBM for its own pool, or a
 // latency-critical loop that must never enter the allocator.  Such a caller passes its own
 // input description and output buffer; the scratch the sampler needs (a counter of unconverged
-// solves and one slot of fp64 edge weights and diagonal per resident CTA) lives in g_static_scratch below.
+// solves and one slot of edge weights, diagonal and residual per resident CTA) lives in g_static_scratch below.
 //
 // When the array is backed by device memory: CUDA loads a module lazily by default (CUDA 12.2
 // and later), so the driver places g_static_scratch on a device when this file's module is
@@ -32,7 +32,7 @@
 
 namespace {
 
-constexpr size_t kStaticScratchBytes = size_t(16) << 20;   // 16 MiB per device
+constexpr size_t kStaticScratchBytes = size_t(40) << 20;   // 40 MiB per device: a slot for each of 152 CTAs at n = 63
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -97,14 +97,14 @@ extern "C" usfft_status usfft_sample_2d_static(const usfft_problem* problem, con
         ns.z[j] = z[j] < 0 ? -1 : z[j];
         ns.tail[j] = tails[j];
     }
-    // scratch layout: [counters, 256 bytes][per-CTA slots of fp64 edge weights and diagonal].
+    // scratch layout: [counters, 256 bytes][per-CTA slots of edge weights, diagonal and residual].
     // The mixed sampler assembles the coefficient in separable form from c and mu directly, so
     // it needs no mode table.
     const int n = pr.n;
     const size_t cnt_bytes = 256;
     const size_t slot_bytes = sample_2d_scratch_bytes(n, USFFT_MIXED, 1);
     if (cnt_bytes + slot_bytes > kStaticScratchBytes)
-        return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: the problem needs more than the 16 MiB static scratch");
+        return static_fail(USFFT_EINVAL, "usfft_sample_2d_static: the problem needs more than the 40 MiB static scratch");
     int blocks = sample_2d_default_blocks(n, USFFT_MIXED);
     const int fit = (int)((kStaticScratchBytes - cnt_bytes) / slot_bytes);
     if (blocks > fit) blocks = fit;

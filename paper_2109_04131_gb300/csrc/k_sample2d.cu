@@ -36,6 +36,7 @@ template <int NPT>
 int dst_resident_blocks(int threads, int d, int n);
 // fp64 sampler with the same preconditioner (k_sample2d_dst64.cu)
 size_t fp64_dst_slot_bytes(int n, int d);
+size_t mixed_slot_bytes(int n);
 int fp64_dst_default_blocks(int n, int d);
 cudaError_t launch_fp64_dst(const Pcg2dArgs& a, int blocks, cudaStream_t s);
 
@@ -412,9 +413,7 @@ int sample_2d_default_blocks(int n, int precision) {
 size_t sample_2d_scratch_bytes(int n, int precision, int blocks) {
     if (precision == USFFT_FP64) return 0;
     if (precision == USFFT_FP64_DST) return fp64_dst_slot_bytes(n, USFFT_MAX_D) * (size_t)blocks;
-    const size_t W = (size_t)n + 2;
-    if (precision == USFFT_MIXED)
-        return sizeof(double) * (n > 63 ? 7 * W * W + 22 * ((size_t)n + 1) : 3 * W * W) * (size_t)blocks;
+    if (precision == USFFT_MIXED) return mixed_slot_bytes(n) * (size_t)blocks;
     return sizeof(double) * 2 * (size_t)n * (n + 1) * (size_t)blocks;
 }
 

@@ -4,8 +4,14 @@
 // weights w_e = mean of the two adjacent triangle coefficients).  The solve is fp64
 // iterative refinement around an fp32 flexible preconditioned CG:
 //   x = 0, r = b;  repeat:  solve K d = r / ||r|| in fp32 to tol_inner,
-//                           x += ||r|| d (fp64),  r = b - K x with fp64 weights,
+//                           x += ||r|| d (fp64),  r = b - K x,
 //   until ||r|| <= tol ||b||.
+// The residual after the first correction, as large as b, is formed in fp64 from x with the
+// fp64 weights.  After every later correction it is updated as r -= ||r|| K d, with K d formed
+// in double-float from the correction's fp32 values and the weights' double-float pairs: its
+// rounding error, about 1e-14 of ||r|| K d, is relative to the current residual (1e-4 of ||b||
+// or less), so the update adds under 1e-17 ||b|| where the fp64 evaluation of b - K x itself
+// carries about 1e-13 ||b|| (the diagonal times x is about 1e4 b), and it runs on the FP32 pipe.
 // Preconditioner: the inverse of the constant-coefficient operator K_0 (w_e = 1) between two
 // symmetric diagonal scalings, D^-1/2 K_0^-1 D^-1/2 with D = diag(K) / diag(K_0); K_0^-1 is
 // applied exactly through its eigenbasis, the 2-D sine transform (DST-I):
@@ -99,6 +105,18 @@ __device__ __forceinline__ float2 df_fma(float2 acc, float2 a, float2 b) {   // 
     return df_add(acc, make_float2(p, pe));
 }
 __device__ __forceinline__ double df_to_double(float2 a) { return df2d(a.x, a.y); }
+// a (double-float) times the float f: the exact product of the high parts plus lo f, unnormalised
+__device__ __forceinline__ float2 df_mulf(float2 a, float f) {
+    const float p = __fmul_rn(a.x, f);
+    return make_float2(p, __fmaf_rn(a.y, f, __fmaf_rn(a.x, f, -p)));
+}
+// a - b with the high parts' difference exact (TwoSum) and the low words added, unnormalised
+__device__ __forceinline__ float2 df_sub_lazy(float2 a, float2 b) {
+    const float s = __fadd_rn(a.x, -b.x);
+    const float bb = __fadd_rn(s, -a.x);
+    const float e = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(s, -bb)), __fadd_rn(-b.x, -bb));
+    return make_float2(s, __fadd_rn(e, __fadd_rn(a.y, -b.y)));
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -395,6 +413,15 @@ __device__ __forceinline__ Norm2 block_norm2(double v, double* buf, double prev,
     return o;
 }
 
+// doubles of one CTA's scratch slot of the small-mesh kernel (n <= 63): seven arrays of
+// (P+2)^2 >= W^2 doubles (P = n rounded up to 16, so that the array offsets are compile-time
+// constants of the kernel instance), each rounded up to an even count so that the float4 view
+// stays 16-byte aligned
+__host__ __device__ constexpr int mixed_small_array_doubles(int P) { return ((P + 2) * (P + 2) + 1) & ~1; }
+__host__ __device__ inline size_t mixed_small_slot_doubles(int n) {
+    return 7 * (size_t)mixed_small_array_doubles((n + 15) / 16 * 16);
+}
+
 // P = the transform size, n rounded up to a multiple of 16 (a compile-time constant, so the
 // k-loop of the fragment loads and mma unrolls)
 template <int NPT, int P>
@@ -424,9 +451,17 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
     int* mj2 = mj1 + a.ns.d;
     const int J1 = Lo.J1, JA = Lo.JA;
     const int T = blockDim.x, tid = threadIdx.x;
-    double* w64l = a.scratch + (size_t)blockIdx.x * 3 * W * W;   // fp64 weights and diagonal, same halo layout
-    double* w64d = w64l + W * W;
-    double* d64 = w64d + W * W;
+    // the CTA's scratch slot (mixed_small_slot_doubles): fp64 weights (left, down) and diagonal,
+    // the low words of the four edge weights' double-float pairs (the high words are wq), the
+    // double-float diagonal, and the residual r in double-float (each node's own thread keeps it
+    // there across the inner solve); halo layout, arrays W2 doubles apart
+    constexpr int W2 = mixed_small_array_doubles(P);
+    double* w64l = a.scratch + (size_t)blockIdx.x * (7 * W2);
+    double* w64d = w64l + W2;
+    double* d64 = w64d + W2;
+    float4* wql = reinterpret_cast<float4*>(d64 + W2);
+    float2* Ddf = reinterpret_cast<float2*>(d64 + 3 * W2);
+    float2* rdf = reinterpret_cast<float2*>(d64 + 4 * W2);
 
     // per-thread node indices, packed: halo position (low 16 bits) | transform-grid position
     // (high 16 bits); -1 marks a thread slot without a node (W^2, P LD < 2^15 for n <= 63).
@@ -463,6 +498,8 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
         w64l[e] = 0.0;
         w64d[e] = 0.0;
         d64[e] = 0.0;
+        wql[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        Ddf[e] = make_float2(0.f, 0.f);
     }
     // separable coefficient: psi_j(centroid) = sin(j1 pi x1) sin(j2 pi x2); the centroids of
     // square (P,Q) are ((P+2/3)h, (Q+1/3)h) (lower triangle) and ((P+1/3)h, (Q+2/3)h) (upper)
@@ -485,7 +522,9 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
     const double rr0 = (double)G * b * b;
     const double stop = a.tol * a.tol * rr0;
     const double nr0 = sqrt(rr0);
-    // square e = Q (n+1) + P: Q from a multiply-high by ceil(2^32 / (n+1)), exact for e (n+1) < 2^32
+    // square e = P (n+1) + Q (Q fastest, so that consecutive threads write consecutive halo nodes
+    // h = (P+1) W + Q + 1 of the scratch arrays): P from a multiply-high by ceil(2^32 / (n+1)),
+    // exact for e (n+1) < 2^32
     const unsigned mul_n1 = (unsigned)((0x100000000ull + (unsigned)n1 - 1) / (unsigned)n1);
     const float nstop = (float)(a.tol * nr0);        // sqrt(stop)
     const float tol_in = (float)a.tol_inner;
@@ -511,34 +550,38 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
         // triangle coefficients a = 1 + sum_j1 At Tr (affine) or exp(sum_j1 At Tr) (lognormal):
         // the rank-J1 sums in double-float, the exponential in fp64
         const float2 one = make_float2(1.f, 0.f);
-        float2* low = reinterpret_cast<float2*>(xh);   // lower-triangle coefficients (temporary)
+        float2* low = reinterpret_cast<float2*>(xh);   // lower-triangle coefficients by square (temporary)
         for (int e = tid; e < sq; e += T) {
-            const int Q = (int)__umulhi((unsigned)e, mul_n1), Pp = e - Q * n1;
+            const int Pp = (int)__umulhi((unsigned)e, mul_n1), Q = e - Pp * n1;
             float2 acc = make_float2(0.f, 0.f);
             for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 1) * n1 + Pp], Tr[(j1 * 2 + 0) * n1 + Q]);
             low[e] = logn ? df_split(exp(df_to_double(acc))) : df_add(one, acc);
         }
         __syncthreads();
         for (int e = tid; e < sq; e += T) {
-            const int Q = (int)__umulhi((unsigned)e, mul_n1), Pp = e - Q * n1;
+            const int Pp = (int)__umulhi((unsigned)e, mul_n1), Q = e - Pp * n1;
             float2 acc = make_float2(0.f, 0.f);
             for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 0) * n1 + Pp], Tr[(j1 * 2 + 1) * n1 + Q]);
             const float2 au = logn ? df_split(exp(df_to_double(acc))) : df_add(one, acc);
             if (Q < n) {            // edge (Pp,Q+1)-(Pp+1,Q+1): left of node (Pp+1,Q+1)
-                float2 w = df_add(low[(Q + 1) * n1 + Pp], au);
+                float2 w = df_add(low[Pp * n1 + Q + 1], au);
                 w = make_float2(0.5f * w.x, 0.5f * w.y);              // exact
                 const int h = (Pp + 1) * W + Q + 1;
                 w64l[h] = df_to_double(w);
                 wq[h].x = w.x;          // left edge of h
                 wq[h - W].y = w.x;      // right edge of its left neighbour
+                wql[h].x = w.y;
+                wql[h - W].y = w.y;
             }
             if (Pp >= 1) {          // edge (Pp,Q)-(Pp,Q+1): below node (Pp,Q+1)
-                float2 w = df_add(au, low[Q * n1 + (Pp - 1)]);
+                float2 w = df_add(au, low[(Pp - 1) * n1 + Q]);
                 w = make_float2(0.5f * w.x, 0.5f * w.y);
                 const int h = Pp * W + Q + 1;
                 w64d[h] = df_to_double(w);
                 wq[h].z = w.x;          // lower edge of h
                 wq[h - 1].w = w.x;      // upper edge of the node below
+                wql[h].z = w.y;
+                wql[h - 1].w = w.y;
             }
         }
         __syncthreads();
@@ -551,6 +594,10 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                 const double dg = (w64l[h] + w64l[h + W]) + (w64d[h] + w64d[h + 1]);
                 d64[h] = dg;
                 scs[h] = rsqrtf(0.25f * d2f_round(dg));
+                const float4 wh = wq[h], wl = __ldcg(wql + h);
+                const float2 s = df_add(df_add(make_float2(wh.x, wl.x), make_float2(wh.y, wl.y)),
+                                        df_add(make_float2(wh.z, wl.z), make_float2(wh.w, wl.w)));
+                Ddf[h] = s;
             }
         }
         __syncthreads();
@@ -560,10 +607,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
         }
         __syncthreads();
 
-        // ---- fp64 iterative refinement around fp32 flexible PCG ----
-        double r64[NPT];
-#pragma unroll
-        for (int k = 0; k < NPT; ++k) r64[k] = (nid[k] >= 0) ? b : 0.0;
+        // ---- iterative refinement around fp32 flexible PCG (r = b at first, then rdf) ----
         double rr64 = rr0, nr = nr0;
         float inv = inv0, nrf = nrf0;
         int more = rr0 > stop;
@@ -585,7 +629,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                 d32[k] = 0.f;
                 p32[k] = 0.f;
                 q32[k] = 0.f;
-                r32[k] = d2f_round(r64[k]) * inv;
+                r32[k] = (nid[k] < 0) ? 0.f : (outer == 0 ? d2f_round(b) : rdf[nid[k] & 0xffff].x) * inv;
             }
             // inner target: tol_inner, or less when this step only has to close the remaining
             // gap to the outer tolerance (0.3 x the reduction still missing)
@@ -645,29 +689,60 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                 if (rr <= istop) break;
             }
             total += it;
-            // x += ||r|| d in fp64, then the fp64 residual with the fp64 weights
+            // x += ||r|| d in fp64; after the first correction d also goes to the halo grid (ph)
+            // for the double-float update of r
 #pragma unroll
             for (int k = 0; k < NPT; ++k)
-                if (nid[k] >= 0) xh[nid[k] & 0xffff] = fma(nr, f2d_exact(d32[k]), xh[nid[k] & 0xffff]);
+                if (nid[k] >= 0) {
+                    const int h = nid[k] & 0xffff;
+                    xh[h] = fma(nr, f2d_exact(d32[k]), xh[h]);
+                    if (outer > 0) ph[h] = d32[k];
+                }
             __syncthreads();
             // ||r||^2 in fp32 from r / ||r_prev|| (about 1e-5 and below: far inside the fp32 range);
             // the norm only sets the stop and the scale of the next correction, and x and r use
             // the same value of it
             float rs_l = 0.f;
+            if (outer == 0) {
+                // r = b - K x in fp64 with the fp64 weights, then split into double-float
 #pragma unroll
-            for (int k = 0; k < NPT; ++k) {
-                r64[k] = 0.0;
-                if (nid[k] >= 0) {
-                    const int h = nid[k] & 0xffff;
-                    const double w0 = __ldcg(w64l + h), w1 = __ldcg(w64l + h + W);
-                    const double w2 = __ldcg(w64d + h), w3 = __ldcg(w64d + h + 1);
-                    double acc = w0 * xh[h - W];
-                    acc = fma(w1, xh[h + W], acc);
-                    acc = fma(w2, xh[h - 1], acc);
-                    acc = fma(w3, xh[h + 1], acc);
-                    r64[k] = b - fma(__ldcg(d64 + h), xh[h], -acc);
-                    const float rs = d2f_round(r64[k]) * inv;
-                    rs_l = fmaf(rs, rs, rs_l);
+                for (int k = 0; k < NPT; ++k) {
+                    if (nid[k] >= 0) {
+                        const int h = nid[k] & 0xffff;
+                        const double w0 = __ldcg(w64l + h), w1 = __ldcg(w64l + h + W);
+                        const double w2 = __ldcg(w64d + h), w3 = __ldcg(w64d + h + 1);
+                        double acc = w0 * xh[h - W];
+                        acc = fma(w1, xh[h + W], acc);
+                        acc = fma(w2, xh[h - 1], acc);
+                        acc = fma(w3, xh[h + 1], acc);
+                        const float2 r = df_split(b - fma(__ldcg(d64 + h), xh[h], -acc));
+                        rdf[h] = r;
+                        const float rs = r.x * inv;
+                        rs_l = fmaf(rs, rs, rs_l);
+                    }
+                }
+            } else {
+                // r -= ||r|| K d in double-float: K d = D d_h - sum_e w_e d_e (D, w_e double-float
+                // pairs, d fp32), ||r|| split once
+                const float2 nrd = df_split(nr);
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    if (nid[k] >= 0) {
+                        const int h = nid[k] & 0xffff;
+                        const float4 wh = wq[h], wl = __ldcg(wql + h);
+                        float2 kd = df_mulf(__ldcg(Ddf + h), d32[k]);
+                        kd = df_sub_lazy(kd, df_mulf(make_float2(wh.x, wl.x), ph[h - W]));
+                        kd = df_sub_lazy(kd, df_mulf(make_float2(wh.y, wl.y), ph[h + W]));
+                        kd = df_sub_lazy(kd, df_mulf(make_float2(wh.z, wl.z), ph[h - 1]));
+                        kd = df_sub_lazy(kd, df_mulf(make_float2(wh.w, wl.w), ph[h + 1]));
+                        // t = ||r|| K d (exact product of the high parts), r - t renormalised
+                        const float p = __fmul_rn(nrd.x, kd.x);
+                        const float pe = __fmaf_rn(nrd.x, kd.y, __fmaf_rn(nrd.y, kd.x, __fmaf_rn(nrd.x, kd.x, -p)));
+                        const float2 r = df_add(rdf[h], make_float2(-p, -pe));
+                        rdf[h] = r;
+                        const float rs = r.x * inv;
+                        rs_l = fmaf(rs, rs, rs_l);
+                    }
                 }
             }
             const Norm2 nm = block_norm2((double)rs_l, red64, nr, stop);
@@ -1035,6 +1110,10 @@ cudaError_t launch_mixed_big(const Pcg2dArgs& a, int blocks, cudaStream_t s) {
 }
 
 size_t dst_smem_bytes(int n, int d) { return dst_layout(n, d).total; }
+
+size_t mixed_slot_bytes(int n) {
+    return sizeof(double) * (n > 63 ? big_slot_doubles(n) : mixed_small_slot_doubles(n));
+}
 
 // the kernel instance for (NPT, P = n rounded up to 16); nullptr for a pair no n produces
 template <int NPT>
