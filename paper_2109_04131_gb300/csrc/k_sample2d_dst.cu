@@ -110,6 +110,25 @@ __device__ __forceinline__ float2 df_mulf(float2 a, float f) {
     const float p = __fmul_rn(a.x, f);
     return make_float2(p, __fmaf_rn(a.y, f, __fmaf_rn(a.x, f, -p)));
 }
+// the exact difference a - b of two floats as a double-float (TwoSum)
+__device__ __forceinline__ float2 df_two_diff(float a, float b) {
+    const float s = __fadd_rn(a, -b);
+    const float bb = __fadd_rn(s, -a);
+    return make_float2(s, __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(-b, -bb)));
+}
+// a b of two double-floats: the exact product of the high parts plus the cross terms, unnormalised
+__device__ __forceinline__ float2 df_mul_lazy(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    return make_float2(p, __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.x, -p))));
+}
+// a + b with the high parts' sum exact (TwoSum) and the low words added, unnormalised
+__device__ __forceinline__ float2 df_add_lazy(float2 a, float2 b) {
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fadd_rn(s, -a.x);
+    const float e = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(s, -bb)), __fadd_rn(b.x, -bb));
+    return make_float2(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
 // a - b with the high parts' difference exact (TwoSum) and the low words added, unnormalised
 __device__ __forceinline__ float2 df_sub_lazy(float2 a, float2 b) {
     const float s = __fadd_rn(a.x, -b.x);
@@ -384,16 +403,20 @@ struct Norm2 {
     float inv, rootf;
     int above;
 };
-__device__ __forceinline__ Norm2 block_norm2(double v, double* buf, double prev, double stop) {
+// The partial sums are of type T: fp32 where the per-thread terms are fp32 squares of r / ||r_prev||
+// (the norm only needs a few digits), fp64 otherwise.
+template <typename T>
+__device__ __forceinline__ Norm2 block_norm2(T v, double* buf, double prev, double stop) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T* part = reinterpret_cast<T*>(buf);      // buf[0..31] as partials; buf[32..35] the results
     v = warp_sum(v);
-    if (lane == 0) buf[warp] = v;
+    if (lane == 0) part[warp] = v;
     __syncthreads();
     if (warp == 0) {
-        double w = lane < nw ? buf[lane] : 0.0;
+        T w = lane < nw ? part[lane] : T(0);
         w = warp_sum(w);
         if (lane == 0) {
-            const double sq = w * prev * prev, root = sqrt(w) * prev;
+            const double sq = (double)w * prev * prev, root = sqrt((double)w) * prev;
             buf[32] = sq;
             buf[33] = root;
             float* f = reinterpret_cast<float*>(buf + 34);
@@ -745,7 +768,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                     }
                 }
             }
-            const Norm2 nm = block_norm2((double)rs_l, red64, nr, stop);
+            const Norm2 nm = block_norm2(rs_l, red64, nr, stop);
             rr64 = nm.sq;
             nr = nm.root;
             inv = nm.inv;
@@ -771,8 +794,9 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
 // sine-transform operands (S, L, two transform buffers: 174 KB at P = 128), the separable-assembly
 // tables and the reduction buffers.  One CTA of 1024 threads per system; nodes are visited in
 // loops g = tid, tid + T, ... (column-major enumeration, halo h = (p+1) W + (q+1), transform
-// position p LD + q, as in the small kernel).  Scratch slot (in units of W^2): fp64 x, weights
-// (left, down), diagonal, residual (5); fp32 weights (left, down), scaling, p, r, z, q, d, w (5).
+// position p LD + q, as in the small kernel).  Scratch slot: 7 W^2 doubles (fp64 x; the edge
+// weights' double-float low words; the double-float residual; fp32 weights, scaling, p, r, q, d, w)
+// and the fp64 mode table.
 // ---------------------------------------------------------------------------------------------
 struct BigLayout {
     int W, LD, J1, JA;
@@ -841,13 +865,16 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
     // (g < n^2, n <= 127); a division by the run-time n costs tens of integer instructions
     const unsigned mul_n = (unsigned)((0x100000000ull + (unsigned)n - 1) / (unsigned)n);
     const unsigned mul_n1 = (unsigned)((0x100000000ull + (unsigned)n1 - 1) / (unsigned)n1);
-    // the CTA's scratch slot: fp64 x and edge weights, fp32 weights, scaling, p, r, q, d, w (7 W^2
-    // doubles), then the fp64 mode table At
+    // the CTA's scratch slot: fp64 x, the low words of the edge weights' double-float pairs (left,
+    // down), the residual in double-float, the fp32 weights (the pairs' high words), scaling, p, r,
+    // q, d, w (7 W^2 doubles), then the fp64 mode table At.  The fp64 weights are the exact sums
+    // hi + lo of the pairs.
     double* x64 = a.scratch + (size_t)blockIdx.x * big_slot_doubles(n);
     double* At = x64 + 7 * (size_t)WW;
-    double* w64l = x64 + WW;
-    double* w64d = w64l + WW;
-    float* wl = reinterpret_cast<float*>(w64d + WW);
+    float* wll = reinterpret_cast<float*>(x64 + WW);
+    float* wdl = wll + WW;
+    float2* rdf = reinterpret_cast<float2*>(x64 + 2 * (size_t)WW);
+    float* wl = reinterpret_cast<float*>(x64 + 3 * (size_t)WW);
     float* wd = wl + WW;
     float* scs = wd + WW;
     float* ph = scs + WW;
@@ -874,8 +901,9 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
         wd[e] = 0.f;
         ph[e] = 0.f;
         zv[e] = 0.f;
-        w64l[e] = 0.0;
-        w64d[e] = 0.0;
+        wll[e] = 0.f;
+        wdl[e] = 0.f;
+        dv[e] = 0.f;            // the residual update reads d at the halo
         x64[e] = 0.0;
     }
     {
@@ -928,8 +956,8 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 float2 w = df_add(lo, au);
                 w = make_float2(0.5f * w.x, 0.5f * w.y);
                 const int h = (Pp + 1) * W + Q + 1;
-                w64l[h] = df_to_double(w);
                 wl[h] = w.x;
+                wll[h] = w.y;
             }
             if (Pp >= 1) {          // edge (Pp,Q)-(Pp,Q+1): below node (Pp,Q+1); lower triangle of (Pp-1, Q)
                 float2 lo = make_float2(0.f, 0.f);
@@ -938,15 +966,17 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 float2 w = df_add(au, lo);
                 w = make_float2(0.5f * w.x, 0.5f * w.y);
                 const int h = Pp * W + Q + 1;
-                w64d[h] = df_to_double(w);
                 wd[h] = w.x;
+                wdl[h] = w.y;
             }
         }
         __syncthreads();
         for (int g = tid; g < G; g += T) {
             const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
-            const double dg = (w64l[h] + w64l[h + W]) + (w64d[h] + w64d[h + 1]);
-            scs[h] = rsqrtf(0.25f * d2f_round(dg));
+            // the diagonal (sum of the four edge weights) in double-float, for the scaling only
+            const float2 dg = df_add(df_add(make_float2(wl[h], wll[h]), make_float2(wl[h + W], wll[h + W])),
+                                     df_add(make_float2(wd[h], wdl[h]), make_float2(wd[h + 1], wdl[h + 1])));
+            scs[h] = rsqrtf(0.25f * dg.x);
             x64[h] = 0.0;
             rv[h] = d2f_round(b);        // r = b, kept as fp32 (the inner solve starts from fp32(r) / ||r||)
         }
@@ -1042,23 +1072,45 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 x64[h] = fma(nr, f2d_exact(dv[h]), x64[h]);
             }
             __syncthreads();
-            // residual in difference form, b - sum_e w_e (x_i - x_j): at these mesh widths the
-            // terms diag x_i and w x_j are ~1e4 times b and cancel, the differences do not
-            double rl64 = 0.0;
-            for (int g = tid; g < G; g += T) {
-                const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
-                const double xi = x64[h];
-                double acc = w64l[h] * (xi - x64[h - W]);
-                acc = fma(w64l[h + W], xi - x64[h + W], acc);
-                acc = fma(w64d[h], xi - x64[h - 1], acc);
-                acc = fma(w64d[h + 1], xi - x64[h + 1], acc);
-                const double r = b - acc;
-                rv[h] = d2f_round(r);
-                rl64 = fma(r, r, rl64);
+            // the residual: after the first correction b - sum_e w_e (x_i - x_j) in fp64 with the fp64
+            // weights (hi + lo, exact) in difference form -- at these mesh widths the terms diag x_i
+            // and w x_j are ~1e4 times b and cancel, the differences do not; after each later
+            // correction r -= ||r|| sum_e w_e (d_i - d_j) in double-float (the differences of the
+            // fp32 correction exact by TwoSum), whose rounding is relative to the current residual
+            float rs_l = 0.f;
+            if (outer == 0) {
+                for (int g = tid; g < G; g += T) {
+                    const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
+                    const double xi = x64[h];
+                    double acc = df2d(wl[h], wll[h]) * (xi - x64[h - W]);
+                    acc = fma(df2d(wl[h + W], wll[h + W]), xi - x64[h + W], acc);
+                    acc = fma(df2d(wd[h], wdl[h]), xi - x64[h - 1], acc);
+                    acc = fma(df2d(wd[h + 1], wdl[h + 1]), xi - x64[h + 1], acc);
+                    const float2 r = df_split(b - acc);
+                    rdf[h] = r;
+                    rv[h] = r.x;
+                    const float rs = r.x * inv;
+                    rs_l = fmaf(rs, rs, rs_l);
+                }
+            } else {
+                const float2 nrd = df_split(nr);
+                for (int g = tid; g < G; g += T) {
+                    const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
+                    const float di = dv[h];
+                    float2 kd = df_mul_lazy(make_float2(wl[h], wll[h]), df_two_diff(di, dv[h - W]));
+                    kd = df_add_lazy(kd, df_mul_lazy(make_float2(wl[h + W], wll[h + W]), df_two_diff(di, dv[h + W])));
+                    kd = df_add_lazy(kd, df_mul_lazy(make_float2(wd[h], wdl[h]), df_two_diff(di, dv[h - 1])));
+                    kd = df_add_lazy(kd, df_mul_lazy(make_float2(wd[h + 1], wdl[h + 1]), df_two_diff(di, dv[h + 1])));
+                    const float2 r = df_add(rdf[h], df_neg(df_mul_lazy(nrd, kd)));
+                    rdf[h] = r;
+                    rv[h] = r.x;
+                    const float rs = r.x * inv;
+                    rs_l = fmaf(rs, rs, rs_l);
+                }
             }
             const double rr_prev = rr64;
             {
-                const Norm2 nm = block_norm2(rl64, red64, 1.0, stop);
+                const Norm2 nm = block_norm2(rs_l, red64, nr, stop);
                 rr64 = nm.sq;
                 nr = nm.root;
                 inv = nm.inv;
@@ -1066,8 +1118,9 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             }
             ++outer;
             // At these mesh widths the fp64 residual of the 5-point system has a rounding floor
-            // near 1e-13 relative (the granularity of x times the diagonal, ~1e4 b): an outer
-            // step that no longer halves the residual norm below 1e-11 relative has reached it.
+            // near 1e-13 relative (the granularity of x times the diagonal, ~1e4 b), which the
+            // residual of the first correction carries; an outer step that no longer halves the
+            // residual norm below 1e-11 relative is taken to have reached it.
             if (rr64 > stop && rr64 > 0.25 * rr_prev && rr64 <= 1e-22 * rr0) {
                 at_floor = true;
                 break;
