@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
     for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
         const int64_t i = lattice_node(a.ns, a.i0 + sys);
         // ---- assembly: fp64 weights to the CTA's scratch slot, fp32 copies to shared memory ----
-        for (int j = tid; j < a.ns.d; j += T) sj[j] = node_theta(a.ns, j, i);
+        for (int j = tid; j < a.ns.d; j += T) sj[j] = amp[j] * node_theta(a.ns, j, i);   // c j^-mu theta_j(y)
         __syncthreads();
         const bool logn = a.coef_model == USFFT_COEF_LOGNORMAL_SIN;
         const int sq = n1 * n1, d = a.ns.d;
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
             const int j1 = e / (2 * n1) + 1, o = (e / n1) % 2, Q = e % n1;
             double acc = 0.0;
             for (int j = 0; j < d; ++j)
-                if (mj1[j] == j1) acc = fma(amp[j] * sj[j], At[((mj2[j] - 1) * 2 + o) * n1 + Q], acc);
+                if (mj1[j] == j1) acc = fma(sj[j], At[((mj2[j] - 1) * 2 + o) * n1 + Q], acc);
             Tr[e] = df_split(acc);
         }
         __syncthreads();
@@ -608,19 +608,19 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
             }
         }
         __syncthreads();
-        // fp64 diagonal of every node (sum of its four edge weights) for the refinement residual;
+        // the diagonal of every node (sum of its four edge weights) in double-float from the
+        // weights' pairs, and as fp64 (its exact value hi + lo) for the first refinement residual;
         // the symmetric diagonal scaling of the preconditioner, sc = (diag / 4)^-1/2
 #pragma unroll
         for (int k = 0; k < NPT; ++k) {
             if (nid[k] >= 0) {
                 const int h = nid[k] & 0xffff;
-                const double dg = (w64l[h] + w64l[h + W]) + (w64d[h] + w64d[h + 1]);
-                d64[h] = dg;
-                scs[h] = rsqrtf(0.25f * d2f_round(dg));
                 const float4 wh = wq[h], wl = __ldcg(wql + h);
                 const float2 s = df_add(df_add(make_float2(wh.x, wl.x), make_float2(wh.y, wl.y)),
                                         df_add(make_float2(wh.z, wl.z), make_float2(wh.w, wl.w)));
                 Ddf[h] = s;
+                d64[h] = df_to_double(s);
+                scs[h] = rsqrtf(0.25f * s.x);
             }
         }
         __syncthreads();
@@ -930,7 +930,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
 
     for (int64_t sys = blockIdx.x; sys < a.count; sys += gridDim.x) {
         const int64_t i = lattice_node(a.ns, a.i0 + sys);
-        for (int j = tid; j < a.ns.d; j += T) sj[j] = node_theta(a.ns, j, i);
+        for (int j = tid; j < a.ns.d; j += T) sj[j] = amp[j] * node_theta(a.ns, j, i);   // c j^-mu theta_j(y)
         __syncthreads();
         const bool logn = a.coef_model == USFFT_COEF_LOGNORMAL_SIN;
         const int d = a.ns.d;
@@ -938,7 +938,7 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             const int j1 = e / (2 * n1) + 1, o = (e / n1) % 2, Q = e % n1;
             double acc = 0.0;
             for (int j = 0; j < d; ++j)
-                if (mj1[j] == j1) acc = fma(amp[j] * sj[j], At[((mj2[j] - 1) * 2 + o) * n1 + Q], acc);
+                if (mj1[j] == j1) acc = fma(sj[j], At[((mj2[j] - 1) * 2 + o) * n1 + Q], acc);
             Tr[e] = df_split(acc);
         }
         __syncthreads();
