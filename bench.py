@@ -777,6 +777,19 @@ def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind, n_batch=32, n_serve=
     ei = np.zeros(G)
     st, ms_err, _ = timed(lambda: lib.usfft_errors(h, Y.data_ptr(), n_test, 1, e2.ctypes.data, ei.ctypes.data))
     assert st == 0
+    # step 3 on multiple rank-1 lattices (usfft_reconstruct_multiple), then the errors with it
+    (Im, Cm), ms_mrec, wall_mrec = timed(pmx.reconstruct_multiple)
+    _, M_mult = pmx.get_random_lattices()
+    e2m = np.zeros(G)
+    eim = np.zeros(G)
+    st, _, _ = timed(lambda: lib.usfft_errors(h, Y.data_ptr(), n_test, 1, e2m.ctypes.data, eim.ctypes.data))
+    assert st == 0 and np.array_equal(Im, I)
+    n_mult = int(np.sum(M_mult))
+    mult = {"n_I": len(Im), "lattices": int(len(M_mult)), "M": [int(v) for v in M_mult], "samples": n_mult,
+            "samples_bound": int(math.ceil(2 * math.log(2 * max(len(Im), 1))) * 4 * max(len(Im) - 1, 0)),
+            "ms": ms_mrec, "wall_ms": wall_mrec, "lattice_samples_per_s": n_mult / (ms_mrec / 1e3),
+            "err2_max": float(np.max(e2m)), "errinf_max": float(np.max(eim)), "err2_median": float(np.median(e2m)),
+            "max_rel_diff_vs_single_lattice": float(np.max(np.abs(Cm - C)) / max(float(np.max(np.abs(C))), 1e-300))}
     flops_eval = 8.0 * n_test * nI * G                  # complex multiply-add per (point, frequency, node)
     ach = flops_eval / (ms_eval / 1e3) / 1e12
     stat_bytes = 16.0 * G * nI
@@ -807,6 +820,7 @@ def next_rows_measure(w, pmx, t0, n_test, peaks, peak_kind, n_batch=32, n_serve=
         "samples_single_lattice_t0_plus_1_to_d": int(sum(r["samples"] for r in single)),
         "reconstruct": {"n_I": nI, "M": int(M_rec), "ms": ms_rec, "wall_ms": wall_rec,
                         "lattice_samples_per_s": M_rec / (ms_rec / 1e3)},
+        "reconstruct_multiple": mult,
         "statistics": {"ms": ms_stat, "bytes": stat_bytes, "achieved_gbs": stat_gbs,
                        "frac_of_hbm": stat_gbs / peaks["hbm_gbs"], "peak_note": f"{peak_kind} hbm_gbs",
                        "gsi_l1_min": float(np.min(gsi[:, 0])), "variance_max": float(np.max(var))},

@@ -245,6 +245,20 @@ usfft_status usfft_get_set(const usfft_plan_t* plan, int8_t* freqs, int64_t n_ca
 usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, double* coefs,
                                int coefs_on_device);
 
+/* Step 3 on multiple rank-1 lattices, the paper's choice there (Algorithm 1, step 3; Appendix A,
+ * the sampling bound M <= ceil(2 ln(2|I|)) 4 (|I| - 1)).  Same arguments, outputs, errors and
+ * stored reconstruction as usfft_reconstruct.  The lattices are those of usfft_multiple_lattices
+ * for I and params.seed: sizes from the smallest 7-smooth size >= 2 (|I| - 1) upwards, each
+ * generating vector drawn (draws keyed by phase 6), added until every k of I is alone at its index
+ * k.z_l mod M_l in at least one lattice (USFFT_ELATTICE if 64 lattices do not get there).  The FE
+ * problem is solved at the nodes of every lattice (all d coordinates on the lattice, no tails),
+ * each node's length-M_l FFT is read at k.z_l mod M_l, and c_k is the value of the first lattice
+ * in which k is alone: the exact coefficient for trigonometric polynomials supported in I.
+ * Afterwards usfft_get_random_lattices returns these lattices (count L, t = d) and the
+ * single-lattice inspection calls describe the last one. */
+usfft_status usfft_reconstruct_multiple(usfft_plan_t* plan, int64_t* n, int8_t* freqs, double* coefs,
+                                        int coefs_on_device);
+
 /* Evaluation at explicit parameter points (Section 4).  y is [n][d] fp64 row-major (one
  * point y^(j) per row; coordinates on the torus, any real value is taken mod 1 by the
  * 1-periodic coefficient model).  With on_device != 0, y and the output are device pointers
@@ -315,7 +329,8 @@ usfft_status usfft_set_keep_iterations(usfft_plan_t* plan, int on);
 usfft_status usfft_get_iteration(const usfft_plan_t* plan, int i, double* U, double* C, uint32_t* bitmap,
                                  int32_t* count);
 
-/* The random rank-1 lattices of the last coupled step when params.rr_lattices > 0: *count
+/* The random rank-1 lattices of the last coupled step when params.rr_lattices > 0 (after
+ * usfft_reconstruct_multiple: step 3's lattices, count L, t = d): *count
  * receives r~ * L (0 after a single-lattice step or a 1-D step), *t the number of lattice
  * coordinates; z (may be NULL) receives [count][t] generating vectors and M (may be NULL)
  * [count] sizes, lattice q = (i-1)*L + (l-1) of detection iteration i.  With random lattices
@@ -425,6 +440,18 @@ const char* usfft_version(void);
  * [1, 64], i < 1, L outside [1, 31] or factor outside (0, 1e6). */
 usfft_status usfft_random_lattices(int t, int i, int64_t n_prev, int64_t n_t, int64_t s_t, int L, double factor,
                                    uint64_t seed, int64_t* z, int64_t* M);
+
+/* The multiple rank-1 lattices of usfft_reconstruct_multiple on the host (no GPU needed), for
+ * the frequency set freqs ([n][d] int8 rows, host): lattice l = 1, 2, ... has size M_1 = the
+ * smallest 7-smooth size >= max(2 (n - 1), 2), M_(l+1) = the smallest 7-smooth size > M_l, and
+ * generating vector components z_j, each the first draw in [1, M_l - 1] keyed (seed, 6, l, j, a),
+ * a = 0..63, that is coprime to M_l (else 1).  Lattices are added until every k is alone at its
+ * index k.z_l mod M_l in at least one of them.  *count receives the number of lattices, z (may be
+ * NULL; capacity [max_lattices][d]) their generating vectors and M (may be NULL; capacity
+ * [max_lattices]) their sizes.  USFFT_ELATTICE if max_lattices lattices (1..1024) are not enough
+ * (the arrays then hold all of them); USFFT_EINVAL for bad arguments. */
+usfft_status usfft_multiple_lattices(const int8_t* freqs, int64_t n, int d, uint64_t seed, int max_lattices,
+                                     int64_t* z, int64_t* M, int32_t* count);
 
 /* The reconstructing rank-1 lattice search used by usfft_increment for the candidate set
  * J ([n][t] int8, row-major): the smallest admissible (7-smooth) size M >= n, then

@@ -134,3 +134,39 @@ def random_lattices(t: int, i: int, n_prev: int, n_t: int, s_t: int, L: int, fac
         out.append((z, M))
         M = next_admissible(M + 1)
     return out
+
+
+def multiple_lattices(I: np.ndarray, d: int, seed: int, max_lattices: int = 64):
+    """The multiple rank-1 lattices of step 3 (Algorithm 1, step 3 with the multiple R1L approach,
+    Appendix A; the rule is a reading): sizes start at the smallest admissible size >=
+    max(2 (|I| - 1), 2), the size of the bound ceil(2 ln(2|I|)) 4 (|I| - 1) on the total, and each next
+    size is the smallest admissible one above the last; each component of z_l is a unit mod M_l, the
+    first draw uniform in [1, M_l - 1] keyed (seed, PHASE_MULTI_R1L, l, j, a), a = 0, 1, ..., 63,
+    coprime to M_l, else 1.  Lattices are drawn until every k in I is alone at its index k.z_l mod
+    M_l (no other frequency of I maps there) in at least one of them.
+    Returns ([(z_l, M_l)], first) with first[k] the first such lattice (0-based), or None in place
+    of first if max_lattices lattices leave some k without one."""
+    n = len(I)
+    first = np.full(n, -1, dtype=np.int64)
+    out = []
+    if n == 0:
+        return out, first
+    M = next_admissible(max(2 * (n - 1), 2))
+    for l in range(1, max_lattices + 1):
+        z = np.ones(d, dtype=np.int64)
+        for j in range(1, d + 1):
+            for a in range(64):
+                v = rng.uniform_int(1, M - 1, seed, rng.PHASE_MULTI_R1L, l, j, a)
+                if math.gcd(v, M) == 1:
+                    z[j - 1] = v
+                    break
+        out.append((z, M))
+        m = lattice_indices(I, z, M)
+        values, counts = np.unique(m, return_counts=True)
+        alone = np.isin(m, values[counts == 1])
+        first[(first < 0) & alone] = l - 1
+        if np.all(first >= 0):
+            return out, first
+        M = next_admissible(M + 1)
+    return out, None
+

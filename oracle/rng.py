@@ -27,6 +27,7 @@ PHASE_TAIL = 2         # tails y'_{t+1..d} of the coupled step t (step 2b)
 PHASE_LATTICE = 3      # generating-vector components of the lattice search (coupled steps)
 PHASE_RECON = 4        # generating-vector components of the step-3 lattice
 PHASE_RANDOM_R1L = 5   # generating vectors of the random rank-1 lattices (coupled steps)
+PHASE_MULTI_R1L = 6    # generating vectors of the multiple rank-1 lattices of step 3
 
 
 def mix64(z: int) -> int:

@@ -255,6 +255,30 @@ class OracleRun:
         self.samples_used += M
         return I, z, M, dft.coefficients(U, m, M)
 
+    def reconstruct_multiple(self):
+        """Step 3 on multiple rank-1 lattices (oracle.lattice.multiple_lattices): the samples of
+        every lattice (all d coordinates on the lattice, no tails), their DFTs read at k.z_l mod
+        M_l, and c_k from the first lattice in which k is alone at its index, where the lattice
+        DFT is exactly c_k for a trigonometric polynomial supported in I (the aliasing formula of
+        Appendix A).  Returns (I, [(z_l, M_l)], C [G, |I|])."""
+        assert self.t == self.prob.d
+        I = self.I_prefix
+        d = self.prob.d
+        lats, first = lattice.multiple_lattices(I, d, self.p.seed)
+        if len(I) == 0:
+            return I, lats, np.zeros((0, 0), dtype=np.complex128)
+        assert first is not None, "some frequency of I shares its index in every lattice"
+        C = None
+        for l, (z_l, M_l) in enumerate(lats):
+            mine = np.nonzero(first == l)[0]
+            U = sample(self.prob, NodeSet(d, list(range(d)), z_l, M_l, {}), self.mesh)
+            self.samples_used += M_l
+            c_l = dft.coefficients(U, lattice.lattice_indices(I[mine], z_l, M_l), M_l)
+            if C is None:
+                C = np.zeros((c_l.shape[0], len(I)), dtype=np.complex128)
+            C[:, mine] = c_l
+        return I, lats, C
+
     def resume(self, t: int, I_prefix: np.ndarray, theta: float):
         """Continue from the state after increment t: I^(1..t) and theta (checkpoint)."""
         self.t = t

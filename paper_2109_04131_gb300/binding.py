@@ -6,7 +6,7 @@ allocator (through the allocator hook of usfft_params) and its work runs on the
 current PyTorch stream unless another stream is given.
 
 Module-level functions carry the C names (usfft_plan, usfft_increment, usfft_replay,
-usfft_rewind, usfft_resume, usfft_get_set, usfft_reconstruct, usfft_sample_points, usfft_evaluate,
+usfft_rewind, usfft_resume, usfft_get_set, usfft_reconstruct, usfft_reconstruct_multiple, usfft_sample_points, usfft_evaluate,
 usfft_errors, usfft_statistics, usfft_plan_bytes, usfft_increment_many, usfft_get_lattice, usfft_get_candidates,
 usfft_get_samples, usfft_get_coefficients, usfft_get_selection, usfft_set_keep_iterations,
 usfft_get_iteration, usfft_last_error,
@@ -84,6 +84,7 @@ SIGNATURES = {
     "usfft_get_set": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int32)]),
     "usfft_reconstruct": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), _P, _P, ctypes.c_int]),
+    "usfft_reconstruct_multiple": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), _P, _P, ctypes.c_int]),
     "usfft_sample_points": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int]),
     "usfft_evaluate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int]),
     "usfft_errors": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, _P, _P]),
@@ -114,6 +115,8 @@ SIGNATURES = {
                                             ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int64)]),
     "usfft_random_lattices": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                              ctypes.c_int, ctypes.c_double, ctypes.c_uint64, _P, _P]),
+    "usfft_multiple_lattices": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, _P, _P,
+                                               ctypes.POINTER(ctypes.c_int32)]),
     "usfft_draw_key": (ctypes.c_uint64, [ctypes.c_uint64, _P, ctypes.c_int]),
     "usfft_draw_uniform": (ctypes.c_double, [ctypes.c_uint64, _P, ctypes.c_int]),
     "usfft_sample_2d_static": (ctypes.c_int, [ctypes.POINTER(UsfftProblem), _P, _P, ctypes.c_int64, ctypes.c_int64,
@@ -246,6 +249,10 @@ def usfft_reconstruct(plan):
     return plan.reconstruct()
 
 
+def usfft_reconstruct_multiple(plan):
+    return plan.reconstruct_multiple()
+
+
 def usfft_sample_points(plan, Y):
     return plan.sample_points(Y)
 
@@ -372,6 +379,19 @@ def usfft_tune_import(text):
     _check(lib.usfft_tune_import(None if text is None else text.encode()), None)
 
 
+def usfft_multiple_lattices(freqs, seed, max_lattices=64):
+    """Host-only multiple rank-1 lattice rule of step 3 for the set freqs [n][d]: (z [L][d], M [L])."""
+    lib = load_library()
+    F = np.ascontiguousarray(np.asarray(freqs, dtype=np.int8))
+    n, d = F.shape
+    z = np.zeros((max_lattices, d), dtype=np.int64)
+    M = np.zeros(max_lattices, dtype=np.int64)
+    cnt = ctypes.c_int32(0)
+    _check(lib.usfft_multiple_lattices(F.ctypes.data if n else None, n, d, seed, max_lattices, z.ctypes.data,
+                                       M.ctypes.data, ctypes.byref(cnt)), None)
+    return z[:cnt.value], M[:cnt.value]
+
+
 def usfft_random_lattices(t, i, n_prev, n_t, s_t, L, factor, seed):
     """Host-only random rank-1 lattice rule of the library: (z [L][t], M [L])."""
     lib = load_library()
@@ -493,6 +513,18 @@ class Plan:
         C = np.zeros((self.problem.G, n.value, 2))
         out = C if C.size else np.zeros(2)          # an empty set still records the (zero) approximation
         self._ck(self._lib.usfft_reconstruct(self.handle, ctypes.byref(n), I.ctypes.data if n.value else None,
+                                             out.ctypes.data, 0))
+        return I.astype(np.int64), C[..., 0] + 1j * C[..., 1]
+
+    def reconstruct_multiple(self):
+        """(I [n][d] int64, C [G][n] complex128): step 3 on multiple rank-1 lattices."""
+        n = ctypes.c_int64(0)
+        self._ck(self._lib.usfft_reconstruct_multiple(self.handle, ctypes.byref(n), None, None, 0))
+        d = self.problem.d
+        I = np.zeros((n.value, d), dtype=np.int8)
+        C = np.zeros((self.problem.G, n.value, 2))
+        out = C if C.size else np.zeros(2)          # an empty set still records the (zero) approximation
+        self._ck(self._lib.usfft_reconstruct_multiple(self.handle, ctypes.byref(n), I.ctypes.data if n.value else None,
                                              out.ctypes.data, 0))
         return I.astype(np.int64), C[..., 0] + 1j * C[..., 1]
 

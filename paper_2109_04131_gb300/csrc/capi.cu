@@ -86,7 +86,9 @@ struct usfft_plan_s {
     std::vector<int8_t> Irec_h;
     // random rank-1 lattice detection of the last coupled step (params.rr_lattices > 0):
     // lattice q = i*L + l of iteration i, its FFT plan and its slices of the gather/twiddle buffers
-    bool rr_active = false;
+    // (also step 3 on multiple rank-1 lattices, usfft_reconstruct_multiple: one iteration, every
+    // estimate from its first alias-free lattice, rr_pick_only)
+    bool rr_active = false, rr_pick_only = false;
     int rr_L = 0, rr_iters = 0;
     std::vector<int64_t> rr_M, rr_z;
     std::vector<FftPlan> rr_fp;
@@ -406,11 +408,13 @@ usfft_status prepare_step(usfft_plan_t* plan, int64_t M, const std::vector<int64
     return USFFT_OK;
 }
 
-// buffers, gather plans, twiddles and estimate sources of a random-lattice step: rt
-// iterations of L lattices each over the nJ candidates J (t columns)
-usfft_status prepare_rr(usfft_plan_t* plan, const std::vector<int8_t>& J, int64_t nJ, int t, int rt, int s_t) {
-    const int L = plan->par.rr_lattices, G = plan->G;
-    const double factor = plan->par.rr_size_factor > 0.0 ? plan->par.rr_size_factor : 2.0;
+// buffers, gather plans, twiddles and estimate sources of a step on several lattices: rt
+// iterations of L lattices each over the nJ candidates J (t columns); lattice l of iteration i is
+// zall[((i-1) L + l) t ...] with size Mall[(i-1) L + l].  The estimate of candidate k in iteration i
+// comes from the first of its lattices in which no other candidate shares k's index.
+usfft_status prepare_lattice_set(usfft_plan_t* plan, const std::vector<int8_t>& J, int64_t nJ, int t, int rt, int L,
+                                 const std::vector<int64_t>& zall, const std::vector<int64_t>& Mall) {
+    const int G = plan->G;
     plan->rr_L = L;
     plan->rr_iters = rt;
     plan->rr_M.clear();
@@ -424,16 +428,16 @@ usfft_status prepare_rr(usfft_plan_t* plan, const std::vector<int8_t>& J, int64_
     int64_t Mmax = 0;
     std::vector<int64_t> m((size_t)nJ), sorted;
     for (int i = 1; i <= rt; ++i) {
-        std::vector<int64_t> zi, Mi;
-        random_lattices(t, i, plan->nIpre, (int64_t)plan->I1d[(size_t)t].size(), s_t, L, factor, plan->par.seed, zi, Mi);
+        const int64_t* zi = zall.data() + (size_t)(i - 1) * L * t;
+        const int64_t* Mi = Mall.data() + (size_t)(i - 1) * L;
         for (int l = 0; l < L; ++l) {
             const int64_t M = Mi[(size_t)l];
-            if (M > (int64_t)1 << 24) return fail(plan, USFFT_EINVAL, "random lattice larger than 4096^2");
+            if (M > (int64_t)1 << 24) return fail(plan, USFFT_EINVAL, "lattice larger than 4096^2");
             if (plan->prob.kind != USFFT_TRIGPOLY && plan->prob.theta_map == USFFT_MAP_NORMAL &&
                 lattice_hits_pole(M, plan->prob.map_shift))
-                return fail(plan, USFFT_EINVAL, "a random lattice node lies on a pole of the lognormal map");
+                return fail(plan, USFFT_EINVAL, "a lattice node lies on a pole of the lognormal map");
             const FftPlan fp = make_fft_plan(M);
-            if (fp.L2 <= 0) return fail(plan, USFFT_EINVAL, "random lattice size has no FFT factorisation");
+            if (fp.L2 <= 0) return fail(plan, USFFT_EINVAL, "lattice size has no FFT factorisation");
             for (int64_t a = 0; a < nJ; ++a) {
                 int64_t acc = 0;
                 for (int j = 0; j < t; ++j) acc += (int64_t)J[(size_t)(a * t + j)] * zi[(size_t)(l * t + j)];
@@ -472,7 +476,7 @@ usfft_status prepare_rr(usfft_plan_t* plan, const std::vector<int8_t>& J, int64_
             scr_max = std::max(scr_max, fft_scratch_bytes(fp, G));
             Mmax = std::max(Mmax, M);
             plan->rr_M.push_back(M);
-            plan->rr_z.insert(plan->rr_z.end(), zi.begin() + (size_t)l * t, zi.begin() + (size_t)(l + 1) * t);
+            plan->rr_z.insert(plan->rr_z.end(), zi + (size_t)l * t, zi + (size_t)(l + 1) * t);
             plan->rr_fp.push_back(fp);
         }
     }
@@ -512,6 +516,20 @@ usfft_status prepare_rr(usfft_plan_t* plan, const std::vector<int8_t>& J, int64_
     return USFFT_OK;
 }
 
+// the random rank-1 lattices of params.rr_lattices for the coupled step t (rt iterations)
+usfft_status prepare_rr(usfft_plan_t* plan, const std::vector<int8_t>& J, int64_t nJ, int t, int rt, int s_t) {
+    const int L = plan->par.rr_lattices;
+    const double factor = plan->par.rr_size_factor > 0.0 ? plan->par.rr_size_factor : 2.0;
+    std::vector<int64_t> zall, Mall, zi, Mi;
+    plan->rr_pick_only = false;
+    for (int i = 1; i <= rt; ++i) {
+        random_lattices(t, i, plan->nIpre, (int64_t)plan->I1d[(size_t)t].size(), s_t, L, factor, plan->par.seed, zi, Mi);
+        zall.insert(zall.end(), zi.begin(), zi.end());
+        Mall.insert(Mall.end(), Mi.begin(), Mi.end());
+    }
+    return prepare_lattice_set(plan, J, nJ, t, rt, L, zall, Mall);
+}
+
 // device part of a random-lattice step: per iteration L x (sample -> FFT+gather), the
 // estimate (alias-free lattice or median), select/union
 usfft_status run_rr_device(usfft_plan_t* plan) {
@@ -534,8 +552,13 @@ usfft_status run_rr_device(usfft_plan_t* plan) {
         }
         {
             StageTimer timer(plan, USFFT_STAGE_FFT);
-            CK(launch_random_lattice_combine((const double2*)plan->rr_C.p, L, G, nJ, (const int*)plan->rr_src.p + (size_t)i * nJ,
-                                             (double2*)plan->C.p, plan->stream, &plan->launches));
+            const int* src = (const int*)plan->rr_src.p + (size_t)i * nJ;
+            if (plan->rr_pick_only)
+                CK(launch_lattice_pick((const double2*)plan->rr_C.p, L, G, nJ, src, (double2*)plan->C.p, plan->stream,
+                                       &plan->launches));
+            else
+                CK(launch_random_lattice_combine((const double2*)plan->rr_C.p, L, G, nJ, src, (double2*)plan->C.p,
+                                                 plan->stream, &plan->launches));
         }
         if (plan->s_tilde > 0) {
             StageTimer timer(plan, USFFT_STAGE_SELECT);
@@ -1430,6 +1453,7 @@ usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, do
     plan->cg_iters_max = 0;
     plan->nrec = -1;
     plan->rr_active = false;
+    plan->rr_pick_only = false;
     CK(cudaMemsetAsync(plan->failc.p, 0, sizeof(unsigned), plan->stream));
     usfft_status st = prepare_step(plan, M, m);
     if (st != USFFT_OK) return st;
@@ -1450,6 +1474,73 @@ usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, do
     if ((st = read_cg_stats(plan, M)) != USFFT_OK) return st;
     const size_t bytes = sizeof(double2) * (size_t)nI * plan->G;
     // keep I and the coefficients for usfft_evaluate / usfft_errors
+    if ((st = ensure(plan, plan->Crec, bytes, "reconstruction coefficients")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->Irec, (size_t)nI * d, "reconstruction set")) != USFFT_OK) return st;
+    CK(cudaMemcpyAsync(plan->Crec.p, plan->C.p, bytes, cudaMemcpyDeviceToDevice, plan->stream));
+    CK(cudaMemcpyAsync(plan->Irec.p, plan->Ipre.data(), (size_t)nI * d, cudaMemcpyHostToDevice, plan->stream));
+    plan->h2d += (int64_t)nI * d;
+    CK(cudaMemcpyAsync(coefs, plan->C.p, bytes, coefs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       plan->stream));
+    if ((st = wait_stream(plan)) != USFFT_OK) return st;
+    plan->nrec = nI;
+    plan->Irec_h = plan->Ipre;
+    return USFFT_OK;
+}
+
+// most lattices step 3 may take on multiple rank-1 lattices before it reports USFFT_ELATTICE
+static const int kMaxReconLattices = 64;
+
+usfft_status usfft_reconstruct_multiple(usfft_plan_t* plan, int64_t* n, int8_t* freqs, double* coefs,
+                                        int coefs_on_device) {
+    if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
+    if (plan->t != plan->d) return fail(plan, USFFT_ESTATE, "usfft_reconstruct_multiple needs all d increments done");
+    if (n) *n = plan->nIpre;
+    if (freqs) memcpy(freqs, plan->Ipre.data(), plan->Ipre.size());
+    if (!coefs) return USFFT_OK;
+    const int d = plan->d;
+    const int64_t nI = plan->nIpre;
+    if (nI == 0) {             // nothing detected: the approximation is zero
+        plan->nrec = 0;
+        plan->Irec_h.clear();
+        return USFFT_OK;
+    }
+    // the lattices (Algorithm 1, step 3 on multiple rank-1 lattices): added until every k of I
+    // is alone at its index in one of them
+    std::vector<int64_t> z, M;
+    std::vector<int> first;
+    if (!multiple_lattices(plan->Ipre.data(), nI, d, plan->par.seed, kMaxReconLattices, z, M, first))
+        return fail(plan, USFFT_ELATTICE, "multiple rank-1 lattices: a frequency of I shares its index in all 64 lattices");
+    const int L = (int)M.size();
+    plan->launches = 0;
+    plan->cg_iters_total = 0;
+    plan->cg_iters_max = 0;
+    plan->nrec = -1;
+    CK(cudaMemsetAsync(plan->failc.p, 0, sizeof(unsigned), plan->stream));
+    plan->J = plan->Ipre;
+    plan->last_coupled = true;
+    plan->last_t = d;
+    plan->replay_valid = false;
+    plan->rr_active = true;
+    plan->s_tilde = 0;                       // no threshold in step 3
+    usfft_status st = prepare_lattice_set(plan, plan->Ipre, nI, d, 1, L, z, M);
+    plan->rr_pick_only = true;
+    if (st != USFFT_OK) {
+        plan->rr_active = false;
+        return st;
+    }
+    plan->specs.clear();
+    for (int l = 0; l < L; ++l) {
+        NodeSpec ns;
+        memset(&ns, 0, sizeof ns);
+        ns.M = M[(size_t)l];
+        ns.d = d;
+        set_map(ns, plan->prob);
+        for (int j = 0; j < d; ++j) ns.z[j] = z[(size_t)l * d + j];
+        plan->specs.push_back(ns);
+    }
+    if ((st = run_step_device(plan, false)) != USFFT_OK) return st;
+    if ((st = read_cg_stats(plan, plan->M)) != USFFT_OK) return st;
+    const size_t bytes = sizeof(double2) * (size_t)nI * plan->G;
     if ((st = ensure(plan, plan->Crec, bytes, "reconstruction coefficients")) != USFFT_OK) return st;
     if ((st = ensure(plan, plan->Irec, (size_t)nI * d, "reconstruction set")) != USFFT_OK) return st;
     CK(cudaMemcpyAsync(plan->Crec.p, plan->C.p, bytes, cudaMemcpyDeviceToDevice, plan->stream));
@@ -1684,6 +1775,19 @@ usfft_status usfft_random_lattices(int t, int i, int64_t n_prev, int64_t n_t, in
     memcpy(z, zz.data(), sizeof(int64_t) * zz.size());
     memcpy(M, mm.data(), sizeof(int64_t) * mm.size());
     return USFFT_OK;
+}
+
+usfft_status usfft_multiple_lattices(const int8_t* freqs, int64_t n, int d, uint64_t seed, int max_lattices, int64_t* z,
+                                     int64_t* M, int32_t* count) {
+    if (n < 0 || (n > 0 && !freqs) || d < 1 || d > USFFT_MAX_D || max_lattices < 1 || max_lattices > 1024 || !count)
+        return fail(nullptr, USFFT_EINVAL, "usfft_multiple_lattices: invalid argument");
+    std::vector<int64_t> zz, mm;
+    std::vector<int> first;
+    const bool ok = multiple_lattices(freqs, n, d, seed, max_lattices, zz, mm, first);
+    *count = (int32_t)mm.size();
+    if (z) memcpy(z, zz.data(), sizeof(int64_t) * zz.size());
+    if (M) memcpy(M, mm.data(), sizeof(int64_t) * mm.size());
+    return ok ? USFFT_OK : fail(nullptr, USFFT_ELATTICE, "usfft_multiple_lattices: max_lattices lattices leave a frequency shared");
 }
 
 uint64_t usfft_draw_key(uint64_t seed, const uint64_t* fields, int nfields) {

@@ -113,6 +113,53 @@ void random_lattices(int t, int i, int64_t n_prev, int64_t n_t, int64_t s_t, int
     }
 }
 
+// Step 3 with multiple rank-1 lattices (Algorithm 1, step 3; Appendix A: the lattice sizes of the
+// bound M <= ceil(2 ln(2|I|)) 4 (|I| - 1), i.e. sizes from 2 (|I| - 1) on).  Each lattice is kept
+// only as long as some k of I is not yet alone at its index in an earlier one.
+bool multiple_lattices(const int8_t* I, int64_t n, int d, uint64_t seed, int max_lattices, std::vector<int64_t>& z,
+                       std::vector<int64_t>& M, std::vector<int>& first) {
+    z.clear();
+    M.clear();
+    first.assign((size_t)std::max<int64_t>(n, 0), -1);
+    if (n <= 0) return true;
+    int64_t m = next_admissible(std::max<int64_t>(2 * (n - 1), 2));
+    int64_t open = n;
+    std::vector<int64_t> idx((size_t)n), sorted;
+    for (int l = 1; l <= max_lattices && open > 0; ++l) {
+        std::vector<int64_t> zl((size_t)d, 1);
+        for (int j = 1; j <= d; ++j) {
+            for (int a = 0; a < 64; ++a) {
+                const uint64_t f[4] = {PHASE_MULTI_R1L, (uint64_t)l, (uint64_t)j, (uint64_t)a};
+                const int64_t v = rng_uniform_int(1, m - 1, seed, f, 4);
+                if (gcd64(v, m) == 1) {
+                    zl[(size_t)(j - 1)] = v;
+                    break;
+                }
+            }
+        }
+        for (int64_t k = 0; k < n; ++k) {
+            int64_t acc = 0;
+            for (int j = 0; j < d; ++j) acc += (int64_t)I[(size_t)(k * d + j)] * zl[(size_t)j];
+            const int64_t r = acc % m;
+            idx[(size_t)k] = r < 0 ? r + m : r;
+        }
+        sorted = idx;
+        std::sort(sorted.begin(), sorted.end());
+        for (int64_t k = 0; k < n; ++k) {
+            if (first[(size_t)k] >= 0) continue;
+            auto range = std::equal_range(sorted.begin(), sorted.end(), idx[(size_t)k]);
+            if (range.second - range.first == 1) {
+                first[(size_t)k] = l - 1;
+                --open;
+            }
+        }
+        z.insert(z.end(), zl.begin(), zl.end());
+        M.push_back(m);
+        m = next_admissible(m + 1);
+    }
+    return open == 0;
+}
+
 void candidate_set(const int8_t* I_prev, int64_t n_prev, int t_prev, const std::vector<int>& I_t, int N,
                    std::vector<int8_t>& J, int64_t& nJ) {
     const int t = t_prev + 1;

@@ -18,7 +18,8 @@ namespace usfft {
 
 // Counter-based SplitMix64 draws (Steele, Lea, Flood 2014): key(seed, f1, f2, ...)
 // folds one SplitMix64 step per field, h <- mix64((h ^ f) + golden gamma).
-enum Phase : uint64_t { PHASE_1D_TAIL = 1, PHASE_TAIL = 2, PHASE_LATTICE = 3, PHASE_RECON = 4, PHASE_RANDOM_R1L = 5 };
+enum Phase : uint64_t { PHASE_1D_TAIL = 1, PHASE_TAIL = 2, PHASE_LATTICE = 3, PHASE_RECON = 4, PHASE_RANDOM_R1L = 5,
+                        PHASE_MULTI_R1L = 6 };
 uint64_t rng_key(uint64_t seed, const uint64_t* fields, int nfields);
 double rng_uniform(uint64_t seed, const uint64_t* fields, int nfields);                 // [0,1)
 int64_t rng_uniform_int(int64_t lo, int64_t hi, uint64_t seed, const uint64_t* fields, int nfields);
@@ -42,6 +43,15 @@ bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials
 // a = 0..63, that is coprime to M_l (else 1).  z receives L*t entries, M receives L sizes.
 void random_lattices(int t, int i, int64_t n_prev, int64_t n_t, int64_t s_t, int L, double factor, uint64_t seed,
                      std::vector<int64_t>& z, std::vector<int64_t>& M);
+
+// The multiple rank-1 lattices of step 3 for the frequency set I ([n][d] int8 rows): lattice l =
+// 1, 2, ... has size M_1 = the smallest admissible size >= max(2 (n - 1), 2), M_(l+1) = the smallest
+// admissible size > M_l, and d components, each the first draw in [1, M_l - 1] keyed (seed,
+// PHASE_MULTI_R1L, l, j, a), a = 0..63, that is coprime to M_l (else 1).  Lattices are added until
+// every k in I is alone at its index k.z_l mod M_l in at least one of them; first[k] receives the
+// first such l (0-based).  false if max_lattices lattices do not get there.
+bool multiple_lattices(const int8_t* I, int64_t n, int d, uint64_t seed, int max_lattices, std::vector<int64_t>& z,
+                       std::vector<int64_t>& M, std::vector<int>& first);
 
 // Candidate set J_t = I_prev x I_t within [-N,N]^t (lexicographic in the positions).
 void candidate_set(const int8_t* I_prev, int64_t n_prev, int t_prev, const std::vector<int>& I_t, int N,
@@ -143,6 +153,9 @@ cudaError_t launch_fft_gather(const FftPlan& p, int G, const double* U, const vo
 // Random-lattice estimate (Algorithm A): C[g][k] = Call[src[k]][g][k] where src[k] >= 0 (the
 // first lattice with k alone at its index), else the median over the L lattices of the real
 // and, separately, the imaginary parts (L odd, <= 31).  Call is [L][G][nJ].
+// C[g][k] = Call[src[k]][g][k] (step 3 on multiple rank-1 lattices: src[k] in [0, L) for every k)
+cudaError_t launch_lattice_pick(const double2* Call, int L, int G, int64_t nJ, const int* src, double2* C,
+                                cudaStream_t s, int* launches);
 cudaError_t launch_random_lattice_combine(const double2* Call, int L, int G, int64_t nJ, const int* src, double2* C,
                                           cudaStream_t s, int* launches);
 

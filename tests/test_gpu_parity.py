@@ -423,6 +423,66 @@ def test_reconstruct_2d_matches_oracle(B, precision):
 
 
 
+def _reconstruct_multiple_both(B, prob, params):
+    plan = B.Plan(prob, params)
+    run = OracleRun(prob, params, keep=True)
+    for _ in range(prob.d):
+        if run.t > 0:
+            plan.resume(run.t, run.I_prefix, run.theta)
+        run.increment()
+        plan.increment()
+    plan.resume(run.t, run.I_prefix, run.theta)
+    I_o, lats, C_o = run.reconstruct_multiple()
+    I_g, C_g = plan.reconstruct_multiple()
+    assert np.array_equal(I_g, I_o)
+    z, M = plan.get_random_lattices()          # step 3's lattices, bit-exact
+    assert list(M) == [m for _, m in lats] and all(np.array_equal(z[l], lats[l][0]) for l in range(len(lats)))
+    return plan, I_g, C_g, C_o
+
+
+@pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED])
+def test_reconstruct_multiple_2d_matches_oracle(B, precision):
+    # step 3 on multiple rank-1 lattices: every lattice's FE solves, FFTs and gathers, and the pick of
+    # each coefficient from its first alias-free lattice, against the oracle element by element
+    w = W.with_precision(W.small_2d(n=15, d=3, seed=2, N=4, s=20), precision)
+    plan, I, C, C_o = _reconstruct_multiple_both(B, w.problem, w.params)
+    assert C.shape == C_o.shape and len(I) > 0
+    assert node_rel(C, C_o) < TOL
+    _, M = plan.get_random_lattices()
+    assert len(M) >= 1 and M[0] >= 2 * (len(I) - 1)
+    # the stored reconstruction is this one: evaluate and the errors use it
+    Y = np.random.default_rng(5).random((16, w.problem.d))
+    assert np.all(np.isfinite(plan.evaluate(Y)))
+    # and the single-lattice step 3 afterwards still gives its own result
+    I1, C1 = plan.reconstruct()
+    assert np.array_equal(I1, I) and C1.shape == C.shape
+    plan.close()
+
+
+@pytest.mark.parametrize("G,seed", [(9, 8), (600, 31)])
+def test_reconstruct_multiple_trigpoly_coefficients(B, G, seed):
+    # exact recovery (Appendix A): each coefficient of a polynomial supported in I comes out of the
+    # first lattice where it is alone; at G = 600 the whole run is the library's alone
+    prob = W.trigpoly(G=G, d=4, N=5, seed=seed, base_terms=5, node_terms=2, kmax=3, mag_lo=1e-4)
+    params = W.Params(N=5, s=40, s_local=40, delta=1e-9, delta_is_relative=False, r=1, seed=seed)
+    if G <= 9:
+        plan, I, C, C_o = _reconstruct_multiple_both(B, prob, params)
+        assert node_rel(C, C_o) < TOL
+    else:
+        plan = B.Plan(prob, params)
+        for _ in range(prob.d):
+            plan.increment()
+        I, C = plan.reconstruct_multiple()
+        _, M = plan.get_random_lattices()
+        assert len(M) >= 2                      # |I| of several hundred needs more than one lattice
+    assert len(I) > 0
+    for g in range(prob.G):
+        truth = {tuple(int(v) for v in f): c for f, c in zip(prob.tp_freqs[g], prob.tp_coefs[g]) if c != 0}
+        want = np.array([truth.get(tuple(int(v) for v in k), 0.0) for k in I])
+        assert np.max(np.abs(C[g] - want)) < 1e-13
+    plan.close()
+
+
 @pytest.mark.parametrize("precision", [W.PRECISION_FP64, W.PRECISION_MIXED])
 def test_tent_and_lognormal_maps_match_oracle(B, precision):
     tent = W.with_map(W.small_2d(n=15, d=4, seed=3, N=5, s=30), W.MAP_TENT, -1.0, 1.0)

@@ -164,3 +164,74 @@ def test_random_lattices_recover_trigonometric_polynomials(G, seed):
     # the step-3 reconstruction still uses one reconstructing lattice
     I, z, M, C = run.reconstruct()
     assert lattice.is_reconstructing(I, z, M)
+
+
+@pytest.mark.parametrize("G,seed", [(3, 8), (9, 21)])
+def test_step3_multiple_lattices_return_the_polynomial_coefficients(G, seed):
+    # Algorithm 1, step 3 on multiple rank-1 lattices (Appendix A): in a lattice where k is alone
+    # at its index, the lattice DFT at k.z mod M is c_k itself for a polynomial supported in I, so
+    # reading every coefficient from its first such lattice recovers the polynomial exactly
+    from oracle import lattice
+    d, N = 4, 5
+    prob = W.trigpoly(G=G, d=d, N=N, seed=seed, base_terms=5, node_terms=2, kmax=3, mag_lo=1e-4)
+    params = W.Params(N=N, s=40, s_local=40, delta=1e-9, delta_is_relative=False, r=1, seed=seed)
+    assert _margins_ok(prob, params, params.delta)
+    run = OracleRun(prob, params, keep=True)
+    for _ in range(d):
+        run.increment()
+    I, lats, C = run.reconstruct_multiple()
+    sup = _support(prob)
+    assert {tuple(int(v) for v in k) for k in I} == set().union(*[set(s) for s in sup])
+    assert C.shape == (G, len(I))
+    for g in range(G):
+        want = np.array([sup[g].get(tuple(int(v) for v in k), 0.0) for k in I])
+        assert np.max(np.abs(C[g] - want)) < 1e-13
+    # sizes: the first one of the bound's range 2 (|I| - 1) and distinct 7-smooth sizes after it
+    Ms = [M for _, M in lats]
+    assert Ms[0] == lattice.next_admissible(max(2 * (len(I) - 1), 2))
+    assert all(lattice.is_smooth7(M) for M in Ms) and all(a < b for a, b in zip(Ms, Ms[1:]))
+    assert run.samples_used >= sum(Ms)
+
+
+def _alone(I, z, M):
+    m = [int(np.dot(k, z)) % M for k in I]
+    return np.array([m.count(v) == 1 for v in m])
+
+
+@pytest.mark.parametrize("seed,n,d", [(1, 40, 3), (2, 200, 5), (3, 700, 8)])
+def test_multiple_lattices_cover_every_frequency(seed, n, d):
+    # the construction's stopping rule, recomputed by brute force: every k of I is alone at its
+    # index in the lattice first[k] and in no earlier one; the rule stops at the first lattice
+    # that completes the cover; and the sample total stays within the paper's bound
+    # ceil(2 ln(2|I|)) 4 (|I| - 1) (Appendix A, with c = 2 and delta = 1/2)
+    import math
+    from oracle import lattice
+    rs = np.random.default_rng(seed)
+    I = np.unique(rs.integers(-16, 17, size=(n, d)), axis=0).astype(np.int64)
+    lats, first = lattice.multiple_lattices(I, d, seed)
+    assert first is not None
+    alone = np.array([_alone(I, z, M) for z, M in lats])            # [L, |I|]
+    for k in range(len(I)):
+        assert alone[first[k], k] and not alone[:first[k], k].any()
+    assert first.max() == len(lats) - 1
+    total = sum(M for _, M in lats)
+    assert total <= math.ceil(2 * math.log(2 * len(I))) * 4 * (len(I) - 1)
+    assert all(np.all((z >= 1) & (z < M)) and all(math.gcd(int(v), M) == 1 for v in z) for z, M in lats)
+
+
+def test_lattice_dft_is_the_aliasing_sum():
+    # brute force on a tiny set: the lattice DFT of a trigonometric polynomial at index m is the sum
+    # of c_k over all k with k.z = m (mod M), so c_k alone at its index is read exactly, and a
+    # shared index gives the sum of the colliding coefficients
+    from oracle import dft, lattice
+    rs = np.random.default_rng(4)
+    d, M = 2, 7
+    z = np.array([1, 3])
+    K = np.array([[0, 0], [1, 0], [0, 1], [2, -1], [-1, 2], [3, 3]])
+    c = rs.normal(size=len(K)) + 1j * rs.normal(size=len(K))
+    nodes = (np.outer(np.arange(M), z) % M) / M                       # y_i = frac(i z / M)
+    f = np.array([np.sum(c * np.exp(2j * np.pi * (K @ y))) for y in nodes])
+    m = lattice.lattice_indices(K, z, M)
+    got = dft.coefficients(f.real[:, None], m, M)[0] + 1j * dft.coefficients(f.imag[:, None], m, M)[0]
+    for a in range(len(K)):
+        assert abs(got[a] - c[m == m[a]].sum()) < 1e-13
