@@ -634,6 +634,10 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
         double rr64 = rr0, nr = nr0;
         float inv = inv0, nrf = nrf0;
         int more = rr0 > stop;
+        // the high words of r for the next step's fp32 right-hand side (dead during the inner solve)
+        float rhi[NPT];
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) rhi[k] = (nid[k] >= 0) ? d2f_round(b) : 0.f;
         int total = 0, outer = 0;
         while (more && outer < 16) {
             // Flexible PCG in the single-reduction form of Chronopoulos and Gear on K d = r / ||r||:
@@ -652,7 +656,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                 d32[k] = 0.f;
                 p32[k] = 0.f;
                 q32[k] = 0.f;
-                r32[k] = (nid[k] < 0) ? 0.f : (outer == 0 ? d2f_round(b) : rdf[nid[k] & 0xffff].x) * inv;
+                r32[k] = rhi[k] * inv;
             }
             // inner target: tol_inner, or less when this step only has to close the remaining
             // gap to the outer tolerance (0.3 x the reduction still missing)
@@ -730,6 +734,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                 // r = b - K x in fp64 with the fp64 weights, then split into double-float
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
+                    rhi[k] = 0.f;
                     if (nid[k] >= 0) {
                         const int h = nid[k] & 0xffff;
                         const double w0 = __ldcg(w64l + h), w1 = __ldcg(w64l + h + W);
@@ -740,6 +745,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                         acc = fma(w3, xh[h + 1], acc);
                         const float2 r = df_split(b - fma(__ldcg(d64 + h), xh[h], -acc));
                         rdf[h] = r;
+                        rhi[k] = r.x;
                         const float rs = r.x * inv;
                         rs_l = fmaf(rs, rs, rs_l);
                     }
@@ -750,6 +756,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                 const float2 nrd = df_split(nr);
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) {
+                    rhi[k] = 0.f;
                     if (nid[k] >= 0) {
                         const int h = nid[k] & 0xffff;
                         const float4 wh = wq[h], wl = __ldcg(wql + h);
@@ -763,6 +770,7 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                         const float pe = __fmaf_rn(nrd.x, kd.y, __fmaf_rn(nrd.y, kd.x, __fmaf_rn(nrd.x, kd.x, -p)));
                         const float2 r = df_add(rdf[h], make_float2(-p, -pe));
                         rdf[h] = r;
+                        rhi[k] = r.x;
                         const float rs = r.x * inv;
                         rs_l = fmaf(rs, rs, rs_l);
                     }
