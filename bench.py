@@ -668,7 +668,7 @@ def config_1d(seeds=10):
     out = {"workload": "1-D P1 FE on (0,1), 31 interior nodes, affine periodic coefficient, d=4, Gamma=[-16,16]^4, "
                        "s=50, delta=1e-12 relative, r=1; full runs t=1..4"}
     for name, prec in (("fp64", W.PRECISION_FP64), ("mixed", W.PRECISION_MIXED)):
-        lat, dev_ms, samples = [], [], 0
+        lat, dev_ms, samples, where = [], [], 0, []
         for sd in range(1, seeds + 1):
             w = W.with_precision(W.c1(sd), prec)
             plan = binding.Plan(w.problem, w.params)
@@ -683,12 +683,15 @@ def config_1d(seeds=10):
                 info = plan.increment()
                 lat.append(1e3 * (time.perf_counter() - t0))
                 dev_ms.append(info["ms_device"])
+                where.append((sd, int(info["t"]), int(info["M"])))
                 samples += info["samples"]
             plan.close()
         out[name] = {"lattice_samples": samples, "value": samples / (sum(lat) / 1e3), "unit": UNIT,
                      "device_samples_per_s": samples / (sum(dev_ms) / 1e3),
                      "increment_latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99)},
-                     "increment_device_ms": {"p50": percentile(dev_ms, 50), "p99": percentile(dev_ms, 99)}}
+                     "increment_device_ms": {"p50": percentile(dev_ms, 50), "p99": percentile(dev_ms, 99)},
+                     "slowest_increment": {"seed_t_M": where[int(np.argmax(dev_ms))], "ms_device": float(np.max(dev_ms)),
+                                           "ms_wall": float(lat[int(np.argmax(dev_ms))])}}
     return out
 
 

@@ -107,6 +107,7 @@ struct F64 {
     static constexpr bool kFastDiv = false;   // index division by a multiply-high (measured slower here)
     static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
     static __device__ __forceinline__ C pair(double x, double y) { return make_double2(x, y); }
+    static __device__ __forceinline__ C pair_trunc(double x, double y) { return make_double2(x, y); }
     static __device__ __forceinline__ C add(C a, C b) { return make_double2(a.x + b.x, a.y + b.y); }
     static __device__ __forceinline__ C sub(C a, C b) { return make_double2(a.x - b.x, a.y - b.y); }
     static __device__ __forceinline__ C mul(C a, C b) {
@@ -164,6 +165,24 @@ struct DF {
     static __device__ __forceinline__ C zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
     static __device__ __forceinline__ C pair(double x, double y) {
         const float2 a = split(x), b = split(y);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    // x as a pair without fp64 arithmetic: hi = x truncated to 24 significant bits (exact), lo = the
+    // remaining 29 bits of the significand, rounded to float and scaled by a power of two (exact);
+    // |lo| < ulp(hi), so the pair is unnormalised the way the butterflies' results are.  Magnitudes
+    // outside [2^-74, 2^127) (and inf, nan) take the rounded split with one fp64 subtraction.  Used by
+    // the two-pass kernels' loads (2.5% faster there; the in-place kernel measured 1% slower with it).
+    static __device__ __forceinline__ float2 split_trunc(double x) {
+        const uint32_t uh = (uint32_t)__double2hiint(x), ul = (uint32_t)__double2loint(x);
+        const uint32_t e = (uh >> 20) & 0x7ffu;
+        if (e < 949u || e > 1150u) return d2df(x);
+        const uint32_t sign = uh & 0x80000000u;
+        const float hi = __uint_as_float(sign | ((e - 896u) << 23) | ((uh & 0xfffffu) << 3) | (ul >> 29));
+        const float lo = __fmul_rn(__uint2float_rn(ul & 0x1fffffffu), __uint_as_float((e - 948u) << 23));
+        return make_float2(hi, sign ? -lo : lo);
+    }
+    static __device__ __forceinline__ C pair_trunc(double x, double y) {
+        const float2 a = split_trunc(x), b = split_trunc(y);
         return make_float4(a.x, a.y, b.x, b.y);
     }
     static __device__ __forceinline__ C add(C a, C b) {
@@ -377,7 +396,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass1_kernel(const __grid_con
         const int64_t row = (int64_t)o * a.in_outer + (int64_t)l * a.in_step;
         const double x = g < a.G ? __ldcs(a.Ur + row * a.G + g) : 0.0;
         const double y = g + 1 < a.G ? __ldcs(a.Ur + row * a.G + g + 1) : 0.0;
-        b0[idx] = A::pair(x, y);
+        b0[idx] = A::pair_trunc(x, y);
     }
     __syncthreads();
     const C* res = fft_tile<A>(b0, b1, tw, W, a, Gt);
@@ -424,7 +443,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_final_kernel(const __grid_con
             const int g = 2 * (c0 + c);
             const double x = g < a.G ? __ldcs(a.Ur + row * a.G + g) : 0.0;
             const double y = g + 1 < a.G ? __ldcs(a.Ur + row * a.G + g + 1) : 0.0;
-            v = A::pair(x, y);
+            v = A::pair_trunc(x, y);
         }
         b0[idx] = v;
     }
