@@ -1422,6 +1422,26 @@ usfft_status usfft_get_iteration(const usfft_plan_t* plan_c, int i, double* U, d
     return wait_stream(plan);
 }
 
+// the coefficients of step 3 (in plan->C, on I = plan->Ipre) kept with I for usfft_evaluate /
+// usfft_errors / usfft_statistics, and copied to the caller's host or device buffer
+static usfft_status store_reconstruction(usfft_plan_t* plan, double* coefs, int coefs_on_device) {
+    const int64_t nI = plan->nIpre;
+    const int d = plan->d;
+    const size_t bytes = sizeof(double2) * (size_t)nI * plan->G;
+    usfft_status st;
+    if ((st = ensure(plan, plan->Crec, bytes, "reconstruction coefficients")) != USFFT_OK) return st;
+    if ((st = ensure(plan, plan->Irec, (size_t)nI * d, "reconstruction set")) != USFFT_OK) return st;
+    CK(cudaMemcpyAsync(plan->Crec.p, plan->C.p, bytes, cudaMemcpyDeviceToDevice, plan->stream));
+    CK(cudaMemcpyAsync(plan->Irec.p, plan->Ipre.data(), (size_t)nI * d, cudaMemcpyHostToDevice, plan->stream));
+    plan->h2d += (int64_t)nI * d;
+    CK(cudaMemcpyAsync(coefs, plan->C.p, bytes, coefs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       plan->stream));
+    if ((st = wait_stream(plan)) != USFFT_OK) return st;
+    plan->nrec = nI;
+    plan->Irec_h = plan->Ipre;
+    return USFFT_OK;
+}
+
 usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, double* coefs, int coefs_on_device) {
     if (!plan) return fail(nullptr, USFFT_EINVAL, "plan is NULL");
     if (plan->t != plan->d) return fail(plan, USFFT_ESTATE, "usfft_reconstruct needs all d increments done");
@@ -1472,19 +1492,7 @@ usfft_status usfft_reconstruct(usfft_plan_t* plan, int64_t* n, int8_t* freqs, do
     plan->s_tilde = 0;                       // no threshold in step 3
     if ((st = run_step_device(plan, false)) != USFFT_OK) return st;
     if ((st = read_cg_stats(plan, M)) != USFFT_OK) return st;
-    const size_t bytes = sizeof(double2) * (size_t)nI * plan->G;
-    // keep I and the coefficients for usfft_evaluate / usfft_errors
-    if ((st = ensure(plan, plan->Crec, bytes, "reconstruction coefficients")) != USFFT_OK) return st;
-    if ((st = ensure(plan, plan->Irec, (size_t)nI * d, "reconstruction set")) != USFFT_OK) return st;
-    CK(cudaMemcpyAsync(plan->Crec.p, plan->C.p, bytes, cudaMemcpyDeviceToDevice, plan->stream));
-    CK(cudaMemcpyAsync(plan->Irec.p, plan->Ipre.data(), (size_t)nI * d, cudaMemcpyHostToDevice, plan->stream));
-    plan->h2d += (int64_t)nI * d;
-    CK(cudaMemcpyAsync(coefs, plan->C.p, bytes, coefs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       plan->stream));
-    if ((st = wait_stream(plan)) != USFFT_OK) return st;
-    plan->nrec = nI;
-    plan->Irec_h = plan->Ipre;
-    return USFFT_OK;
+    return store_reconstruction(plan, coefs, coefs_on_device);
 }
 
 // most lattices step 3 may take on multiple rank-1 lattices before it reports USFFT_ELATTICE
@@ -1540,18 +1548,7 @@ usfft_status usfft_reconstruct_multiple(usfft_plan_t* plan, int64_t* n, int8_t* 
     }
     if ((st = run_step_device(plan, false)) != USFFT_OK) return st;
     if ((st = read_cg_stats(plan, plan->M)) != USFFT_OK) return st;
-    const size_t bytes = sizeof(double2) * (size_t)nI * plan->G;
-    if ((st = ensure(plan, plan->Crec, bytes, "reconstruction coefficients")) != USFFT_OK) return st;
-    if ((st = ensure(plan, plan->Irec, (size_t)nI * d, "reconstruction set")) != USFFT_OK) return st;
-    CK(cudaMemcpyAsync(plan->Crec.p, plan->C.p, bytes, cudaMemcpyDeviceToDevice, plan->stream));
-    CK(cudaMemcpyAsync(plan->Irec.p, plan->Ipre.data(), (size_t)nI * d, cudaMemcpyHostToDevice, plan->stream));
-    plan->h2d += (int64_t)nI * d;
-    CK(cudaMemcpyAsync(coefs, plan->C.p, bytes, coefs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       plan->stream));
-    if ((st = wait_stream(plan)) != USFFT_OK) return st;
-    plan->nrec = nI;
-    plan->Irec_h = plan->Ipre;
-    return USFFT_OK;
+    return store_reconstruction(plan, coefs, coefs_on_device);
 }
 
 // ---- evaluation at given points (Section 4) ----------------------------------------------
