@@ -105,6 +105,34 @@ __device__ __forceinline__ float2 df_fma(float2 acc, float2 a, float2 b) {   // 
     return df_add(acc, make_float2(p, pe));
 }
 __device__ __forceinline__ double df_to_double(float2 a) { return df2d(a.x, a.y); }
+// exp of a double-float x on the FP32 pipe, for the lognormal coefficient.  Range reduction
+// x = k ln2 + r with k = rint(x / ln2) (Cody and Waite: ln2 = L0 + L1 + L2, L0 with 12 significant
+// bits so that k L0 and x - k L0 are exact), |r| <= 0.35; exp(r) from its Taylor series to degree 15
+// (the remainder r^16/16! < 1.2e-19 relative) by Horner in double-float with the coefficients 1/j!
+// as double-float constants; then the exact scaling by 2^k.  Relative error a few 1e-15 (Horner's
+// 15 double-float steps).  Outside |x| < 60 (where 2^k or the low word would leave the float
+// range) the fp64 exp is used.  Not inlined: the small-mesh kernel, whose affine workloads never
+// call it, measured 0.2% faster without its code inline.
+__device__ __noinline__ float2 df_exp(float2 x) {
+    if (!(fabsf(x.x) < 60.f)) return df_split(exp(df_to_double(x)));
+    const float k = rintf(x.x * 1.44269504f);
+    const float L0 = 0x1.62ep-1f, L1 = 0x1.0bfbe8p-15f, L2 = 0x1.cf79acp-40f;
+    float2 r = make_float2(__fmaf_rn(-k, L0, x.x), x.y);          // x.hi - k L0: exact
+    const float p1 = __fmul_rn(k, L1);
+    r = df_add(r, make_float2(-p1, -__fmaf_rn(k, L1, -p1)));       // - k L1, exactly as a pair
+    r = df_add(r, make_float2(-__fmul_rn(k, L2), 0.f));            // - k L2
+    const float ch[16] = {1.0f, 1.0f, 0.5f, 0x1.555556p-3f, 0x1.555556p-5f, 0x1.111112p-7f, 0x1.6c16c2p-10f,
+                          0x1.a01a02p-13f, 0x1.a01a02p-16f, 0x1.71de3ap-19f, 0x1.27e4fcp-22f, 0x1.ae6456p-26f,
+                          0x1.1eed8ep-29f, 0x1.612462p-33f, 0x1.93974ap-37f, 0x1.ae7f3ep-41f};
+    const float cl[16] = {0.f, 0.f, 0.f, -0x1.555556p-28f, -0x1.555556p-30f, -0x1.ddddde0p-32f, -0x1.27d27ep-35f,
+                          -0x1.7f97fap-39f, -0x1.7f97fap-42f, 0x1.55b1ccp-45f, -0x1.10ec14p-47f, 0x1.fd5138p-52f,
+                          0x1.ff1b12p-54f, -0x1.8af25ep-58f, 0x1.180f94p-62f, 0x1.ccee08p-67f};
+    float2 p = make_float2(ch[15], cl[15]);
+#pragma unroll
+    for (int j = 14; j >= 0; --j) p = df_fma(make_float2(ch[j], cl[j]), p, r);
+    const float s2 = __uint_as_float((uint32_t)((int)k + 127) << 23);  // 2^k, |k| <= 87
+    return make_float2(__fmul_rn(p.x, s2), __fmul_rn(p.y, s2));
+}
 // a (double-float) times the float f: the exact product of the high parts plus lo f, unnormalised
 __device__ __forceinline__ float2 df_mulf(float2 a, float f) {
     const float p = __fmul_rn(a.x, f);
@@ -578,14 +606,14 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
             const int Pp = (int)__umulhi((unsigned)e, mul_n1), Q = e - Pp * n1;
             float2 acc = make_float2(0.f, 0.f);
             for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 1) * n1 + Pp], Tr[(j1 * 2 + 0) * n1 + Q]);
-            low[e] = logn ? df_split(exp(df_to_double(acc))) : df_add(one, acc);
+            low[e] = logn ? df_exp(acc) : df_add(one, acc);
         }
         __syncthreads();
         for (int e = tid; e < sq; e += T) {
             const int Pp = (int)__umulhi((unsigned)e, mul_n1), Q = e - Pp * n1;
             float2 acc = make_float2(0.f, 0.f);
             for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 0) * n1 + Pp], Tr[(j1 * 2 + 1) * n1 + Q]);
-            const float2 au = logn ? df_split(exp(df_to_double(acc))) : df_add(one, acc);
+            const float2 au = logn ? df_exp(acc) : df_add(one, acc);
             if (Q < n) {            // edge (Pp,Q+1)-(Pp+1,Q+1): left of node (Pp+1,Q+1)
                 float2 w = df_add(low[Pp * n1 + Q + 1], au);
                 w = make_float2(0.5f * w.x, 0.5f * w.y);              // exact
@@ -950,28 +978,33 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             Tr[e] = df_split(acc);
         }
         __syncthreads();
-        // weights: the lower-triangle coefficient of square (P, Q) is recomputed where needed
+        // triangle coefficients a = 1 + sum_j1 At Tr (affine) or exp(sum_j1 At Tr) (lognormal), squares
+        // e = P (n+1) + Q (Q fastest: consecutive threads write consecutive halo nodes): first every
+        // square's lower-triangle coefficient, once, into the r and q slot arrays (free until the solve;
+        // 2 W^2 floats hold the (n+1)^2 pairs), then the upper ones and the edge weights
         const float2 one = make_float2(1.f, 0.f);
+        float2* low = reinterpret_cast<float2*>(rv);
         for (int e = tid; e < n1 * n1; e += T) {
-            const int Q = (int)__umulhi((unsigned)e, mul_n1), Pp = e - Q * n1;
+            const int Pp = (int)__umulhi((unsigned)e, mul_n1), Q = e - Pp * n1;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 1) * n1 + Pp], Tr[(j1 * 2 + 0) * n1 + Q]);
+            low[e] = logn ? df_exp(acc) : df_add(one, acc);
+        }
+        __syncthreads();
+        for (int e = tid; e < n1 * n1; e += T) {
+            const int Pp = (int)__umulhi((unsigned)e, mul_n1), Q = e - Pp * n1;
             float2 acc = make_float2(0.f, 0.f);
             for (int j1 = 0; j1 < J1; ++j1) acc = df_fma(acc, AtF[(j1 * 2 + 0) * n1 + Pp], Tr[(j1 * 2 + 1) * n1 + Q]);
-            const float2 au = logn ? df_split(exp(df_to_double(acc))) : df_add(one, acc);
+            const float2 au = logn ? df_exp(acc) : df_add(one, acc);
             if (Q < n) {            // edge (Pp,Q+1)-(Pp+1,Q+1): left of node (Pp+1,Q+1); lower triangle of (Pp, Q+1)
-                float2 lo = make_float2(0.f, 0.f);
-                for (int j1 = 0; j1 < J1; ++j1) lo = df_fma(lo, AtF[(j1 * 2 + 1) * n1 + Pp], Tr[(j1 * 2 + 0) * n1 + Q + 1]);
-                lo = logn ? df_split(exp(df_to_double(lo))) : df_add(one, lo);
-                float2 w = df_add(lo, au);
+                float2 w = df_add(low[Pp * n1 + Q + 1], au);
                 w = make_float2(0.5f * w.x, 0.5f * w.y);
                 const int h = (Pp + 1) * W + Q + 1;
                 wl[h] = w.x;
                 wll[h] = w.y;
             }
             if (Pp >= 1) {          // edge (Pp,Q)-(Pp,Q+1): below node (Pp,Q+1); lower triangle of (Pp-1, Q)
-                float2 lo = make_float2(0.f, 0.f);
-                for (int j1 = 0; j1 < J1; ++j1) lo = df_fma(lo, AtF[(j1 * 2 + 1) * n1 + Pp - 1], Tr[(j1 * 2 + 0) * n1 + Q]);
-                lo = logn ? df_split(exp(df_to_double(lo))) : df_add(one, lo);
-                float2 w = df_add(au, lo);
+                float2 w = df_add(au, low[(Pp - 1) * n1 + Q]);
                 w = make_float2(0.5f * w.x, 0.5f * w.y);
                 const int h = Pp * W + Q + 1;
                 wd[h] = w.x;
