@@ -1028,11 +1028,9 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
         float inv = (float)(1.0 / nr), nrf = (float)nr;
         int total = 0, outer = 0;
         bool at_floor = false;     // the residual stagnated at its rounding floor (see below)
-        auto precond = [&]() {     // zv = D^-1/2 K_0^-1 D^-1/2 rv
-            for (int g = tid; g < G; g += T) {
-                const int pp = (int)__umulhi((unsigned)g, mul_n), qq = g - pp * n, h = (pp + 1) * W + qq + 1;
-                Ta[pp * LD + qq] = __float2bfloat16_rn(scs[h] * rv[h]);
-            }
+        // zv = D^-1/2 K_0^-1 D^-1/2 rv; Ta already holds D^-1/2 rv on the transform grid, written by the
+        // pass that last changed rv (the step start or the previous iteration's update)
+        auto precond = [&]() {
             __syncthreads();
             gemm_bf16<P, false, false>(S, Ta, Tb, nullptr, n, c2);
             __syncthreads();
@@ -1050,8 +1048,10 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
         while (rr64 > stop && outer < 16) {
             // single-reduction flexible PCG (the small-mesh kernel's inner solve; p in ph, w = K z in wv)
             for (int g = tid; g < G; g += T) {
-                const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
-                rv[h] = rv[h] * inv;       // fp32(r) / ||r||
+                const int gq = (int)__umulhi((unsigned)g, mul_n), qq = g - gq * n, h = (gq + 1) * W + qq + 1;
+                const float r = rv[h] * inv;       // fp32(r) / ||r||
+                rv[h] = r;
+                Ta[gq * LD + qq] = __float2bfloat16_rn(scs[h] * r);
                 dv[h] = 0.f;
                 ph[h] = 0.f;
                 qv[h] = 0.f;
@@ -1093,13 +1093,15 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 const float qq_new = v[6] + beta * (2.f * v[7] + beta * qq);
                 const float rr = v[3] - 2.f * alpha * (v[4] + beta * v[5]) + alpha * alpha * qq_new;
                 for (int g = tid; g < G; g += T) {
-                    const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
+                    const int gq = (int)__umulhi((unsigned)g, mul_n), qq = g - gq * n, h = (gq + 1) * W + qq + 1;
                     const float p = fmaf(beta, ph[h], zv[h]);
                     const float q = fmaf(beta, qv[h], wv[h]);
                     ph[h] = p;
                     qv[h] = q;
                     dv[h] = fmaf(alpha, p, dv[h]);
-                    rv[h] = fmaf(-alpha, q, rv[h]);
+                    const float r = fmaf(-alpha, q, rv[h]);
+                    rv[h] = r;
+                    Ta[gq * LD + qq] = __float2bfloat16_rn(scs[h] * r);   // the next preconditioner's input
                 }
                 gamma_prev = v[0];
                 pq_prev = pq;
