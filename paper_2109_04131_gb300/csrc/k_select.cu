@@ -11,7 +11,9 @@
 // over the bit patterns of |c|^2 (non-negative doubles order like their bits), eight
 // 8-bit digits with a 256-bin shared histogram; then every key above it is taken and the
 // remaining quota of keys equal to it goes to the smallest indices (warp ballots and
-// prefix counts over index-ordered chunks).
+// prefix counts over index-ordered chunks).  The digit passes scan a compacted list instead of
+// all candidates once the keys still in play fit it (at most kSelList: right after the keys are
+// formed when few pass the threshold, else once the selected digit's bucket is that small).
 #include <cuda_runtime.h>
 
 #include "usfft_internal.h"
@@ -19,6 +21,7 @@
 namespace usfft {
 
 static const int kSelThreads = 256;
+static const int kSelList = 1024;   // keys of the selected radix bucket compacted once it holds at most this many
 
 __device__ __forceinline__ double mag2_rn(double2 c) {
     return __dadd_rn(__dmul_rn(c.x, c.x), __dmul_rn(c.y, c.y));
@@ -58,6 +61,8 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
     __shared__ unsigned int sh_want;
     __shared__ unsigned int warp_cnt[kSelThreads / 32];
     __shared__ unsigned int sh_total;
+    __shared__ unsigned int sh_bucket, sh_listn;
+    __shared__ unsigned long long slist[kSelList];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = blockDim.x >> 5;
     if (local_bits) {
@@ -99,15 +104,35 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
             __syncthreads();
             continue;
         }
-        // exact s~-th largest key: MSB-first radix select, 8-bit digits
+        // exact s~-th largest key: MSB-first radix select, 8-bit digits.  Once the selected digit's bucket
+        // holds at most kSelList keys they are copied to slist and the later passes scan only them
+        // (every other key fails their prefix test anyway)
+        int listn = -1;
+        if (total <= (unsigned int)kSelList) {      // few keys above the threshold: compact them right away
+            if (tid == 0) sh_listn = 0u;
+            __syncthreads();
+            for (int64_t k = tid; k < nJ; k += blockDim.x) {
+                const unsigned long long key = key_of(k);
+                if (key) slist[atomicAdd(&sh_listn, 1u)] = key;
+            }
+            __syncthreads();
+            listn = (int)sh_listn;
+        }
         for (int shift = 56; shift >= 0; shift -= 8) {
             hist[tid] = 0u;     // blockDim.x == 256
             __syncthreads();
             const unsigned long long prefix = sh_prefix;
             const unsigned long long himask = (shift == 56) ? 0ull : ~((1ull << (shift + 8)) - 1ull);
-            for (int64_t k = tid; k < nJ; k += blockDim.x) {
-                const unsigned long long key = key_of(k);
-                if (key && (key & himask) == prefix) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
+            if (listn < 0) {
+                for (int64_t k = tid; k < nJ; k += blockDim.x) {
+                    const unsigned long long key = key_of(k);
+                    if (key && (key & himask) == prefix) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
+                }
+            } else {
+                for (int q = tid; q < listn; q += blockDim.x) {
+                    const unsigned long long key = slist[q];
+                    if ((key & himask) == prefix) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
+                }
             }
             __syncthreads();
             if (warp == 0) {
@@ -131,18 +156,32 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
                     unsigned int cum = excl;
                     int dsel = 255 - 8 * lane;
 #pragma unroll
+                    unsigned int cnt_sel = 0;
                     for (int q = 0; q < 8; ++q) {
                         if (cum + c[q] >= want) {
                             dsel = 255 - 8 * lane - q;
+                            cnt_sel = c[q];
                             break;
                         }
                         cum += c[q];
                     }
                     sh_want = want - cum;
                     sh_prefix = prefix | ((unsigned long long)dsel << shift);
+                    sh_bucket = cnt_sel;
                 }
             }
             __syncthreads();
+            if (listn < 0 && shift > 0 && sh_bucket <= (unsigned int)kSelList) {
+                if (tid == 0) sh_listn = 0u;
+                __syncthreads();
+                const unsigned long long mask = ~((1ull << shift) - 1ull), pfx = sh_prefix;
+                for (int64_t k = tid; k < nJ; k += blockDim.x) {
+                    const unsigned long long key = key_of(k);
+                    if (key && (key & mask) == pfx) slist[atomicAdd(&sh_listn, 1u)] = key;
+                }
+                __syncthreads();
+                listn = (int)sh_listn;
+            }
         }
         const unsigned long long tau = sh_prefix;
         const unsigned int take_eq = sh_want;        // how many keys == tau to take
