@@ -890,7 +890,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--t", type=int, default=3, help="coupled increment timed as one step")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--ref-rows", type=int, default=0,
                     help="lattice nodes per reference step (0: 24 per host core, the cpu_baseline sample)")
     ap.add_argument("--skip-cpu", action="store_true")
