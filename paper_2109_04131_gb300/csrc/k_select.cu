@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(kSelThreads) select_union_kernel(const double2
                 if (hit) {
                     unsigned int cum = excl;
                     int dsel = 255 - 8 * lane;
-#pragma unroll
                     unsigned int cnt_sel = 0;
+#pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         if (cum + c[q] >= want) {
                             dsel = 255 - 8 * lane - q;
