@@ -1040,21 +1040,40 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             __syncthreads();
             gemm_bf16<P, true, false>(Tb, S, Ta, nullptr, n, c2);
             __syncthreads();
-            for (int g = tid; g < G; g += T) {
-                const int pp = (int)__umulhi((unsigned)g, mul_n), qq = g - pp * n, h = (pp + 1) * W + qq + 1;
-                zv[h] = scs[h] * __bfloat162float(Ta[pp * LD + qq]);
+            for (int g0 = tid; g0 < G; g0 += 2 * T) {      // two nodes per iteration, loads first
+                const int g1 = g0 + T;
+                const bool has1 = g1 < G;
+                const int p0 = (int)__umulhi((unsigned)g0, mul_n), q0 = g0 - p0 * n, h0 = (p0 + 1) * W + q0 + 1;
+                const int p1 = has1 ? (int)__umulhi((unsigned)g1, mul_n) : p0, q1 = has1 ? g1 - p1 * n : q0;
+                const int h1 = (p1 + 1) * W + q1 + 1;
+                const float s0 = scs[h0], s1 = scs[h1];
+                const float t0 = __bfloat162float(Ta[p0 * LD + q0]), t1 = __bfloat162float(Ta[p1 * LD + q1]);
+                zv[h0] = s0 * t0;
+                if (has1) zv[h1] = s1 * t1;
             }
         };
         while (rr64 > stop && outer < 16) {
             // single-reduction flexible PCG (the small-mesh kernel's inner solve; p in ph, w = K z in wv)
-            for (int g = tid; g < G; g += T) {
-                const int gq = (int)__umulhi((unsigned)g, mul_n), qq = g - gq * n, h = (gq + 1) * W + qq + 1;
-                const float r = rv[h] * inv;       // fp32(r) / ||r||
-                rv[h] = r;
-                Ta[gq * LD + qq] = __float2bfloat16_rn(scs[h] * r);
-                dv[h] = 0.f;
-                ph[h] = 0.f;
-                qv[h] = 0.f;
+            for (int g0 = tid; g0 < G; g0 += 2 * T) {      // two nodes per iteration, loads first
+                const int g1 = g0 + T;
+                const bool has1 = g1 < G;
+                const int p0 = (int)__umulhi((unsigned)g0, mul_n), q0 = g0 - p0 * n, h0 = (p0 + 1) * W + q0 + 1;
+                const int p1 = has1 ? (int)__umulhi((unsigned)g1, mul_n) : p0, q1 = has1 ? g1 - p1 * n : q0;
+                const int h1 = (p1 + 1) * W + q1 + 1;
+                const float r0 = rv[h0] * inv, r1 = rv[h1] * inv;   // fp32(r) / ||r||
+                const float s0 = scs[h0], s1 = scs[h1];
+                rv[h0] = r0;
+                Ta[p0 * LD + q0] = __float2bfloat16_rn(s0 * r0);
+                dv[h0] = 0.f;
+                ph[h0] = 0.f;
+                qv[h0] = 0.f;
+                if (has1) {
+                    rv[h1] = r1;
+                    Ta[p1 * LD + q1] = __float2bfloat16_rn(s1 * r1);
+                    dv[h1] = 0.f;
+                    ph[h1] = 0.f;
+                    qv[h1] = 0.f;
+                }
             }
             __syncthreads();
             const float gap = 0.3f * nstop / nrf;
@@ -1065,25 +1084,46 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 precond();
                 __syncthreads();
                 float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                for (int g = tid; g < G; g += T) {
-                    const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
-                    const float w0 = wl[h], w1 = wl[h + W], w2 = wd[h], w3 = wd[h + 1];
-                    const float zk = zv[h];
-                    float acc = w0 * zv[h - W];
-                    acc = fmaf(w1, zv[h + W], acc);
-                    acc = fmaf(w2, zv[h - 1], acc);
-                    acc = fmaf(w3, zv[h + 1], acc);
-                    const float wk = fmaf((w0 + w1) + (w2 + w3), zk, -acc);
-                    wv[h] = wk;
-                    const float rk = rv[h], qk = qv[h];
-                    v[0] = fmaf(rk, zk, v[0]);
-                    v[1] = fmaf(zk, wk, v[1]);
-                    v[2] = fmaf(zk, qk, v[2]);
-                    v[3] = fmaf(rk, rk, v[3]);
-                    v[4] = fmaf(rk, wk, v[4]);
-                    v[5] = fmaf(rk, qk, v[5]);
-                    v[6] = fmaf(wk, wk, v[6]);
-                    v[7] = fmaf(wk, qk, v[7]);
+                // two nodes per iteration (g and g + T), every slot load of both before any store
+                for (int g0 = tid; g0 < G; g0 += 2 * T) {
+                    const int g1 = g0 + T;
+                    const bool has1 = g1 < G;
+                    const int gq0 = (int)__umulhi((unsigned)g0, mul_n), h0 = (gq0 + 1) * W + (g0 - gq0 * n) + 1;
+                    const int gq1 = (int)__umulhi((unsigned)g1, mul_n);
+                    const int h1 = has1 ? (gq1 + 1) * W + (g1 - gq1 * n) + 1 : h0;
+                    const float a0 = wl[h0], a1 = wl[h0 + W], a2 = wd[h0], a3 = wd[h0 + 1], r0 = rv[h0], q0 = qv[h0];
+                    const float b0 = wl[h1], b1 = wl[h1 + W], b2 = wd[h1], b3 = wd[h1 + 1], r1 = rv[h1], q1 = qv[h1];
+                    const float z0 = zv[h0], z1 = zv[h1];
+                    float acc0 = a0 * zv[h0 - W];
+                    acc0 = fmaf(a1, zv[h0 + W], acc0);
+                    acc0 = fmaf(a2, zv[h0 - 1], acc0);
+                    acc0 = fmaf(a3, zv[h0 + 1], acc0);
+                    const float w0k = fmaf((a0 + a1) + (a2 + a3), z0, -acc0);
+                    float acc1 = b0 * zv[h1 - W];
+                    acc1 = fmaf(b1, zv[h1 + W], acc1);
+                    acc1 = fmaf(b2, zv[h1 - 1], acc1);
+                    acc1 = fmaf(b3, zv[h1 + 1], acc1);
+                    const float w1k = fmaf((b0 + b1) + (b2 + b3), z1, -acc1);
+                    wv[h0] = w0k;
+                    v[0] = fmaf(r0, z0, v[0]);
+                    v[1] = fmaf(z0, w0k, v[1]);
+                    v[2] = fmaf(z0, q0, v[2]);
+                    v[3] = fmaf(r0, r0, v[3]);
+                    v[4] = fmaf(r0, w0k, v[4]);
+                    v[5] = fmaf(r0, q0, v[5]);
+                    v[6] = fmaf(w0k, w0k, v[6]);
+                    v[7] = fmaf(w0k, q0, v[7]);
+                    if (has1) {
+                        wv[h1] = w1k;
+                        v[0] = fmaf(r1, z1, v[0]);
+                        v[1] = fmaf(z1, w1k, v[1]);
+                        v[2] = fmaf(z1, q1, v[2]);
+                        v[3] = fmaf(r1, r1, v[3]);
+                        v[4] = fmaf(r1, w1k, v[4]);
+                        v[5] = fmaf(r1, q1, v[5]);
+                        v[6] = fmaf(w1k, w1k, v[6]);
+                        v[7] = fmaf(w1k, q1, v[7]);
+                    }
                 }
                 block_sum8<32>(v, red32);
                 if (it == 0) istop = tin * tin * v[3];
@@ -1092,16 +1132,31 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 alpha = v[0] / pq;
                 const float qq_new = v[6] + beta * (2.f * v[7] + beta * qq);
                 const float rr = v[3] - 2.f * alpha * (v[4] + beta * v[5]) + alpha * alpha * qq_new;
-                for (int g = tid; g < G; g += T) {
-                    const int gq = (int)__umulhi((unsigned)g, mul_n), qq = g - gq * n, h = (gq + 1) * W + qq + 1;
-                    const float p = fmaf(beta, ph[h], zv[h]);
-                    const float q = fmaf(beta, qv[h], wv[h]);
-                    ph[h] = p;
-                    qv[h] = q;
-                    dv[h] = fmaf(alpha, p, dv[h]);
-                    const float r = fmaf(-alpha, q, rv[h]);
-                    rv[h] = r;
-                    Ta[gq * LD + qq] = __float2bfloat16_rn(scs[h] * r);   // the next preconditioner's input
+                // two nodes per iteration, every slot load of both before any store (the compiler may not
+                // move a load past a store through these pointers)
+                for (int g0 = tid; g0 < G; g0 += 2 * T) {
+                    const int g1 = g0 + T;
+                    const bool has1 = g1 < G;
+                    const int gq0 = (int)__umulhi((unsigned)g0, mul_n), qq0 = g0 - gq0 * n, h0 = (gq0 + 1) * W + qq0 + 1;
+                    const int gq1 = (int)__umulhi((unsigned)g1, mul_n), qq1 = g1 - gq1 * n;
+                    const int h1 = has1 ? (gq1 + 1) * W + qq1 + 1 : h0;
+                    const float ph0 = ph[h0], qv0 = qv[h0], wv0 = wv[h0], dv0 = dv[h0], rv0 = rv[h0], sc0 = scs[h0];
+                    const float ph1 = ph[h1], qv1 = qv[h1], wv1 = wv[h1], dv1 = dv[h1], rv1 = rv[h1], sc1 = scs[h1];
+                    const float pn0 = fmaf(beta, ph0, zv[h0]), qn0 = fmaf(beta, qv0, wv0);
+                    const float pn1 = fmaf(beta, ph1, zv[h1]), qn1 = fmaf(beta, qv1, wv1);
+                    const float rn0 = fmaf(-alpha, qn0, rv0), rn1 = fmaf(-alpha, qn1, rv1);
+                    ph[h0] = pn0;
+                    qv[h0] = qn0;
+                    dv[h0] = fmaf(alpha, pn0, dv0);
+                    rv[h0] = rn0;
+                    Ta[gq0 * LD + qq0] = __float2bfloat16_rn(sc0 * rn0);   // the next preconditioner's input
+                    if (has1) {
+                        ph[h1] = pn1;
+                        qv[h1] = qn1;
+                        dv[h1] = fmaf(alpha, pn1, dv1);
+                        rv[h1] = rn1;
+                        Ta[gq1 * LD + qq1] = __float2bfloat16_rn(sc1 * rn1);
+                    }
                 }
                 gamma_prev = v[0];
                 pq_prev = pq;
@@ -1110,9 +1165,16 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
                 if (rr <= istop) break;
             }
             total += it;
-            for (int g = tid; g < G; g += T) {
-                const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
-                x64[h] = fma(nr, f2d_exact(dv[h]), x64[h]);
+            for (int g0 = tid; g0 < G; g0 += 2 * T) {      // two nodes per iteration, loads first
+                const int g1 = g0 + T;
+                const bool has1 = g1 < G;
+                const int p0 = (int)__umulhi((unsigned)g0, mul_n), h0 = (p0 + 1) * W + (g0 - p0 * n) + 1;
+                const int p1 = has1 ? (int)__umulhi((unsigned)g1, mul_n) : p0;
+                const int h1 = has1 ? (p1 + 1) * W + (g1 - p1 * n) + 1 : h0;
+                const float d0 = dv[h0], d1 = dv[h1];
+                const double x0 = x64[h0], x1 = x64[h1];
+                x64[h0] = fma(nr, f2d_exact(d0), x0);
+                if (has1) x64[h1] = fma(nr, f2d_exact(d1), x1);
             }
             __syncthreads();
             // the residual: after the first correction b - sum_e w_e (x_i - x_j) in fp64 with the fp64
@@ -1121,34 +1183,62 @@ __global__ void __launch_bounds__(1024) pcg2d_mixed_big_kernel(const __grid_cons
             // correction r -= ||r|| sum_e w_e (d_i - d_j) in double-float (the differences of the
             // fp32 correction exact by TwoSum), whose rounding is relative to the current residual
             float rs_l = 0.f;
+            // two nodes per iteration (g and g + T, the same order of the norm's terms as one at a
+            // time), both nodes' slot loads before any store
             if (outer == 0) {
-                for (int g = tid; g < G; g += T) {
-                    const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
+                auto resid0 = [&](int h) -> float2 {
                     const double xi = x64[h];
                     double acc = df2d(wl[h], wll[h]) * (xi - x64[h - W]);
                     acc = fma(df2d(wl[h + W], wll[h + W]), xi - x64[h + W], acc);
                     acc = fma(df2d(wd[h], wdl[h]), xi - x64[h - 1], acc);
                     acc = fma(df2d(wd[h + 1], wdl[h + 1]), xi - x64[h + 1], acc);
-                    const float2 r = df_split(b - acc);
-                    rdf[h] = r;
-                    rv[h] = r.x;
-                    const float rs = r.x * inv;
-                    rs_l = fmaf(rs, rs, rs_l);
+                    return df_split(b - acc);
+                };
+                for (int g0 = tid; g0 < G; g0 += 2 * T) {
+                    const int g1 = g0 + T;
+                    const bool has1 = g1 < G;
+                    const int p0 = (int)__umulhi((unsigned)g0, mul_n), h0 = (p0 + 1) * W + (g0 - p0 * n) + 1;
+                    const int p1 = has1 ? (int)__umulhi((unsigned)g1, mul_n) : p0;
+                    const int h1 = has1 ? (p1 + 1) * W + (g1 - p1 * n) + 1 : h0;
+                    const float2 ra = resid0(h0), rb = resid0(h1);
+                    rdf[h0] = ra;
+                    rv[h0] = ra.x;
+                    const float rsa = ra.x * inv;
+                    rs_l = fmaf(rsa, rsa, rs_l);
+                    if (has1) {
+                        rdf[h1] = rb;
+                        rv[h1] = rb.x;
+                        const float rsb = rb.x * inv;
+                        rs_l = fmaf(rsb, rsb, rs_l);
+                    }
                 }
             } else {
                 const float2 nrd = df_split(nr);
-                for (int g = tid; g < G; g += T) {
-                    const int gq = (int)__umulhi((unsigned)g, mul_n), h = (gq + 1) * W + (g - gq * n) + 1;
+                auto resid1 = [&](int h) -> float2 {
                     const float di = dv[h];
                     float2 kd = df_mul_lazy(make_float2(wl[h], wll[h]), df_two_diff(di, dv[h - W]));
                     kd = df_add_lazy(kd, df_mul_lazy(make_float2(wl[h + W], wll[h + W]), df_two_diff(di, dv[h + W])));
                     kd = df_add_lazy(kd, df_mul_lazy(make_float2(wd[h], wdl[h]), df_two_diff(di, dv[h - 1])));
                     kd = df_add_lazy(kd, df_mul_lazy(make_float2(wd[h + 1], wdl[h + 1]), df_two_diff(di, dv[h + 1])));
-                    const float2 r = df_add(rdf[h], df_neg(df_mul_lazy(nrd, kd)));
-                    rdf[h] = r;
-                    rv[h] = r.x;
-                    const float rs = r.x * inv;
-                    rs_l = fmaf(rs, rs, rs_l);
+                    return df_add(rdf[h], df_neg(df_mul_lazy(nrd, kd)));
+                };
+                for (int g0 = tid; g0 < G; g0 += 2 * T) {
+                    const int g1 = g0 + T;
+                    const bool has1 = g1 < G;
+                    const int p0 = (int)__umulhi((unsigned)g0, mul_n), h0 = (p0 + 1) * W + (g0 - p0 * n) + 1;
+                    const int p1 = has1 ? (int)__umulhi((unsigned)g1, mul_n) : p0;
+                    const int h1 = has1 ? (p1 + 1) * W + (g1 - p1 * n) + 1 : h0;
+                    const float2 ra = resid1(h0), rb = resid1(h1);
+                    rdf[h0] = ra;
+                    rv[h0] = ra.x;
+                    const float rsa = ra.x * inv;
+                    rs_l = fmaf(rsa, rsa, rs_l);
+                    if (has1) {
+                        rdf[h1] = rb;
+                        rv[h1] = rb.x;
+                        const float rsb = rb.x * inv;
+                        rs_l = fmaf(rsb, rsb, rs_l);
+                    }
                 }
             }
             const double rr_prev = rr64;
