@@ -639,16 +639,23 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
         // the diagonal of every node (sum of its four edge weights) in double-float from the
         // weights' pairs, and as fp64 (its exact value hi + lo) for the first refinement residual;
         // the symmetric diagonal scaling of the preconditioner, sc = (diag / 4)^-1/2
+        // (the slot's loads of all the thread's nodes issued before its first store)
+        {
+            float4 wlk[NPT];
 #pragma unroll
-        for (int k = 0; k < NPT; ++k) {
-            if (nid[k] >= 0) {
-                const int h = nid[k] & 0xffff;
-                const float4 wh = wq[h], wl = __ldcg(wql + h);
-                const float2 s = df_add(df_add(make_float2(wh.x, wl.x), make_float2(wh.y, wl.y)),
-                                        df_add(make_float2(wh.z, wl.z), make_float2(wh.w, wl.w)));
-                Ddf[h] = s;
-                d64[h] = df_to_double(s);
-                scs[h] = rsqrtf(0.25f * s.x);
+            for (int k = 0; k < NPT; ++k)
+                wlk[k] = nid[k] >= 0 ? __ldcg(wql + (nid[k] & 0xffff)) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                if (nid[k] >= 0) {
+                    const int h = nid[k] & 0xffff;
+                    const float4 wh = wq[h], wl = wlk[k];
+                    const float2 s = df_add(df_add(make_float2(wh.x, wl.x), make_float2(wh.y, wl.y)),
+                                            df_add(make_float2(wh.z, wl.z), make_float2(wh.w, wl.w)));
+                    Ddf[h] = s;
+                    d64[h] = df_to_double(s);
+                    scs[h] = rsqrtf(0.25f * s.x);
+                }
             }
         }
         __syncthreads();
@@ -758,24 +765,38 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
             // the norm only sets the stop and the scale of the next correction, and x and r use
             // the same value of it
             float rs_l = 0.f;
+            // the slot's loads for RB nodes at a time issued before any of their stores
+            constexpr int RB = NPT < 2 ? NPT : 2;
             if (outer == 0) {
                 // r = b - K x in fp64 with the fp64 weights, then split into double-float
 #pragma unroll
-                for (int k = 0; k < NPT; ++k) {
-                    rhi[k] = 0.f;
-                    if (nid[k] >= 0) {
-                        const int h = nid[k] & 0xffff;
-                        const double w0 = __ldcg(w64l + h), w1 = __ldcg(w64l + h + W);
-                        const double w2 = __ldcg(w64d + h), w3 = __ldcg(w64d + h + 1);
-                        double acc = w0 * xh[h - W];
-                        acc = fma(w1, xh[h + W], acc);
-                        acc = fma(w2, xh[h - 1], acc);
-                        acc = fma(w3, xh[h + 1], acc);
-                        const float2 r = df_split(b - fma(__ldcg(d64 + h), xh[h], -acc));
-                        rdf[h] = r;
-                        rhi[k] = r.x;
-                        const float rs = r.x * inv;
-                        rs_l = fmaf(rs, rs, rs_l);
+                for (int k0 = 0; k0 < NPT; k0 += RB) {
+                    double wk[RB][5];
+#pragma unroll
+                    for (int kk = 0; kk < RB; ++kk) {
+                        const int h = nid[k0 + kk] >= 0 ? nid[k0 + kk] & 0xffff : W + 1;
+                        wk[kk][0] = __ldcg(w64l + h);
+                        wk[kk][1] = __ldcg(w64l + h + W);
+                        wk[kk][2] = __ldcg(w64d + h);
+                        wk[kk][3] = __ldcg(w64d + h + 1);
+                        wk[kk][4] = __ldcg(d64 + h);
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < RB; ++kk) {
+                        const int k = k0 + kk;
+                        rhi[k] = 0.f;
+                        if (nid[k] >= 0) {
+                            const int h = nid[k] & 0xffff;
+                            double acc = wk[kk][0] * xh[h - W];
+                            acc = fma(wk[kk][1], xh[h + W], acc);
+                            acc = fma(wk[kk][2], xh[h - 1], acc);
+                            acc = fma(wk[kk][3], xh[h + 1], acc);
+                            const float2 r = df_split(b - fma(wk[kk][4], xh[h], -acc));
+                            rdf[h] = r;
+                            rhi[k] = r.x;
+                            const float rs = r.x * inv;
+                            rs_l = fmaf(rs, rs, rs_l);
+                        }
                     }
                 }
             } else {
@@ -783,12 +804,24 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                 // pairs, d fp32), ||r|| split once
                 const float2 nrd = df_split(nr);
 #pragma unroll
-                for (int k = 0; k < NPT; ++k) {
+                for (int k0 = 0; k0 < NPT; k0 += RB) {
+                  float4 wlk[RB];
+                  float2 ddk[RB], rdk[RB];
+#pragma unroll
+                  for (int kk = 0; kk < RB; ++kk) {
+                      const int h = nid[k0 + kk] >= 0 ? nid[k0 + kk] & 0xffff : W + 1;
+                      wlk[kk] = __ldcg(wql + h);
+                      ddk[kk] = __ldcg(Ddf + h);
+                      rdk[kk] = __ldcg(rdf + h);
+                  }
+#pragma unroll
+                  for (int kk = 0; kk < RB; ++kk) {
+                    const int k = k0 + kk;
                     rhi[k] = 0.f;
                     if (nid[k] >= 0) {
                         const int h = nid[k] & 0xffff;
-                        const float4 wh = wq[h], wl = __ldcg(wql + h);
-                        float2 kd = df_mulf(__ldcg(Ddf + h), d32[k]);
+                        const float4 wh = wq[h], wl = wlk[kk];
+                        float2 kd = df_mulf(ddk[kk], d32[k]);
                         kd = df_sub_lazy(kd, df_mulf(make_float2(wh.x, wl.x), ph[h - W]));
                         kd = df_sub_lazy(kd, df_mulf(make_float2(wh.y, wl.y), ph[h + W]));
                         kd = df_sub_lazy(kd, df_mulf(make_float2(wh.z, wl.z), ph[h - 1]));
@@ -796,12 +829,13 @@ __global__ void __launch_bounds__(512) pcg2d_mixed_dst_kernel(const __grid_const
                         // t = ||r|| K d (exact product of the high parts), r - t renormalised
                         const float p = __fmul_rn(nrd.x, kd.x);
                         const float pe = __fmaf_rn(nrd.x, kd.y, __fmaf_rn(nrd.y, kd.x, __fmaf_rn(nrd.x, kd.x, -p)));
-                        const float2 r = df_add(rdf[h], make_float2(-p, -pe));
+                        const float2 r = df_add(rdk[kk], make_float2(-p, -pe));
                         rdf[h] = r;
                         rhi[k] = r.x;
                         const float rs = r.x * inv;
                         rs_l = fmaf(rs, rs, rs_l);
                     }
+                  }
                 }
             }
             const Norm2 nm = block_norm2(rs_l, red64, nr, stop);
