@@ -319,8 +319,28 @@ bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials
         M = 0;
         return true;
     }
-    // a repeated candidate can never be separated: fail at once
-    if (has_repeated_row(J, n, t)) return false;
+    // a repeated candidate can never be separated: the search gives up at once after its first
+    // unsuccessful batch of sizes (any success already proves the rows distinct, so the sort of
+    // the check is skipped in the common case)
+    bool checked_repeats = false;
+    // The trials check the rows in a fixed pseudo-random order (Fisher-Yates with SplitMix64
+    // draws of a constant key).  Injectivity does not depend on the order, so (z, M) are those of
+    // the candidate order; but in that (lexicographic) order the first rows share their leading
+    // coordinates and rarely collide, and a failing trial met its first collision after about
+    // 1100 of the 2-D workload's 4667 rows at t = 3, against about 130 in the mixed order.
+    std::vector<int8_t> Jmix;
+    if (n >= 64) {
+        std::vector<int64_t> order((size_t)n);
+        for (int64_t a = 0; a < n; ++a) order[(size_t)a] = a;
+        for (int64_t a = n - 1; a > 0; --a) {
+            const int64_t b = (int64_t)(splitmix_finalise((uint64_t)a + kGoldenGamma) % (uint64_t)(a + 1));
+            std::swap(order[(size_t)a], order[(size_t)b]);
+        }
+        Jmix.resize((size_t)n * t);
+        for (int64_t a = 0; a < n; ++a)
+            std::copy(J + order[(size_t)a] * t, J + (order[(size_t)a] + 1) * t, Jmix.data() + (size_t)a * t);
+        J = Jmix.data();
+    }
     // The sizes in order; the result is the first size with a successful trial and its first
     // such trial.  For large candidate sets the next few sizes are examined at once in borrowed
     // host threads (each size's trials in order in one thread) and the smallest size index with
@@ -363,6 +383,10 @@ bool lattice_search(const int8_t* J, int64_t n, int t, uint64_t seed, int trials
             return true;
         }
         size += (int)ms.size();
+        if (!checked_repeats) {
+            checked_repeats = true;
+            if (has_repeated_row(J, n, t)) return false;
+        }
     }
     return false;
 }
