@@ -144,6 +144,21 @@ def test_lattice_search_long_rows_and_repeated_rows(binding, t):
         binding.usfft_search_lattice(Jd, t, 3)
 
 
+def test_lattice_search_large_set_with_a_repeated_row(binding):
+    # a candidate set of the parallel path's size with one row planted twice: no lattice can
+    # separate it, and the search reports that (after its first batch of sizes) instead of a lattice
+    r = np.random.default_rng(17)
+    prev = np.unique(r.integers(-12, 13, size=(500, 2)), axis=0)
+    J = lattice.candidate_set(prev, np.arange(-6, 7), N=32)
+    assert len(J) >= 1024
+    z0, M0 = lattice.search(J, 3, 9)
+    z1, M1 = binding.usfft_search_lattice(J, 3, 9)
+    assert M1 == M0 and np.array_equal(z1, z0)
+    Jd = np.concatenate([J[:700], J[350:351], J[700:]])
+    with pytest.raises(binding.UsfftError):
+        binding.usfft_search_lattice(Jd, 3, 9)
+
+
 def test_lattice_search_on_the_c1_increments(binding):
     # the candidate sets the oracle builds for the 1-D workload (increments 2..4)
     from oracle.usfft import OracleRun
